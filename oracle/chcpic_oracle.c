@@ -1,0 +1,558 @@
+/*
+ * chcpic_oracle.c -- plain, slow, FP64 CPU oracle for one time step of the
+ * charge-conserving particle-in-cell (ChCPIC) scheme with the alternating-order
+ * form factor of order l_a = 1 1/2 (I. V. Sokolov, "Alternating-Order
+ * Interpolation in a Charge-Conserving Scheme for Particle-In-Cell
+ * Simulations", arXiv:1101.0809).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference that the
+ * CUDA library is checked against.  Only the test suite, the package smoke
+ * check and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header, table or constant with the CUDA path and never calls it; the CUDA
+ * path never calls it either.
+ *
+ * Everything is double precision, single threaded, one particle at a time in
+ * storage order, in the order of the paper's Appendix.  Nothing is blocked,
+ * fused or reordered.
+ *
+ * Conventions (Sec. 2 of the paper):
+ *   - Normalized coordinates x~ = x/dx, t~ = t/dt (Eq. coorddimless); a
+ *     particle position is an absolute real number per axis, kept in [0, N).
+ *     c_a = c*dt/d_a are the Courant numbers.
+ *   - Yee staggering (Sec. 2).  Array element [i,j,k] holds
+ *         Ex at (i, j+1/2, k+1/2)   Ey at (i+1/2, j, k+1/2)   Ez at (i+1/2, j+1/2, k)
+ *         Bx at (i+1/2, j, k)       By at (i, j+1/2, k)       Bz at (i, j, k+1/2)
+ *     J is placed like E; rho at (i+1/2, j+1/2, k+1/2).  Arrays are x-fastest:
+ *     linear index = (k*ny + j)*nx + i, all indices periodic.
+ *   - 2D3V runs (dims == 2) have an ignorable z: nz == 1, every interpolation
+ *     weight loses its z factor (its sum over k is 1, Eq. one), and the current
+ *     is the 3D current of Eq. current summed over the ignorable index k.
+ *   - Gaussian units (Eqs. 1-4).
+ *
+ * Parity pins for every function here live in tests/test_oracle_pins.py.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int dims;              /* 2 or 3 */
+    int nx, ny, nz;        /* cells per axis (nz == 1 when dims == 2) */
+    double dx, dy, dz;     /* cell sizes */
+    double dt, c;          /* time step, speed of light */
+} orc_grid;
+
+typedef struct {
+    double q, m, weight;   /* physical charge and mass; macro-particle weight */
+    long long n;           /* number of macro-particles */
+    double *x[3];          /* normalized absolute positions, each in [0, N_a) */
+    double *w[3];          /* momentum-to-mass ratio w = gamma*v */
+} orc_species;
+
+typedef struct {
+    double kinetic;        /* sum m_p c (sqrt(w^2+c^2) - c), w at n-1/2 */
+    double field_E;        /* V/(8 pi) sum E^2 at time n */
+    double field_B;        /* V/(8 pi) sum B^2 at time n */
+    double half_step_corr; /* sum (q_p dt/2) u^{n-1/2} . E(x^n) */
+    double total;          /* sum of the four terms above */
+    double momentum[3];    /* sum m_p w */
+    double charge;         /* V * sum rho over cells (particles + background) */
+} orc_diag;
+
+static const double ORC_PI = 3.14159265358979323846;
+
+static long long wrap_index(long long i, long long n)
+{
+    long long m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+static long long cell_index(const orc_grid *g, long long i, long long j, long long k)
+{
+    return (wrap_index(k, g->nz) * g->ny + wrap_index(j, g->ny)) * g->nx + wrap_index(i, g->nx);
+}
+
+static double cell_volume(const orc_grid *g)
+{
+    return g->dims == 2 ? g->dx * g->dy : g->dx * g->dy * g->dz;
+}
+
+/* ---------------------------------------------------------------------------
+ * Alternating-order form factor, l_a = 1 1/2 (Sec. 4.4, closed-form values).
+ * With i = int(x_p) and d = x_p - i:
+ *   point values of f = f^(1) at the integer points i, i+1:         (1-d, d)
+ *   cell integrals dF = f^(2) at the half-integers i-1/2, i+1/2, i+3/2:
+ *        ((1-d)^2/2, 3/4 - (1/2-d)^2, d^2/2)
+ * "int" is read as floor on the wrapped, non-negative position.
+ * The half-integer point i+1/2+b-1 (b = 0,1,2) is the centre of cell i-1+b.
+ * ------------------------------------------------------------------------- */
+void orc_form_factor(double xp, long long *i, double f[2], double dF[3])
+{
+    double fl = floor(xp);
+    double d = xp - fl;
+    *i = (long long)fl;
+    f[0] = 1.0 - d;
+    f[1] = d;
+    dF[0] = 0.5 * (1.0 - d) * (1.0 - d);
+    dF[1] = 0.75 - (0.5 - d) * (0.5 - d);
+    dF[2] = 0.5 * d * d;
+}
+
+/* Per-axis weights of one particle.  In 2D the z axis is degenerate: one
+ * point k = 0 with weight 1 for both kinds of point, which drops the z factor
+ * from every product below. */
+typedef struct {
+    long long i0[3];
+    double f[3][2];
+    double dF[3][3];
+} orc_weights;
+
+static void particle_weights(const orc_grid *g, const double xp[3], orc_weights *wt)
+{
+    for (int a = 0; a < 3; ++a) {
+        if (a == 2 && g->dims == 2) {
+            wt->i0[2] = 0;
+            wt->f[2][0] = 1.0; wt->f[2][1] = 0.0;
+            wt->dF[2][0] = 0.0; wt->dF[2][1] = 1.0; wt->dF[2][2] = 0.0;
+            continue;
+        }
+        orc_form_factor(xp[a], &wt->i0[a], wt->f[a], wt->dF[a]);
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Field gather (Sec. 2 interpolation sums, weights alpha of Eq. alphax and
+ * beta of Eq. betax).  Along its own axis an E component takes the lower-order
+ * point values f at integer points; along the two other axes it takes the cell
+ * integrals dF at half-integer points.  A B component is the other way round.
+ * ------------------------------------------------------------------------- */
+void orc_gather(const orc_grid *g, const double *const E[3], const double *const B[3],
+                const double xp[3], double Ep[3], double Bp[3])
+{
+    orc_weights wt;
+    particle_weights(g, xp, &wt);
+    const long long i0 = wt.i0[0], j0 = wt.i0[1], k0 = wt.i0[2];
+    const int nzb = g->dims == 2 ? 1 : 2;   /* integer-point count along z */
+    const int nzc = g->dims == 2 ? 1 : 3;   /* half-integer-point count along z */
+    const int kzc = g->dims == 2 ? 0 : -1;  /* first half-integer cell offset along z */
+    const double *fz = wt.f[2], *dFz = g->dims == 2 ? &wt.dF[2][1] : wt.dF[2];
+
+    for (int a = 0; a < 3; ++a) { Ep[a] = 0.0; Bp[a] = 0.0; }
+
+    /* E^(x) at (i, j+1/2, k+1/2): alpha^(x) = f_i(x) dF_{j+1/2}(y) dF_{k+1/2}(z) */
+    for (int c = 0; c < nzc; ++c)
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 2; ++a)
+                Ep[0] += wt.f[0][a] * wt.dF[1][b] * dFz[c] *
+                         E[0][cell_index(g, i0 + a, j0 - 1 + b, k0 + kzc + c)];
+    /* E^(y) at (i+1/2, j, k+1/2): alpha^(y) = dF_{i+1/2}(x) f_j(y) dF_{k+1/2}(z) */
+    for (int c = 0; c < nzc; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 3; ++a)
+                Ep[1] += wt.dF[0][a] * wt.f[1][b] * dFz[c] *
+                         E[1][cell_index(g, i0 - 1 + a, j0 + b, k0 + kzc + c)];
+    /* E^(z) at (i+1/2, j+1/2, k): alpha^(z) = dF_{i+1/2}(x) dF_{j+1/2}(y) f_k(z) */
+    for (int c = 0; c < nzb; ++c)
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a)
+                Ep[2] += wt.dF[0][a] * wt.dF[1][b] * fz[c] *
+                         E[2][cell_index(g, i0 - 1 + a, j0 - 1 + b, k0 + c)];
+    /* B^(x) at (i+1/2, j, k): beta^(x) = dF_{i+1/2}(x) f_j(y) f_k(z) */
+    for (int c = 0; c < nzb; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 3; ++a)
+                Bp[0] += wt.dF[0][a] * wt.f[1][b] * fz[c] *
+                         B[0][cell_index(g, i0 - 1 + a, j0 + b, k0 + c)];
+    /* B^(y) at (i, j+1/2, k): beta^(y) = f_i(x) dF_{j+1/2}(y) f_k(z) */
+    for (int c = 0; c < nzb; ++c)
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 2; ++a)
+                Bp[1] += wt.f[0][a] * wt.dF[1][b] * fz[c] *
+                         B[1][cell_index(g, i0 + a, j0 - 1 + b, k0 + c)];
+    /* B^(z) at (i, j, k+1/2): beta^(z) = f_i(x) f_j(y) dF_{k+1/2}(z) */
+    for (int c = 0; c < nzc; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a)
+                Bp[2] += wt.f[0][a] * wt.f[1][b] * dFz[c] *
+                         B[2][cell_index(g, i0 + a, j0 + b, k0 + kzc + c)];
+}
+
+/* ---------------------------------------------------------------------------
+ * Relativistic momentum push (Appendix, step 2; Eq. 1), with q/m and dt:
+ *   e = q dt/(2m) E;  w~ = w + e;  b = q dt/(2 m sqrt(w~^2 + c^2)) B;
+ *   w_n = w~ + w~ x b;  w' = w~ + e + 2 (w_n x b)/(1 + b^2).
+ * ------------------------------------------------------------------------- */
+static void cross(const double a[3], const double b[3], double r[3])
+{
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void orc_boris(double w[3], const double Ep[3], const double Bp[3], double qm, double dt, double c)
+{
+    double e[3], wt[3], b[3], wn[3], t[3];
+    for (int a = 0; a < 3; ++a) e[a] = 0.5 * qm * dt * Ep[a];
+    for (int a = 0; a < 3; ++a) wt[a] = w[a] + e[a];
+    double gam = sqrt(wt[0] * wt[0] + wt[1] * wt[1] + wt[2] * wt[2] + c * c);
+    for (int a = 0; a < 3; ++a) b[a] = 0.5 * qm * dt * Bp[a] / gam;
+    cross(wt, b, t);
+    for (int a = 0; a < 3; ++a) wn[a] = wt[a] + t[a];
+    double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    cross(wn, b, t);
+    for (int a = 0; a < 3; ++a) w[a] = wt[a] + e[a] + 2.0 * t[a] / (1.0 + b2);
+}
+
+/* Velocity and new position (Appendix, Eq. coordscheme):
+ *   u/c = w / sqrt(w^2 + c^2);  x^{n+1} = x^n + (u/c) . diag(c_x, c_y, c_z).
+ * The returned position is NOT wrapped into the box.  In 2D, x1[2] = x0[2]. */
+void orc_move(const orc_grid *g, const double w[3], const double x0[3], double x1[3], double u[3])
+{
+    double gam = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + g->c * g->c);
+    double cN[3] = { g->c * g->dt / g->dx, g->c * g->dt / g->dy, g->c * g->dt / g->dz };
+    for (int a = 0; a < 3; ++a) u[a] = g->c * w[a] / gam;
+    for (int a = 0; a < 3; ++a) x1[a] = x0[a] + (w[a] / gam) * cN[a];
+    if (g->dims == 2) x1[2] = x0[2];
+}
+
+/* Periodic wrap of a position into [0, N) per axis. */
+void orc_wrap(const orc_grid *g, double x[3])
+{
+    const int n[3] = { g->nx, g->ny, g->nz };
+    for (int a = 0; a < g->dims; ++a) {
+        double N = (double)n[a];
+        while (x[a] < 0.0) {
+            x[a] += N;
+            if (x[a] >= N) x[a] = 0.0;   /* a tiny negative rounds up to N */
+        }
+        while (x[a] >= N) x[a] -= N;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Virtual-path current of one particle (Sec. 3.2, Eq. current; Appendix step 2d).
+ * Per axis the cells touched by the old or the new cloud form the window
+ * [lo, hi]; dF at x^n and at x^{n+1} are laid on it, dF(+-) = dF(x^{n+1}) +- dF(x^n),
+ * and the partial sums D(i) = F_i(x^{n+1}) - F_i(x^n) = sum_{i' <= i} dF(-)_{i'-1/2}
+ * give the face factor.  Then, for the x faces,
+ *   xi^(x)_{i,j+1/2,k+1/2} = -(1/4)(dx/dt) D_x(i)
+ *          [dF(+)_{j+1/2}(y) dF(+)_{k+1/2}(z) + (1/3) dF(-)_{j+1/2}(y) dF(-)_{k+1/2}(z)]
+ * and cyclically for y, z; J += (q_p/V) xi (Eq. xi).
+ * 2D (ignorable z): summing the 3D xi over k with sum_k dF(+)_z = 2,
+ * sum_k dF(-)_z = 0 and sum_k D_z(k) = z^n - z^{n+1} (Eq. sumcurrent) gives
+ *   xi^(x) = -(1/2)(dx/dt) D_x(i) dF(+)_{j+1/2}(y),
+ *   xi^(y) = -(1/2)(dy/dt) D_y(j) dF(+)_{i+1/2}(x),
+ *   xi^(z) = (1/4) u_z [dF(+)_x dF(+)_y + (1/3) dF(-)_x dF(-)_y].
+ * x1 is the unwrapped new position; u is the velocity u^{n+1/2}.
+ * Returns the largest |sum_window dF(-)| (exactly zero in exact arithmetic).
+ * ------------------------------------------------------------------------- */
+#define ORC_MAXWIN 16
+
+typedef struct {
+    long long lo;          /* first window cell */
+    int len;               /* window cells lo .. lo+len-1 */
+    double Pp[ORC_MAXWIN]; /* dF(+) per window cell */
+    double Pm[ORC_MAXWIN]; /* dF(-) per window cell */
+    double D[ORC_MAXWIN];  /* D at the face on the left of window cell s (s = 1..len-1) */
+    double closure;        /* sum of dF(-) over the window */
+} orc_axis_current;
+
+static int axis_current(double x0, double x1, orc_axis_current *ac)
+{
+    long long i0, i1;
+    double f0[2], f1[2], dF0[3], dF1[3];
+    orc_form_factor(x0, &i0, f0, dF0);
+    orc_form_factor(x1, &i1, f1, dF1);
+    long long lo = (i0 < i1 ? i0 : i1) - 1;
+    long long hi = (i0 > i1 ? i0 : i1) + 1;
+    int len = (int)(hi - lo + 1);
+    if (len > ORC_MAXWIN) return -1;
+    double old_w[ORC_MAXWIN], new_w[ORC_MAXWIN];
+    for (int s = 0; s < len; ++s) { old_w[s] = 0.0; new_w[s] = 0.0; }
+    for (int b = 0; b < 3; ++b) {
+        old_w[i0 - 1 + b - lo] = dF0[b];
+        new_w[i1 - 1 + b - lo] = dF1[b];
+    }
+    ac->lo = lo;
+    ac->len = len;
+    for (int s = 0; s < len; ++s) {
+        ac->Pp[s] = new_w[s] + old_w[s];
+        ac->Pm[s] = new_w[s] - old_w[s];
+    }
+    /* D at face lo+s is the sum of dF(-) over the cells left of it */
+    double run = 0.0;
+    ac->D[0] = 0.0;
+    for (int s = 1; s < len; ++s) {
+        run += ac->Pm[s - 1];
+        ac->D[s] = run;
+    }
+    ac->closure = run + ac->Pm[len - 1];
+    return 0;
+}
+
+double orc_deposit(const orc_grid *g, const double x0[3], const double x1[3], const double u[3],
+                   double qp, double *J[3])
+{
+    orc_axis_current ax[3];
+    for (int a = 0; a < g->dims; ++a)
+        if (axis_current(x0[a], x1[a], &ax[a]) != 0) return INFINITY;
+    const double qV = qp / cell_volume(g);
+    const double dtn = g->dt;
+    double worst = 0.0;
+    for (int a = 0; a < g->dims; ++a)
+        if (fabs(ax[a].closure) > worst) worst = fabs(ax[a].closure);
+
+    if (g->dims == 3) {
+        /* x faces: face index i = lo_x + s (s = 1..len-1), cells j, k */
+        for (int sk = 0; sk < ax[2].len; ++sk)
+            for (int sj = 0; sj < ax[1].len; ++sj)
+                for (int si = 1; si < ax[0].len; ++si) {
+                    double xi = -0.25 * (g->dx / dtn) * ax[0].D[si] *
+                                (ax[1].Pp[sj] * ax[2].Pp[sk] + ax[1].Pm[sj] * ax[2].Pm[sk] / 3.0);
+                    J[0][cell_index(g, ax[0].lo + si, ax[1].lo + sj, ax[2].lo + sk)] += qV * xi;
+                }
+        /* y faces */
+        for (int sk = 0; sk < ax[2].len; ++sk)
+            for (int sj = 1; sj < ax[1].len; ++sj)
+                for (int si = 0; si < ax[0].len; ++si) {
+                    double xi = -0.25 * (g->dy / dtn) * ax[1].D[sj] *
+                                (ax[0].Pp[si] * ax[2].Pp[sk] + ax[0].Pm[si] * ax[2].Pm[sk] / 3.0);
+                    J[1][cell_index(g, ax[0].lo + si, ax[1].lo + sj, ax[2].lo + sk)] += qV * xi;
+                }
+        /* z faces */
+        for (int sk = 1; sk < ax[2].len; ++sk)
+            for (int sj = 0; sj < ax[1].len; ++sj)
+                for (int si = 0; si < ax[0].len; ++si) {
+                    double xi = -0.25 * (g->dz / dtn) * ax[2].D[sk] *
+                                (ax[0].Pp[si] * ax[1].Pp[sj] + ax[0].Pm[si] * ax[1].Pm[sj] / 3.0);
+                    J[2][cell_index(g, ax[0].lo + si, ax[1].lo + sj, ax[2].lo + sk)] += qV * xi;
+                }
+    } else {
+        for (int sj = 0; sj < ax[1].len; ++sj)
+            for (int si = 1; si < ax[0].len; ++si) {
+                double xi = -0.5 * (g->dx / dtn) * ax[0].D[si] * ax[1].Pp[sj];
+                J[0][cell_index(g, ax[0].lo + si, ax[1].lo + sj, 0)] += qV * xi;
+            }
+        for (int sj = 1; sj < ax[1].len; ++sj)
+            for (int si = 0; si < ax[0].len; ++si) {
+                double xi = -0.5 * (g->dy / dtn) * ax[1].D[sj] * ax[0].Pp[si];
+                J[1][cell_index(g, ax[0].lo + si, ax[1].lo + sj, 0)] += qV * xi;
+            }
+        for (int sj = 0; sj < ax[1].len; ++sj)
+            for (int si = 0; si < ax[0].len; ++si) {
+                double xi = 0.25 * u[2] *
+                            (ax[0].Pp[si] * ax[1].Pp[sj] + ax[0].Pm[si] * ax[1].Pm[sj] / 3.0);
+                J[2][cell_index(g, ax[0].lo + si, ax[1].lo + sj, 0)] += qV * xi;
+            }
+    }
+    return worst;
+}
+
+/* Charge density of one species (Eq. rho): rho_{i+1/2,...} += (q_p/V) dF_x dF_y dF_z. */
+void orc_rho(const orc_grid *g, long long n, const double *const x[3], double qp, double *rho)
+{
+    const double qV = qp / cell_volume(g);
+    for (long long p = 0; p < n; ++p) {
+        double xp[3] = { x[0][p], x[1][p], g->dims == 3 ? x[2][p] : 0.0 };
+        orc_weights wt;
+        particle_weights(g, xp, &wt);
+        const int nzc = g->dims == 2 ? 1 : 3;
+        const int kzc = g->dims == 2 ? 0 : -1;
+        const double *dFz = g->dims == 2 ? &wt.dF[2][1] : wt.dF[2];
+        for (int c = 0; c < nzc; ++c)
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a)
+                    rho[cell_index(g, wt.i0[0] - 1 + a, wt.i0[1] - 1 + b, wt.i0[2] + kzc + c)] +=
+                        qV * wt.dF[0][a] * wt.dF[1][b] * dFz[c];
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Yee field updates (Appendix, Eqs. updateB and escheme), completed cyclically.
+ *   B half step:  B -= (1/2) c_h curl E, e.g.
+ *     Bx[i,j,k] -= (c_y/2)(Ez[i,j,k]-Ez[i,j-1,k]) - (c_z/2)(Ey[i,j,k]-Ey[i,j,k-1])
+ *   E full step:  E += -4 pi dt J + c_h curl B, e.g.
+ *     Ex[i,j,k] += -4 pi dt Jx + c_y(Bz[i,j+1,k]-Bz[i,j,k]) - c_z(By[i,j,k+1]-By[i,j,k])
+ * In 2D every z difference is zero.
+ * ------------------------------------------------------------------------- */
+void orc_yee_half_B(const orc_grid *g, const double *const E[3], double *B[3])
+{
+    const double cx = g->c * g->dt / g->dx, cy = g->c * g->dt / g->dy;
+    const double cz = g->dims == 2 ? 0.0 : g->c * g->dt / g->dz;
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    double *nb[3];
+    for (int a = 0; a < 3; ++a) nb[a] = (double *)malloc(sizeof(double) * N);
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                long long p = cell_index(g, i, j, k);
+                nb[0][p] = B[0][p] - 0.5 * cy * (E[2][p] - E[2][cell_index(g, i, j - 1, k)])
+                                   + 0.5 * cz * (E[1][p] - E[1][cell_index(g, i, j, k - 1)]);
+                nb[1][p] = B[1][p] - 0.5 * cz * (E[0][p] - E[0][cell_index(g, i, j, k - 1)])
+                                   + 0.5 * cx * (E[2][p] - E[2][cell_index(g, i - 1, j, k)]);
+                nb[2][p] = B[2][p] - 0.5 * cx * (E[1][p] - E[1][cell_index(g, i - 1, j, k)])
+                                   + 0.5 * cy * (E[0][p] - E[0][cell_index(g, i, j - 1, k)]);
+            }
+    for (int a = 0; a < 3; ++a) {
+        memcpy(B[a], nb[a], sizeof(double) * N);
+        free(nb[a]);
+    }
+}
+
+void orc_yee_E(const orc_grid *g, const double *const B[3], const double *const J[3], double *E[3])
+{
+    const double cx = g->c * g->dt / g->dx, cy = g->c * g->dt / g->dy;
+    const double cz = g->dims == 2 ? 0.0 : g->c * g->dt / g->dz;
+    const double fpdt = 4.0 * ORC_PI * g->dt;
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                long long p = cell_index(g, i, j, k);
+                E[0][p] += -fpdt * J[0][p] + cy * (B[2][cell_index(g, i, j + 1, k)] - B[2][p])
+                                           - cz * (B[1][cell_index(g, i, j, k + 1)] - B[1][p]);
+                E[1][p] += -fpdt * J[1][p] + cz * (B[0][cell_index(g, i, j, k + 1)] - B[0][p])
+                                           - cx * (B[2][cell_index(g, i + 1, j, k)] - B[2][p]);
+                E[2][p] += -fpdt * J[2][p] + cx * (B[1][cell_index(g, i + 1, j, k)] - B[1][p])
+                                           - cy * (B[0][cell_index(g, i, j + 1, k)] - B[0][p]);
+            }
+}
+
+/* ---------------------------------------------------------------------------
+ * Particle part of the step for one species (Appendix, step 2): per particle,
+ * in storage order, form factor at x^n, gather E and B (B at time n), push,
+ * move, deposit, wrap.  Returns the worst deposit closure |sum dF(-)|.
+ * ------------------------------------------------------------------------- */
+double orc_push_deposit(const orc_grid *g, const double *const E[3], const double *const B[3],
+                        double *J[3], orc_species *sp)
+{
+    const double qm = sp->q / sp->m;
+    const double qp = sp->q * sp->weight;
+    double worst = 0.0;
+    for (long long p = 0; p < sp->n; ++p) {
+        double x0[3] = { sp->x[0][p], sp->x[1][p], g->dims == 3 ? sp->x[2][p] : 0.0 };
+        double w[3] = { sp->w[0][p], sp->w[1][p], sp->w[2][p] };
+        double Ep[3], Bp[3], x1[3], u[3];
+        orc_gather(g, E, B, x0, Ep, Bp);
+        orc_boris(w, Ep, Bp, qm, g->dt, g->c);
+        orc_move(g, w, x0, x1, u);
+        double cl = orc_deposit(g, x0, x1, u, qp, J);
+        if (cl > worst) worst = cl;
+        orc_wrap(g, x1);
+        for (int a = 0; a < 3; ++a) sp->w[a][p] = w[a];
+        for (int a = 0; a < g->dims; ++a) sp->x[a][p] = x1[a];
+    }
+    return worst;
+}
+
+/* One full time step (Appendix): B half step with E^n; particles; B half step
+ * with the same E^n; E full step with J^{n+1/2} and B^{n+1/2}.  J is zeroed
+ * first and holds J^{n+1/2} on return.  Returns the worst deposit closure. */
+double orc_step(const orc_grid *g, double *E[3], double *B[3], double *J[3], int nsp, orc_species *sp)
+{
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    for (int a = 0; a < 3; ++a) memset(J[a], 0, sizeof(double) * N);
+    orc_yee_half_B(g, (const double *const *)E, B);
+    double worst = 0.0;
+    for (int s = 0; s < nsp; ++s) {
+        double cl = orc_push_deposit(g, (const double *const *)E, (const double *const *)B, J, &sp[s]);
+        if (cl > worst) worst = cl;
+    }
+    orc_yee_half_B(g, (const double *const *)E, B);
+    orc_yee_E(g, (const double *const *)B, (const double *const *)J, E);
+    return worst;
+}
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics at time level n (state E^n, B^{n-1/2}, x^n, w^{n-1/2}):
+ *   rho^n from the stored positions (Eq. rho) plus a uniform background;
+ *   the Gauss residual r = div_h E - 4 pi rho (Eq. chargelaw; Sec. 2 Poisson form),
+ *     div_h E = (Ex[i+1]-Ex[i])/dx + (Ey[j+1]-Ey[j])/dy + (Ez[k+1]-Ez[k])/dz;
+ *   the energy integral of Sec. 4.1 summed over particles, with the kinetic part
+ *   taken without rest mass and the magnetic energy of B^n = B^{n-1/2} - (1/2)c_h curl E^n;
+ *   the particle momentum sum m_p w.
+ * rho and resid are outputs of N cells each.
+ * ------------------------------------------------------------------------- */
+void orc_diagnostics(const orc_grid *g, const double *const E[3], const double *const Bh[3],
+                     int nsp, const orc_species *sp, double rho_bg, double *rho, double *resid,
+                     orc_diag *out)
+{
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    const double V = cell_volume(g);
+    memset(out, 0, sizeof(*out));
+    for (long long p = 0; p < N; ++p) rho[p] = 0.0;
+    for (int s = 0; s < nsp; ++s)
+        orc_rho(g, sp[s].n, (const double *const *)sp[s].x, sp[s].q * sp[s].weight, rho);
+    for (long long p = 0; p < N; ++p) rho[p] += rho_bg;
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                long long p = cell_index(g, i, j, k);
+                double div = (E[0][cell_index(g, i + 1, j, k)] - E[0][p]) / g->dx +
+                             (E[1][cell_index(g, i, j + 1, k)] - E[1][p]) / g->dy;
+                if (g->dims == 3) div += (E[2][cell_index(g, i, j, k + 1)] - E[2][p]) / g->dz;
+                resid[p] = div - 4.0 * ORC_PI * rho[p];
+                out->charge += V * rho[p];
+            }
+    double *Bn[3];
+    for (int a = 0; a < 3; ++a) {
+        Bn[a] = (double *)malloc(sizeof(double) * N);
+        memcpy(Bn[a], Bh[a], sizeof(double) * N);
+    }
+    orc_yee_half_B(g, E, Bn);
+    for (long long p = 0; p < N; ++p)
+        for (int a = 0; a < 3; ++a) {
+            out->field_E += V / (8.0 * ORC_PI) * E[a][p] * E[a][p];
+            out->field_B += V / (8.0 * ORC_PI) * Bn[a][p] * Bn[a][p];
+        }
+    for (int s = 0; s < nsp; ++s) {
+        const double mp = sp[s].m * sp[s].weight, qp = sp[s].q * sp[s].weight;
+        for (long long p = 0; p < sp[s].n; ++p) {
+            double xp[3] = { sp[s].x[0][p], sp[s].x[1][p], g->dims == 3 ? sp[s].x[2][p] : 0.0 };
+            double w[3] = { sp[s].w[0][p], sp[s].w[1][p], sp[s].w[2][p] };
+            double w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+            double gam = sqrt(w2 + g->c * g->c);
+            out->kinetic += mp * g->c * (gam - g->c);
+            double Ep[3], Bp[3];
+            orc_gather(g, E, (const double *const *)Bn, xp, Ep, Bp);
+            for (int a = 0; a < 3; ++a) {
+                out->half_step_corr += 0.5 * qp * g->dt * (g->c * w[a] / gam) * Ep[a];
+                out->momentum[a] += mp * w[a];
+            }
+        }
+    }
+    out->total = out->kinetic + out->field_E + out->field_B + out->half_step_corr;
+    for (int a = 0; a < 3; ++a) free(Bn[a]);
+}
+
+/* ---------------------------------------------------------------------------
+ * Tile sort.  The key of a particle is the linear index of the tile that holds
+ * its cell: tile (ti, tj, tk) = (i/Tx, j/Ty, k/Tz), key = (tk*nty + tj)*ntx + ti
+ * with nt_a = ceil(n_a/T_a).  The permutation is the stable counting sort by
+ * key: perm[o] is the input index that lands at output slot o; equal keys keep
+ * their input order.
+ * ------------------------------------------------------------------------- */
+void orc_tile_keys(const orc_grid *g, const int tile[3], long long n, const double *const x[3], int *key)
+{
+    const long long ntx = (g->nx + tile[0] - 1) / tile[0];
+    const long long nty = (g->ny + tile[1] - 1) / tile[1];
+    for (long long p = 0; p < n; ++p) {
+        long long i = (long long)floor(x[0][p]), j = (long long)floor(x[1][p]);
+        long long k = g->dims == 3 ? (long long)floor(x[2][p]) : 0;
+        long long tk = g->dims == 3 ? k / tile[2] : 0;
+        key[p] = (int)((tk * nty + j / tile[1]) * ntx + i / tile[0]);
+    }
+}
+
+int orc_sort_perm(long long n, const int *key, int nkeys, long long *perm)
+{
+    long long *start = (long long *)calloc((size_t)nkeys + 1, sizeof(long long));
+    if (!start) return -1;
+    for (long long p = 0; p < n; ++p) {
+        if (key[p] < 0 || key[p] >= nkeys) { free(start); return -2; }
+        start[key[p] + 1] += 1;
+    }
+    for (int t = 0; t < nkeys; ++t) start[t + 1] += start[t];
+    for (long long p = 0; p < n; ++p) perm[start[key[p]]++] = p;
+    free(start);
+    return 0;
+}
