@@ -1,0 +1,183 @@
+/*
+ * pic.h -- C ABI of libpic, a single-GPU (GB300, sm_103a) implementation of the
+ * hot path of the charge-conserving particle-in-cell step of I. V. Sokolov,
+ * "Alternating-Order Interpolation in a Charge-Conserving Scheme for
+ * Particle-In-Cell Simulations" (arXiv:1101.0809).
+ *
+ * State follows the paper's statement of the problem (Sec. 2 and Appendix):
+ * on a periodic Yee grid the library holds E^n and B^{n-1/2}; per particle it
+ * holds x^n and w^{n-1/2}, w = gamma*v the momentum-to-mass ratio (Eq. 1).
+ * Coordinates are normalized, x~ = x/dx (Eq. coorddimless); units are Gaussian.
+ *
+ * Staggering (Sec. 2).  Field arrays are x-fastest, element [i,j,k] at linear
+ * index (k*ny + j)*nx + i, and hold
+ *     Ex at (i, j+1/2, k+1/2)   Ey at (i+1/2, j, k+1/2)   Ez at (i+1/2, j+1/2, k)
+ *     Bx at (i+1/2, j, k)       By at (i, j+1/2, k)       Bz at (i, j, k+1/2)
+ * J is placed like E.  A 2D3V grid (dims = 2) has an ignorable z and nz = 1.
+ *
+ * Precision.  PIC_FP64 runs every particle and field operation in double.
+ * PIC_FP32 stores int32 cell + float offsets, float momenta and fields, and
+ * accumulates currents in float; its diagnostics are still computed in double.
+ * Field arrays passed to pic_set_fields / pic_get_fields use the grid's
+ * precision (double for PIC_FP64, float for PIC_FP32).  Particle momenta and
+ * offsets returned by pic_get_particles use it too.
+ *
+ * Conventions shared by every call:
+ *   - every call returns int: PIC_OK (0) or one PIC_ERR_* code; the message of
+ *     the last failure on the calling thread is returned by pic_last_error();
+ *   - no call aborts, traps or throws across the ABI;
+ *   - the library owns all device memory of a grid; inputs are copied;
+ *   - on_device = 1 means the pointers are device pointers, ordered on the
+ *     grid's CUDA stream; on_device = 0 means host pointers (the call then
+ *     synchronizes the stream before returning);
+ *   - work is enqueued on the grid's stream; pic_step, pic_gather_push,
+ *     pic_deposit_current, pic_yee_update and pic_sort return without waiting.
+ *     Device-side failures (a non-finite momentum) are latched in an error word
+ *     that pic_sync and pic_diagnostics read and report as PIC_ERR_NONFINITE.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PIC_OK = 0,
+    PIC_ERR_INVALID_ARG = 1,  /* a null pointer, a size out of range, a bad enum */
+    PIC_ERR_CFL = 2,          /* c*dt/d_a >= 1 on some axis, or the Yee limit violated */
+    PIC_ERR_OOM = 3,          /* a device allocation failed */
+    PIC_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+    PIC_ERR_NONFINITE = 5,    /* a particle momentum became NaN or infinite */
+    PIC_ERR_OUT_OF_TILE = 6,  /* reserved: particles are never dropped, out-of-tile ones take the global path */
+    PIC_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+    PIC_ERR_STATE = 8         /* call out of order (e.g. deposit before gather_push) */
+};
+
+enum { PIC_FP64 = 0, PIC_FP32 = 1 };
+enum { PIC_B_HALF = 1, PIC_E_FULL = 2 };
+
+typedef struct pic_grid pic_grid;   /* opaque */
+
+/* Geometry and run parameters.  dt and c are in the same units as dx; the
+ * Courant numbers are c_a = c*dt/d_a (Sec. 2). */
+typedef struct {
+    int dims;               /* 2 (z ignorable) or 3 */
+    int nx, ny, nz;         /* cells per axis; nz must be 1 when dims == 2 */
+    double dx, dy, dz;      /* cell sizes (dz ignored when dims == 2) */
+    double dt, c;           /* time step; speed of light */
+    int precision;          /* PIC_FP64 or PIC_FP32 */
+    int order2;             /* twice the alternating order l_a; only 3 (l_a = 1 1/2, Sec. 4.4) */
+    int tile[3];            /* tile extents in cells for the sort and the shared-memory
+                               stages (0 = default: 8x8x8 in 3D, 16x16 in 2D) */
+    int halo;               /* drift guard in cells around a tile (0..2; -1 = default 1) */
+    int sort_interval;      /* sort the particles by tile every K steps (>= 1; 0 = default 10) */
+    int particles_per_block;/* particles per thread block work item (0 = default 8192) */
+    double rho_bg;          /* uniform immobile background charge density (enters rho only) */
+    void *cuda_stream;      /* cudaStream_t to enqueue on; NULL = the legacy default stream */
+} pic_grid_desc;
+
+/* One species.  The macro-particle charge is q_p = weight*q, its mass m_p = weight*m;
+ * the push uses q/m (Eq. 1), the deposit q_p/V (Eq. xi). */
+typedef struct {
+    double q, m, weight;
+} pic_species_desc;
+
+/* FP64 diagnostics at time level n, i.e. between two pic_step calls where the
+ * state is E^n, B^{n-1/2}, x^n, w^{n-1/2}:
+ *   kinetic        sum m_p c (sqrt(w^2 + c^2) - c)
+ *   field_E        V/(8 pi) sum E^2
+ *   field_B        V/(8 pi) sum B^2 with B^n = B^{n-1/2} - (1/2) c curl E^n
+ *   half_step_corr sum (q_p dt/2) u^{n-1/2} . E(x^n)       (energy integral, Sec. 4.1)
+ *   total          kinetic + field_E + field_B + half_step_corr
+ *   momentum       sum m_p w
+ *   total_charge   V * sum_cells rho (particles and background)
+ *   gauss_resid_*  max and root-mean-square over cells of |r^n - r^ref|, where
+ *                  r = div E - 4 pi rho (Eq. chargelaw) and r^ref is the residual
+ *                  at the first pic_diagnostics call after the last load or set.
+ */
+typedef struct {
+    double kinetic, field_E, field_B, half_step_corr, total;
+    double momentum[3];
+    double total_charge;
+    double gauss_resid_max, gauss_resid_rms;
+    long long n_particles;
+    int error_word;
+} pic_diag;
+
+/* Create a grid with zero fields and no particles.  The grid uses the stream in
+ * desc->cuda_stream for all its work.  Returns PIC_ERR_CFL when a Courant number
+ * c*dt/d_a is >= 1 (the deposit window assumes a particle crosses at most one
+ * face per axis per step) or when c*dt*sqrt(sum 1/d_a^2) >= 1 (Yee stability). */
+int pic_create_grid(const pic_grid_desc *desc, pic_grid **out);
+
+/* Free a grid and all its device memory.  Null is accepted. */
+int pic_destroy(pic_grid *g);
+
+/* Copy E^n and B^{n-1/2} in.  Each pointer holds nx*ny*nz values of the grid's
+ * precision.  Clears the residual reference of pic_diagnostics. */
+int pic_set_fields(pic_grid *g, const void *const E[3], const void *const B[3], int on_device);
+
+/* Copy E, B and the last deposited J (J^{n+1/2} after pic_step or
+ * pic_deposit_current) out.  Any of the three arrays of pointers may be null. */
+int pic_get_fields(pic_grid *g, void *E[3], void *B[3], void *J[3], int on_device);
+
+/* Load (replace) one species.  x[a] are n normalized absolute positions per
+ * axis (any real value; wrapped periodically into [0, N_a)), w[a] the momenta
+ * w^{n-1/2}; both double.  x[2] is ignored in 2D.  species is 0..31 and may
+ * skip indices.  All particles of the grid are re-sorted by tile on return.
+ * Particle k of this call gets id k (see pic_get_particles). */
+int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, long long n,
+                       const double *const x[3], const double *const w[3], int on_device);
+
+/* Number of particles of a species (0 if not loaded). */
+long long pic_num_particles(pic_grid *g, int species);
+
+/* Copy one species out in the library's current storage order: cell (linear
+ * cell index (k*ny + j)*nx + i), offset[a] in [0, 1) so that x_a = i_a + offset_a,
+ * w[a], and id (the particle's index in its pic_load_particles call).  Any
+ * pointer may be null; offset[2] is not written in 2D. */
+int pic_get_particles(pic_grid *g, int species, int *cell, void *offset[3], void *w[3], int *id,
+                      int on_device);
+
+/* Appendix step 2a-2c for every particle: alternating-order form factor at x^n
+ * (Sec. 4.4), gather of E (Eq. alphax) and B (Eq. betax), relativistic push
+ * (Eq. 1, Appendix), new position (Eq. coordscheme).  Needs B^n: call
+ * pic_yee_update(g, PIC_B_HALF) first.  Keeps x^n for pic_deposit_current. */
+int pic_gather_push(pic_grid *g);
+
+/* Appendix step 2d: J^{n+1/2} = sum_p (q_p/V) xi(x^n, x^{n+1}) by the six-box-path
+ * virtual-path current (Eq. current) from the positions kept by the last
+ * pic_gather_push and the current ones.  J is zeroed first.  Returns
+ * PIC_ERR_STATE if no pic_gather_push preceded it since the last load or sort. */
+int pic_deposit_current(pic_grid *g);
+
+/* Yee updates (Appendix).  PIC_B_HALF: B -= (1/2) c curl_h E (Eq. updateB).
+ * PIC_E_FULL: E += -4 pi dt J + c curl_h B (Eq. escheme). */
+int pic_yee_update(pic_grid *g, int which);
+
+/* nsteps full steps of the Appendix: B half step, [tile sort every
+ * sort_interval steps], gather + push + deposit fused in one pass over the
+ * tile-sorted particles, B half step, E full step. */
+int pic_step(pic_grid *g, int nsteps);
+
+/* Stable counting sort of all particles by tile (ties keep their order). */
+int pic_sort(pic_grid *g);
+
+/* FP64 diagnostics (see pic_diag).  Synchronizes the grid's stream. */
+int pic_diagnostics(pic_grid *g, pic_diag *out);
+
+/* Synchronize the grid's stream and report a latched device error, if any. */
+int pic_sync(pic_grid *g);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *pic_last_error(void);
+
+/* Number of kernels this grid has launched since creation (for accounting). */
+long long pic_kernel_launches(pic_grid *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

@@ -1,0 +1,642 @@
+// pic_api.cu -- the C ABI of libpic (include/pic.h): argument checks, device
+// memory, stream ordering, and the order of the step of the paper's Appendix.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+
+#include "../../include/pic.h"
+#include "pic_internal.h"
+
+using namespace pic;
+
+namespace {
+
+thread_local char t_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();   // clear a non-sticky error
+    return fail(e == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr int kDiagBlocks = 1024;
+
+size_t elem(const pic_grid *g) { return g->prec == PIC_FP64 ? sizeof(double) : sizeof(float); }
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+cudaError_t dalloc_bytes(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    return cudaMalloc(p, bytes);
+}
+
+void dfree(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+void free_pool(PoolBuf &P)
+{
+    dfree(P.cell);
+    dfree(P.id);
+    for (int c = 0; c < 3; ++c) {
+        dfree(P.off[c]);
+        dfree(P.w[c]);
+    }
+    P = PoolBuf();
+}
+
+cudaError_t alloc_pool(pic_grid *g, PoolBuf &P, long long n)
+{
+    P = PoolBuf();
+    cudaError_t e;
+    if ((e = dalloc(&P.cell, n)) != cudaSuccess) return e;
+    if ((e = dalloc(&P.id, n)) != cudaSuccess) return e;
+    for (int c = 0; c < 3; ++c) {
+        if (c < g->dims && (e = dalloc_bytes(&P.off[c], n * elem(g))) != cudaSuccess) return e;
+        if ((e = dalloc_bytes(&P.w[c], n * elem(g))) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void free_sort(pic_grid *g)
+{
+    for (int b = 0; b < 2; ++b) {
+        dfree(g->sort.keys[b]);
+        dfree(g->sort.vals[b]);
+    }
+    dfree(g->sort.hist);
+    dfree(g->sort.block_sums);
+    g->sort = SortScratch();
+    dfree(g->tile_start);
+    dfree(g->item_scan);
+    dfree(g->items);
+    g->tile_start = nullptr;
+    g->item_scan = nullptr;
+    g->items = nullptr;
+}
+
+int launch_count_add(pic_grid *g, int n)
+{
+    g->launches += n;
+    return n;
+}
+
+// (Re)allocate everything whose size depends on the particle count.
+int size_particle_buffers(pic_grid *g, long long total)
+{
+    free_sort(g);
+    dfree(g->old_cell);
+    g->old_cell = nullptr;
+    for (int c = 0; c < 3; ++c) {
+        dfree(g->old_off[c]);
+        g->old_off[c] = nullptr;
+    }
+    const long long nchunks = (total + 4095) / 4096;
+    const long long hist = 256 * std::max(1LL, nchunks);
+    const long long sums = std::max<long long>((hist + 2047) / 2048, (g->total_tiles + 2047) / 2048) + 1;
+    for (int b = 0; b < 2; ++b) {
+        CK(dalloc(&g->sort.keys[b], std::max(1LL, total)), "sort keys");
+        CK(dalloc(&g->sort.vals[b], std::max(1LL, total)), "sort values");
+    }
+    CK(dalloc(&g->sort.hist, hist), "sort histogram");
+    CK(dalloc(&g->sort.block_sums, sums), "scan sums");
+    g->sort.capacity = total;
+    g->sort.hist_capacity = hist;
+    g->sort.sums_capacity = sums;
+    CK(dalloc(&g->tile_start, (size_t)g->total_tiles + 1), "tile starts");
+    CK(dalloc(&g->item_scan, (size_t)g->total_tiles + 1), "item scan");
+    g->max_items = g->total_tiles + (int)((total + g->ppi - 1) / g->ppi) + 1;
+    CK(dalloc(&g->items, (size_t)g->max_items), "work items");
+    CK(dalloc(&g->old_cell, std::max(1LL, total)), "saved cells");
+    for (int c = 0; c < g->dims; ++c) CK(dalloc_bytes(&g->old_off[c], std::max(1LL, total) * elem(g)), "saved offsets");
+    return PIC_OK;
+}
+
+int upload_groups(pic_grid *g)
+{
+    dfree(g->d_groups);
+    dfree(g->d_group_base);
+    g->d_groups = nullptr;
+    g->d_group_base = nullptr;
+    const int ng = (int)g->groups.size();
+    std::vector<GroupDev> gd(std::max(1, ng));
+    std::vector<long long> base(ng + 1, 0);
+    int tb = 0;
+    long long pb = 0;
+    for (int q = 0; q < ng; ++q) {
+        HostGroup &h = g->groups[q];
+        const RunDev &rn = g->runs[h.run].dev;
+        h.tile_base = tb;
+        h.ntiles = rn.ntile[0] * rn.ntile[1] * rn.ntile[2];
+        h.base = pb;
+        tb += h.ntiles;
+        pb += h.n;
+        gd[q].run = h.run;
+        gd[q].tile_base = h.tile_base;
+        gd[q].base = h.base;
+        gd[q].n = h.n;
+        gd[q].qm = h.q / h.m;
+        gd[q].qp = h.q * h.weight;
+        gd[q].mp = h.m * h.weight;
+        base[q] = h.base;
+    }
+    base[ng] = pb;
+    g->total_tiles = tb;
+    CK(dalloc(&g->d_groups, gd.size()), "groups");
+    CK(cudaMemcpy(g->d_groups, gd.data(), sizeof(GroupDev) * gd.size(), cudaMemcpyHostToDevice), "groups upload");
+    CK(dalloc(&g->d_group_base, base.size()), "group bases");
+    CK(cudaMemcpy(g->d_group_base, base.data(), sizeof(long long) * base.size(), cudaMemcpyHostToDevice),
+       "group bases upload");
+    return PIC_OK;
+}
+
+int do_sort(pic_grid *g)
+{
+    int nl = 0;
+    cudaError_t e = sort_and_build_items(g->prec, g->dims, g->stream, g->total, g->pool, g->pool_alt, g->d_groups,
+                                         g->d_group_base, (int)g->groups.size(), g->d_runs, g->total_tiles, g->sort,
+                                         g->tile_start, g->item_scan, g->items, g->n_items, g->ppi, &nl);
+    launch_count_add(g, nl);
+    if (e != cudaSuccess) return cuda_fail(e, "tile sort");
+    if (g->total > 0 && !g->groups.empty()) std::swap(g->pool, g->pool_alt);
+    g->steps_since_sort = 0;
+    g->have_old = false;
+    return PIC_OK;
+}
+
+int launch_part(pic_grid *g, int mode)
+{
+    cudaError_t e = launch_particles(g->dims, g->prec, mode, g->stream, g->items, g->n_items, g->max_items, g->d_runs,
+                                     g->d_groups, g->pool, g->E, g->B, g->J, g->old_cell, g->old_off, g->halo,
+                                     g->tile[0], g->tile[1], g->tile[2], g->d_err);
+    launch_count_add(g, g->max_items > 0 ? 1 : 0);
+    if (e != cudaSuccess) return cuda_fail(e, "particle kernel");
+    return PIC_OK;
+}
+
+int launch_fields(pic_grid *g, int which, int zero_j)
+{
+    long long maxc = 0;
+    for (auto &r : g->runs) maxc = std::max(maxc, (long long)r.dev.n[0] * r.dev.n[1] * r.dev.n[2]);
+    cudaError_t e = launch_yee(g->prec, which, zero_j, g->stream, g->d_runs, (int)g->runs.size(), maxc, g->E, g->B,
+                               g->J, g->dims);
+    launch_count_add(g, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "Yee kernel");
+    return PIC_OK;
+}
+
+int check_desc(const pic_grid_desc *d, pic_grid *g, RunDev &rd)
+{
+    if (!d) return fail(PIC_ERR_INVALID_ARG, "null descriptor");
+    if (d->dims != 2 && d->dims != 3) return fail(PIC_ERR_INVALID_ARG, "dims must be 2 or 3 (got %d)", d->dims);
+    if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return fail(PIC_ERR_INVALID_ARG, "cell counts must be positive");
+    if (d->dims == 2 && d->nz != 1) return fail(PIC_ERR_INVALID_ARG, "nz must be 1 for a 2D grid");
+    if (d->precision != PIC_FP64 && d->precision != PIC_FP32) return fail(PIC_ERR_INVALID_ARG, "bad precision");
+    if (d->order2 != 3 && d->order2 != 0)
+        return fail(PIC_ERR_INVALID_ARG, "only the alternating order l_a = 1 1/2 (order2 = 3) is built");
+    const double dd[3] = {d->dx, d->dy, d->dims == 3 ? d->dz : 1.0};
+    for (int a = 0; a < 3; ++a)
+        if (!(dd[a] > 0.0) || !std::isfinite(dd[a])) return fail(PIC_ERR_INVALID_ARG, "cell sizes must be positive");
+    if (!(d->dt > 0.0) || !(d->c > 0.0) || !std::isfinite(d->dt) || !std::isfinite(d->c))
+        return fail(PIC_ERR_INVALID_ARG, "dt and c must be positive");
+    double s = 0.0;
+    for (int a = 0; a < d->dims; ++a) {
+        const double cN = d->c * d->dt / dd[a];
+        if (cN >= 1.0) return fail(PIC_ERR_CFL, "Courant number c*dt/d = %g >= 1 on axis %d", cN, a);
+        s += 1.0 / (dd[a] * dd[a]);
+    }
+    if (d->c * d->dt * std::sqrt(s) >= 1.0) return fail(PIC_ERR_CFL, "Yee stability limit c*dt*sqrt(sum 1/d^2) >= 1");
+    const int n[3] = {d->nx, d->ny, d->nz};
+    int t[3];
+    for (int a = 0; a < 3; ++a) t[a] = d->tile[a] > 0 ? d->tile[a] : (d->dims == 3 ? 8 : 16);
+    if (d->dims == 2) t[2] = 1;
+    const int halo = d->halo < 0 ? 1 : d->halo;
+    if (halo > 2) return fail(PIC_ERR_INVALID_ARG, "halo must be 0..2");
+    for (int a = 0; a < d->dims; ++a) {
+        t[a] = std::min(t[a], n[a]);
+        if (n[a] < t[a] + 2 * halo + 4)
+            return fail(PIC_ERR_INVALID_ARG,
+                        "axis %d has %d cells; the tile (%d) plus its staged halo (%d) must fit in the grid", a, n[a],
+                        t[a], 2 * halo + 4);
+    }
+    g->dims = d->dims;
+    g->prec = d->precision;
+    g->halo = halo;
+    g->sort_interval = d->sort_interval > 0 ? d->sort_interval : 10;
+    g->ppi = d->particles_per_block > 0 ? d->particles_per_block : 8192;
+    for (int a = 0; a < 3; ++a) g->tile[a] = t[a];
+    memset(&rd, 0, sizeof(rd));
+    for (int a = 0; a < 3; ++a) {
+        rd.n[a] = n[a];
+        rd.tile[a] = t[a];
+        rd.ntile[a] = (n[a] + t[a] - 1) / t[a];
+        rd.d[a] = dd[a];
+        rd.cN[a] = d->c * d->dt / dd[a];
+    }
+    if (d->dims == 2) rd.cN[2] = 0.0;
+    rd.dt = d->dt;
+    rd.c = d->c;
+    rd.V = d->dims == 3 ? dd[0] * dd[1] * dd[2] : dd[0] * dd[1];
+    rd.rho_bg = d->rho_bg;
+    rd.cell_base = 0;
+    return PIC_OK;
+}
+
+void destroy_grid(pic_grid *g)
+{
+    if (!g) return;
+    if (g->stream || true) cudaStreamSynchronize(g->stream);
+    for (int c = 0; c < 3; ++c) {
+        dfree(g->E[c]);
+        dfree(g->B[c]);
+        dfree(g->J[c]);
+        dfree(g->old_off[c]);
+    }
+    dfree(g->old_cell);
+    dfree(g->d_runs);
+    dfree(g->d_groups);
+    dfree(g->d_group_base);
+    free_pool(g->pool);
+    free_pool(g->pool_alt);
+    free_sort(g);
+    dfree(g->n_items);
+    dfree(g->diag.rho);
+    dfree(g->diag.resid_ref);
+    dfree(g->diag.partials);
+    dfree(g->diag.result);
+    dfree(g->d_err);
+    delete g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pic_last_error(void) { return t_err; }
+
+int pic_create_grid(const pic_grid_desc *desc, pic_grid **out)
+{
+    if (!out) return fail(PIC_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    pic_grid *g = new (std::nothrow) pic_grid();
+    if (!g) return fail(PIC_ERR_OOM, "host allocation failed");
+    RunDev rd;
+    int rc = check_desc(desc, g, rd);
+    if (rc != PIC_OK) {
+        delete g;
+        return rc;
+    }
+    g->stream = (cudaStream_t)desc->cuda_stream;
+    HostRun hr;
+    hr.dev = rd;
+    hr.dims = g->dims;
+    g->runs.push_back(hr);
+    g->total_cells = (long long)rd.n[0] * rd.n[1] * rd.n[2];
+    auto bail = [&](cudaError_t e, const char *what) {
+        int r = cuda_fail(e, what);
+        destroy_grid(g);
+        return r;
+    };
+    cudaError_t e;
+    for (int c = 0; c < 3; ++c) {
+        if ((e = dalloc_bytes(&g->E[c], g->total_cells * elem(g))) != cudaSuccess) return bail(e, "E");
+        if ((e = dalloc_bytes(&g->B[c], g->total_cells * elem(g))) != cudaSuccess) return bail(e, "B");
+        if ((e = dalloc_bytes(&g->J[c], g->total_cells * elem(g))) != cudaSuccess) return bail(e, "J");
+        if ((e = cudaMemsetAsync(g->E[c], 0, g->total_cells * elem(g), g->stream)) != cudaSuccess) return bail(e, "E");
+        if ((e = cudaMemsetAsync(g->B[c], 0, g->total_cells * elem(g), g->stream)) != cudaSuccess) return bail(e, "B");
+        if ((e = cudaMemsetAsync(g->J[c], 0, g->total_cells * elem(g), g->stream)) != cudaSuccess) return bail(e, "J");
+    }
+    if ((e = dalloc(&g->d_runs, 1)) != cudaSuccess) return bail(e, "runs");
+    if ((e = cudaMemcpy(g->d_runs, &rd, sizeof(rd), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "runs");
+    if ((e = dalloc(&g->d_err, 1)) != cudaSuccess) return bail(e, "error word");
+    if ((e = cudaMemset(g->d_err, 0, sizeof(int))) != cudaSuccess) return bail(e, "error word");
+    if ((e = dalloc(&g->n_items, 1)) != cudaSuccess) return bail(e, "item count");
+    if ((e = cudaMemset(g->n_items, 0, sizeof(int))) != cudaSuccess) return bail(e, "item count");
+    if ((e = dalloc(&g->diag.rho, g->total_cells)) != cudaSuccess) return bail(e, "rho");
+    if ((e = dalloc(&g->diag.resid_ref, g->total_cells)) != cudaSuccess) return bail(e, "residual reference");
+    if ((e = dalloc(&g->diag.partials, (size_t)2 * kDiagBlocks * 8)) != cudaSuccess) return bail(e, "partials");
+    if ((e = dalloc(&g->diag.result, (size_t)kDiagResults)) != cudaSuccess) return bail(e, "diag result");
+    // shared memory of the particle kernels
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    for (int mode = 0; mode < 3; ++mode) {
+        const size_t b = particles_smem_bytes(g->dims, g->prec, mode, g->tile[0], g->tile[1], g->tile[2], g->halo);
+        if ((long long)b > optin) {
+            destroy_grid(g);
+            return fail(PIC_ERR_INVALID_ARG, "tile %dx%dx%d with halo %d needs %zu B of shared memory (> %d)",
+                        desc->tile[0], desc->tile[1], desc->tile[2], desc->halo, b, optin);
+        }
+        if ((e = particles_set_smem_limit(g->dims, g->prec, mode, b)) != cudaSuccess) return bail(e, "smem limit");
+    }
+    if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return bail(e, "create");
+    *out = g;
+    return PIC_OK;
+}
+
+int pic_destroy(pic_grid *g)
+{
+    destroy_grid(g);
+    return PIC_OK;
+}
+
+long long pic_kernel_launches(pic_grid *g) { return g ? g->launches : 0; }
+
+static cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+static cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+int pic_set_fields(pic_grid *g, const void *const E[3], const void *const B[3], int on_device)
+{
+    if (!g || !E || !B) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    const size_t bytes = g->total_cells * elem(g);
+    for (int c = 0; c < 3; ++c) {
+        if (!E[c] || !B[c]) return fail(PIC_ERR_INVALID_ARG, "null field component");
+        CK(cudaMemcpyAsync(g->E[c], E[c], bytes, kind_in(on_device), g->stream), "set E");
+        CK(cudaMemcpyAsync(g->B[c], B[c], bytes, kind_in(on_device), g->stream), "set B");
+    }
+    if (!on_device) CK(cudaStreamSynchronize(g->stream), "set fields");
+    g->have_ref = false;
+    return PIC_OK;
+}
+
+int pic_get_fields(pic_grid *g, void *E[3], void *B[3], void *J[3], int on_device)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    const size_t bytes = g->total_cells * elem(g);
+    for (int c = 0; c < 3; ++c) {
+        if (E && E[c]) CK(cudaMemcpyAsync(E[c], g->E[c], bytes, kind_out(on_device), g->stream), "get E");
+        if (B && B[c]) CK(cudaMemcpyAsync(B[c], g->B[c], bytes, kind_out(on_device), g->stream), "get B");
+        if (J && J[c]) CK(cudaMemcpyAsync(J[c], g->J[c], bytes, kind_out(on_device), g->stream), "get J");
+    }
+    if (!on_device) CK(cudaStreamSynchronize(g->stream), "get fields");
+    return PIC_OK;
+}
+
+int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, long long n, const double *const x[3],
+                       const double *const w[3], int on_device)
+{
+    if (!g || !sp) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    if (species < 0 || species >= kMaxSpecies) return fail(PIC_ERR_INVALID_ARG, "species must be 0..%d", kMaxSpecies - 1);
+    if (n < 0 || n > 2000000000LL) return fail(PIC_ERR_INVALID_ARG, "particle count out of range");
+    if (!(sp->m > 0.0) || !std::isfinite(sp->q) || !std::isfinite(sp->weight))
+        return fail(PIC_ERR_INVALID_ARG, "species needs m > 0 and finite q, weight");
+    if (n > 0) {
+        if (!x || !w) return fail(PIC_ERR_INVALID_ARG, "null particle arrays");
+        for (int a = 0; a < 3; ++a) {
+            if ((a < g->dims && !x[a]) || !w[a]) return fail(PIC_ERR_INVALID_ARG, "null particle component");
+        }
+    }
+    CK(cudaStreamSynchronize(g->stream), "load: prior work");
+    // new group layout: every loaded species of run 0, ordered by species index
+    std::vector<HostGroup> old = g->groups;
+    std::vector<HostGroup> ng;
+    bool placed = false;
+    for (auto &h : old) {
+        if (h.species == species) continue;
+        if (!placed && h.species > species) {
+            HostGroup nh{};
+            nh.run = 0; nh.species = species; nh.q = sp->q; nh.m = sp->m; nh.weight = sp->weight; nh.n = n;
+            ng.push_back(nh);
+            placed = true;
+        }
+        ng.push_back(h);
+    }
+    if (!placed) {
+        HostGroup nh{};
+        nh.run = 0; nh.species = species; nh.q = sp->q; nh.m = sp->m; nh.weight = sp->weight; nh.n = n;
+        ng.push_back(nh);
+    }
+    long long total = 0;
+    for (auto &h : ng) total += h.n;
+    PoolBuf np, na;
+    cudaError_t e = alloc_pool(g, np, total);
+    if (e == cudaSuccess) e = alloc_pool(g, na, total);
+    if (e != cudaSuccess) {
+        free_pool(np);
+        free_pool(na);
+        return cuda_fail(e, "particle pool");
+    }
+    // copy the other species into their new places
+    long long pb = 0;
+    for (auto &h : ng) {
+        if (h.species != species) {
+            for (auto &o : old)
+                if (o.species == h.species) {
+                    e = launch_copy_pool(g->prec, g->stream, g->pool, o.base, np, pb, o.n);
+                    launch_count_add(g, o.n > 0);
+                }
+            if (e != cudaSuccess) break;
+        }
+        h.base = pb;
+        pb += h.n;
+    }
+    if (e != cudaSuccess) {
+        free_pool(np);
+        free_pool(na);
+        return cuda_fail(e, "pool copy");
+    }
+    // convert the new species in
+    long long new_base = 0;
+    for (auto &h : ng)
+        if (h.species == species) new_base = h.base;
+    double *tmp = nullptr;
+    const double *xs[3] = {nullptr, nullptr, nullptr}, *ws[3] = {nullptr, nullptr, nullptr};
+    if (n > 0) {
+        if (on_device) {
+            for (int a = 0; a < 3; ++a) {
+                xs[a] = a < g->dims ? x[a] : nullptr;
+                ws[a] = w[a];
+            }
+        } else {
+            e = cudaMalloc(&tmp, sizeof(double) * 6 * n);
+            if (e == cudaSuccess) {
+                for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+                    if (a < g->dims) e = cudaMemcpyAsync(tmp + a * n, x[a], sizeof(double) * n, cudaMemcpyHostToDevice, g->stream);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(tmp + (3 + a) * n, w[a], sizeof(double) * n, cudaMemcpyHostToDevice, g->stream);
+                    xs[a] = tmp + a * n;
+                    ws[a] = tmp + (3 + a) * n;
+                }
+            }
+        }
+        if (e == cudaSuccess) {
+            const RunDev &rn = g->runs[0].dev;
+            e = launch_load(g->prec, g->stream, n, xs[0], xs[1], g->dims == 3 ? xs[2] : xs[0], ws[0], ws[1], ws[2],
+                            g->dims, rn.n[0], rn.n[1], rn.n[2], np, new_base);
+            launch_count_add(g, 1);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+        free_pool(np);
+        free_pool(na);
+        return cuda_fail(e, "particle load");
+    }
+    free_pool(g->pool);
+    free_pool(g->pool_alt);
+    g->pool = np;
+    g->pool_alt = na;
+    g->groups = ng;
+    g->total = total;
+    int rc = upload_groups(g);
+    if (rc != PIC_OK) return rc;
+    rc = size_particle_buffers(g, total);
+    if (rc != PIC_OK) return rc;
+    rc = do_sort(g);
+    if (rc != PIC_OK) return rc;
+    g->have_ref = false;
+    CK(cudaStreamSynchronize(g->stream), "load: sort");
+    return PIC_OK;
+}
+
+long long pic_num_particles(pic_grid *g, int species)
+{
+    if (!g) return 0;
+    for (auto &h : g->groups)
+        if (h.species == species) return h.n;
+    return 0;
+}
+
+int pic_get_particles(pic_grid *g, int species, int *cell, void *offset[3], void *w[3], int *id, int on_device)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    const HostGroup *h = nullptr;
+    for (auto &q : g->groups)
+        if (q.species == species) h = &q;
+    if (!h) return fail(PIC_ERR_INVALID_ARG, "species %d is not loaded", species);
+    if (h->n == 0) return PIC_OK;
+    const cudaMemcpyKind k = kind_out(on_device);
+    const size_t es = elem(g);
+    if (cell) CK(cudaMemcpyAsync(cell, g->pool.cell + h->base, sizeof(int) * h->n, k, g->stream), "get cells");
+    if (id) CK(cudaMemcpyAsync(id, g->pool.id + h->base, sizeof(int) * h->n, k, g->stream), "get ids");
+    for (int a = 0; a < 3; ++a) {
+        if (offset && offset[a] && a < g->dims)
+            CK(cudaMemcpyAsync(offset[a], (char *)g->pool.off[a] + h->base * es, es * h->n, k, g->stream), "get offsets");
+        if (w && w[a]) CK(cudaMemcpyAsync(w[a], (char *)g->pool.w[a] + h->base * es, es * h->n, k, g->stream), "get momenta");
+    }
+    if (!on_device) CK(cudaStreamSynchronize(g->stream), "get particles");
+    return PIC_OK;
+}
+
+int pic_gather_push(pic_grid *g)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    if (g->total == 0) return PIC_OK;
+    int rc = launch_part(g, 1);
+    if (rc == PIC_OK) g->have_old = true;
+    return rc;
+}
+
+int pic_deposit_current(pic_grid *g)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(g->J[c], 0, g->total_cells * elem(g), g->stream), "zero J");
+    if (g->total == 0) return PIC_OK;
+    if (!g->have_old) return fail(PIC_ERR_STATE, "pic_deposit_current needs a preceding pic_gather_push");
+    return launch_part(g, 2);
+}
+
+int pic_yee_update(pic_grid *g, int which)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    if (which != PIC_B_HALF && which != PIC_E_FULL) return fail(PIC_ERR_INVALID_ARG, "which must be PIC_B_HALF or PIC_E_FULL");
+    return launch_fields(g, which, 0);
+}
+
+int pic_sort(pic_grid *g)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    return do_sort(g);
+}
+
+int pic_step(pic_grid *g, int nsteps)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    if (nsteps < 0) return fail(PIC_ERR_INVALID_ARG, "negative step count");
+    for (int s = 0; s < nsteps; ++s) {
+        int rc;
+        if (g->steps_since_sort >= g->sort_interval && (rc = do_sort(g)) != PIC_OK) return rc;
+        if ((rc = launch_fields(g, PIC_B_HALF, 1)) != PIC_OK) return rc;
+        if (g->total > 0 && (rc = launch_part(g, 0)) != PIC_OK) return rc;
+        if ((rc = launch_fields(g, PIC_B_HALF, 0)) != PIC_OK) return rc;
+        if ((rc = launch_fields(g, PIC_E_FULL, 0)) != PIC_OK) return rc;
+        g->steps_since_sort += 1;
+        g->have_old = false;
+    }
+    return PIC_OK;
+}
+
+int pic_sync(pic_grid *g)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    CK(cudaStreamSynchronize(g->stream), "sync");
+    int err = 0;
+    CK(cudaMemcpy(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+    if (err & ERR_NONFINITE) return fail(PIC_ERR_NONFINITE, "a particle momentum became non-finite");
+    return PIC_OK;
+}
+
+int pic_diagnostics(pic_grid *g, pic_diag *out)
+{
+    if (!g || !out) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    memset(out, 0, sizeof(*out));
+    int nl = 0;
+    const RunDev &rn = g->runs[0].dev;
+    cudaError_t e = launch_diagnostics_run(g->dims, g->prec, g->stream, g->d_runs, 0,
+                                           (long long)rn.n[0] * rn.n[1] * rn.n[2], rn.cell_base, g->d_groups,
+                                           g->d_group_base, (int)g->groups.size(), g->total, g->pool, g->E, g->B,
+                                           g->diag, g->have_ref ? 0 : 1, kDiagBlocks, kDiagBlocks, &nl);
+    launch_count_add(g, nl);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
+    double r[kDiagResults];
+    CK(cudaMemcpyAsync(r, g->diag.result, sizeof(r), cudaMemcpyDeviceToHost, g->stream), "diagnostics copy");
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream), "error word");
+    CK(cudaStreamSynchronize(g->stream), "diagnostics");
+    g->have_ref = true;
+    out->kinetic = r[0];
+    out->field_E = r[1];
+    out->field_B = r[2];
+    out->half_step_corr = r[3];
+    out->total = r[4];
+    out->momentum[0] = r[5];
+    out->momentum[1] = r[6];
+    out->momentum[2] = r[7];
+    out->total_charge = r[8];
+    out->gauss_resid_max = r[9];
+    out->gauss_resid_rms = r[10];
+    out->n_particles = (long long)llround(r[11]);
+    out->error_word = err;
+    if (err & ERR_NONFINITE) return fail(PIC_ERR_NONFINITE, "a particle momentum became non-finite");
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,366 @@
+// pic_device.cuh -- device-side data structures and per-particle arithmetic of
+// the charge-conserving PIC step (Sokolov, arXiv:1101.0809), shared by the
+// particle kernels.  Everything here is templated on the dimension (2 = 2D3V
+// with an ignorable z, 3 = 3D3V) and on the real type R (float or double).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+// ---------------------------------------------------------------------------
+// Device-side descriptors.  A batch holds one or more independent runs; each
+// (run, species) pair is a "group" owning a contiguous range of the particle
+// pool.  Tiles of all groups share one global numbering (group tile_base + the
+// tile's linear index inside its run) that is the sort key.
+// ---------------------------------------------------------------------------
+struct RunDev {
+    int n[3];             // cells per axis (n[2] = 1 in 2D)
+    int tile[3];          // tile extents (tile[2] = 1 in 2D)
+    int ntile[3];         // tiles per axis, ceil(n/tile)
+    long long cell_base;  // first cell of this run in the concatenated field arrays
+    double cN[3];         // Courant numbers c*dt/d_a
+    double dt, c;
+    double d[3];
+    double V;             // cell volume (dx*dy in 2D)
+    double rho_bg;        // uniform background charge density
+};
+
+struct GroupDev {
+    int run;
+    int tile_base;        // global tile id of this group's tile 0
+    long long base, n;    // particle range [base, base+n) in the pool
+    double qm;            // q/m
+    double qp;            // macro charge q_p = weight*q
+    double mp;            // macro mass m_p = weight*m
+};
+
+struct WorkItem {
+    int group;
+    int tile;             // tile index inside the run
+    long long begin, end; // particle range of this item
+};
+
+template <typename R>
+struct Pool {
+    int *cell;
+    R *off[3];
+    R *w[3];
+    int *id;
+};
+
+template <typename R>
+struct Fields {
+    R *E[3];
+    R *B[3];
+    R *J[3];
+};
+
+enum : int { ERR_NONFINITE = 1 };
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// ---------------------------------------------------------------------------
+// Alternating-order form factor l_a = 1 1/2 (Sec. 4.4): with d the in-cell
+// offset of the particle, the lower-order point values at the integer points
+// i, i+1 are f = (1-d, d), and the cell integrals at the half-integer points
+// i-1/2, i+1/2, i+3/2 (centres of cells i-1, i, i+1) are
+// S = ((1-d)^2/2, 3/4 - (1/2-d)^2, d^2/2).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void form_factor(R d, R f[2], R S[3])
+{
+    const R h = R(0.5);
+    const R e = R(1) - d;
+    const R m = h - d;
+    f[0] = e;
+    f[1] = d;
+    S[0] = h * e * e;
+    S[1] = R(0.75) - m * m;
+    S[2] = h * d * d;
+}
+
+// ---------------------------------------------------------------------------
+// Field readers.  Offsets (dx, dy, dz) are relative to the particle's cell.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct SmemReader {          // E/B tile with halo in shared memory
+    const R *E[3];
+    const R *B[3];
+    int base, s1, s2;        // index of the particle cell, strides in y and z
+    __device__ __forceinline__ R e(int a, int dx, int dy, int dz) const { return E[a][base + dx + s1 * dy + s2 * dz]; }
+    __device__ __forceinline__ R b(int a, int dx, int dy, int dz) const { return B[a][base + dx + s1 * dy + s2 * dz]; }
+};
+
+template <typename R>
+struct GlobalReader {        // periodic global arrays (particles outside their tile's halo)
+    const R *E[3];
+    const R *B[3];
+    long long xi[4], yj[4], zk[4];   // wrapped offsets for relative -1..2 per axis
+    __device__ __forceinline__ long long at(int dx, int dy, int dz) const { return xi[dx + 1] + yj[dy + 1] + zk[dz + 1]; }
+    __device__ __forceinline__ R e(int a, int dx, int dy, int dz) const { return E[a][at(dx, dy, dz)]; }
+    __device__ __forceinline__ R b(int a, int dx, int dy, int dz) const { return B[a][at(dx, dy, dz)]; }
+};
+
+// ---------------------------------------------------------------------------
+// Gather (Sec. 2 interpolation sums with alpha of Eq. alphax and beta of
+// Eq. betax).  Along its own axis an E component uses f, along the others S;
+// a B component uses S along its own axis and f along the others.  2D drops
+// every z factor (it sums to one).
+// ---------------------------------------------------------------------------
+template <int DIM, typename R, class Rd>
+__device__ __forceinline__ void gather(const Rd &rd, const R fx[2], const R Sx[3], const R fy[2], const R Sy[3],
+                                       const R fz[2], const R Sz[3], R Ep[3], R Bp[3])
+{
+    if (DIM == 3) {
+        R ex = 0, ey = 0, ez = 0, bx = 0, by = 0, bz = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const R wyz = Sy[b] * Sz[c];
+                ex += wyz * (fx[0] * rd.e(0, 0, b - 1, c - 1) + fx[1] * rd.e(0, 1, b - 1, c - 1));
+            }
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const R wyz = fy[b] * Sz[c];
+                ey += wyz * (Sx[0] * rd.e(1, -1, b, c - 1) + Sx[1] * rd.e(1, 0, b, c - 1) + Sx[2] * rd.e(1, 1, b, c - 1));
+                const R wyz2 = fy[b] * (c < 2 ? fz[c] : R(0));
+                if (c < 2)
+                    bx += wyz2 * (Sx[0] * rd.b(0, -1, b, c) + Sx[1] * rd.b(0, 0, b, c) + Sx[2] * rd.b(0, 1, b, c));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const R wyz = Sy[b] * fz[c];
+                ez += wyz * (Sx[0] * rd.e(2, -1, b - 1, c) + Sx[1] * rd.e(2, 0, b - 1, c) + Sx[2] * rd.e(2, 1, b - 1, c));
+                by += wyz * (fx[0] * rd.b(1, 0, b - 1, c) + fx[1] * rd.b(1, 1, b - 1, c));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const R wyz = fy[b] * Sz[c];
+                bz += wyz * (fx[0] * rd.b(2, 0, b, c - 1) + fx[1] * rd.b(2, 1, b, c - 1));
+            }
+        }
+        Ep[0] = ex; Ep[1] = ey; Ep[2] = ez;
+        Bp[0] = bx; Bp[1] = by; Bp[2] = bz;
+    } else {
+        R ex = 0, ey = 0, ez = 0, bx = 0, by = 0, bz = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            ex += Sy[b] * (fx[0] * rd.e(0, 0, b - 1, 0) + fx[1] * rd.e(0, 1, b - 1, 0));
+            ez += Sy[b] * (Sx[0] * rd.e(2, -1, b - 1, 0) + Sx[1] * rd.e(2, 0, b - 1, 0) + Sx[2] * rd.e(2, 1, b - 1, 0));
+            by += Sy[b] * (fx[0] * rd.b(1, 0, b - 1, 0) + fx[1] * rd.b(1, 1, b - 1, 0));
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            ey += fy[b] * (Sx[0] * rd.e(1, -1, b, 0) + Sx[1] * rd.e(1, 0, b, 0) + Sx[2] * rd.e(1, 1, b, 0));
+            bx += fy[b] * (Sx[0] * rd.b(0, -1, b, 0) + Sx[1] * rd.b(0, 0, b, 0) + Sx[2] * rd.b(0, 1, b, 0));
+            bz += fy[b] * (fx[0] * rd.b(2, 0, b, 0) + fx[1] * rd.b(2, 1, b, 0));
+        }
+        Ep[0] = ex; Ep[1] = ey; Ep[2] = ez;
+        Bp[0] = bx; Bp[1] = by; Bp[2] = bz;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Relativistic push of the Appendix (Eq. 1): e = (q dt/2m) E; w~ = w + e;
+// b = (q dt/2m) B / sqrt(w~^2 + c^2); w_n = w~ + w~ x b;
+// w' = w~ + e + 2 (w_n x b)/(1 + b^2).   hq = q dt/(2m).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void boris(R w[3], const R Ep[3], const R Bp[3], R hq, R c2)
+{
+    const R e0 = hq * Ep[0], e1 = hq * Ep[1], e2 = hq * Ep[2];
+    const R t0 = w[0] + e0, t1 = w[1] + e1, t2 = w[2] + e2;
+    const R s = hq / sqrt(t0 * t0 + t1 * t1 + t2 * t2 + c2);
+    const R b0 = s * Bp[0], b1 = s * Bp[1], b2 = s * Bp[2];
+    const R n0 = t0 + (t1 * b2 - t2 * b1);
+    const R n1 = t1 + (t2 * b0 - t0 * b2);
+    const R n2 = t2 + (t0 * b1 - t1 * b0);
+    const R f = R(2) / (R(1) + b0 * b0 + b1 * b1 + b2 * b2);
+    w[0] = t0 + e0 + f * (n1 * b2 - n2 * b1);
+    w[1] = t1 + e1 + f * (n2 * b0 - n0 * b2);
+    w[2] = t2 + e2 + f * (n0 * b1 - n1 * b0);
+}
+
+// ---------------------------------------------------------------------------
+// Offset-to-cell renormalization after a move by delta (|delta| < 1): returns
+// the cell shift k and the new offset o' in [0, 1) with cell + o' = old cell +
+// o + delta.  The float version forms o + delta - k with two error-free
+// TwoSum steps (Knuth) and rounds once, so o' is the float nearest to the exact
+// value, as a double-precision renormalization followed by one rounding would
+// give, without a single double-precision instruction.  An offset that rounds
+// to 1 moves to the next cell with offset 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int renormalize(float o, float delta, float &out)
+{
+    const float s = __fadd_rn(o, delta);
+    const float bv = __fsub_rn(s, o);
+    const float err1 = __fadd_rn(__fsub_rn(o, __fsub_rn(s, bv)), __fsub_rn(delta, bv));
+    const float k = floorf(s);
+    const float t = __fsub_rn(s, k);
+    const float bt = __fsub_rn(t, s);
+    const float err2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bt)), __fsub_rn(-k, bt));
+    float r = __fadd_rn(t, __fadd_rn(err1, err2));
+    int ki = (int)k;
+    if (r < 0.f) {
+        ki -= 1;
+        r = __fadd_rn(r, 1.0f);
+    }
+    if (r >= 1.f) {
+        ki += 1;
+        r = __fsub_rn(r, 1.0f);
+    }
+    out = r;
+    return ki;
+}
+
+__device__ __forceinline__ int renormalize(double o, double delta, double &out)
+{
+    const double s = o + delta;
+    const double k = floor(s);
+    double r = s - k;
+    int ki = (int)k;
+    if (r >= 1.0) {
+        ki += 1;
+        r -= 1.0;
+    }
+    out = r;
+    return ki;
+}
+
+// ---------------------------------------------------------------------------
+// Virtual-path current (Sec. 3.2, Eq. current; Appendix step 2d).  Per axis,
+// with the old cloud on cells -1..1 around the old cell and the new one on
+// s-1..s+1 (s in {-1,0,1} the cell shift), the window is four cells starting at
+// lo = -1 + min(s, 0).  Pp = dF(x^{n+1}) + dF(x^n) and Pm = dF(x^{n+1}) - dF(x^n)
+// per window cell, and D[q] = F_f(x^{n+1}) - F_f(x^n) = sum_{w <= q} Pm[w] at the
+// face f = lo + q + 1 (q = 0..2; the face after the window has D = 0).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct AxisWin {
+    R Pp[4], Pm[4], D[3];
+    int lo;
+};
+
+template <typename R>
+__device__ __forceinline__ void axis_window(R d0, R d1, int s, AxisWin<R> &a)
+{
+    R f0[2], S0[3], f1[2], S1[3];
+    form_factor(d0, f0, S0);
+    form_factor(d1, f1, S1);
+    const bool neg = s < 0, pos = s > 0;
+    const R o0 = neg ? R(0) : S0[0];
+    const R o1 = neg ? S0[0] : S0[1];
+    const R o2 = neg ? S0[1] : S0[2];
+    const R o3 = neg ? S0[2] : R(0);
+    const R n0 = pos ? R(0) : S1[0];
+    const R n1 = pos ? S1[0] : S1[1];
+    const R n2 = pos ? S1[1] : S1[2];
+    const R n3 = pos ? S1[2] : R(0);
+    a.Pp[0] = n0 + o0; a.Pm[0] = n0 - o0;
+    a.Pp[1] = n1 + o1; a.Pm[1] = n1 - o1;
+    a.Pp[2] = n2 + o2; a.Pm[2] = n2 - o2;
+    a.Pp[3] = n3 + o3; a.Pm[3] = n3 - o3;
+    a.D[0] = a.Pm[0];
+    a.D[1] = a.D[0] + a.Pm[1];
+    a.D[2] = a.D[1] + a.Pm[2];
+    a.lo = neg ? -2 : -1;
+}
+
+// Current accumulators; offsets are relative to the particle's OLD cell.
+template <typename R>
+struct SmemAcc {
+    R *J[3];
+    int base, s1, s2;
+    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, R v) const
+    {
+        atomicAdd(&J[a][base + dx + s1 * dy + s2 * dz], v);
+    }
+};
+
+template <typename R>
+struct GlobalAcc {
+    R *J[3];
+    long long cell_base;
+    int i, j, k, nx, ny, nz;
+    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, R v) const
+    {
+        const long long idx = cell_base + (long long)wrapi(i + dx, nx) +
+                              (long long)nx * ((long long)wrapi(j + dy, ny) + (long long)ny * wrapi(k + dz, nz));
+        atomicAdd(&J[a][idx], v);
+    }
+};
+
+// Deposit one particle.  kf[a] = -(1/4)(d_a/dt) q_p/V in 3D and -(1/2)(d_a/dt) q_p/V
+// (a = x, y) with kf[2] = (1/4) q_p/V in 2D (reading of Eq. current summed
+// over the ignorable z: xi^x = -(1/2)(dx/dt) D_x Pp_y, xi^z = (1/4) u_z [Pp Pp + Pm Pm/3]).
+template <int DIM, typename R, class Acc>
+__device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, const AxisWin<R> &Y, const AxisWin<R> &Z,
+                                        const R kf[3], R uz)
+{
+    const R third = R(1) / R(3);
+    if (DIM == 3) {
+#pragma unroll
+        for (int wz = 0; wz < 4; ++wz) {
+#pragma unroll
+            for (int wy = 0; wy < 4; ++wy) {
+                const R T = Y.Pp[wy] * Z.Pp[wz] + third * Y.Pm[wy] * Z.Pm[wz];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc.add(0, X.lo + 1 + q, Y.lo + wy, Z.lo + wz, kf[0] * X.D[q] * T);
+            }
+        }
+#pragma unroll
+        for (int wz = 0; wz < 4; ++wz) {
+#pragma unroll
+            for (int wx = 0; wx < 4; ++wx) {
+                const R T = X.Pp[wx] * Z.Pp[wz] + third * X.Pm[wx] * Z.Pm[wz];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc.add(1, X.lo + wx, Y.lo + 1 + q, Z.lo + wz, kf[1] * Y.D[q] * T);
+            }
+        }
+#pragma unroll
+        for (int wy = 0; wy < 4; ++wy) {
+#pragma unroll
+            for (int wx = 0; wx < 4; ++wx) {
+                const R T = X.Pp[wx] * Y.Pp[wy] + third * X.Pm[wx] * Y.Pm[wy];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc.add(2, X.lo + wx, Y.lo + wy, Z.lo + 1 + q, kf[2] * Z.D[q] * T);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int wy = 0; wy < 4; ++wy) {
+            const R t = kf[0] * Y.Pp[wy];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc.add(0, X.lo + 1 + q, Y.lo + wy, 0, t * X.D[q]);
+        }
+#pragma unroll
+        for (int wx = 0; wx < 4; ++wx) {
+            const R t = kf[1] * X.Pp[wx];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc.add(1, X.lo + wx, Y.lo + 1 + q, 0, t * Y.D[q]);
+        }
+        const R kz = kf[2] * uz;
+#pragma unroll
+        for (int wy = 0; wy < 4; ++wy) {
+#pragma unroll
+            for (int wx = 0; wx < 4; ++wx) {
+                const R T = X.Pp[wx] * Y.Pp[wy] + third * X.Pm[wx] * Y.Pm[wy];
+                acc.add(2, X.lo + wx, Y.lo + wy, 0, kz * T);
+            }
+        }
+    }
+}
+
+}  // namespace pic

@@ -1,0 +1,245 @@
+// pic_diag.cu -- FP64 diagnostics of one run at time level n (state E^n,
+// B^{n-1/2}, x^n, w^{n-1/2}), whatever the precision of the state:
+//   rho^n from the stored positions (Eq. rho), the Gauss residual
+//   r = div_h E - 4 pi rho (Eq. chargelaw, Poisson form of Sec. 2) against a
+//   stored reference, the energy integral of Sec. 4.1 (kinetic part without
+//   rest mass, B^n = B^{n-1/2} - (1/2) c curl_h E^n), and the momentum sum.
+// Sums are per-block tree reductions written to fixed slots and reduced by one
+// block in slot order.
+#include "pic_internal.h"
+
+namespace pic {
+
+constexpr int kDiagThreads = 256;
+constexpr int kPartVals = 8;   // values per partial slot
+constexpr double kPi = 3.14159265358979323846;
+
+template <typename R>
+struct ConvReader {   // reads the state's precision, returns double, periodic indices
+    const R *E[3];
+    const R *B[3];
+    long long xi[4], yj[4], zk[4];
+    __device__ __forceinline__ long long at(int dx, int dy, int dz) const { return xi[dx + 1] + yj[dy + 1] + zk[dz + 1]; }
+    __device__ __forceinline__ double e(int a, int dx, int dy, int dz) const { return (double)E[a][at(dx, dy, dz)]; }
+    __device__ __forceinline__ double b(int a, int dx, int dy, int dz) const { return (double)B[a][at(dx, dy, dz)]; }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block reduction of kPartVals values (sums, except slot `max_slot` which is a max).
+__device__ void block_reduce_store(double v[kPartVals], int max_slot, double *out)
+{
+    __shared__ double sh[kDiagThreads / 32][kPartVals];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kPartVals; ++q) {
+        const double r = q == max_slot ? warp_max(v[q]) : warp_sum(v[q]);
+        if (lane == 0) sh[warp][q] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < kPartVals) {
+        const int q = threadIdx.x;
+        double acc = sh[0][q];
+        for (int w = 1; w < kDiagThreads / 32; ++w) acc = q == max_slot ? fmax(acc, sh[w][q]) : acc + sh[w][q];
+        out[q] = acc;
+    }
+}
+
+// Particles: rho deposit (atomics) and kinetic / momentum / half-step sums.
+// Partial slots: 0 kinetic, 1-3 momentum, 4 half-step correction, 5 count.
+template <int DIM, typename R>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_particles(int run, long long total, const long long *group_base,
+                                                                 int ngroups, const GroupDev *groups, const RunDev *runs,
+                                                                 Pool<R> P, Fields<R> F, double *rho, double *partials)
+{
+    double v[kPartVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total; p += stride) {
+        int lo = 0, hi = ngroups;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (group_base[mid] <= p) lo = mid; else hi = mid;
+        }
+        const GroupDev g = groups[lo];
+        if (g.run != run) continue;
+        const RunDev rn = runs[g.run];
+        const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
+        const int c = P.cell[p];
+        const int i = c % nx, rest = c / nx, j = rest % ny, k = DIM == 3 ? rest / ny : 0;
+        double fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
+        form_factor((double)P.off[0][p], fx, Sx);
+        form_factor((double)P.off[1][p], fy, Sy);
+        if (DIM == 3) {
+            form_factor((double)P.off[2][p], fz, Sz);
+        } else {
+            fz[0] = 1; fz[1] = 0; Sz[0] = 0; Sz[1] = 1; Sz[2] = 0;
+        }
+        const double qV = g.qp / rn.V;
+        const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
+        for (int dz = kz0; dz <= kz1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const long long idx = rn.cell_base + wrapi(i + dx, nx) +
+                                          (long long)nx * (wrapi(j + dy, ny) + (long long)ny * (DIM == 3 ? wrapi(k + dz, nz) : 0));
+                    atomicAdd(&rho[idx], qV * Sx[dx + 1] * Sy[dy + 1] * Sz[dz + 1]);
+                }
+        const double w0 = (double)P.w[0][p], w1 = (double)P.w[1][p], w2 = (double)P.w[2][p];
+        const double gam = sqrt(w0 * w0 + w1 * w1 + w2 * w2 + rn.c * rn.c);
+        v[0] += g.mp * rn.c * (gam - rn.c);
+        v[1] += g.mp * w0;
+        v[2] += g.mp * w1;
+        v[3] += g.mp * w2;
+        ConvReader<R> rd;
+        for (int q = 0; q < 3; ++q) { rd.E[q] = F.E[q]; rd.B[q] = F.B[q]; }
+        for (int q = 0; q < 4; ++q) {
+            rd.xi[q] = rn.cell_base + wrapi(i - 1 + q, nx);
+            rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
+            rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
+        }
+        double Ep[3], Bp[3];
+        gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+        v[4] += 0.5 * g.qp * rn.dt * rn.c * (w0 * Ep[0] + w1 * Ep[1] + w2 * Ep[2]) / gam;
+        v[5] += 1.0;
+    }
+    block_reduce_store(v, -1, partials + (long long)blockIdx.x * kPartVals);
+}
+
+// Cells: residual against the reference, charge, field energies.
+// Partial slots: 0 max |r - r_ref|, 1 sum (r - r_ref)^2, 2 charge, 3 sum E^2, 4 sum B^2.
+template <int DIM, typename R>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_cells(const RunDev *runs, int run, Fields<R> F, const double *rho,
+                                                             double *ref, int set_ref, double *partials)
+{
+    double v[kPartVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const RunDev rn = runs[run];
+    const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
+    const long long ncell = (long long)nx * ny * nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const double hx = 0.5 * rn.cN[0], hy = 0.5 * rn.cN[1], hz = 0.5 * rn.cN[2];
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < ncell; l += stride) {
+        const int i = (int)(l % nx);
+        const long long r = l / nx;
+        const int j = (int)(r % ny), k = (int)(r / ny);
+        const long long p = rn.cell_base + l;
+        const long long pip = p + (i == nx - 1 ? -(nx - 1) : 1), pim = p + (i == 0 ? nx - 1 : -1);
+        const long long pjp = p + (long long)nx * (j == ny - 1 ? -(ny - 1) : 1);
+        const long long pjm = p + (long long)nx * (j == 0 ? ny - 1 : -1);
+        const double ex = F.E[0][p], ey = F.E[1][p], ez = F.E[2][p];
+        double div = ((double)F.E[0][pip] - ex) / rn.d[0] + ((double)F.E[1][pjp] - ey) / rn.d[1];
+        double bx = (double)F.B[0][p] - hy * (ez - (double)F.E[2][pjm]);
+        double by = (double)F.B[1][p] + hx * (ez - (double)F.E[2][pim]);
+        double bz = (double)F.B[2][p] - hx * (ey - (double)F.E[1][pim]) + hy * (ex - (double)F.E[0][pjm]);
+        if (DIM == 3) {
+            const long long pkp = p + (long long)nx * ny * (k == nz - 1 ? -(nz - 1) : 1);
+            const long long pkm = p + (long long)nx * ny * (k == 0 ? nz - 1 : -1);
+            div += ((double)F.E[2][pkp] - ez) / rn.d[2];
+            bx += hz * (ey - (double)F.E[1][pkm]);
+            by -= hz * (ex - (double)F.E[0][pkm]);
+        }
+        const double rt = rho[p] + rn.rho_bg;
+        const double res = div - 4.0 * kPi * rt;
+        if (set_ref) ref[p] = res;
+        const double dr = res - ref[p];
+        v[0] = fmax(v[0], fabs(dr));
+        v[1] += dr * dr;
+        v[2] += rt * rn.V;
+        v[3] += ex * ex + ey * ey + ez * ez;
+        v[4] += bx * bx + by * by + bz * bz;
+    }
+    block_reduce_store(v, 0, partials + (long long)blockIdx.x * kPartVals);
+}
+
+// One block: fixed-order reduction of the partial slots into result[0..11]:
+// kinetic, field_E, field_B, half_step_corr, total, px, py, pz, charge,
+// resid_max, resid_rms, n_particles.
+__global__ void k_diag_final(const double *pp, int np, const double *pc, int nc, const RunDev *runs, int run,
+                             double *result)
+{
+    __shared__ double acc[12];
+    if (threadIdx.x == 0) {
+        const RunDev rn = runs[run];
+        double s[kPartVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int b = 0; b < np; ++b)
+            for (int q = 0; q < kPartVals; ++q) s[q] += pp[b * kPartVals + q];
+        double c[kPartVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int b = 0; b < nc; ++b) {
+            c[0] = fmax(c[0], pc[b * kPartVals + 0]);
+            for (int q = 1; q < kPartVals; ++q) c[q] += pc[b * kPartVals + q];
+        }
+        const double ncell = (double)rn.n[0] * rn.n[1] * rn.n[2];
+        const double fe = rn.V / (8.0 * kPi);
+        acc[0] = s[0];
+        acc[1] = fe * c[3];
+        acc[2] = fe * c[4];
+        acc[3] = s[4];
+        acc[4] = acc[0] + acc[1] + acc[2] + acc[3];
+        acc[5] = s[1];
+        acc[6] = s[2];
+        acc[7] = s[3];
+        acc[8] = c[2];
+        acc[9] = c[0];
+        acc[10] = sqrt(c[1] / ncell);
+        acc[11] = s[5];
+        for (int q = 0; q < 12; ++q) result[q] = acc[q];
+    }
+}
+
+template <int DIM, typename R>
+static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run, long long run_cells,
+                          const GroupDev *groups, const long long *group_base, int ngroups, long long total,
+                          const PoolBuf &P, void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
+                          int np_blocks, int nc_blocks, int *launches)
+{
+    Pool<R> pool;
+    pool.cell = P.cell;
+    pool.id = P.id;
+    Fields<R> F;
+    for (int c = 0; c < 3; ++c) {
+        pool.off[c] = (R *)P.off[c];
+        pool.w[c] = (R *)P.w[c];
+        F.E[c] = (R *)E[c];
+        F.B[c] = (R *)B[c];
+        F.J[c] = nullptr;
+    }
+    k_diag_particles<DIM, R><<<np_blocks, kDiagThreads, 0, st>>>(run, total, group_base, ngroups, groups, runs, pool,
+                                                                 F, scr.rho, scr.partials);
+    k_diag_cells<DIM, R><<<nc_blocks, kDiagThreads, 0, st>>>(runs, run, F, scr.rho, scr.resid_ref, set_ref,
+                                                             scr.partials + (long long)np_blocks * kPartVals);
+    k_diag_final<<<1, 32, 0, st>>>(scr.partials, np_blocks, scr.partials + (long long)np_blocks * kPartVals,
+                                   nc_blocks, runs, run, scr.result);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics_run(int dims, int prec, cudaStream_t st, const RunDev *runs, int run,
+                                   long long run_cells, long long cell_base, const GroupDev *groups,
+                                   const long long *group_base, int ngroups, long long total, const PoolBuf &P,
+                                   void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
+                                   int np_blocks, int nc_blocks, int *launches)
+{
+    cudaError_t e = cudaMemsetAsync(scr.rho + cell_base, 0, sizeof(double) * run_cells, st);
+    if (e != cudaSuccess) return e;
+    if (dims == 3)
+        return prec == 0 ? diag_t<3, double>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
+                                             scr, set_ref, np_blocks, nc_blocks, launches)
+                         : diag_t<3, float>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
+                                            scr, set_ref, np_blocks, nc_blocks, launches);
+    return prec == 0 ? diag_t<2, double>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
+                                         set_ref, np_blocks, nc_blocks, launches)
+                     : diag_t<2, float>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
+                                        set_ref, np_blocks, nc_blocks, launches);
+}
+
+}  // namespace pic

@@ -1,0 +1,139 @@
+// pic_internal.h -- host-side state of a libpic grid and the kernel launchers
+// each translation unit provides.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "pic_device.cuh"
+
+struct pic_grid;
+
+namespace pic {
+
+constexpr int kMaxSpecies = 32;
+constexpr int kThreads = 256;      // threads per block of the particle kernels
+
+struct HostRun {
+    RunDev dev;                    // copy of the device descriptor
+    int dims;
+};
+
+struct HostGroup {
+    int run, species;
+    double q, m, weight;
+    long long base, n;
+    int tile_base, ntiles;
+};
+
+// Device buffers of a particle pool (one of two, swapped by the sort).
+struct PoolBuf {
+    int *cell = nullptr;
+    void *off[3] = {nullptr, nullptr, nullptr};
+    void *w[3] = {nullptr, nullptr, nullptr};
+    int *id = nullptr;
+};
+
+// Launch helpers implemented in the .cu files.  All enqueue on `st` and return
+// a cudaError_t from the launch.
+cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, const WorkItem *items,
+                             const int *n_items, int max_items, const RunDev *runs, const GroupDev *groups,
+                             const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
+                             int *old_cell, void *const old_off[3], int halo, int max_tile_x,
+                             int max_tile_y, int max_tile_z, int *err);
+size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo);
+cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes);
+
+cudaError_t launch_load(int prec, cudaStream_t st, long long n, const double *x0, const double *x1,
+                        const double *x2, const double *w0, const double *w1, const double *w2,
+                        int dims, int nx, int ny, int nz, const PoolBuf &P, long long base);
+
+cudaError_t launch_yee(int prec, int which, int zero_j, cudaStream_t st, const RunDev *runs, int nruns,
+                       long long max_cells, void *const E[3], void *const B[3], void *const J[3], int dims);
+
+cudaError_t launch_copy_pool(int prec, cudaStream_t st, const PoolBuf &src, long long src_base,
+                             const PoolBuf &dst, long long dst_base, long long n);
+
+// Sort: computes keys, sorts them stably, permutes the pool from `src` into
+// `dst`, fills tile_start[0..total_tiles] and the work items.
+struct SortScratch {
+    unsigned *keys[2] = {nullptr, nullptr};
+    unsigned *vals[2] = {nullptr, nullptr};
+    unsigned *hist = nullptr;      // 256 * max_chunks
+    unsigned *block_sums = nullptr;
+    long long capacity = 0;
+    long long hist_capacity = 0;
+    long long sums_capacity = 0;
+};
+
+cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long total, const PoolBuf &src,
+                                 const PoolBuf &dst, const GroupDev *groups, const long long *group_base_dev,
+                                 int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
+                                 long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
+                                 int particles_per_item, int *launches);
+
+// Diagnostics: accumulates into out (13 doubles) on the device.
+struct DiagScratch {
+    double *rho = nullptr;
+    double *resid_ref = nullptr;
+    double *partials = nullptr;    // per block partial sums, 8 values per block
+    double *result = nullptr;      // kDiagResults reduced values
+};
+
+cudaError_t launch_diagnostics_run(int dims, int prec, cudaStream_t st, const RunDev *runs, int run,
+                                   long long run_cells, long long cell_base, const GroupDev *groups,
+                                   const long long *group_base, int ngroups, long long total, const PoolBuf &P,
+                                   void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
+                                   int np_blocks, int nc_blocks, int *launches);
+constexpr int kDiagResults = 12;
+
+}  // namespace pic
+
+struct pic_grid {
+    int dims = 3, prec = 0;
+    int halo = 1, sort_interval = 10, ppi = 8192;
+    int tile[3] = {8, 8, 8};
+    cudaStream_t stream = nullptr;
+
+    std::vector<pic::HostRun> runs;
+    pic::RunDev *d_runs = nullptr;
+    long long total_cells = 0;
+
+    // fields, concatenated over runs
+    void *E[3] = {nullptr, nullptr, nullptr};
+    void *B[3] = {nullptr, nullptr, nullptr};
+    void *J[3] = {nullptr, nullptr, nullptr};
+
+    // species / groups
+    std::vector<pic::HostGroup> groups;
+    pic::GroupDev *d_groups = nullptr;
+    long long *d_group_base = nullptr;
+    int total_tiles = 0;
+
+    // particle pool (double-buffered by the sort)
+    pic::PoolBuf pool, pool_alt;
+    long long total = 0, capacity = 0;
+
+    // saved x^n for the unfused deposit
+    int *old_cell = nullptr;
+    void *old_off[3] = {nullptr, nullptr, nullptr};
+    bool have_old = false;
+
+    // sort products
+    pic::SortScratch sort;
+    long long *tile_start = nullptr;
+    unsigned *item_scan = nullptr;
+    pic::WorkItem *items = nullptr;
+    int *n_items = nullptr;
+    int max_items = 0;
+    int steps_since_sort = 0;
+
+    // diagnostics
+    pic::DiagScratch diag;
+    bool have_ref = false;
+
+    int *d_err = nullptr;
+    long long launches = 0;
+};

@@ -1,0 +1,445 @@
+// pic_particles.cu -- per-particle kernels of the charge-conserving PIC step
+// (Sokolov, arXiv:1101.0809, Appendix step 2): alternating-order gather, push,
+// move and virtual-path deposit, run over tile-sorted particles.
+//
+// One thread block takes one work item: a contiguous range of particles that
+// the last sort put in one tile.  The block stages E and B of the tile plus a
+// halo of (halo + 1) cells in shared memory, and a current tile with a halo of
+// (halo + 2) cells.  Each thread streams particles (coalesced SoA loads),
+// gathers from shared memory, pushes, renormalizes offset and cell, writes the
+// particle back and scatters its 144 (3D) or 40 (2D) face currents into the
+// shared current tile with shared-memory atomics.  A particle that has drifted
+// more than `halo` cells outside the tile since the last sort takes the same
+// arithmetic on the global arrays instead (periodic indices, global atomics).
+// At the end the block adds its current tile to the global J with atomics.
+#include "pic_internal.h"
+
+namespace pic {
+
+template <typename R>
+struct PartArgs {
+    const WorkItem *items;
+    const int *n_items;
+    const RunDev *runs;
+    const GroupDev *groups;
+    Pool<R> P;
+    Fields<R> F;
+    int *old_cell;
+    R *old_off[3];
+    int halo;
+    int *err;
+};
+
+extern __shared__ __align__(16) unsigned char g_smem[];
+
+__device__ __forceinline__ bool finite3(float a, float b, float c) { return isfinite(a) && isfinite(b) && isfinite(c); }
+__device__ __forceinline__ bool finite3(double a, double b, double c) { return isfinite(a) && isfinite(b) && isfinite(c); }
+
+// Tile-local coordinate of global index i for a tile starting at o with extent T:
+// the periodic image in [-G, T+G) if there is one (the grid is wider than the
+// staged region, so at most one image lies there), else a value outside it.
+__device__ __forceinline__ int local_coord(int i, int o, int T, int G, int n)
+{
+    int l = i - o;
+    if (l >= T + G) l -= n;
+    if (l < -G) l += n;
+    return l;
+}
+
+// MODE 0: fused gather + push + move + deposit (pic_step).
+// MODE 1: gather + push + move, keeping x^n (pic_gather_push).
+// MODE 2: deposit from the kept x^n and the current x^{n+1} (pic_deposit_current).
+template <int DIM, typename R, int MODE>
+__global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
+{
+    if ((int)blockIdx.x >= *a.n_items) return;
+    const WorkItem it = a.items[blockIdx.x];
+    const GroupDev gr = a.groups[it.group];
+    const RunDev rn = a.runs[gr.run];
+    const int G = a.halo;
+    const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
+    const int T0 = rn.tile[0], T1 = rn.tile[1], T2 = DIM == 3 ? rn.tile[2] : 1;
+    const int tx = it.tile % rn.ntile[0];
+    const int ty = (it.tile / rn.ntile[0]) % rn.ntile[1];
+    const int tz = DIM == 3 ? it.tile / (rn.ntile[0] * rn.ntile[1]) : 0;
+    const int ox = tx * T0, oy = ty * T1, oz = tz * T2;
+    const int fe0 = T0 + 2 * G + 2, fe1 = T1 + 2 * G + 2, fe2 = DIM == 3 ? T2 + 2 * G + 2 : 1;
+    const int je0 = T0 + 2 * G + 4, je1 = T1 + 2 * G + 4, je2 = DIM == 3 ? T2 + 2 * G + 4 : 1;
+    const int nf = fe0 * fe1 * fe2, nj = je0 * je1 * je2;
+    constexpr bool NEED_F = MODE != 2;
+    constexpr bool NEED_J = MODE != 1;
+    const long long cb = rn.cell_base;
+
+    R *sm = reinterpret_cast<R *>(g_smem);
+    R *sE[3], *sB[3], *sJ[3];
+    int soff = 0;
+    if (NEED_F) {
+        for (int c = 0; c < 3; ++c) { sE[c] = sm + soff; soff += nf; }
+        for (int c = 0; c < 3; ++c) { sB[c] = sm + soff; soff += nf; }
+    }
+    if (NEED_J) {
+        for (int c = 0; c < 3; ++c) { sJ[c] = sm + soff; soff += nj; }
+    }
+
+    if (NEED_F) {
+        for (int l = threadIdx.x; l < nf; l += blockDim.x) {
+            const int lx = l % fe0, r = l / fe0, ly = r % fe1, lz = r / fe1;
+            const int gx = wrapi(ox - G - 1 + lx, nx);
+            const int gy = wrapi(oy - G - 1 + ly, ny);
+            const int gz = DIM == 3 ? wrapi(oz - G - 1 + lz, nz) : 0;
+            const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sE[c][l] = a.F.E[c][gi];
+                sB[c][l] = a.F.B[c][gi];
+            }
+        }
+    }
+    if (NEED_J) {
+        for (int l = threadIdx.x; l < nj; l += blockDim.x) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sJ[c][l] = R(0);
+        }
+    }
+    __syncthreads();
+
+    const R hq = R(0.5 * gr.qm * rn.dt);
+    const R cl = R(rn.c);
+    const R c2 = cl * cl;
+    const R cN0 = R(rn.cN[0]), cN1 = R(rn.cN[1]), cN2 = R(rn.cN[2]);
+    R kf[3];
+    if (DIM == 3) {
+        for (int c = 0; c < 3; ++c) kf[c] = R(-0.25 * rn.d[c] / rn.dt * gr.qp / rn.V);
+    } else {
+        kf[0] = R(-0.5 * rn.d[0] / rn.dt * gr.qp / rn.V);
+        kf[1] = R(-0.5 * rn.d[1] / rn.dt * gr.qp / rn.V);
+        kf[2] = R(0.25 * gr.qp / rn.V);
+    }
+
+    for (long long p = it.begin + threadIdx.x; p < it.end; p += blockDim.x) {
+        // ---- the particle's state at x^n (old) -------------------------------
+        const int cell0 = MODE == 2 ? a.old_cell[p] : a.P.cell[p];
+        const R o0 = MODE == 2 ? a.old_off[0][p] : a.P.off[0][p];
+        const R o1 = MODE == 2 ? a.old_off[1][p] : a.P.off[1][p];
+        const R o2 = DIM == 3 ? (MODE == 2 ? a.old_off[2][p] : a.P.off[2][p]) : R(0);
+        R w[3] = {R(0), R(0), R(0)};
+        if (MODE != 2 || DIM == 2) {
+            w[0] = a.P.w[0][p];
+            w[1] = a.P.w[1][p];
+            w[2] = a.P.w[2][p];
+        }
+        const int i = cell0 % nx;
+        const int rest = cell0 / nx;
+        const int j = rest % ny;
+        const int k = DIM == 3 ? rest / ny : 0;
+        const int li = local_coord(i, ox, T0, G, nx);
+        const int lj = local_coord(j, oy, T1, G, ny);
+        const int lk = DIM == 3 ? local_coord(k, oz, T2, G, nz) : 0;
+        const bool inr = li >= -G && li < T0 + G && lj >= -G && lj < T1 + G &&
+                         (DIM == 2 || (lk >= -G && lk < T2 + G));
+
+        R n0 = o0, n1 = o1, n2 = o2;
+        int s0 = 0, s1 = 0, s2 = 0;
+        R uz = R(0);
+        if (MODE != 2) {
+            R fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
+            form_factor(o0, fx, Sx);
+            form_factor(o1, fy, Sy);
+            if (DIM == 3) {
+                form_factor(o2, fz, Sz);
+            } else {
+                fz[0] = R(1); fz[1] = R(0);
+                Sz[0] = R(0); Sz[1] = R(1); Sz[2] = R(0);
+            }
+            R Ep[3], Bp[3];
+            if (inr) {
+                SmemReader<R> rd;
+                for (int c = 0; c < 3; ++c) { rd.E[c] = sE[c]; rd.B[c] = sB[c]; }
+                rd.base = (li + G + 1) + fe0 * ((lj + G + 1) + (DIM == 3 ? fe1 * (lk + G + 1) : 0));
+                rd.s1 = fe0;
+                rd.s2 = fe0 * fe1;
+                gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+            } else {
+                GlobalReader<R> rd;
+                for (int c = 0; c < 3; ++c) { rd.E[c] = a.F.E[c]; rd.B[c] = a.F.B[c]; }
+                for (int q = 0; q < 4; ++q) {
+                    rd.xi[q] = cb + wrapi(i - 1 + q, nx);
+                    rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
+                    rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
+                }
+                gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+            }
+            boris(w, Ep, Bp, hq, c2);
+            if (!finite3(w[0], w[1], w[2])) {
+                atomicOr(a.err, ERR_NONFINITE);
+                continue;   // the particle keeps x^n and contributes no current
+            }
+            const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
+            s0 = renormalize(o0, w[0] * ig * cN0, n0);
+            s1 = renormalize(o1, w[1] * ig * cN1, n1);
+            if (DIM == 3) s2 = renormalize(o2, w[2] * ig * cN2, n2);
+            uz = cl * w[2] * ig;
+            const int i1 = wrapi(i + s0, nx), j1 = wrapi(j + s1, ny), k1 = DIM == 3 ? wrapi(k + s2, nz) : 0;
+            const int cell1 = i1 + nx * (j1 + ny * k1);
+            if (MODE == 1) {
+                a.old_cell[p] = cell0;
+                a.old_off[0][p] = o0;
+                a.old_off[1][p] = o1;
+                if (DIM == 3) a.old_off[2][p] = o2;
+            }
+            a.P.cell[p] = cell1;
+            a.P.off[0][p] = n0;
+            a.P.off[1][p] = n1;
+            if (DIM == 3) a.P.off[2][p] = n2;
+            a.P.w[0][p] = w[0];
+            a.P.w[1][p] = w[1];
+            a.P.w[2][p] = w[2];
+        } else {
+            // deposit-only: x^{n+1} is the stored state, the shift follows from the cells
+            const int cell1 = a.P.cell[p];
+            n0 = a.P.off[0][p];
+            n1 = a.P.off[1][p];
+            if (DIM == 3) n2 = a.P.off[2][p];
+            const int i1 = cell1 % nx, r1 = cell1 / nx, j1 = r1 % ny, k1 = DIM == 3 ? r1 / ny : 0;
+            s0 = i1 - i; if (s0 > 1) s0 -= nx; if (s0 < -1) s0 += nx;
+            s1 = j1 - j; if (s1 > 1) s1 -= ny; if (s1 < -1) s1 += ny;
+            if (DIM == 3) { s2 = k1 - k; if (s2 > 1) s2 -= nz; if (s2 < -1) s2 += nz; }
+            if (DIM == 2) {
+                const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
+                uz = cl * w[2] * ig;
+            }
+        }
+        if (MODE == 1) continue;
+
+        // ---- virtual-path current (Eq. current) -------------------------------
+        AxisWin<R> X, Y, Z;
+        axis_window(o0, n0, s0, X);
+        axis_window(o1, n1, s1, Y);
+        if (DIM == 3) axis_window(o2, n2, s2, Z);
+        if (inr) {
+            SmemAcc<R> acc;
+            for (int c = 0; c < 3; ++c) acc.J[c] = sJ[c];
+            acc.base = (li + G + 2) + je0 * ((lj + G + 2) + (DIM == 3 ? je1 * (lk + G + 2) : 0));
+            acc.s1 = je0;
+            acc.s2 = je0 * je1;
+            deposit<DIM>(acc, X, Y, DIM == 3 ? Z : X, kf, uz);
+        } else {
+            GlobalAcc<R> acc;
+            for (int c = 0; c < 3; ++c) acc.J[c] = a.F.J[c];
+            acc.cell_base = cb;
+            acc.i = i; acc.j = j; acc.k = k;
+            acc.nx = nx; acc.ny = ny; acc.nz = nz;
+            deposit<DIM>(acc, X, Y, DIM == 3 ? Z : X, kf, uz);
+        }
+    }
+
+    if (NEED_J) {
+        __syncthreads();
+        for (int l = threadIdx.x; l < nj; l += blockDim.x) {
+            const int lx = l % je0, r = l / je0, ly = r % je1, lz = r / je1;
+            const int gx = wrapi(ox - G - 2 + lx, nx);
+            const int gy = wrapi(oy - G - 2 + ly, ny);
+            const int gz = DIM == 3 ? wrapi(oz - G - 2 + lz, nz) : 0;
+            const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const R v = sJ[c][l];
+                if (v != R(0)) atomicAdd(&a.F.J[c][gi], v);
+            }
+        }
+    }
+}
+
+template <int DIM, typename R, int MODE>
+static cudaError_t launch_t(cudaStream_t st, int max_items, size_t smem, const PartArgs<R> &a)
+{
+    if (max_items <= 0) return cudaSuccess;
+    k_particles<DIM, R, MODE><<<max_items, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int DIM, typename R>
+static cudaError_t launch_mode(int mode, cudaStream_t st, int max_items, size_t smem, const PartArgs<R> &a)
+{
+    switch (mode) {
+    case 0: return launch_t<DIM, R, 0>(st, max_items, smem, a);
+    case 1: return launch_t<DIM, R, 1>(st, max_items, smem, a);
+    default: return launch_t<DIM, R, 2>(st, max_items, smem, a);
+    }
+}
+
+size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo)
+{
+    const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
+    const long long fe = (long long)(tx + 2 * halo + 2) * (ty + 2 * halo + 2) * (dims == 3 ? tz + 2 * halo + 2 : 1);
+    const long long je = (long long)(tx + 2 * halo + 4) * (ty + 2 * halo + 4) * (dims == 3 ? tz + 2 * halo + 4 : 1);
+    size_t n = 0;
+    if (mode != 2) n += 6 * fe;
+    if (mode != 1) n += 3 * je;
+    return n * es;
+}
+
+template <int DIM, typename R>
+static cudaError_t set_limit_t(int mode, size_t bytes)
+{
+    const int b = (int)bytes;
+    switch (mode) {
+    case 0: return cudaFuncSetAttribute(k_particles<DIM, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 1: return cudaFuncSetAttribute(k_particles<DIM, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    default: return cudaFuncSetAttribute(k_particles<DIM, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    }
+}
+
+cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes)
+{
+    if (dims == 3) return prec == 0 ? set_limit_t<3, double>(mode, bytes) : set_limit_t<3, float>(mode, bytes);
+    return prec == 0 ? set_limit_t<2, double>(mode, bytes) : set_limit_t<2, float>(mode, bytes);
+}
+
+template <typename R>
+static PartArgs<R> make_args(const WorkItem *items, const int *n_items, const RunDev *runs, const GroupDev *groups,
+                             const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3], int *old_cell,
+                             void *const old_off[3], int halo, int *err)
+{
+    PartArgs<R> a;
+    a.items = items;
+    a.n_items = n_items;
+    a.runs = runs;
+    a.groups = groups;
+    a.P.cell = P.cell;
+    a.P.id = P.id;
+    for (int c = 0; c < 3; ++c) {
+        a.P.off[c] = static_cast<R *>(P.off[c]);
+        a.P.w[c] = static_cast<R *>(P.w[c]);
+        a.F.E[c] = static_cast<R *>(E[c]);
+        a.F.B[c] = static_cast<R *>(B[c]);
+        a.F.J[c] = static_cast<R *>(J[c]);
+        a.old_off[c] = static_cast<R *>(old_off[c]);
+    }
+    a.old_cell = old_cell;
+    a.halo = halo;
+    a.err = err;
+    return a;
+}
+
+cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, const WorkItem *items,
+                             const int *n_items, int max_items, const RunDev *runs, const GroupDev *groups,
+                             const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
+                             int *old_cell, void *const old_off[3], int halo, int max_tile_x, int max_tile_y,
+                             int max_tile_z, int *err)
+{
+    const size_t smem = particles_smem_bytes(dims, prec, mode, max_tile_x, max_tile_y, max_tile_z, halo);
+    if (prec == 0) {
+        auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
+        return dims == 3 ? launch_mode<3, double>(mode, st, max_items, smem, a)
+                         : launch_mode<2, double>(mode, st, max_items, smem, a);
+    }
+    auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
+    return dims == 3 ? launch_mode<3, float>(mode, st, max_items, smem, a)
+                     : launch_mode<2, float>(mode, st, max_items, smem, a);
+}
+
+// ---------------------------------------------------------------------------
+// Loader: absolute normalized FP64 positions -> (cell, offset) of the pool's
+// precision, periodic wrap into [0, N); an offset that rounds to 1 moves to the
+// next cell with offset 0.  Momenta are converted; id = index in the call.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_load(long long n, const double *x0, const double *x1, const double *x2, const double *w0,
+                       const double *w1, const double *w2, int dims, int nx, int ny, int nz, int *cell,
+                       R *off0, R *off1, R *off2, R *wo0, R *wo1, R *wo2, int *id, long long base)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double *xs[3] = {x0, x1, x2};
+    R *offs[3] = {off0, off1, off2};
+    const int nn[3] = {nx, ny, nz};
+    int ci[3] = {0, 0, 0};
+    for (int a = 0; a < dims; ++a) {
+        const double N = (double)nn[a];
+        double x = xs[a][p];
+        x -= N * floor(x / N);
+        if (x >= N) x -= N;
+        if (x < 0.0) x = 0.0;
+        double fl = floor(x);
+        int c = (int)fl;
+        if (c >= nn[a]) c = nn[a] - 1;
+        R o = (R)(x - (double)c);
+        if (o >= R(1)) {
+            o = R(0);
+            c = c + 1 == nn[a] ? 0 : c + 1;
+        }
+        ci[a] = c;
+        offs[a][base + p] = o;
+    }
+    cell[base + p] = ci[0] + nx * (ci[1] + ny * ci[2]);
+    wo0[base + p] = (R)w0[p];
+    wo1[base + p] = (R)w1[p];
+    wo2[base + p] = (R)w2[p];
+    id[base + p] = (int)p;
+}
+
+cudaError_t launch_load(int prec, cudaStream_t st, long long n, const double *x0, const double *x1,
+                        const double *x2, const double *w0, const double *w1, const double *w2, int dims, int nx,
+                        int ny, int nz, const PoolBuf &P, long long base)
+{
+    if (n <= 0) return cudaSuccess;
+    const int nt = 256;
+    const long long nb = (n + nt - 1) / nt;
+    if (prec == 0) {
+        k_load<double><<<(unsigned)nb, nt, 0, st>>>(n, x0, x1, dims == 3 ? x2 : x0, w0, w1, w2, dims, nx, ny, nz,
+                                                    P.cell, (double *)P.off[0], (double *)P.off[1],
+                                                    dims == 3 ? (double *)P.off[2] : (double *)P.off[0],
+                                                    (double *)P.w[0], (double *)P.w[1], (double *)P.w[2], P.id, base);
+    } else {
+        k_load<float><<<(unsigned)nb, nt, 0, st>>>(n, x0, x1, dims == 3 ? x2 : x0, w0, w1, w2, dims, nx, ny, nz,
+                                                   P.cell, (float *)P.off[0], (float *)P.off[1],
+                                                   dims == 3 ? (float *)P.off[2] : (float *)P.off[0],
+                                                   (float *)P.w[0], (float *)P.w[1], (float *)P.w[2], P.id, base);
+    }
+    return cudaGetLastError();
+}
+
+// Device-to-device copy of a range of pool entries (used when the pool is re-laid out).
+template <typename R>
+__global__ void k_copy_pool(long long n, const int *sc, const R *so0, const R *so1, const R *so2, const R *sw0,
+                            const R *sw1, const R *sw2, const int *sid, int *dc, R *do0, R *do1, R *do2, R *dw0,
+                            R *dw1, R *dw2, int *did)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    dc[p] = sc[p];
+    do0[p] = so0[p];
+    do1[p] = so1[p];
+    if (do2) do2[p] = so2[p];
+    dw0[p] = sw0[p];
+    dw1[p] = sw1[p];
+    dw2[p] = sw2[p];
+    did[p] = sid[p];
+}
+
+cudaError_t launch_copy_pool(int prec, cudaStream_t st, const PoolBuf &src, long long sb, const PoolBuf &dst,
+                             long long db, long long n)
+{
+    if (n <= 0) return cudaSuccess;
+    const int nt = 256;
+    const unsigned nb = (unsigned)((n + nt - 1) / nt);
+    if (prec == 0) {
+        auto S = [&](void *p) { return p ? (double *)p + sb : nullptr; };
+        auto D = [&](void *p) { return p ? (double *)p + db : nullptr; };
+        k_copy_pool<double><<<nb, nt, 0, st>>>(n, src.cell + sb, S(src.off[0]), S(src.off[1]), S(src.off[2]),
+                                               S(src.w[0]), S(src.w[1]), S(src.w[2]), src.id + sb, dst.cell + db,
+                                               D(dst.off[0]), D(dst.off[1]), D(dst.off[2]), D(dst.w[0]),
+                                               D(dst.w[1]), D(dst.w[2]), dst.id + db);
+    } else {
+        auto S = [&](void *p) { return p ? (float *)p + sb : nullptr; };
+        auto D = [&](void *p) { return p ? (float *)p + db : nullptr; };
+        k_copy_pool<float><<<nb, nt, 0, st>>>(n, src.cell + sb, S(src.off[0]), S(src.off[1]), S(src.off[2]),
+                                              S(src.w[0]), S(src.w[1]), S(src.w[2]), src.id + sb, dst.cell + db,
+                                              D(dst.off[0]), D(dst.off[1]), D(dst.off[2]), D(dst.w[0]),
+                                              D(dst.w[1]), D(dst.w[2]), dst.id + db);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pic

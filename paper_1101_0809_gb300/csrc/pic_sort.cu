@@ -1,0 +1,346 @@
+// pic_sort.cu -- stable counting sort of the particle pool by tile, and the
+// work list of the particle kernels.
+//
+// The key of a particle is its global tile id: the tile_base of its group
+// (run, species) plus the linear index of the tile holding its cell,
+// (k/Tz * nty + j/Ty) * ntx + i/Tx.  The sort is a least-significant-digit
+// radix sort with 8-bit digits; every pass is a stable counting sort: per
+// chunk of 4096 keys a digit histogram, one exclusive scan over all
+// (digit, chunk) counts in digit-major order, then a scatter in which every key
+// lands at its digit's chunk offset plus its rank among equal digits earlier in
+// the chunk (warp match + per-warp counts), so equal keys keep their order.
+// The permutation then moves every particle array once.
+#include "pic_internal.h"
+
+namespace pic {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kChunk = kSortThreads * kSortItems;   // keys per chunk
+constexpr int kScanItems = 8;
+constexpr int kScanSeg = kSortThreads * kScanItems; // elements per scan block
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of unsigned counts: per-block sums, one block scanning the
+// sums, then every block scanning its segment with its offset.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned *warp_tot, unsigned &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        unsigned t = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;   // inclusive warp prefix
+    }
+    __syncthreads();
+    const unsigned before = warp == 0 ? 0u : warp_tot[warp - 1];
+    total = warp_tot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_scan_sums(const unsigned *in, long long n, unsigned *sums)
+{
+    __shared__ unsigned wt[32];
+    const long long base = blockIdx.x * (long long)kScanSeg + threadIdx.x * kScanItems;
+    unsigned s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q)
+        if (base + q < n) s += in[base + q];
+    unsigned total;
+    block_exclusive_scan(s, wt, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_single(unsigned *a, long long n)
+{
+    __shared__ unsigned wt[32];
+    unsigned carry = 0;
+    for (long long seg = 0; seg < n; seg += kScanSeg) {
+        const long long base = seg + threadIdx.x * kScanItems;
+        unsigned v[kScanItems];
+        unsigned s = 0;
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            v[q] = base + q < n ? a[base + q] : 0u;
+            s += v[q];
+        }
+        unsigned total;
+        unsigned run = carry + block_exclusive_scan(s, wt, total);
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            if (base + q < n) a[base + q] = run;
+            run += v[q];
+        }
+        carry += total;
+    }
+}
+
+__global__ void k_scan_apply(unsigned *a, long long n, const unsigned *sums)
+{
+    __shared__ unsigned wt[32];
+    const long long base = blockIdx.x * (long long)kScanSeg + threadIdx.x * kScanItems;
+    unsigned v[kScanItems];
+    unsigned s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        v[q] = base + q < n ? a[base + q] : 0u;
+        s += v[q];
+    }
+    unsigned total;
+    unsigned run = sums[blockIdx.x] + block_exclusive_scan(s, wt, total);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        if (base + q < n) a[base + q] = run;
+        run += v[q];
+    }
+}
+
+static cudaError_t exclusive_scan(unsigned *a, long long n, unsigned *sums, cudaStream_t st, int *launches)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long nb = (n + kScanSeg - 1) / kScanSeg;
+    if (nb == 1) {
+        k_scan_single<<<1, kSortThreads, 0, st>>>(a, n);
+        *launches += 1;
+        return cudaGetLastError();
+    }
+    k_scan_sums<<<(unsigned)nb, kSortThreads, 0, st>>>(a, n, sums);
+    k_scan_single<<<1, kSortThreads, 0, st>>>(sums, nb);
+    k_scan_apply<<<(unsigned)nb, kSortThreads, 0, st>>>(a, n, sums);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Keys: global tile id of every particle; vals: its index.
+// ---------------------------------------------------------------------------
+__global__ void k_keys(long long total, const int *cell, const long long *group_base, int ngroups,
+                       const GroupDev *groups, const RunDev *runs, unsigned *keys, unsigned *vals)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    int lo = 0, hi = ngroups;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (group_base[mid] <= p) lo = mid; else hi = mid;
+    }
+    const GroupDev g = groups[lo];
+    const RunDev &r = runs[g.run];
+    const int c = cell[p];
+    const int i = c % r.n[0];
+    const int rest = c / r.n[0];
+    const int j = rest % r.n[1];
+    const int k = rest / r.n[1];
+    const int t = ((k / r.tile[2]) * r.ntile[1] + j / r.tile[1]) * r.ntile[0] + i / r.tile[0];
+    keys[p] = (unsigned)(g.tile_base + t);
+    vals[p] = (unsigned)p;
+}
+
+__global__ void k_upsweep(const unsigned *keys, long long n, int shift, unsigned *hist, long long nchunks)
+{
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = blockIdx.x * (long long)kChunk;
+#pragma unroll 4
+    for (int r = 0; r < kSortItems; ++r) {
+        const long long idx = base + r * kSortThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nchunks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_downsweep(const unsigned *keys, const unsigned *vals, long long n,
+                                                            int shift, const unsigned *hist, long long nchunks,
+                                                            unsigned *keys_out, unsigned *vals_out)
+{
+    __shared__ unsigned off[256];
+    __shared__ unsigned tot[256];
+    __shared__ unsigned wh[kSortThreads / 32][256];
+    __shared__ unsigned pre[kSortThreads / 32][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    off[tid] = hist[tid * nchunks + blockIdx.x];
+    tot[tid] = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) wh[w][tid] = 0;
+    __syncthreads();
+    const long long base = blockIdx.x * (long long)kChunk;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < kSortItems; ++r) {
+        const long long idx = base + r * kSortThreads + tid;
+        const bool valid = idx < n;
+        const unsigned key = valid ? keys[idx] : 0u;
+        const unsigned val = valid ? vals[idx] : 0u;
+        const unsigned d = valid ? ((key >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned rank = __popc(peers & lt);
+        if (valid && (__ffs(peers) - 1) == lane) wh[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            unsigned run = tot[tid];
+#pragma unroll
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                const unsigned c = wh[w][tid];
+                pre[w][tid] = run;
+                run += c;
+                wh[w][tid] = 0;
+            }
+            tot[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const unsigned dst = off[d] + pre[warp][d] + rank;
+            keys_out[dst] = key;
+            vals_out[dst] = val;
+        }
+    }
+}
+
+// Permute every particle array: dst[o] = src[perm[o]].
+template <typename R, int DIM>
+__global__ void k_permute(long long n, const unsigned *perm, Pool<R> src, Pool<R> dst)
+{
+    const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const unsigned s = perm[o];
+    dst.cell[o] = src.cell[s];
+    dst.off[0][o] = src.off[0][s];
+    dst.off[1][o] = src.off[1][s];
+    if (DIM == 3) dst.off[2][o] = src.off[2][s];
+    dst.w[0][o] = src.w[0][s];
+    dst.w[1][o] = src.w[1][s];
+    dst.w[2][o] = src.w[2][s];
+    dst.id[o] = src.id[s];
+}
+
+// tile_start[t] = first sorted position with key >= t, for t in [0, total_tiles].
+__global__ void k_tile_start(const unsigned *keys, long long n, int total_tiles, long long *tile_start)
+{
+    const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const long long k = keys[o];
+    const long long kp = o == 0 ? -1 : (long long)keys[o - 1];
+    for (long long t = kp + 1; t <= k; ++t) tile_start[t] = o;
+    if (o == n - 1)
+        for (long long t = k + 1; t <= total_tiles; ++t) tile_start[t] = n;
+}
+
+__global__ void k_item_counts(const long long *tile_start, int total_tiles, int ppi, unsigned *counts)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total_tiles) return;
+    const long long c = tile_start[t + 1] - tile_start[t];
+    counts[t] = (unsigned)((c + ppi - 1) / ppi);
+}
+
+__global__ void k_items(const long long *tile_start, const unsigned *scan, int total_tiles, int ppi,
+                        const GroupDev *groups, int ngroups, WorkItem *items, int *n_items)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total_tiles) return;
+    const long long b = tile_start[t], e = tile_start[t + 1];
+    const int cnt = (int)((e - b + ppi - 1) / ppi);
+    int lo = 0, hi = ngroups;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (groups[mid].tile_base <= t) lo = mid; else hi = mid;
+    }
+    const unsigned s = scan[t];
+    for (int q = 0; q < cnt; ++q) {
+        WorkItem w;
+        w.group = lo;
+        w.tile = t - groups[lo].tile_base;
+        w.begin = b + (long long)q * ppi;
+        w.end = w.begin + ppi < e ? w.begin + ppi : e;
+        items[s + q] = w;
+    }
+    if (t == total_tiles - 1) *n_items = (int)(s + cnt);
+}
+
+cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long total, const PoolBuf &src,
+                                 const PoolBuf &dst, const GroupDev *groups, const long long *group_base_dev,
+                                 int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
+                                 long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
+                                 int particles_per_item, int *launches)
+{
+    cudaError_t e;
+    if (total <= 0 || ngroups <= 0) {
+        e = cudaMemsetAsync(n_items, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        return cudaMemsetAsync(tile_start, 0, sizeof(long long) * (total_tiles + 1), st);
+    }
+    const int nt = 256;
+    const unsigned nbp = (unsigned)((total + nt - 1) / nt);
+    k_keys<<<nbp, nt, 0, st>>>(total, src.cell, group_base_dev, ngroups, groups, runs, scr.keys[0], scr.vals[0]);
+    *launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+    int nbits = 1;
+    while ((1ll << nbits) < (long long)total_tiles) ++nbits;
+    const long long nchunks = (total + kChunk - 1) / kChunk;
+    int cur = 0;
+    for (int shift = 0; shift < nbits; shift += 8) {
+        k_upsweep<<<(unsigned)nchunks, kSortThreads, 0, st>>>(scr.keys[cur], total, shift, scr.hist, nchunks);
+        *launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = exclusive_scan(scr.hist, 256 * nchunks, scr.block_sums, st, launches)) != cudaSuccess) return e;
+        k_downsweep<<<(unsigned)nchunks, kSortThreads, 0, st>>>(scr.keys[cur], scr.vals[cur], total, shift,
+                                                                scr.hist, nchunks, scr.keys[1 - cur],
+                                                                scr.vals[1 - cur]);
+        *launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cur = 1 - cur;
+    }
+
+    if (prec == 0) {
+        Pool<double> s, d;
+        s.cell = src.cell; s.id = src.id; d.cell = dst.cell; d.id = dst.id;
+        for (int c = 0; c < 3; ++c) {
+            s.off[c] = (double *)src.off[c]; s.w[c] = (double *)src.w[c];
+            d.off[c] = (double *)dst.off[c]; d.w[c] = (double *)dst.w[c];
+        }
+        if (dims == 3) k_permute<double, 3><<<nbp, nt, 0, st>>>(total, scr.vals[cur], s, d);
+        else k_permute<double, 2><<<nbp, nt, 0, st>>>(total, scr.vals[cur], s, d);
+    } else {
+        Pool<float> s, d;
+        s.cell = src.cell; s.id = src.id; d.cell = dst.cell; d.id = dst.id;
+        for (int c = 0; c < 3; ++c) {
+            s.off[c] = (float *)src.off[c]; s.w[c] = (float *)src.w[c];
+            d.off[c] = (float *)dst.off[c]; d.w[c] = (float *)dst.w[c];
+        }
+        if (dims == 3) k_permute<float, 3><<<nbp, nt, 0, st>>>(total, scr.vals[cur], s, d);
+        else k_permute<float, 2><<<nbp, nt, 0, st>>>(total, scr.vals[cur], s, d);
+    }
+    *launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+    k_tile_start<<<nbp, nt, 0, st>>>(scr.keys[cur], total, total_tiles, tile_start);
+    *launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const unsigned nbt = (unsigned)((total_tiles + nt - 1) / nt);
+    k_item_counts<<<nbt, nt, 0, st>>>(tile_start, total_tiles, particles_per_item, item_scan);
+    *launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = exclusive_scan(item_scan, total_tiles, scr.block_sums, st, launches)) != cudaSuccess) return e;
+    k_items<<<nbt, nt, 0, st>>>(tile_start, item_scan, total_tiles, particles_per_item, groups, ngroups, items,
+                                n_items);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace pic

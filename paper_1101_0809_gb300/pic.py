@@ -1,0 +1,257 @@
+"""Python binding of libpic (include/pic.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: all of it runs in the CUDA kernels of libpic.so.
+Arrays may be numpy arrays (host, on_device = 0) or CUDA torch tensors
+(device, on_device = 1, ordered on the grid's stream).  If libpic.so is missing
+the import of this module raises: there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpic.so")
+
+PIC_OK, PIC_ERR_INVALID_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_CUDA = 0, 1, 2, 3, 4
+PIC_ERR_NONFINITE, PIC_ERR_OUT_OF_TILE, PIC_ERR_TIMEOUT, PIC_ERR_STATE = 5, 6, 7, 8
+PIC_FP64, PIC_FP32 = 0, 1
+PIC_B_HALF, PIC_E_FULL = 1, 2
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libpic error {code}: {msg}")
+        self.code = code
+
+
+class pic_grid_desc(C.Structure):
+    _fields_ = [("dims", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("dt", C.c_double), ("c", C.c_double),
+                ("precision", C.c_int), ("order2", C.c_int), ("tile", C.c_int * 3),
+                ("halo", C.c_int), ("sort_interval", C.c_int), ("particles_per_block", C.c_int),
+                ("rho_bg", C.c_double), ("cuda_stream", C.c_void_p)]
+
+
+class pic_species_desc(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("weight", C.c_double)]
+
+
+class pic_diag(C.Structure):
+    _fields_ = [("kinetic", C.c_double), ("field_E", C.c_double), ("field_B", C.c_double),
+                ("half_step_corr", C.c_double), ("total", C.c_double),
+                ("momentum", C.c_double * 3), ("total_charge", C.c_double),
+                ("gauss_resid_max", C.c_double), ("gauss_resid_rms", C.c_double),
+                ("n_particles", C.c_longlong), ("error_word", C.c_int)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run paper_1101_0809_gb300/build.py "
+                      "(or __graft_entry__.build()) first")
+_lib = C.CDLL(LIB_PATH)
+_VP = C.c_void_p
+_VP3 = C.c_void_p * 3
+_lib.pic_last_error.restype = C.c_char_p
+_lib.pic_num_particles.restype = C.c_longlong
+_lib.pic_kernel_launches.restype = C.c_longlong
+_lib.pic_create_grid.argtypes = [C.POINTER(pic_grid_desc), C.POINTER(_VP)]
+_lib.pic_destroy.argtypes = [_VP]
+_lib.pic_set_fields.argtypes = [_VP, _VP3, _VP3, C.c_int]
+_lib.pic_get_fields.argtypes = [_VP, _VP3, _VP3, _VP3, C.c_int]
+_lib.pic_load_particles.argtypes = [_VP, C.c_int, C.POINTER(pic_species_desc), C.c_longlong, _VP3, _VP3, C.c_int]
+_lib.pic_num_particles.argtypes = [_VP, C.c_int]
+_lib.pic_get_particles.argtypes = [_VP, C.c_int, _VP, _VP3, _VP3, _VP, C.c_int]
+for _n in ("pic_gather_push", "pic_deposit_current", "pic_sort", "pic_sync"):
+    getattr(_lib, _n).argtypes = [_VP]
+_lib.pic_yee_update.argtypes = [_VP, C.c_int]
+_lib.pic_step.argtypes = [_VP, C.c_int]
+_lib.pic_diagnostics.argtypes = [_VP, C.POINTER(pic_diag)]
+_lib.pic_kernel_launches.argtypes = [_VP]
+
+
+def library():
+    """The loaded ctypes library (for symbol checks)."""
+    return _lib
+
+
+def _check(rc):
+    if rc != PIC_OK:
+        raise PicError(rc, _lib.pic_last_error().decode())
+
+
+def _addr(a):
+    """(address, on_device) of a numpy array or torch tensor; None -> (None, None)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous, "arrays must be contiguous"
+        return a.ctypes.data, 0
+    # torch tensor
+    assert a.is_contiguous(), "tensors must be contiguous"
+    return a.data_ptr(), 1 if a.is_cuda else 0
+
+
+def _triple(arrs):
+    addrs, devs = [], set()
+    for a in arrs:
+        p, d = _addr(a)
+        addrs.append(p)
+        if d is not None:
+            devs.add(d)
+    if len(devs) > 1:
+        raise ValueError("mixing host and device arrays in one call")
+    return _VP3(*addrs), (devs.pop() if devs else 0)
+
+
+def pic_create_grid(desc: pic_grid_desc):
+    h = _VP()
+    _check(_lib.pic_create_grid(C.byref(desc), C.byref(h)))
+    return h
+
+
+def pic_destroy(g):
+    _check(_lib.pic_destroy(g))
+
+
+def pic_set_fields(g, E, B):
+    e, de = _triple(E)
+    b, db = _triple(B)
+    if de != db:
+        raise ValueError("E and B must both be host or both be device arrays")
+    _check(_lib.pic_set_fields(g, e, b, de))
+
+
+def pic_get_fields(g, E=None, B=None, J=None):
+    e, de = _triple(E or [None] * 3)
+    b, db = _triple(B or [None] * 3)
+    j, dj = _triple(J or [None] * 3)
+    devs = {d for d, arr in ((de, E), (db, B), (dj, J)) if arr is not None}
+    if len(devs) > 1:
+        raise ValueError("mixing host and device arrays in one call")
+    _check(_lib.pic_get_fields(g, e, b, j, devs.pop() if devs else 0))
+
+
+def pic_load_particles(g, species, q, m, weight, x, w):
+    """x, w: sequences of 3 float64 arrays (x[2] ignored in 2D) or (3, n) arrays."""
+    n = int(len(w[0]))
+    sp = pic_species_desc(q, m, weight)
+    xs, dx = _triple([x[0], x[1], x[2]])
+    ws, dw = _triple([w[0], w[1], w[2]])
+    if dx != dw:
+        raise ValueError("x and w must both be host or both be device arrays")
+    _check(_lib.pic_load_particles(g, species, C.byref(sp), n, xs, ws, dx))
+
+
+def pic_num_particles(g, species):
+    return int(_lib.pic_num_particles(g, species))
+
+
+def pic_get_particles(g, species, cell=None, offset=None, w=None, ident=None):
+    pc, d1 = _addr(cell)
+    pi, d2 = _addr(ident)
+    o, d3 = _triple(offset or [None] * 3)
+    ww, d4 = _triple(w or [None] * 3)
+    devs = {d for d, arr in ((d1, cell), (d2, ident), (d3, offset), (d4, w)) if arr is not None}
+    if len(devs) > 1:
+        raise ValueError("mixing host and device arrays in one call")
+    _check(_lib.pic_get_particles(g, species, pc, o, ww, pi, devs.pop() if devs else 0))
+
+
+def pic_gather_push(g):
+    _check(_lib.pic_gather_push(g))
+
+
+def pic_deposit_current(g):
+    _check(_lib.pic_deposit_current(g))
+
+
+def pic_yee_update(g, which):
+    _check(_lib.pic_yee_update(g, which))
+
+
+def pic_step(g, nsteps=1):
+    _check(_lib.pic_step(g, nsteps))
+
+
+def pic_sort(g):
+    _check(_lib.pic_sort(g))
+
+
+def pic_sync(g):
+    _check(_lib.pic_sync(g))
+
+
+def pic_diagnostics(g):
+    d = pic_diag()
+    _check(_lib.pic_diagnostics(g, C.byref(d)))
+    out = {k: getattr(d, k) for k in ("kinetic", "field_E", "field_B", "half_step_corr", "total",
+                                       "total_charge", "gauss_resid_max", "gauss_resid_rms",
+                                       "n_particles", "error_word")}
+    out["momentum"] = np.array(d.momentum[:])
+    return out
+
+
+def pic_kernel_launches(g):
+    return int(_lib.pic_kernel_launches(g))
+
+
+def make_desc(dims, n, d, dt, c, precision=PIC_FP64, tile=(0, 0, 0), halo=-1, sort_interval=0,
+              particles_per_block=0, rho_bg=0.0, stream=None):
+    """Fill a pic_grid_desc; ``stream`` is a raw cudaStream_t handle (int) or None."""
+    return pic_grid_desc(dims, n[0], n[1], n[2] if dims == 3 else 1, d[0], d[1], d[2], dt, c,
+                         precision, 3, (C.c_int * 3)(*tile), halo, sort_interval,
+                         particles_per_block, rho_bg, stream)
+
+
+class Grid:
+    """Owning handle around pic_create_grid / pic_destroy (marshalling only)."""
+
+    def __init__(self, desc: pic_grid_desc):
+        self.desc = desc
+        self.h = pic_create_grid(desc)
+        self.dims = desc.dims
+        self.precision = desc.precision
+        self.shape = (desc.nz if desc.dims == 3 else 1, desc.ny, desc.nx)
+        self.dtype = np.float64 if desc.precision == PIC_FP64 else np.float32
+
+    def close(self):
+        if self.h:
+            pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # host-side convenience wrappers around the C calls (numpy in, numpy out)
+    def set_fields(self, E, B):
+        E = [np.ascontiguousarray(a, dtype=self.dtype) for a in E]
+        B = [np.ascontiguousarray(a, dtype=self.dtype) for a in B]
+        pic_set_fields(self.h, E, B)
+
+    def get_fields(self):
+        E = [np.empty(self.shape, self.dtype) for _ in range(3)]
+        B = [np.empty(self.shape, self.dtype) for _ in range(3)]
+        J = [np.empty(self.shape, self.dtype) for _ in range(3)]
+        pic_get_fields(self.h, E, B, J)
+        return E, B, J
+
+    def load(self, species, q, m, weight, x, w):
+        x = [np.ascontiguousarray(x[a], dtype=np.float64) for a in range(3)]
+        w = [np.ascontiguousarray(w[a], dtype=np.float64) for a in range(3)]
+        pic_load_particles(self.h, species, q, m, weight, x, w)
+
+    def particles(self, species):
+        n = pic_num_particles(self.h, species)
+        cell = np.empty(n, np.int32)
+        ident = np.empty(n, np.int32)
+        off = [np.empty(n, self.dtype) for _ in range(3)]
+        w = [np.empty(n, self.dtype) for _ in range(3)]
+        if self.dims == 2:
+            off[2][:] = 0
+        pic_get_particles(self.h, species, cell, off if self.dims == 3 else [off[0], off[1], None], w, ident)
+        return cell, off, w, ident
