@@ -1,0 +1,363 @@
+"""Throughput of the charge-conserving PIC step on one GB300 (or N independent
+replicas, one per GPU).
+
+Workload: 3D3V periodic 128^3 plasma, electrons and ions (mass ratio 1836), 32
+macro-particles per cell each (134,217,728 particles), v_th,e = 0.1c,
+dt = 0.45 dx/c, synthetic seeded inputs.  A "step" is one full time step of the
+paper's Appendix on every particle: B half step, gather + push + move +
+virtual-path deposit, B half step, E full step, and the tile sort every 10
+steps.  The headline value is the FP32 form; the FP64 path is timed beside it.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on bounded samples of the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s and % HBM roofline (fwd, fwd+adjoint) FP32 vs FP64 at 1 GB300"
+UNIT = "particle-steps/s"
+WORKLOAD = ("3D3V periodic 128^3 Yee grid, electrons + ions (mass ratio 1836), 32 per cell each "
+            "(134,217,728 particles), v_th,e = 0.1c, dt = 0.45 dx/c, l_a = 1 1/2 gather, "
+            "virtual-path deposit")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="cells per axis")
+    ap.add_argument("--ppc", type=int, default=32, help="macro-particles per cell per species")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def time_oracle(n, ppc, target_s=15.0, steps=None, fraction=None):
+    """Time the FP64 CPU oracle (single thread) on a random subsample of the
+    workload's particles on the full grid; returns (particle-steps/s, sample text)."""
+    import oracle as O
+    from paper_1101_0809_gb300 import workloads as W
+
+    def run(frac, nsteps):
+        wl = W.c1_thermal3d(n=n, ppc=ppc, steps=nsteps, fraction=frac)
+        g = O.Grid(wl.dims, wl.n, wl.d, wl.dt, wl.c)
+        sp = [O.Species(s.q, s.m, s.weight, s.x, s.w) for s in wl.species]
+        E, B, J = g.zeros(), g.zeros(), g.zeros()
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            O.step(g, E, B, J, sp)
+        dt = time.perf_counter() - t0
+        return sum(s.x.shape[1] for s in sp), dt
+
+    if fraction is None:
+        probe_frac = 1.0 / 1024
+        np_, dt = run(probe_frac, 1)
+        per = dt / max(np_, 1)
+        fraction = min(1.0, (target_s / 2) / per / (2 * ppc * n ** 3))
+        steps = 2
+    npart, dt = run(fraction, steps)
+    rate = npart * steps / dt
+    sample = (f"{npart} of {2 * ppc * n ** 3} particles (random subsample, same weights) on the full "
+              f"{n}^3 grid, {steps} full steps, {dt:.1f} s single-threaded")
+    return rate, sample
+
+
+def reference_arm(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    # bounded samples: every step of the K + W run is a small random subsample
+    total_s = 0.0
+    parts = 0
+    frac = 1.0 / 2048
+    rate0, _ = time_oracle(args.n, args.ppc, steps=max(args.warmup, 1), fraction=frac)
+    import oracle as O  # noqa: F401
+    rate, sample = time_oracle(args.n, args.ppc, steps=args.steps, fraction=frac)
+    npart = round(frac * 2 * args.ppc * args.n ** 3)
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * npart / rate,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("pic_device.cuh", "pic_particles.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1101_0809_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_particle(precision):
+    """Bytes of DRAM traffic per particle of the fused particle kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"k_particles_fused_3d_{precision}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_particle"])
+    except (KeyError, ValueError):
+        return None
+
+
+def build_grid(P, wl, precision, stream):
+    desc = P.make_desc(wl.dims, wl.n, wl.d, wl.dt, wl.c, precision, tile=wl.tile, halo=1,
+                       sort_interval=wl.sort_interval, particles_per_block=8192, rho_bg=wl.rho_bg,
+                       stream=stream)
+    grid = P.Grid(desc)
+    for s, sp in enumerate(wl.species):
+        grid.load(s, sp.q, sp.m, sp.weight, sp.x, sp.w)
+    return grid
+
+
+def timed_steps(P, torch, grid, steps, dist=None, sampler=None):
+    st = torch.cuda.current_stream()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = P.pic_kernel_launches(grid.h)
+    P.pic_profile(grid.h, True)
+    if sampler:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        P.pic_step(grid.h, 1)
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    prof = P.pic_profile_read(grid.h)
+    P.pic_profile(grid.h, False)
+    launches = P.pic_kernel_launches(grid.h) - l0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, prof, launches, clocks
+
+
+def our_arm(args):
+    import torch
+    rank, local, world = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as D
+        torch.cuda.set_device(local)
+        D.init_process_group("nccl")
+        dist = D
+    else:
+        torch.cuda.set_device(0)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_note = "measured" if peaks else "fallback"
+
+    # CPU baseline first, before any GPU work in this process
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, sample = time_oracle(args.n, args.ppc)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    from paper_1101_0809_gb300 import build as B
+    B.build()
+    from paper_1101_0809_gb300 import pic as P
+    from paper_1101_0809_gb300 import workloads as W
+
+    wl = W.c1_thermal3d(n=args.n, ppc=args.ppc, steps=args.steps)
+    npart = wl.n_particles
+    ncell = wl.n_cells
+    stream = torch.cuda.current_stream().cuda_stream
+    sampler = ClockSampler(local)
+
+    # ---- FP32 form, device-resident --------------------------------------------------
+    grid = build_grid(P, wl, P.PIC_FP32, stream)
+    for _ in range(args.warmup):
+        P.pic_step(grid.h, 1)
+    P.pic_sync(grid.h)
+    ms, prof, launches, clocks = timed_steps(P, torch, grid, args.steps, dist, sampler)
+    P.pic_sync(grid.h)
+    ms_step = ms / args.steps
+    value = world * npart * args.steps / (ms * 1e-3)
+    pk_ms, pk_n = prof["particles"]
+    # algorithmic bytes of the fused kernel: particle SoA read + write (int32 cell,
+    # 3 float offsets, 3 float momenta) and the E, B read + J write of the grid
+    alg_bytes = npart * 2 * (4 + 12 + 12) + ncell * (6 * 4 + 3 * 4)
+    achieved = alg_bytes / (pk_ms / pk_n * 1e-3) / 1e9
+    tpp = ncu_traffic_per_particle("fp32")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": (tpp * npart) if tpp else None,
+            "kernel": "k_particles<3,float,fused>", "peak_source": peak_note,
+            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": pk_ms / pk_n,
+            "step_share": {k: v[0] / ms for k, v in prof.items()}}
+
+    # ---- end to end through the public API with host buffers ---------------------------
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        for sp in wl.species:
+            x = [torch.from_numpy(np.ascontiguousarray(sp.x[a])).pin_memory() for a in range(3)]
+            w = [torch.from_numpy(np.ascontiguousarray(sp.w[a])).pin_memory() for a in range(3)]
+            pinned.append((sp, x, w))
+        fields = [torch.zeros(wl.n[::-1], dtype=torch.float32).pin_memory() for _ in range(6)]
+        e2e_steps = max(1, min(args.steps, 3))
+
+        def e2e_step():
+            P.pic_set_fields(grid.h, fields[:3], fields[3:])
+            for s, (sp, x, w) in enumerate(pinned):
+                P.pic_load_particles(grid.h, s, sp.q, sp.m, sp.weight, x, w)
+            P.pic_step(grid.h, 1)
+            return P.pic_diagnostics(grid.h)
+
+        e2e_step()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        h2d = npart * 6 * 8 + 6 * ncell * 4
+        e2e = {"value": world * npart * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 136, "steps": e2e_steps,
+               "step": "pic_set_fields + pic_load_particles (pinned host FP64 x, w) + pic_step + pic_diagnostics"}
+        del pinned, fields
+    grid.close()
+    del grid
+
+    # ---- FP64 path ----------------------------------------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        g64 = build_grid(P, wl, P.PIC_FP64, stream)
+        for _ in range(min(args.warmup, 2)):
+            P.pic_step(g64.h, 1)
+        P.pic_sync(g64.h)
+        k64 = max(1, min(args.steps, args.fp64_steps))
+        ms64, prof64, l64, _ = timed_steps(P, torch, g64, k64, dist, None)
+        P.pic_sync(g64.h)
+        pk64_ms, pk64_n = prof64["particles"]
+        alg64 = npart * 2 * (4 + 24 + 24) + ncell * (6 * 8 + 3 * 8)
+        ach64 = alg64 / (pk64_ms / pk64_n * 1e-3) / 1e9
+        fp64 = {"value": world * npart * k64 / (ms64 * 1e-3), "unit": UNIT, "steps": k64,
+                "ms_per_step": ms64 / k64, "dtype": "f64",
+                "roofline_hbm": {"achieved": ach64, "peak": hbm_peak, "unit": "GB/s", "frac": ach64 / hbm_peak},
+                "fp32_speedup": (npart * args.steps / (ms * 1e-3)) / (npart * k64 / (ms64 * 1e-3))}
+        g64.close()
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "model": "ChCPIC step, FP32 form", "global_batch": world * npart,
+                          "particles_per_gpu": npart, "cells": ncell, "tile": list(wl.tile),
+                          "sort_interval": wl.sort_interval, "halo": 1, "particles_per_block": 8192,
+                          "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                          "l2": "inputs larger than L2 (3.76 GB of particle SoA per replica); no flush"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+               "fp64": fp64}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -176,6 +176,21 @@ const char *pic_last_error(void);
 /* Number of kernels this grid has launched since creation (for accounting). */
 long long pic_kernel_launches(pic_grid *g);
 
+/* Launch-group timing with CUDA events recorded on the grid's stream.
+ * pic_profile(g, 1) clears the totals and starts recording an event pair around
+ * every launch group below; pic_profile(g, 0) stops.  pic_profile_read
+ * synchronizes the stream and returns, per group, the summed device time in
+ * milliseconds and the number of groups timed since the last pic_profile(g, 1). */
+enum {
+    PIC_PROF_YEE_B = 0,       /* B half steps (with the J clear) */
+    PIC_PROF_PARTICLES = 1,   /* the particle kernel(s): fused step, gather_push or deposit */
+    PIC_PROF_YEE_E = 2,       /* E full step */
+    PIC_PROF_SORT = 3,        /* the tile sort and work-list build */
+    PIC_PROF_N = 4
+};
+int pic_profile(pic_grid *g, int enable);
+int pic_profile_read(pic_grid *g, double ms[PIC_PROF_N], long long count[PIC_PROF_N]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,47 @@ int launch_count_add(pic_grid *g, int n)
     return n;
 }
 
+cudaEvent_t prof_event(pic_grid *g)
+{
+    if (!g->prof_free.empty()) {
+        cudaEvent_t e = g->prof_free.back();
+        g->prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records an event pair around one launch group when profiling is on.
+struct ProfScope {
+    pic_grid *g;
+    int cat;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(pic_grid *g_, int cat_) : g(g_), cat(cat_)
+    {
+        if (!g->profiling) return;
+        a = prof_event(g);
+        b = prof_event(g);
+        if (a && b) cudaEventRecord(a, g->stream);
+    }
+    ~ProfScope()
+    {
+        if (!a || !b) return;
+        cudaEventRecord(b, g->stream);
+        g->prof_marks.push_back({cat, {a, b}});
+    }
+};
+
+void prof_clear(pic_grid *g)
+{
+    for (auto &m : g->prof_marks) {
+        g->prof_free.push_back(m.second.first);
+        g->prof_free.push_back(m.second.second);
+    }
+    g->prof_marks.clear();
+}
+
 // (Re)allocate everything whose size depends on the particle count.
 int size_particle_buffers(pic_grid *g, long long total)
 {
@@ -179,6 +220,7 @@ int upload_groups(pic_grid *g)
 
 int do_sort(pic_grid *g)
 {
+    ProfScope ps(g, PIC_PROF_SORT);
     int nl = 0;
     cudaError_t e = sort_and_build_items(g->prec, g->dims, g->stream, g->total, g->pool, g->pool_alt, g->d_groups,
                                          g->d_group_base, (int)g->groups.size(), g->d_runs, g->total_tiles, g->sort,
@@ -193,6 +235,7 @@ int do_sort(pic_grid *g)
 
 int launch_part(pic_grid *g, int mode)
 {
+    ProfScope ps(g, PIC_PROF_PARTICLES);
     cudaError_t e = launch_particles(g->dims, g->prec, mode, g->stream, g->items, g->n_items, g->max_items, g->d_runs,
                                      g->d_groups, g->pool, g->E, g->B, g->J, g->old_cell, g->old_off, g->halo,
                                      g->tile[0], g->tile[1], g->tile[2], g->d_err);
@@ -205,6 +248,7 @@ int launch_fields(pic_grid *g, int which, int zero_j)
 {
     long long maxc = 0;
     for (auto &r : g->runs) maxc = std::max(maxc, (long long)r.dev.n[0] * r.dev.n[1] * r.dev.n[2]);
+    ProfScope ps(g, which == PIC_B_HALF ? PIC_PROF_YEE_B : PIC_PROF_YEE_E);
     cudaError_t e = launch_yee(g->prec, which, zero_j, g->stream, g->d_runs, (int)g->runs.size(), maxc, g->E, g->B,
                                g->J, g->dims);
     launch_count_add(g, 1);
@@ -292,6 +336,9 @@ void destroy_grid(pic_grid *g)
     dfree(g->diag.partials);
     dfree(g->diag.result);
     dfree(g->d_err);
+    dfree(g->stage);
+    prof_clear(g);
+    for (auto e : g->prof_free) cudaEventDestroy(e);
     delete g;
 }
 
@@ -414,6 +461,54 @@ int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, lon
         }
     }
     CK(cudaStreamSynchronize(g->stream), "load: prior work");
+    // stage host arrays in a persistent device buffer (FP64 x and w)
+    const double *xs[3] = {nullptr, nullptr, nullptr}, *ws[3] = {nullptr, nullptr, nullptr};
+    if (n > 0) {
+        if (on_device) {
+            for (int a = 0; a < 3; ++a) {
+                xs[a] = a < g->dims ? x[a] : nullptr;
+                ws[a] = w[a];
+            }
+        } else {
+            if (g->stage_n < 6 * n) {
+                dfree(g->stage);
+                g->stage = nullptr;
+                g->stage_n = 0;
+                CK(dalloc(&g->stage, (size_t)(6 * n)), "load staging");
+                g->stage_n = 6 * n;
+            }
+            for (int a = 0; a < 3; ++a) {
+                if (a < g->dims)
+                    CK(cudaMemcpyAsync(g->stage + a * n, x[a], sizeof(double) * n, cudaMemcpyHostToDevice, g->stream),
+                       "stage x");
+                CK(cudaMemcpyAsync(g->stage + (3 + a) * n, w[a], sizeof(double) * n, cudaMemcpyHostToDevice, g->stream),
+                   "stage w");
+                xs[a] = g->stage + a * n;
+                ws[a] = g->stage + (3 + a) * n;
+            }
+        }
+    }
+    // same species, same count: convert in place, keep the pool layout
+    for (auto &h : g->groups) {
+        if (h.species != species || h.n != n) continue;
+        h.q = sp->q;
+        h.m = sp->m;
+        h.weight = sp->weight;
+        int rc = upload_groups(g);
+        if (rc != PIC_OK) return rc;
+        if (n > 0) {
+            const RunDev &rn = g->runs[0].dev;
+            CK(launch_load(g->prec, g->stream, n, xs[0], xs[1], g->dims == 3 ? xs[2] : xs[0], ws[0], ws[1], ws[2],
+                           g->dims, rn.n[0], rn.n[1], rn.n[2], g->pool, h.base),
+               "particle load");
+            launch_count_add(g, 1);
+        }
+        rc = do_sort(g);
+        if (rc != PIC_OK) return rc;
+        g->have_ref = false;
+        if (!on_device) CK(cudaStreamSynchronize(g->stream), "load");
+        return PIC_OK;
+    }
     // new group layout: every loaded species of run 0, ordered by species index
     std::vector<HostGroup> old = g->groups;
     std::vector<HostGroup> ng;
@@ -466,35 +561,13 @@ int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, lon
     long long new_base = 0;
     for (auto &h : ng)
         if (h.species == species) new_base = h.base;
-    double *tmp = nullptr;
-    const double *xs[3] = {nullptr, nullptr, nullptr}, *ws[3] = {nullptr, nullptr, nullptr};
     if (n > 0) {
-        if (on_device) {
-            for (int a = 0; a < 3; ++a) {
-                xs[a] = a < g->dims ? x[a] : nullptr;
-                ws[a] = w[a];
-            }
-        } else {
-            e = cudaMalloc(&tmp, sizeof(double) * 6 * n);
-            if (e == cudaSuccess) {
-                for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
-                    if (a < g->dims) e = cudaMemcpyAsync(tmp + a * n, x[a], sizeof(double) * n, cudaMemcpyHostToDevice, g->stream);
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(tmp + (3 + a) * n, w[a], sizeof(double) * n, cudaMemcpyHostToDevice, g->stream);
-                    xs[a] = tmp + a * n;
-                    ws[a] = tmp + (3 + a) * n;
-                }
-            }
-        }
-        if (e == cudaSuccess) {
-            const RunDev &rn = g->runs[0].dev;
-            e = launch_load(g->prec, g->stream, n, xs[0], xs[1], g->dims == 3 ? xs[2] : xs[0], ws[0], ws[1], ws[2],
-                            g->dims, rn.n[0], rn.n[1], rn.n[2], np, new_base);
-            launch_count_add(g, 1);
-        }
+        const RunDev &rn = g->runs[0].dev;
+        e = launch_load(g->prec, g->stream, n, xs[0], xs[1], g->dims == 3 ? xs[2] : xs[0], ws[0], ws[1], ws[2],
+                        g->dims, rn.n[0], rn.n[1], rn.n[2], np, new_base);
+        launch_count_add(g, 1);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) {
         free_pool(np);
         free_pool(na);
@@ -590,6 +663,31 @@ int pic_step(pic_grid *g, int nsteps)
         if ((rc = launch_fields(g, PIC_E_FULL, 0)) != PIC_OK) return rc;
         g->steps_since_sort += 1;
         g->have_old = false;
+    }
+    return PIC_OK;
+}
+
+int pic_profile(pic_grid *g, int enable)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    if (enable) prof_clear(g);
+    g->profiling = enable != 0;
+    return PIC_OK;
+}
+
+int pic_profile_read(pic_grid *g, double ms[PIC_PROF_N], long long count[PIC_PROF_N])
+{
+    if (!g || !ms || !count) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    CK(cudaStreamSynchronize(g->stream), "profile sync");
+    for (int c = 0; c < PIC_PROF_N; ++c) {
+        ms[c] = 0.0;
+        count[c] = 0;
+    }
+    for (auto &m : g->prof_marks) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, m.second.first, m.second.second), "event time");
+        ms[m.first] += t;
+        count[m.first] += 1;
     }
     return PIC_OK;
 }

@@ -136,4 +136,13 @@ struct pic_grid {
 
     int *d_err = nullptr;
     long long launches = 0;
+
+    // launch-group timing (pic_profile)
+    bool profiling = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_marks;
+    std::vector<cudaEvent_t> prof_free;
+
+    // staging for host-pointer particle loads (grown, never shrunk)
+    double *stage = nullptr;
+    long long stage_n = 0;
 };

@@ -69,6 +69,9 @@ _lib.pic_yee_update.argtypes = [_VP, C.c_int]
 _lib.pic_step.argtypes = [_VP, C.c_int]
 _lib.pic_diagnostics.argtypes = [_VP, C.POINTER(pic_diag)]
 _lib.pic_kernel_launches.argtypes = [_VP]
+_lib.pic_profile.argtypes = [_VP, C.c_int]
+_lib.pic_profile_read.argtypes = [_VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+PIC_PROF_YEE_B, PIC_PROF_PARTICLES, PIC_PROF_YEE_E, PIC_PROF_SORT, PIC_PROF_N = 0, 1, 2, 3, 4
 
 
 def library():
@@ -195,6 +198,19 @@ def pic_diagnostics(g):
 
 def pic_kernel_launches(g):
     return int(_lib.pic_kernel_launches(g))
+
+
+def pic_profile(g, enable):
+    _check(_lib.pic_profile(g, 1 if enable else 0))
+
+
+def pic_profile_read(g):
+    """{group: (total_ms, count)} for the launch groups timed since pic_profile(g, 1)."""
+    ms = (C.c_double * PIC_PROF_N)()
+    cnt = (C.c_longlong * PIC_PROF_N)()
+    _check(_lib.pic_profile_read(g, ms, cnt))
+    names = ("yee_b", "particles", "yee_e", "sort")
+    return {names[i]: (ms[i], cnt[i]) for i in range(PIC_PROF_N)}
 
 
 def make_desc(dims, n, d, dt, c, precision=PIC_FP64, tile=(0, 0, 0), halo=-1, sort_interval=0,
