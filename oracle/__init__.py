@@ -117,7 +117,7 @@ def _species_array(species):
 
 
 def form_factor(xp):
-    """Closed-form l_a = 1 1/2 values at one position (Sec. 4.4): (i, f[2], dF[3])."""
+    """Closed-form l_a = 1 1/2 values at one position (Sec. 4.5): (i, f[2], dF[3])."""
     i = C.c_longlong()
     f = (C.c_double * 2)()
     dF = (C.c_double * 3)()

@@ -78,7 +78,7 @@ static double cell_volume(const orc_grid *g)
 }
 
 /* ---------------------------------------------------------------------------
- * Alternating-order form factor, l_a = 1 1/2 (Sec. 4.4, closed-form values).
+ * Alternating-order form factor, l_a = 1 1/2 (Sec. 4.5, closed-form values).
  * With i = int(x_p) and d = x_p - i:
  *   point values of f = f^(1) at the integer points i, i+1:         (1-d, d)
  *   cell integrals dF = f^(2) at the half-integers i-1/2, i+1/2, i+3/2:

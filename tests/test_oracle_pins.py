@@ -64,7 +64,7 @@ def piecewise_integral(fn, a, b, knots):
 
 def interp_alternating(F, stag, xp, dims):
     """Interpolate grid function F (nz, ny, nx) at xp with the alternating-order
-    form factor built from its definition (Sec. 4.4): the weight of a grid point
+    form factor built from its definition (Sec. 4.5): the weight of a grid point
     is f^(1) = tent at integer points and f^(2) = quad_spline at half-integer
     points; ``stag`` gives the point's offset (0 or 1/2) per axis."""
     nz, ny, nx = F.shape
@@ -351,7 +351,7 @@ def test_p6_deposit_equals_six_path_closed_form():
 
 
 # --- P8: telescoping of the x-current of a particle moving along x, and the 1D
-# self-energy closed form sum (F_i - 1/2)^2/2 = 1/8 + d^2(1-d)^2/4 (Sec. 4.3) ----------
+# self-energy closed form sum (F_i - 1/2)^2/2 = 1/8 + d^2(1-d)^2/4 (Sec. 4.4) ----------
 @pytest.mark.parametrize("d_final", [0.0, 0.25, 0.5, 0.7])
 def test_p8_telescoped_current_gives_F_and_self_energy(d_final):
     g = O.Grid(3, (16, 5, 5), (1.0, 1.0, 1.0), 0.5, 1.0)
