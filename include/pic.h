@@ -67,7 +67,7 @@ typedef struct {
     double dx, dy, dz;      /* cell sizes (dz ignored when dims == 2) */
     double dt, c;           /* time step; speed of light */
     int precision;          /* PIC_FP64 or PIC_FP32 */
-    int order2;             /* twice the alternating order l_a; only 3 (l_a = 1 1/2, Sec. 4.4) */
+    int order2;             /* twice the alternating order l_a; only 3 (l_a = 1 1/2, Sec. 4.5) */
     int tile[3];            /* tile extents in cells for the sort and the shared-memory
                                stages (0 = default: 8x8x8 in 3D, 16x16 in 2D) */
     int halo;               /* drift guard in cells around a tile (0..2; -1 = default 1) */
@@ -141,7 +141,7 @@ int pic_get_particles(pic_grid *g, int species, int *cell, void *offset[3], void
                       int on_device);
 
 /* Appendix step 2a-2c for every particle: alternating-order form factor at x^n
- * (Sec. 4.4), gather of E (Eq. alphax) and B (Eq. betax), relativistic push
+ * (Sec. 4.5), gather of E (Eq. alphax) and B (Eq. betax), relativistic push
  * (Eq. 1, Appendix), new position (Eq. coordscheme).  Needs B^n: call
  * pic_yee_update(g, PIC_B_HALF) first.  Keeps x^n for pic_deposit_current. */
 int pic_gather_push(pic_grid *g);

@@ -65,7 +65,7 @@ __device__ __forceinline__ int wrapi(int i, int n)
 }
 
 // ---------------------------------------------------------------------------
-// Alternating-order form factor l_a = 1 1/2 (Sec. 4.4): with d the in-cell
+// Alternating-order form factor l_a = 1 1/2 (Sec. 4.5): with d the in-cell
 // offset of the particle, the lower-order point values at the integer points
 // i, i+1 are f = (1-d, d), and the cell integrals at the half-integer points
 // i-1/2, i+1/2, i+3/2 (centres of cells i-1, i, i+1) are
