@@ -191,6 +191,35 @@ enum {
 int pic_profile(pic_grid *g, int enable);
 int pic_profile_read(pic_grid *g, double ms[PIC_PROF_N], long long count[PIC_PROF_N]);
 
+/* ---- Tile sort without device allocation -----------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory: code running inside a memory budget that another
+ * runtime owns (a framework's caching allocator, a coupler that reserved the
+ * whole GPU up front) or on a path where a cudaMalloc would synchronize the
+ * device.  It computes the same stable permutation by tile as pic_sort (ties
+ * keep their input order) but keeps every temporary in one fixed device array
+ * of the library (16.25 MiB, held on every GPU that loads libpic until the
+ * process exits) and never calls cudaMalloc, cudaFree or an allocating library
+ * routine.
+ *   cell        n linear cell indices (k*ny + j)*nx + i, device memory
+ *   n           0 .. PIC_NOALLOC_MAX_PARTICLES; larger n returns PIC_ERR_INVALID_ARG
+ *   dims        2 or 3; ncell[3], tile[3] as in pic_grid_desc (z ignored in 2D)
+ *   perm        n outputs, device memory: perm[o] = input index of sorted slot o
+ *   tile_start  ntiles+1 outputs (device memory, may be null): first sorted slot
+ *               of every tile, tile_start[ntiles] = n; tiles numbered
+ *               (tk*nty + tj)*ntx + ti
+ *   cuda_stream stream to run on (NULL = legacy default stream)
+ * A cell index outside the grid returns PIC_ERR_INVALID_ARG.  The call
+ * synchronizes the stream once (after checking the cells) and returns with the
+ * sort enqueued.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  All calls share the one array: two calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race and must be
+ * serialized by the caller. */
+#define PIC_NOALLOC_MAX_PARTICLES 1048576
+int pic_tile_sort_perm_noalloc(const int *cell, long long n, int dims, const int ncell[3], const int tile[3],
+                               int *perm, long long *tile_start, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

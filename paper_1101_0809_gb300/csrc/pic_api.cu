@@ -344,6 +344,11 @@ void destroy_grid(pic_grid *g)
 
 }  // namespace
 
+namespace pic {
+// Sets the message returned by pic_last_error (for entry points in other files).
+void set_last_error(const char *msg) { snprintf(t_err, sizeof(t_err), "%s", msg); }
+}  // namespace pic
+
 extern "C" {
 
 const char *pic_last_error(void) { return t_err; }

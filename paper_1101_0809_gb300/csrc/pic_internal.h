@@ -74,6 +74,11 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
                                  int particles_per_item, int *launches);
 
+cudaError_t radix_sort_pairs(cudaStream_t st, long long n, int nbits, unsigned *const keys[2], unsigned *const vals[2],
+                             unsigned *hist, unsigned *block_sums, int *cur_out);
+cudaError_t launch_tile_start(cudaStream_t st, const unsigned *sorted_keys, long long n, int total_tiles,
+                              long long *tile_start);
+
 // Diagnostics: accumulates into out (13 doubles) on the device.
 struct DiagScratch {
     double *rho = nullptr;
@@ -88,6 +93,8 @@ cudaError_t launch_diagnostics_run(int dims, int prec, cudaStream_t st, const Ru
                                    void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
                                    int np_blocks, int nc_blocks, int *launches);
 constexpr int kDiagResults = 12;
+
+void set_last_error(const char *msg);
 
 }  // namespace pic
 

@@ -343,4 +343,37 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Stable radix sort of (key, value) pairs in caller-provided scratch, and the
+// tile starts of the sorted keys.  Used by the allocation-free sort entry point;
+// the same kernels as sort_and_build_items.
+// ---------------------------------------------------------------------------
+cudaError_t radix_sort_pairs(cudaStream_t st, long long n, int nbits, unsigned *const keys[2], unsigned *const vals[2],
+                             unsigned *hist, unsigned *block_sums, int *cur_out)
+{
+    cudaError_t e;
+    int launches = 0;
+    const long long nchunks = (n + kChunk - 1) / kChunk;
+    int cur = 0;
+    for (int shift = 0; shift < nbits; shift += 8) {
+        k_upsweep<<<(unsigned)nchunks, kSortThreads, 0, st>>>(keys[cur], n, shift, hist, nchunks);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = exclusive_scan(hist, 256 * nchunks, block_sums, st, &launches)) != cudaSuccess) return e;
+        k_downsweep<<<(unsigned)nchunks, kSortThreads, 0, st>>>(keys[cur], vals[cur], n, shift, hist, nchunks,
+                                                                keys[1 - cur], vals[1 - cur]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cur = 1 - cur;
+    }
+    *cur_out = cur;
+    return cudaSuccess;
+}
+
+cudaError_t launch_tile_start(cudaStream_t st, const unsigned *sorted_keys, long long n, int total_tiles,
+                              long long *tile_start)
+{
+    const int nt = 256;
+    k_tile_start<<<(unsigned)((n + nt - 1) / nt), nt, 0, st>>>(sorted_keys, n, total_tiles, tile_start);
+    return cudaGetLastError();
+}
+
 }  // namespace pic

@@ -213,6 +213,20 @@ def pic_profile_read(g):
     return {names[i]: (ms[i], cnt[i]) for i in range(PIC_PROF_N)}
 
 
+PIC_NOALLOC_MAX_PARTICLES = 1048576
+_lib.pic_tile_sort_perm_noalloc.argtypes = [_VP, C.c_longlong, C.c_int, C.c_int * 3, C.c_int * 3, _VP, _VP, _VP]
+
+
+def pic_tile_sort_perm_noalloc(cell, n, dims, ncell, tile, perm, tile_start=None, stream=None):
+    """Stable tile-sort permutation without device allocation; cell, perm and
+    tile_start are device tensors (int32, int32, int64) owned by the caller."""
+    pc, _ = _addr(cell)
+    pp, _ = _addr(perm)
+    pt, _ = _addr(tile_start)
+    _check(_lib.pic_tile_sort_perm_noalloc(pc, n, dims, (C.c_int * 3)(*ncell), (C.c_int * 3)(*tile),
+                                           pp, pt, stream))
+
+
 def make_desc(dims, n, d, dt, c, precision=PIC_FP64, tile=(0, 0, 0), halo=-1, sort_interval=0,
               particles_per_block=0, rho_bg=0.0, stream=None):
     """Fill a pic_grid_desc; ``stream`` is a raw cudaStream_t handle (int) or None."""
