@@ -206,6 +206,22 @@ int upload_groups(pic_grid *g)
         gd[q].qm = h.q / h.m;
         gd[q].qp = h.q * h.weight;
         gd[q].mp = h.m * h.weight;
+        // bound on |contribution| of one particle to one face (|D| <= 1,
+        // |P+| <= 2, |P-| <= 1, |u_z| <= c), then the power-of-two scale that
+        // maps it to 2^R with R = 46 - log2(particles per block) (see FixedAcc)
+        const double qV = std::fabs(gd[q].qp) / rn.V;
+        double bound;
+        if (g->dims == 3) {
+            bound = 0.25 * std::max(rn.d[0], std::max(rn.d[1], rn.d[2])) / rn.dt * qV * (4.0 + 4.0 / 3.0);
+        } else {
+            bound = std::max(0.5 * std::max(rn.d[0], rn.d[1]) / rn.dt * qV * 2.0, 0.25 * qV * rn.c * (4.0 + 4.0 / 3.0));
+        }
+        int lg = 0;
+        while ((1LL << lg) < (long long)g->ppi) ++lg;
+        const int R = 46 - lg;
+        const int e = bound > 0.0 ? R - (int)std::ceil(std::log2(bound)) : 0;
+        gd[q].jscale = (float)std::ldexp(1.0, e);
+        gd[q].jinv = (float)std::ldexp(1.0, -e);
         base[q] = h.base;
     }
     base[ng] = pb;
@@ -295,6 +311,7 @@ int check_desc(const pic_grid_desc *d, pic_grid *g, RunDev &rd)
     g->halo = halo;
     g->sort_interval = d->sort_interval > 0 ? d->sort_interval : 10;
     g->ppi = d->particles_per_block > 0 ? d->particles_per_block : 8192;
+    if (g->ppi > 8192) return fail(PIC_ERR_INVALID_ARG, "particles_per_block must be <= 8192");
     for (int a = 0; a < 3; ++a) g->tile[a] = t[a];
     memset(&rd, 0, sizeof(rd));
     for (int a = 0; a < 3; ++a) {

@@ -34,6 +34,8 @@ struct GroupDev {
     double qm;            // q/m
     double qp;            // macro charge q_p = weight*q
     double mp;            // macro mass m_p = weight*m
+    float jscale;         // fixed-point scale of the FP32 shared current tile (a power of two)
+    float jinv;           // 1 / jscale
 };
 
 struct WorkItem {
@@ -286,6 +288,34 @@ struct SmemAcc {
     __device__ __forceinline__ void add(int a, int dx, int dy, int dz, R v) const
     {
         atomicAdd(&J[a][base + dx + s1 * dy + s2 * dz], v);
+    }
+};
+
+// FP32 form: the shared current tile accumulates in integer fixed point.
+// Shared-memory float atomics run as compare-and-swap loops on this GPU while
+// 32-bit integer atomics are native, so every contribution v is scaled by the
+// power of two `scale` (q = v*scale, exact) and split into hi = rint(q/2^16) and
+// lo = q - hi*2^16 (exact, |lo| <= 2^15), both rounded to integers with the
+// 1.5*2^23 magic-number trick instead of conversion instructions.  The two
+// integer sums are exact; the block converts hi*2^16 + lo back once.  The
+// scale keeps |q| <= 2^33 for every possible contribution and the sums below
+// 2^31 for up to 2^13 particles per block (set on the host).
+struct FixedAcc {
+    int *hi[3];
+    int *lo[3];
+    int base, s1, s2;
+    float scale;
+    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, float v) const
+    {
+        const float magic = 12582912.0f;   // 1.5 * 2^23
+        const float q = v * scale;
+        const float th = fmaf(q, 1.0f / 65536.0f, magic);
+        const float hf = th - magic;
+        const float r = fmaf(-hf, 65536.0f, q);
+        const float tl = r + magic;
+        const int idx = base + dx + s1 * dy + s2 * dz;
+        atomicAdd(&hi[a][idx], __float_as_int(th) - 0x4B400000);
+        atomicAdd(&lo[a][idx], __float_as_int(tl) - 0x4B400000);
     }
 };
 

@@ -46,12 +46,47 @@ __device__ __forceinline__ int local_coord(int i, int o, int T, int G, int n)
     return l;
 }
 
+// Rare path: a particle more than `halo` cells outside its tile since the
+// last sort.  Same arithmetic on the periodic global arrays; kept out of line
+// so that it does not raise the register count of the tiled path.
+template <int DIM, typename R>
+__device__ __noinline__ void gather_global(const Fields<R> &F, long long cb, int i, int j, int k, int nx, int ny,
+                                           int nz, const R *w6, R *Ep, R *Bp)
+{
+    GlobalReader<R> rd;
+    for (int c = 0; c < 3; ++c) { rd.E[c] = F.E[c]; rd.B[c] = F.B[c]; }
+    for (int q = 0; q < 4; ++q) {
+        rd.xi[q] = cb + wrapi(i - 1 + q, nx);
+        rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
+        rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
+    }
+    R fx[2] = {w6[0], w6[1]}, fy[2] = {w6[5], w6[6]}, fz[2] = {w6[10], w6[11]};
+    R Sx[3] = {w6[2], w6[3], w6[4]}, Sy[3] = {w6[7], w6[8], w6[9]}, Sz[3] = {w6[12], w6[13], w6[14]};
+    gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+}
+
+template <int DIM, typename R>
+__device__ __noinline__ void deposit_global(const Fields<R> &F, long long cb, int i, int j, int k, int nx, int ny,
+                                            int nz, const AxisWin<R> *win, const R *kf, R uz)
+{
+    GlobalAcc<R> acc;
+    for (int c = 0; c < 3; ++c) acc.J[c] = F.J[c];
+    acc.cell_base = cb;
+    acc.i = i; acc.j = j; acc.k = k;
+    acc.nx = nx; acc.ny = ny; acc.nz = nz;
+    deposit<DIM>(acc, win[0], win[1], win[2], kf, uz);
+}
+
 // MODE 0: fused gather + push + move + deposit (pic_step).
 // MODE 1: gather + push + move, keeping x^n (pic_gather_push).
 // MODE 2: deposit from the kept x^n and the current x^{n+1} (pic_deposit_current).
+// Shared memory: E and B tiles (6 * nf values of R) for MODES 0, 1; the current
+// tile for MODES 0, 2: in FP32 two int32 fixed-point words per value, in FP64
+// one double -- 24 * nj bytes either way.
 template <int DIM, typename R, int MODE>
 __global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
 {
+    constexpr bool FIX = sizeof(R) == 4;
     if ((int)blockIdx.x >= *a.n_items) return;
     const WorkItem it = a.items[blockIdx.x];
     const GroupDev gr = a.groups[it.group];
@@ -70,15 +105,23 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
     constexpr bool NEED_J = MODE != 1;
     const long long cb = rn.cell_base;
 
-    R *sm = reinterpret_cast<R *>(g_smem);
-    R *sE[3], *sB[3], *sJ[3];
-    int soff = 0;
-    if (NEED_F) {
-        for (int c = 0; c < 3; ++c) { sE[c] = sm + soff; soff += nf; }
-        for (int c = 0; c < 3; ++c) { sB[c] = sm + soff; soff += nf; }
-    }
-    if (NEED_J) {
-        for (int c = 0; c < 3; ++c) { sJ[c] = sm + soff; soff += nj; }
+    R *sE[3], *sB[3];
+    R *sJ[3];          // FP64 current tile
+    int *sJh[3], *sJl[3];   // FP32 fixed-point current tile
+    {
+        unsigned char *sp = g_smem;
+        if (NEED_F) {
+            R *f = reinterpret_cast<R *>(sp);
+            for (int c = 0; c < 3; ++c) { sE[c] = f + c * nf; sB[c] = f + (3 + c) * nf; }
+            sp += 6 * (size_t)nf * sizeof(R);
+        }
+        if (NEED_J) {
+            for (int c = 0; c < 3; ++c) {
+                sJ[c] = reinterpret_cast<R *>(sp) + c * nj;
+                sJh[c] = reinterpret_cast<int *>(sp) + c * nj;
+                sJl[c] = reinterpret_cast<int *>(sp) + (3 + c) * nj;
+            }
+        }
     }
 
     if (NEED_F) {
@@ -96,10 +139,8 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
         }
     }
     if (NEED_J) {
-        for (int l = threadIdx.x; l < nj; l += blockDim.x) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sJ[c][l] = R(0);
-        }
+        int *z = sJh[0];   // 24 * nj bytes = 6 * nj words in both precisions
+        for (int l = threadIdx.x; l < 6 * nj; l += blockDim.x) z[l] = 0;
     }
     __syncthreads();
 
@@ -160,14 +201,9 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
                 rd.s2 = fe0 * fe1;
                 gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
             } else {
-                GlobalReader<R> rd;
-                for (int c = 0; c < 3; ++c) { rd.E[c] = a.F.E[c]; rd.B[c] = a.F.B[c]; }
-                for (int q = 0; q < 4; ++q) {
-                    rd.xi[q] = cb + wrapi(i - 1 + q, nx);
-                    rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
-                    rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
-                }
-                gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                R w6[15] = {fx[0], fx[1], Sx[0], Sx[1], Sx[2], fy[0], fy[1], Sy[0], Sy[1], Sy[2],
+                            fz[0], fz[1], Sz[0], Sz[1], Sz[2]};
+                gather_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, w6, Ep, Bp);
             }
             boris(w, Ep, Bp, hq, c2);
             if (!finite3(w[0], w[1], w[2])) {
@@ -215,26 +251,34 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
         AxisWin<R> X, Y, Z;
         axis_window(o0, n0, s0, X);
         axis_window(o1, n1, s1, Y);
-        if (DIM == 3) axis_window(o2, n2, s2, Z);
+        if (DIM == 3) axis_window(o2, n2, s2, Z); else Z = X;
         if (inr) {
-            SmemAcc<R> acc;
-            for (int c = 0; c < 3; ++c) acc.J[c] = sJ[c];
-            acc.base = (li + G + 2) + je0 * ((lj + G + 2) + (DIM == 3 ? je1 * (lk + G + 2) : 0));
-            acc.s1 = je0;
-            acc.s2 = je0 * je1;
-            deposit<DIM>(acc, X, Y, DIM == 3 ? Z : X, kf, uz);
+            const int base = (li + G + 2) + je0 * ((lj + G + 2) + (DIM == 3 ? je1 * (lk + G + 2) : 0));
+            if constexpr (FIX) {
+                FixedAcc acc;
+                for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
+                acc.base = base;
+                acc.s1 = je0;
+                acc.s2 = je0 * je1;
+                acc.scale = gr.jscale;
+                deposit<DIM>(acc, X, Y, Z, kf, uz);
+            } else {
+                SmemAcc<R> acc;
+                for (int c = 0; c < 3; ++c) acc.J[c] = sJ[c];
+                acc.base = base;
+                acc.s1 = je0;
+                acc.s2 = je0 * je1;
+                deposit<DIM>(acc, X, Y, Z, kf, uz);
+            }
         } else {
-            GlobalAcc<R> acc;
-            for (int c = 0; c < 3; ++c) acc.J[c] = a.F.J[c];
-            acc.cell_base = cb;
-            acc.i = i; acc.j = j; acc.k = k;
-            acc.nx = nx; acc.ny = ny; acc.nz = nz;
-            deposit<DIM>(acc, X, Y, DIM == 3 ? Z : X, kf, uz);
+            AxisWin<R> win[3] = {X, Y, Z};
+            deposit_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, win, kf, uz);
         }
     }
 
     if (NEED_J) {
         __syncthreads();
+        const float jinv = gr.jinv;
         for (int l = threadIdx.x; l < nj; l += blockDim.x) {
             const int lx = l % je0, r = l / je0, ly = r % je1, lz = r / je1;
             const int gx = wrapi(ox - G - 2 + lx, nx);
@@ -243,8 +287,14 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
             const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const R v = sJ[c][l];
-                if (v != R(0)) atomicAdd(&a.F.J[c][gi], v);
+                if constexpr (FIX) {
+                    const int h = sJh[c][l], lo = sJl[c][l];
+                    if ((h | lo) != 0)
+                        atomicAdd(&a.F.J[c][gi], (R)(fmaf((float)h, 65536.0f, (float)lo) * jinv));
+                } else {
+                    const R v = sJ[c][l];
+                    if (v != R(0)) atomicAdd(&a.F.J[c][gi], v);
+                }
             }
         }
     }
@@ -273,10 +323,10 @@ size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz
     const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
     const long long fe = (long long)(tx + 2 * halo + 2) * (ty + 2 * halo + 2) * (dims == 3 ? tz + 2 * halo + 2 : 1);
     const long long je = (long long)(tx + 2 * halo + 4) * (ty + 2 * halo + 4) * (dims == 3 ? tz + 2 * halo + 4 : 1);
-    size_t n = 0;
-    if (mode != 2) n += 6 * fe;
-    if (mode != 1) n += 3 * je;
-    return n * es;
+    size_t b = 0;
+    if (mode != 2) b += 6 * fe * es;
+    if (mode != 1) b += 24 * je;
+    return b;
 }
 
 template <int DIM, typename R>
