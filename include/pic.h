@@ -176,6 +176,41 @@ const char *pic_last_error(void);
 /* Number of kernels this grid has launched since creation (for accounting). */
 long long pic_kernel_launches(pic_grid *g);
 
+/* ---- Batched form -------------------------------------------------------------
+ * pic_create_batch makes nruns independent periodic runs in one grid object.
+ * They share dims, precision, tile, halo, sort interval, particles per block
+ * and stream (all taken from descs[0]); each run keeps its own cell counts, cell
+ * sizes, dt, c and rho_bg, checked as in pic_create_grid.  Fields are stored run
+ * after run; one particle pool holds every (run, species), sorted together, and
+ * every kernel launch covers all runs.  The *_run calls address one run
+ * (0 .. nruns-1); the calls without _run address run 0.  pic_step,
+ * pic_step_persistent and pic_step_graph advance every run. */
+int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out);
+int pic_num_runs(pic_grid *g);
+int pic_set_fields_run(pic_grid *g, int run, const void *const E[3], const void *const B[3], int on_device);
+int pic_get_fields_run(pic_grid *g, int run, void *E[3], void *B[3], void *J[3], int on_device);
+int pic_load_particles_run(pic_grid *g, int run, int species, const pic_species_desc *sp, long long n,
+                           const double *const x[3], const double *const w[3], int on_device);
+long long pic_num_particles_run(pic_grid *g, int run, int species);
+int pic_get_particles_run(pic_grid *g, int run, int species, int *cell, void *offset[3], void *w[3], int *id,
+                          int on_device);
+int pic_diagnostics_run(pic_grid *g, int run, pic_diag *out);
+
+/* The same steps as pic_step, one kernel launch per step: a cooperative
+ * persistent kernel runs the B half step (with the J clear), the fused particle
+ * work of every run, the second B half step and the E step, separated by
+ * grid-wide barriers (its grid is the number of blocks that can be resident at
+ * once).  The tile sort adds its own launches every sort_interval steps. */
+int pic_step_persistent(pic_grid *g, int nsteps);
+
+/* pic_step_persistent replayed from a CUDA graph of 2*sort_interval steps
+ * (two sorts, so that the double-buffered particle pool returns to the buffer
+ * it started in).  The graph is captured on first use, on the grid's stream,
+ * which must not be the legacy default stream; loading particles or calling
+ * pic_sort / pic_step / pic_step_persistent discards it.  Steps that do not
+ * fill a whole graph run uncaptured. */
+int pic_step_graph(pic_grid *g, int nsteps);
+
 /* Launch-group timing with CUDA events recorded on the grid's stream.
  * pic_profile(g, 1) clears the totals and starts recording an event pair around
  * every launch group below; pic_profile(g, 0) stops.  pic_profile_read

@@ -149,6 +149,13 @@ void prof_clear(pic_grid *g)
     g->prof_marks.clear();
 }
 
+void graph_drop(pic_grid *g)
+{
+    if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
+    g->graph_exec = nullptr;
+    g->graph_valid = false;
+}
+
 // (Re)allocate everything whose size depends on the particle count.
 int size_particle_buffers(pic_grid *g, long long total)
 {
@@ -244,6 +251,7 @@ int do_sort(pic_grid *g)
     launch_count_add(g, nl);
     if (e != cudaSuccess) return cuda_fail(e, "tile sort");
     if (g->total > 0 && !g->groups.empty()) std::swap(g->pool, g->pool_alt);
+    if (!g->capturing) graph_drop(g);   // a captured graph assumes its own buffer parity
     g->steps_since_sort = 0;
     g->have_old = false;
     return PIC_OK;
@@ -272,7 +280,10 @@ int launch_fields(pic_grid *g, int which, int zero_j)
     return PIC_OK;
 }
 
-int check_desc(const pic_grid_desc *d, pic_grid *g, RunDev &rd)
+// Validates one run descriptor.  The first run of a batch fixes the settings
+// every run shares (dims, precision, tile, halo, sort interval, block size,
+// stream); later runs must agree on dims and precision.
+int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
 {
     if (!d) return fail(PIC_ERR_INVALID_ARG, "null descriptor");
     if (d->dims != 2 && d->dims != 3) return fail(PIC_ERR_INVALID_ARG, "dims must be 2 or 3 (got %d)", d->dims);
@@ -281,6 +292,8 @@ int check_desc(const pic_grid_desc *d, pic_grid *g, RunDev &rd)
     if (d->precision != PIC_FP64 && d->precision != PIC_FP32) return fail(PIC_ERR_INVALID_ARG, "bad precision");
     if (d->order2 != 3 && d->order2 != 0)
         return fail(PIC_ERR_INVALID_ARG, "only the alternating order l_a = 1 1/2 (order2 = 3) is built");
+    if (!first && (d->dims != g->dims || d->precision != g->prec))
+        return fail(PIC_ERR_INVALID_ARG, "all runs of a batch need the same dims and precision");
     const double dd[3] = {d->dx, d->dy, d->dims == 3 ? d->dz : 1.0};
     for (int a = 0; a < 3; ++a)
         if (!(dd[a] > 0.0) || !std::isfinite(dd[a])) return fail(PIC_ERR_INVALID_ARG, "cell sizes must be positive");
@@ -293,26 +306,28 @@ int check_desc(const pic_grid_desc *d, pic_grid *g, RunDev &rd)
         s += 1.0 / (dd[a] * dd[a]);
     }
     if (d->c * d->dt * std::sqrt(s) >= 1.0) return fail(PIC_ERR_CFL, "Yee stability limit c*dt*sqrt(sum 1/d^2) >= 1");
+    if (first) {
+        g->dims = d->dims;
+        g->prec = d->precision;
+        g->halo = d->halo < 0 ? 1 : d->halo;
+        if (g->halo > 2) return fail(PIC_ERR_INVALID_ARG, "halo must be 0..2");
+        g->sort_interval = d->sort_interval > 0 ? d->sort_interval : 10;
+        g->ppi = d->particles_per_block > 0 ? d->particles_per_block : 8192;
+        if (g->ppi > 8192) return fail(PIC_ERR_INVALID_ARG, "particles_per_block must be <= 8192");
+        for (int a = 0; a < 3; ++a) g->tile[a] = d->tile[a] > 0 ? d->tile[a] : (d->dims == 3 ? 8 : 16);
+        if (d->dims == 2) g->tile[2] = 1;
+    }
     const int n[3] = {d->nx, d->ny, d->nz};
     int t[3];
-    for (int a = 0; a < 3; ++a) t[a] = d->tile[a] > 0 ? d->tile[a] : (d->dims == 3 ? 8 : 16);
-    if (d->dims == 2) t[2] = 1;
-    const int halo = d->halo < 0 ? 1 : d->halo;
-    if (halo > 2) return fail(PIC_ERR_INVALID_ARG, "halo must be 0..2");
+    for (int a = 0; a < 3; ++a) t[a] = std::min(g->tile[a], n[a]);
+    if (first)
+        for (int a = 0; a < 3; ++a) g->tile[a] = t[a];
     for (int a = 0; a < d->dims; ++a) {
-        t[a] = std::min(t[a], n[a]);
-        if (n[a] < t[a] + 2 * halo + 4)
+        if (n[a] < t[a] + 2 * g->halo + 4)
             return fail(PIC_ERR_INVALID_ARG,
                         "axis %d has %d cells; the tile (%d) plus its staged halo (%d) must fit in the grid", a, n[a],
-                        t[a], 2 * halo + 4);
+                        t[a], 2 * g->halo + 4);
     }
-    g->dims = d->dims;
-    g->prec = d->precision;
-    g->halo = halo;
-    g->sort_interval = d->sort_interval > 0 ? d->sort_interval : 10;
-    g->ppi = d->particles_per_block > 0 ? d->particles_per_block : 8192;
-    if (g->ppi > 8192) return fail(PIC_ERR_INVALID_ARG, "particles_per_block must be <= 8192");
-    for (int a = 0; a < 3; ++a) g->tile[a] = t[a];
     memset(&rd, 0, sizeof(rd));
     for (int a = 0; a < 3; ++a) {
         rd.n[a] = n[a];
@@ -354,6 +369,8 @@ void destroy_grid(pic_grid *g)
     dfree(g->diag.result);
     dfree(g->d_err);
     dfree(g->stage);
+    dfree(g->d_run_cell_base);
+    graph_drop(g);
     prof_clear(g);
     for (auto e : g->prof_free) cudaEventDestroy(e);
     delete g;
@@ -370,24 +387,32 @@ extern "C" {
 
 const char *pic_last_error(void) { return t_err; }
 
-int pic_create_grid(const pic_grid_desc *desc, pic_grid **out)
+int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out)
 {
     if (!out) return fail(PIC_ERR_INVALID_ARG, "null output pointer");
     *out = nullptr;
+    if (!descs) return fail(PIC_ERR_INVALID_ARG, "null descriptor");
+    if (nruns <= 0 || nruns > 65535) return fail(PIC_ERR_INVALID_ARG, "run count must be 1..65535");
     pic_grid *g = new (std::nothrow) pic_grid();
     if (!g) return fail(PIC_ERR_OOM, "host allocation failed");
-    RunDev rd;
-    int rc = check_desc(desc, g, rd);
-    if (rc != PIC_OK) {
-        delete g;
-        return rc;
+    std::vector<long long> base(nruns + 1, 0);
+    for (int r = 0; r < nruns; ++r) {
+        RunDev rd;
+        int rc = check_run(&descs[r], g, rd, r == 0);
+        if (rc != PIC_OK) {
+            delete g;
+            return rc;
+        }
+        rd.cell_base = base[r];
+        base[r + 1] = base[r] + (long long)rd.n[0] * rd.n[1] * rd.n[2];
+        HostRun hr;
+        hr.dev = rd;
+        hr.dims = g->dims;
+        g->runs.push_back(hr);
     }
-    g->stream = (cudaStream_t)desc->cuda_stream;
-    HostRun hr;
-    hr.dev = rd;
-    hr.dims = g->dims;
-    g->runs.push_back(hr);
-    g->total_cells = (long long)rd.n[0] * rd.n[1] * rd.n[2];
+    g->stream = (cudaStream_t)descs[0].cuda_stream;
+    g->total_cells = base[nruns];
+    g->have_ref.assign(nruns, 0);
     auto bail = [&](cudaError_t e, const char *what) {
         int r = cuda_fail(e, what);
         destroy_grid(g);
@@ -402,8 +427,15 @@ int pic_create_grid(const pic_grid_desc *desc, pic_grid **out)
         if ((e = cudaMemsetAsync(g->B[c], 0, g->total_cells * elem(g), g->stream)) != cudaSuccess) return bail(e, "B");
         if ((e = cudaMemsetAsync(g->J[c], 0, g->total_cells * elem(g), g->stream)) != cudaSuccess) return bail(e, "J");
     }
-    if ((e = dalloc(&g->d_runs, 1)) != cudaSuccess) return bail(e, "runs");
-    if ((e = cudaMemcpy(g->d_runs, &rd, sizeof(rd), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "runs");
+    std::vector<RunDev> rds;
+    for (auto &r : g->runs) rds.push_back(r.dev);
+    if ((e = dalloc(&g->d_runs, rds.size())) != cudaSuccess) return bail(e, "runs");
+    if ((e = cudaMemcpy(g->d_runs, rds.data(), sizeof(RunDev) * rds.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "runs");
+    if ((e = dalloc(&g->d_run_cell_base, base.size())) != cudaSuccess) return bail(e, "run bases");
+    if ((e = cudaMemcpy(g->d_run_cell_base, base.data(), sizeof(long long) * base.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return bail(e, "run bases");
     if ((e = dalloc(&g->d_err, 1)) != cudaSuccess) return bail(e, "error word");
     if ((e = cudaMemset(g->d_err, 0, sizeof(int))) != cudaSuccess) return bail(e, "error word");
     if ((e = dalloc(&g->n_items, 1)) != cudaSuccess) return bail(e, "item count");
@@ -421,7 +453,7 @@ int pic_create_grid(const pic_grid_desc *desc, pic_grid **out)
         if ((long long)b > optin) {
             destroy_grid(g);
             return fail(PIC_ERR_INVALID_ARG, "tile %dx%dx%d with halo %d needs %zu B of shared memory (> %d)",
-                        desc->tile[0], desc->tile[1], desc->tile[2], desc->halo, b, optin);
+                        descs[0].tile[0], descs[0].tile[1], descs[0].tile[2], descs[0].halo, b, optin);
         }
         if ((e = particles_set_smem_limit(g->dims, g->prec, mode, b)) != cudaSuccess) return bail(e, "smem limit");
     }
@@ -429,6 +461,13 @@ int pic_create_grid(const pic_grid_desc *desc, pic_grid **out)
     *out = g;
     return PIC_OK;
 }
+
+int pic_create_grid(const pic_grid_desc *desc, pic_grid **out)
+{
+    return pic_create_batch(desc, 1, out);
+}
+
+int pic_num_runs(pic_grid *g) { return g ? (int)g->runs.size() : 0; }
 
 int pic_destroy(pic_grid *g)
 {
@@ -441,37 +480,70 @@ long long pic_kernel_launches(pic_grid *g) { return g ? g->launches : 0; }
 static cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 static cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
-int pic_set_fields(pic_grid *g, const void *const E[3], const void *const B[3], int on_device)
+static int check_run_index(pic_grid *g, int run)
 {
-    if (!g || !E || !B) return fail(PIC_ERR_INVALID_ARG, "null argument");
-    const size_t bytes = g->total_cells * elem(g);
-    for (int c = 0; c < 3; ++c) {
-        if (!E[c] || !B[c]) return fail(PIC_ERR_INVALID_ARG, "null field component");
-        CK(cudaMemcpyAsync(g->E[c], E[c], bytes, kind_in(on_device), g->stream), "set E");
-        CK(cudaMemcpyAsync(g->B[c], B[c], bytes, kind_in(on_device), g->stream), "set B");
-    }
-    if (!on_device) CK(cudaStreamSynchronize(g->stream), "set fields");
-    g->have_ref = false;
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    if (run < 0 || run >= (int)g->runs.size()) return fail(PIC_ERR_INVALID_ARG, "run %d is not in the batch", run);
     return PIC_OK;
 }
 
-int pic_get_fields(pic_grid *g, void *E[3], void *B[3], void *J[3], int on_device)
+static long long run_cells(const pic_grid *g, int run)
 {
-    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
-    const size_t bytes = g->total_cells * elem(g);
+    const RunDev &r = g->runs[run].dev;
+    return (long long)r.n[0] * r.n[1] * r.n[2];
+}
+
+int pic_set_fields_run(pic_grid *g, int run, const void *const E[3], const void *const B[3], int on_device)
+{
+    int rc = check_run_index(g, run);
+    if (rc != PIC_OK) return rc;
+    if (!E || !B) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    const size_t es = elem(g), bytes = run_cells(g, run) * es, off = g->runs[run].dev.cell_base * es;
     for (int c = 0; c < 3; ++c) {
-        if (E && E[c]) CK(cudaMemcpyAsync(E[c], g->E[c], bytes, kind_out(on_device), g->stream), "get E");
-        if (B && B[c]) CK(cudaMemcpyAsync(B[c], g->B[c], bytes, kind_out(on_device), g->stream), "get B");
-        if (J && J[c]) CK(cudaMemcpyAsync(J[c], g->J[c], bytes, kind_out(on_device), g->stream), "get J");
+        if (!E[c] || !B[c]) return fail(PIC_ERR_INVALID_ARG, "null field component");
+        CK(cudaMemcpyAsync((char *)g->E[c] + off, E[c], bytes, kind_in(on_device), g->stream), "set E");
+        CK(cudaMemcpyAsync((char *)g->B[c] + off, B[c], bytes, kind_in(on_device), g->stream), "set B");
+    }
+    if (!on_device) CK(cudaStreamSynchronize(g->stream), "set fields");
+    g->have_ref[run] = 0;
+    return PIC_OK;
+}
+
+int pic_set_fields(pic_grid *g, const void *const E[3], const void *const B[3], int on_device)
+{
+    return pic_set_fields_run(g, 0, E, B, on_device);
+}
+
+int pic_get_fields_run(pic_grid *g, int run, void *E[3], void *B[3], void *J[3], int on_device)
+{
+    int rc = check_run_index(g, run);
+    if (rc != PIC_OK) return rc;
+    const size_t es = elem(g), bytes = run_cells(g, run) * es, off = g->runs[run].dev.cell_base * es;
+    for (int c = 0; c < 3; ++c) {
+        if (E && E[c]) CK(cudaMemcpyAsync(E[c], (char *)g->E[c] + off, bytes, kind_out(on_device), g->stream), "get E");
+        if (B && B[c]) CK(cudaMemcpyAsync(B[c], (char *)g->B[c] + off, bytes, kind_out(on_device), g->stream), "get B");
+        if (J && J[c]) CK(cudaMemcpyAsync(J[c], (char *)g->J[c] + off, bytes, kind_out(on_device), g->stream), "get J");
     }
     if (!on_device) CK(cudaStreamSynchronize(g->stream), "get fields");
     return PIC_OK;
 }
 
-int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, long long n, const double *const x[3],
-                       const double *const w[3], int on_device)
+int pic_get_fields(pic_grid *g, void *E[3], void *B[3], void *J[3], int on_device)
 {
-    if (!g || !sp) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    return pic_get_fields_run(g, 0, E, B, J, on_device);
+}
+
+static bool group_before(int run_a, int sp_a, int run_b, int sp_b)
+{
+    return run_a < run_b || (run_a == run_b && sp_a < sp_b);
+}
+
+int pic_load_particles_run(pic_grid *g, int run, int species, const pic_species_desc *sp, long long n,
+                           const double *const x[3], const double *const w[3], int on_device)
+{
+    int rc0 = check_run_index(g, run);
+    if (rc0 != PIC_OK) return rc0;
+    if (!sp) return fail(PIC_ERR_INVALID_ARG, "null argument");
     if (species < 0 || species >= kMaxSpecies) return fail(PIC_ERR_INVALID_ARG, "species must be 0..%d", kMaxSpecies - 1);
     if (n < 0 || n > 2000000000LL) return fail(PIC_ERR_INVALID_ARG, "particle count out of range");
     if (!(sp->m > 0.0) || !std::isfinite(sp->q) || !std::isfinite(sp->weight))
@@ -483,6 +555,7 @@ int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, lon
         }
     }
     CK(cudaStreamSynchronize(g->stream), "load: prior work");
+    const RunDev &rn = g->runs[run].dev;
     // stage host arrays in a persistent device buffer (FP64 x and w)
     const double *xs[3] = {nullptr, nullptr, nullptr}, *ws[3] = {nullptr, nullptr, nullptr};
     if (n > 0) {
@@ -510,16 +583,15 @@ int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, lon
             }
         }
     }
-    // same species, same count: convert in place, keep the pool layout
+    // same (run, species), same count: convert in place, keep the pool layout
     for (auto &h : g->groups) {
-        if (h.species != species || h.n != n) continue;
+        if (h.run != run || h.species != species || h.n != n) continue;
         h.q = sp->q;
         h.m = sp->m;
         h.weight = sp->weight;
         int rc = upload_groups(g);
         if (rc != PIC_OK) return rc;
         if (n > 0) {
-            const RunDev &rn = g->runs[0].dev;
             CK(launch_load(g->prec, g->stream, n, xs[0], xs[1], g->dims == 3 ? xs[2] : xs[0], ws[0], ws[1], ws[2],
                            g->dims, rn.n[0], rn.n[1], rn.n[2], g->pool, h.base),
                "particle load");
@@ -527,31 +599,28 @@ int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, lon
         }
         rc = do_sort(g);
         if (rc != PIC_OK) return rc;
-        g->have_ref = false;
+        g->have_ref[run] = 0;
         if (!on_device) CK(cudaStreamSynchronize(g->stream), "load");
         return PIC_OK;
     }
-    // new group layout: every loaded species of run 0, ordered by species index
+    // new group layout: every loaded (run, species), ordered by run then species
     std::vector<HostGroup> old = g->groups;
     std::vector<HostGroup> ng;
+    HostGroup nh{};
+    nh.run = run; nh.species = species; nh.q = sp->q; nh.m = sp->m; nh.weight = sp->weight; nh.n = n;
     bool placed = false;
     for (auto &h : old) {
-        if (h.species == species) continue;
-        if (!placed && h.species > species) {
-            HostGroup nh{};
-            nh.run = 0; nh.species = species; nh.q = sp->q; nh.m = sp->m; nh.weight = sp->weight; nh.n = n;
+        if (h.run == run && h.species == species) continue;
+        if (!placed && group_before(run, species, h.run, h.species)) {
             ng.push_back(nh);
             placed = true;
         }
         ng.push_back(h);
     }
-    if (!placed) {
-        HostGroup nh{};
-        nh.run = 0; nh.species = species; nh.q = sp->q; nh.m = sp->m; nh.weight = sp->weight; nh.n = n;
-        ng.push_back(nh);
-    }
+    if (!placed) ng.push_back(nh);
     long long total = 0;
     for (auto &h : ng) total += h.n;
+    graph_drop(g);
     PoolBuf np, na;
     cudaError_t e = alloc_pool(g, np, total);
     if (e == cudaSuccess) e = alloc_pool(g, na, total);
@@ -560,31 +629,24 @@ int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, lon
         free_pool(na);
         return cuda_fail(e, "particle pool");
     }
-    // copy the other species into their new places
+    // copy the other groups into their new places
     long long pb = 0;
+    long long new_base = 0;
     for (auto &h : ng) {
-        if (h.species != species) {
+        if (h.run == run && h.species == species) {
+            new_base = pb;
+        } else {
             for (auto &o : old)
-                if (o.species == h.species) {
+                if (o.run == h.run && o.species == h.species && o.n > 0) {
                     e = launch_copy_pool(g->prec, g->stream, g->pool, o.base, np, pb, o.n);
-                    launch_count_add(g, o.n > 0);
+                    launch_count_add(g, 1);
                 }
             if (e != cudaSuccess) break;
         }
         h.base = pb;
         pb += h.n;
     }
-    if (e != cudaSuccess) {
-        free_pool(np);
-        free_pool(na);
-        return cuda_fail(e, "pool copy");
-    }
-    // convert the new species in
-    long long new_base = 0;
-    for (auto &h : ng)
-        if (h.species == species) new_base = h.base;
-    if (n > 0) {
-        const RunDev &rn = g->runs[0].dev;
+    if (e == cudaSuccess && n > 0) {
         e = launch_load(g->prec, g->stream, n, xs[0], xs[1], g->dims == 3 ? xs[2] : xs[0], ws[0], ws[1], ws[2],
                         g->dims, rn.n[0], rn.n[1], rn.n[2], np, new_base);
         launch_count_add(g, 1);
@@ -607,26 +669,36 @@ int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, lon
     if (rc != PIC_OK) return rc;
     rc = do_sort(g);
     if (rc != PIC_OK) return rc;
-    g->have_ref = false;
+    g->have_ref[run] = 0;
     CK(cudaStreamSynchronize(g->stream), "load: sort");
     return PIC_OK;
 }
 
-long long pic_num_particles(pic_grid *g, int species)
+int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, long long n, const double *const x[3],
+                       const double *const w[3], int on_device)
+{
+    return pic_load_particles_run(g, 0, species, sp, n, x, w, on_device);
+}
+
+long long pic_num_particles_run(pic_grid *g, int run, int species)
 {
     if (!g) return 0;
     for (auto &h : g->groups)
-        if (h.species == species) return h.n;
+        if (h.run == run && h.species == species) return h.n;
     return 0;
 }
 
-int pic_get_particles(pic_grid *g, int species, int *cell, void *offset[3], void *w[3], int *id, int on_device)
+long long pic_num_particles(pic_grid *g, int species) { return pic_num_particles_run(g, 0, species); }
+
+int pic_get_particles_run(pic_grid *g, int run, int species, int *cell, void *offset[3], void *w[3], int *id,
+                          int on_device)
 {
-    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    int rc = check_run_index(g, run);
+    if (rc != PIC_OK) return rc;
     const HostGroup *h = nullptr;
     for (auto &q : g->groups)
-        if (q.species == species) h = &q;
-    if (!h) return fail(PIC_ERR_INVALID_ARG, "species %d is not loaded", species);
+        if (q.run == run && q.species == species) h = &q;
+    if (!h) return fail(PIC_ERR_INVALID_ARG, "species %d of run %d is not loaded", species, run);
     if (h->n == 0) return PIC_OK;
     const cudaMemcpyKind k = kind_out(on_device);
     const size_t es = elem(g);
@@ -639,6 +711,11 @@ int pic_get_particles(pic_grid *g, int species, int *cell, void *offset[3], void
     }
     if (!on_device) CK(cudaStreamSynchronize(g->stream), "get particles");
     return PIC_OK;
+}
+
+int pic_get_particles(pic_grid *g, int species, int *cell, void *offset[3], void *w[3], int *id, int on_device)
+{
+    return pic_get_particles_run(g, 0, species, cell, offset, w, id, on_device);
 }
 
 int pic_gather_push(pic_grid *g)
@@ -689,6 +766,103 @@ int pic_step(pic_grid *g, int nsteps)
     return PIC_OK;
 }
 
+// One step of every run in one cooperative launch (plus the sort launches
+// every sort_interval steps).
+static int persistent_step(pic_grid *g)
+{
+    int rc;
+    if (g->steps_since_sort >= g->sort_interval && (rc = do_sort(g)) != PIC_OK) return rc;
+    ProfScope ps(g, PIC_PROF_PARTICLES);
+    cudaError_t e = launch_step_persistent(g->dims, g->prec, g->stream, g->items, g->n_items, g->d_runs, g->d_groups,
+                                           g->pool, g->E, g->B, g->J, g->halo, g->tile[0], g->tile[1], g->tile[2],
+                                           g->d_err, (int)g->runs.size(), g->d_run_cell_base, &g->persist_blocks, 1);
+    launch_count_add(g, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent step");
+    g->steps_since_sort += 1;
+    g->have_old = false;
+    return PIC_OK;
+}
+
+int pic_step_persistent(pic_grid *g, int nsteps)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    if (nsteps < 0) return fail(PIC_ERR_INVALID_ARG, "negative step count");
+    if (g->total == 0) return pic_step(g, nsteps);
+    for (int s = 0; s < nsteps; ++s) {
+        int rc = persistent_step(g);
+        if (rc != PIC_OK) return rc;
+    }
+    return PIC_OK;
+}
+
+// Captures 2 * sort_interval persistent steps, starting with a sort, into a
+// CUDA graph.  Two sorts bring the double-buffered pool back to the buffer it
+// started in, so the graph can be replayed as often as needed.
+static int capture_graph(pic_grid *g)
+{
+    graph_drop(g);
+    if (g->persist_blocks <= 0) {
+        cudaError_t ep = launch_step_persistent(g->dims, g->prec, g->stream, g->items, g->n_items, g->d_runs,
+                                                g->d_groups, g->pool, g->E, g->B, g->J, g->halo, g->tile[0],
+                                                g->tile[1], g->tile[2], g->d_err, (int)g->runs.size(),
+                                                g->d_run_cell_base, &g->persist_blocks, 0);
+        if (ep != cudaSuccess) return cuda_fail(ep, "persistent kernel set-up");
+    }
+    const bool prof = g->profiling;
+    g->profiling = false;
+    g->capturing = true;
+    const long long l0 = g->launches;
+    cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+    int rc = PIC_OK;
+    if (e == cudaSuccess) {
+        for (int s = 0; s < 2 * g->sort_interval && rc == PIC_OK; ++s) rc = persistent_step(g);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+        if (rc == PIC_OK && e2 == cudaSuccess) {
+            e = cudaGraphInstantiate(&g->graph_exec, graph, 0);
+            if (e == cudaSuccess) g->graph_valid = true;
+        } else if (e2 != cudaSuccess) {
+            e = e2;
+        }
+        if (graph) cudaGraphDestroy(graph);
+    }
+    g->graph_launches = g->launches - l0;
+    g->launches = l0;
+    g->profiling = prof;
+    g->capturing = false;
+    if (rc != PIC_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    return PIC_OK;
+}
+
+int pic_step_graph(pic_grid *g, int nsteps)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    if (nsteps < 0) return fail(PIC_ERR_INVALID_ARG, "negative step count");
+    if (!g->stream) return fail(PIC_ERR_INVALID_ARG, "graph replay needs a non-default stream");
+    if (g->total == 0) return pic_step(g, nsteps);
+    const int span = 2 * g->sort_interval;
+    while (nsteps > 0) {
+        if (g->steps_since_sort >= g->sort_interval && nsteps >= span) {
+            if (!g->graph_valid) {
+                const long long since = g->steps_since_sort;
+                int rc = capture_graph(g);
+                if (rc != PIC_OK) return rc;
+                if (g->steps_since_sort != since) return fail(PIC_ERR_STATE, "graph capture changed the sort phase");
+            }
+            ProfScope ps(g, PIC_PROF_PARTICLES);
+            CK(cudaGraphLaunch(g->graph_exec, g->stream), "graph launch");
+            g->launches += g->graph_launches;
+            nsteps -= span;
+            continue;
+        }
+        int rc = persistent_step(g);
+        if (rc != PIC_OK) return rc;
+        nsteps -= 1;
+    }
+    return PIC_OK;
+}
+
 int pic_profile(pic_grid *g, int enable)
 {
     if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
@@ -724,16 +898,18 @@ int pic_sync(pic_grid *g)
     return PIC_OK;
 }
 
-int pic_diagnostics(pic_grid *g, pic_diag *out)
+int pic_diagnostics_run(pic_grid *g, int run, pic_diag *out)
 {
-    if (!g || !out) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    int rc = check_run_index(g, run);
+    if (rc != PIC_OK) return rc;
+    if (!out) return fail(PIC_ERR_INVALID_ARG, "null argument");
     memset(out, 0, sizeof(*out));
     int nl = 0;
-    const RunDev &rn = g->runs[0].dev;
-    cudaError_t e = launch_diagnostics_run(g->dims, g->prec, g->stream, g->d_runs, 0,
+    const RunDev &rn = g->runs[run].dev;
+    cudaError_t e = launch_diagnostics_run(g->dims, g->prec, g->stream, g->d_runs, run,
                                            (long long)rn.n[0] * rn.n[1] * rn.n[2], rn.cell_base, g->d_groups,
                                            g->d_group_base, (int)g->groups.size(), g->total, g->pool, g->E, g->B,
-                                           g->diag, g->have_ref ? 0 : 1, kDiagBlocks, kDiagBlocks, &nl);
+                                           g->diag, g->have_ref[run] ? 0 : 1, kDiagBlocks, kDiagBlocks, &nl);
     launch_count_add(g, nl);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
     double r[kDiagResults];
@@ -741,7 +917,7 @@ int pic_diagnostics(pic_grid *g, pic_diag *out)
     int err = 0;
     CK(cudaMemcpyAsync(&err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream), "error word");
     CK(cudaStreamSynchronize(g->stream), "diagnostics");
-    g->have_ref = true;
+    g->have_ref[run] = 1;
     out->kinetic = r[0];
     out->field_E = r[1];
     out->field_B = r[2];
@@ -758,5 +934,7 @@ int pic_diagnostics(pic_grid *g, pic_diag *out)
     if (err & ERR_NONFINITE) return fail(PIC_ERR_NONFINITE, "a particle momentum became non-finite");
     return PIC_OK;
 }
+
+int pic_diagnostics(pic_grid *g, pic_diag *out) { return pic_diagnostics_run(g, 0, out); }
 
 }  // extern "C"

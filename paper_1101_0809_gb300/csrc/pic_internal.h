@@ -44,6 +44,13 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
                              int *old_cell, void *const old_off[3], int halo, int max_tile_x,
                              int max_tile_y, int max_tile_z, int *err);
 size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo);
+// One cooperative launch per step over every run (see k_step_persistent);
+// *grid_blocks = 0 asks for the occupancy-derived grid and returns it; launch = 0
+// only prepares (attributes and grid size), which must happen outside a capture.
+cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const WorkItem *items, const int *n_items,
+                                   const RunDev *runs, const GroupDev *groups, const PoolBuf &P, void *const E[3],
+                                   void *const B[3], void *const J[3], int halo, int tx, int ty, int tz, int *err,
+                                   int nruns, const long long *run_cell_base, int *grid_blocks, int launch);
 cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes);
 
 cudaError_t launch_load(int prec, cudaStream_t st, long long n, const double *x0, const double *x1,
@@ -137,9 +144,19 @@ struct pic_grid {
     int max_items = 0;
     int steps_since_sort = 0;
 
-    // diagnostics
+    // diagnostics (residual reference per run)
     pic::DiagScratch diag;
-    bool have_ref = false;
+    std::vector<char> have_ref;
+
+    // batches: first cell of every run, nruns + 1 entries on the device
+    long long *d_run_cell_base = nullptr;
+
+    // one-launch-per-step persistent kernel and its CUDA graph (2 sort intervals of steps)
+    int persist_blocks = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool graph_valid = false;
+    bool capturing = false;
+    long long graph_launches = 0;
 
     int *d_err = nullptr;
     long long launches = 0;

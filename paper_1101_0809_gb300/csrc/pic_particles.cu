@@ -12,7 +12,11 @@
 // more than `halo` cells outside the tile since the last sort takes the same
 // arithmetic on the global arrays instead (periodic indices, global atomics).
 // At the end the block adds its current tile to the global J with atomics.
+#include <cooperative_groups.h>
+
 #include "pic_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace pic {
 
@@ -84,11 +88,10 @@ __device__ __noinline__ void deposit_global(const Fields<R> &F, long long cb, in
 // tile for MODES 0, 2: in FP32 two int32 fixed-point words per value, in FP64
 // one double -- 24 * nj bytes either way.
 template <int DIM, typename R, int MODE>
-__global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
+__device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
 {
     constexpr bool FIX = sizeof(R) == 4;
-    if ((int)blockIdx.x >= *a.n_items) return;
-    const WorkItem it = a.items[blockIdx.x];
+    const WorkItem it = a.items[item];
     const GroupDev gr = a.groups[it.group];
     const RunDev rn = a.runs[gr.run];
     const int G = a.halo;
@@ -298,6 +301,56 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
             }
         }
     }
+    __syncthreads();   // the shared tiles are free for the block's next item
+}
+
+template <int DIM, typename R, int MODE>
+__global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
+{
+    if ((int)blockIdx.x >= *a.n_items) return;
+    process_item<DIM, R, MODE>(a, blockIdx.x);
+}
+
+// Run of a batch that owns concatenated cell l (run_cell_base has nruns + 1 entries).
+__device__ __forceinline__ int find_run(const long long *run_cell_base, int nruns, long long l)
+{
+    int lo = 0, hi = nruns;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (run_cell_base[mid] <= l) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// One whole step of every run of a batch in one cooperative launch: B half
+// step (+ J clear) over all cells, grid barrier, the fused particle work items,
+// grid barrier, B half step, grid barrier, E full step.  The grid is sized so
+// that all blocks are resident (cooperative launch), which the barriers need.
+template <int DIM, typename R>
+__global__ void __launch_bounds__(kThreads) k_step_persistent(const PartArgs<R> a, int nruns,
+                                                              const long long *run_cell_base)
+{
+    cg::grid_group grid = cg::this_grid();
+    const long long total = run_cell_base[nruns];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long l = t0; l < total; l += stride) {
+        const int r = find_run(run_cell_base, nruns, l);
+        yee_b_half_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r], 1);
+    }
+    grid.sync();
+    const int ni = *a.n_items;
+    for (int it = blockIdx.x; it < ni; it += gridDim.x) process_item<DIM, R, 0>(a, it);
+    grid.sync();
+    for (long long l = t0; l < total; l += stride) {
+        const int r = find_run(run_cell_base, nruns, l);
+        yee_b_half_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r], 0);
+    }
+    grid.sync();
+    for (long long l = t0; l < total; l += stride) {
+        const int r = find_run(run_cell_base, nruns, l);
+        yee_e_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r]);
+    }
 }
 
 template <int DIM, typename R, int MODE>
@@ -387,6 +440,46 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
     auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
     return dims == 3 ? launch_mode<3, float>(mode, st, max_items, smem, a)
                      : launch_mode<2, float>(mode, st, max_items, smem, a);
+}
+
+template <int DIM, typename R>
+static cudaError_t persistent_t(cudaStream_t st, size_t smem, int nruns, const long long *run_cell_base,
+                                PartArgs<R> a, int *grid_blocks, int launch)
+{
+    auto fn = k_step_persistent<DIM, R>;
+    cudaError_t e;
+    if (*grid_blocks <= 0) {
+        // first use (outside any stream capture): shared-memory limit and grid size
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (per <= 0) return cudaErrorInvalidConfiguration;
+        *grid_blocks = sms * per;
+    }
+    if (!launch) return cudaSuccess;
+    void *args[] = {(void *)&a, (void *)&nruns, (void *)&run_cell_base};
+    return cudaLaunchCooperativeKernel((const void *)fn, dim3(*grid_blocks), dim3(kThreads), args, smem, st);
+}
+
+cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const WorkItem *items, const int *n_items,
+                                   const RunDev *runs, const GroupDev *groups, const PoolBuf &P, void *const E[3],
+                                   void *const B[3], void *const J[3], int halo, int tx, int ty, int tz, int *err,
+                                   int nruns, const long long *run_cell_base, int *grid_blocks, int launch)
+{
+    void *none[3] = {nullptr, nullptr, nullptr};
+    const size_t smem = particles_smem_bytes(dims, prec, 0, tx, ty, tz, halo);
+    if (prec == 0) {
+        auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, nullptr, none, halo, err);
+        return dims == 3 ? persistent_t<3, double>(st, smem, nruns, run_cell_base, a, grid_blocks, launch)
+                         : persistent_t<2, double>(st, smem, nruns, run_cell_base, a, grid_blocks, launch);
+    }
+    auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, nullptr, none, halo, err);
+    return dims == 3 ? persistent_t<3, float>(st, smem, nruns, run_cell_base, a, grid_blocks, launch)
+                     : persistent_t<2, float>(st, smem, nruns, run_cell_base, a, grid_blocks, launch);
 }
 
 // ---------------------------------------------------------------------------

@@ -213,6 +213,92 @@ def pic_profile_read(g):
     return {names[i]: (ms[i], cnt[i]) for i in range(PIC_PROF_N)}
 
 
+_lib.pic_create_batch.argtypes = [C.POINTER(pic_grid_desc), C.c_int, C.POINTER(_VP)]
+_lib.pic_num_runs.argtypes = [_VP]
+_lib.pic_set_fields_run.argtypes = [_VP, C.c_int, _VP3, _VP3, C.c_int]
+_lib.pic_get_fields_run.argtypes = [_VP, C.c_int, _VP3, _VP3, _VP3, C.c_int]
+_lib.pic_load_particles_run.argtypes = [_VP, C.c_int, C.c_int, C.POINTER(pic_species_desc), C.c_longlong,
+                                        _VP3, _VP3, C.c_int]
+_lib.pic_num_particles_run.argtypes = [_VP, C.c_int, C.c_int]
+_lib.pic_num_particles_run.restype = C.c_longlong
+_lib.pic_get_particles_run.argtypes = [_VP, C.c_int, C.c_int, _VP, _VP3, _VP3, _VP, C.c_int]
+_lib.pic_diagnostics_run.argtypes = [_VP, C.c_int, C.POINTER(pic_diag)]
+_lib.pic_step_persistent.argtypes = [_VP, C.c_int]
+_lib.pic_step_graph.argtypes = [_VP, C.c_int]
+
+
+def pic_create_batch(descs):
+    arr = (pic_grid_desc * len(descs))(*descs)
+    h = _VP()
+    _check(_lib.pic_create_batch(arr, len(descs), C.byref(h)))
+    return h
+
+
+def pic_num_runs(g):
+    return int(_lib.pic_num_runs(g))
+
+
+def pic_set_fields_run(g, run, E, B):
+    e, de = _triple(E)
+    b, db = _triple(B)
+    if de != db:
+        raise ValueError("E and B must both be host or both be device arrays")
+    _check(_lib.pic_set_fields_run(g, run, e, b, de))
+
+
+def pic_get_fields_run(g, run, E=None, B=None, J=None):
+    e, de = _triple(E or [None] * 3)
+    b, db = _triple(B or [None] * 3)
+    j, dj = _triple(J or [None] * 3)
+    devs = {d for d, arr in ((de, E), (db, B), (dj, J)) if arr is not None}
+    if len(devs) > 1:
+        raise ValueError("mixing host and device arrays in one call")
+    _check(_lib.pic_get_fields_run(g, run, e, b, j, devs.pop() if devs else 0))
+
+
+def pic_load_particles_run(g, run, species, q, m, weight, x, w):
+    n = int(len(w[0]))
+    sp = pic_species_desc(q, m, weight)
+    xs, dx = _triple([x[0], x[1], x[2]])
+    ws, dw = _triple([w[0], w[1], w[2]])
+    if dx != dw:
+        raise ValueError("x and w must both be host or both be device arrays")
+    _check(_lib.pic_load_particles_run(g, run, species, C.byref(sp), n, xs, ws, dx))
+
+
+def pic_num_particles_run(g, run, species):
+    return int(_lib.pic_num_particles_run(g, run, species))
+
+
+def pic_get_particles_run(g, run, species, cell=None, offset=None, w=None, ident=None):
+    pc, d1 = _addr(cell)
+    pi, d2 = _addr(ident)
+    o, d3 = _triple(offset or [None] * 3)
+    ww, d4 = _triple(w or [None] * 3)
+    devs = {d for d, arr in ((d1, cell), (d2, ident), (d3, offset), (d4, w)) if arr is not None}
+    if len(devs) > 1:
+        raise ValueError("mixing host and device arrays in one call")
+    _check(_lib.pic_get_particles_run(g, run, species, pc, o, ww, pi, devs.pop() if devs else 0))
+
+
+def pic_diagnostics_run(g, run):
+    d = pic_diag()
+    _check(_lib.pic_diagnostics_run(g, run, C.byref(d)))
+    out = {k: getattr(d, k) for k in ("kinetic", "field_E", "field_B", "half_step_corr", "total",
+                                       "total_charge", "gauss_resid_max", "gauss_resid_rms",
+                                       "n_particles", "error_word")}
+    out["momentum"] = np.array(d.momentum[:])
+    return out
+
+
+def pic_step_persistent(g, nsteps=1):
+    _check(_lib.pic_step_persistent(g, nsteps))
+
+
+def pic_step_graph(g, nsteps=1):
+    _check(_lib.pic_step_graph(g, nsteps))
+
+
 PIC_NOALLOC_MAX_PARTICLES = 1048576
 _lib.pic_tile_sort_perm_noalloc.argtypes = [_VP, C.c_longlong, C.c_int, C.c_int * 3, C.c_int * 3, _VP, _VP, _VP]
 
@@ -275,6 +361,18 @@ class Grid:
         w = [np.ascontiguousarray(w[a], dtype=np.float64) for a in range(3)]
         pic_load_particles(self.h, species, q, m, weight, x, w)
 
+    def particles_run(self, run, species):
+        n = pic_num_particles_run(self.h, run, species)
+        cell = np.empty(n, np.int32)
+        ident = np.empty(n, np.int32)
+        off = [np.empty(n, self.dtype) for _ in range(3)]
+        w = [np.empty(n, self.dtype) for _ in range(3)]
+        if self.dims == 2:
+            off[2][:] = 0
+        pic_get_particles_run(self.h, run, species, cell, off if self.dims == 3 else [off[0], off[1], None], w,
+                              ident)
+        return cell, off, w, ident
+
     def particles(self, species):
         n = pic_num_particles(self.h, species)
         cell = np.empty(n, np.int32)
@@ -285,3 +383,34 @@ class Grid:
             off[2][:] = 0
         pic_get_particles(self.h, species, cell, off if self.dims == 3 else [off[0], off[1], None], w, ident)
         return cell, off, w, ident
+
+
+class Batch(Grid):
+    """Owning handle around pic_create_batch: several independent runs."""
+
+    def __init__(self, descs):
+        self.descs = list(descs)
+        self.desc = self.descs[0]
+        self.h = pic_create_batch(self.descs)
+        self.dims = self.desc.dims
+        self.precision = self.desc.precision
+        self.dtype = np.float64 if self.desc.precision == PIC_FP64 else np.float32
+        self.shape = (self.desc.nz if self.desc.dims == 3 else 1, self.desc.ny, self.desc.nx)
+
+    def run_shape(self, run):
+        d = self.descs[run]
+        return (d.nz if d.dims == 3 else 1, d.ny, d.nx)
+
+    def load_run(self, run, species, q, m, weight, x, w):
+        x = [np.ascontiguousarray(x[a], dtype=np.float64) for a in range(3)]
+        w = [np.ascontiguousarray(w[a], dtype=np.float64) for a in range(3)]
+        pic_load_particles_run(self.h, run, species, q, m, weight, x, w)
+
+    def get_fields_run(self, run):
+        shp = self.run_shape(run)
+        E = [np.empty(shp, self.dtype) for _ in range(3)]
+        B = [np.empty(shp, self.dtype) for _ in range(3)]
+        J = [np.empty(shp, self.dtype) for _ in range(3)]
+        pic_get_fields_run(self.h, run, E, B, J)
+        return E, B, J
+

@@ -29,6 +29,23 @@ def close(a, b, tol, what=""):
                              f"got {a.ravel()[k]!r}, want {b.ravel()[k]!r}, rel {err.ravel()[k] / (scale.ravel()[k] + 1e-300):.3e}")
 
 
+def fp64_field_tol(wl, species, tol=FP64_TOL):
+    """FP64 tolerance for J and E.  The oracle keeps absolute positions, so a
+    displacement delta carries its rounding ulp(N); currents are proportional to
+    displacements.  The bound is therefore max(tol, 4 ulp(N_max) / delta_rms),
+    which exceeds 1e-12 only for very slow plasmas (v_th ~ 0.01c)."""
+    n_max = float(max(wl.n[:wl.dims]))
+    d2, cnt = 0.0, 0
+    for sp in species:
+        gam = np.sqrt((sp.w ** 2).sum(axis=0) + wl.c ** 2)
+        for a in range(wl.dims):
+            d = sp.w[a] / gam * (wl.c * wl.dt / wl.d[a])
+            d2 += float((d * d).sum())
+            cnt += d.size
+    delta = math.sqrt(d2 / max(cnt, 1))
+    return max(tol, 4 * float(np.spacing(n_max)) / max(delta, 1e-300))
+
+
 def oracle_grid(wl):
     return O.Grid(wl.dims, wl.n, wl.d, wl.dt, wl.c)
 
