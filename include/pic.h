@@ -191,6 +191,11 @@ int pic_set_fields_run(pic_grid *g, int run, const void *const E[3], const void 
 int pic_get_fields_run(pic_grid *g, int run, void *E[3], void *B[3], void *J[3], int on_device);
 int pic_load_particles_run(pic_grid *g, int run, int species, const pic_species_desc *sp, long long n,
                            const double *const x[3], const double *const w[3], int on_device);
+/* Bulk form of pic_load_particles_run for one species index over `count` runs
+ * with a single pool re-layout and sort: runs[r], sp[r], n[r], and the arrays
+ * x[3*r + a], w[3*r + a] (a = 0, 1, 2) for entry r. */
+int pic_load_particles_runs(pic_grid *g, int count, const int *runs, int species, const pic_species_desc *sp,
+                            const long long *n, const double *const *x, const double *const *w, int on_device);
 long long pic_num_particles_run(pic_grid *g, int run, int species);
 int pic_get_particles_run(pic_grid *g, int run, int species, int *cell, void *offset[3], void *w[3], int *id,
                           int on_device);

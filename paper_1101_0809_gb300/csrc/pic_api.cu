@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <array>
 #include <new>
 
 #include "../../include/pic.h"
@@ -538,86 +539,125 @@ static bool group_before(int run_a, int sp_a, int run_b, int sp_b)
     return run_a < run_b || (run_a == run_b && sp_a < sp_b);
 }
 
-int pic_load_particles_run(pic_grid *g, int run, int species, const pic_species_desc *sp, long long n,
-                           const double *const x[3], const double *const w[3], int on_device)
+struct LoadReq {
+    int run, species;
+    pic_species_desc sp;
+    long long n;
+    const double *x[3];
+    const double *w[3];
+};
+
+// Loads (replaces) several (run, species) groups with one pool re-layout and
+// one sort.  Host arrays are staged in one device buffer first.
+static int load_many(pic_grid *g, std::vector<LoadReq> &reqs, int on_device)
 {
-    int rc0 = check_run_index(g, run);
-    if (rc0 != PIC_OK) return rc0;
-    if (!sp) return fail(PIC_ERR_INVALID_ARG, "null argument");
-    if (species < 0 || species >= kMaxSpecies) return fail(PIC_ERR_INVALID_ARG, "species must be 0..%d", kMaxSpecies - 1);
-    if (n < 0 || n > 2000000000LL) return fail(PIC_ERR_INVALID_ARG, "particle count out of range");
-    if (!(sp->m > 0.0) || !std::isfinite(sp->q) || !std::isfinite(sp->weight))
-        return fail(PIC_ERR_INVALID_ARG, "species needs m > 0 and finite q, weight");
-    if (n > 0) {
-        if (!x || !w) return fail(PIC_ERR_INVALID_ARG, "null particle arrays");
-        for (int a = 0; a < 3; ++a) {
-            if ((a < g->dims && !x[a]) || !w[a]) return fail(PIC_ERR_INVALID_ARG, "null particle component");
-        }
+    for (auto &q : reqs) {
+        int rc0 = check_run_index(g, q.run);
+        if (rc0 != PIC_OK) return rc0;
+        if (q.species < 0 || q.species >= kMaxSpecies)
+            return fail(PIC_ERR_INVALID_ARG, "species must be 0..%d", kMaxSpecies - 1);
+        if (q.n < 0 || q.n > 2000000000LL) return fail(PIC_ERR_INVALID_ARG, "particle count out of range");
+        if (!(q.sp.m > 0.0) || !std::isfinite(q.sp.q) || !std::isfinite(q.sp.weight))
+            return fail(PIC_ERR_INVALID_ARG, "species needs m > 0 and finite q, weight");
+        if (q.n > 0)
+            for (int a = 0; a < 3; ++a)
+                if ((a < g->dims && !q.x[a]) || !q.w[a]) return fail(PIC_ERR_INVALID_ARG, "null particle component");
+        for (auto &o : reqs)
+            if (&o != &q && o.run == q.run && o.species == q.species)
+                return fail(PIC_ERR_INVALID_ARG, "species %d of run %d appears twice", q.species, q.run);
     }
     CK(cudaStreamSynchronize(g->stream), "load: prior work");
-    const RunDev &rn = g->runs[run].dev;
-    // stage host arrays in a persistent device buffer (FP64 x and w)
-    const double *xs[3] = {nullptr, nullptr, nullptr}, *ws[3] = {nullptr, nullptr, nullptr};
-    if (n > 0) {
-        if (on_device) {
-            for (int a = 0; a < 3; ++a) {
-                xs[a] = a < g->dims ? x[a] : nullptr;
-                ws[a] = w[a];
-            }
-        } else {
-            if (g->stage_n < 6 * n) {
-                dfree(g->stage);
-                g->stage = nullptr;
-                g->stage_n = 0;
-                CK(dalloc(&g->stage, (size_t)(6 * n)), "load staging");
-                g->stage_n = 6 * n;
-            }
-            for (int a = 0; a < 3; ++a) {
+    // device pointers of every request's x and w (staged if on the host)
+    std::vector<std::array<const double *, 6>> src(reqs.size());
+    long long need = 0;
+    for (auto &q : reqs) need += 6 * q.n;
+    if (!on_device && g->stage_n < need) {
+        dfree(g->stage);
+        g->stage = nullptr;
+        g->stage_n = 0;
+        CK(dalloc(&g->stage, (size_t)need), "load staging");
+        g->stage_n = need;
+    }
+    long long so = 0;
+    for (size_t r = 0; r < reqs.size(); ++r) {
+        const LoadReq &q = reqs[r];
+        for (int a = 0; a < 3; ++a) {
+            src[r][a] = nullptr;
+            src[r][3 + a] = nullptr;
+        }
+        if (q.n == 0) continue;
+        for (int a = 0; a < 3; ++a) {
+            if (on_device) {
+                src[r][a] = a < g->dims ? q.x[a] : q.x[0];
+                src[r][3 + a] = q.w[a];
+            } else {
                 if (a < g->dims)
-                    CK(cudaMemcpyAsync(g->stage + a * n, x[a], sizeof(double) * n, cudaMemcpyHostToDevice, g->stream),
+                    CK(cudaMemcpyAsync(g->stage + so + a * q.n, q.x[a], sizeof(double) * q.n, cudaMemcpyHostToDevice,
+                                       g->stream),
                        "stage x");
-                CK(cudaMemcpyAsync(g->stage + (3 + a) * n, w[a], sizeof(double) * n, cudaMemcpyHostToDevice, g->stream),
+                CK(cudaMemcpyAsync(g->stage + so + (3 + a) * q.n, q.w[a], sizeof(double) * q.n,
+                                   cudaMemcpyHostToDevice, g->stream),
                    "stage w");
-                xs[a] = g->stage + a * n;
-                ws[a] = g->stage + (3 + a) * n;
+                src[r][a] = g->stage + so + (a < g->dims ? a : 0) * q.n;
+                src[r][3 + a] = g->stage + so + (3 + a) * q.n;
             }
         }
+        so += 6 * q.n;
     }
-    // same (run, species), same count: convert in place, keep the pool layout
-    for (auto &h : g->groups) {
-        if (h.run != run || h.species != species || h.n != n) continue;
-        h.q = sp->q;
-        h.m = sp->m;
-        h.weight = sp->weight;
+    auto convert = [&](size_t r, const PoolBuf &P, long long base) -> cudaError_t {
+        const LoadReq &q = reqs[r];
+        if (q.n == 0) return cudaSuccess;
+        const RunDev &rn = g->runs[q.run].dev;
+        launch_count_add(g, 1);
+        return launch_load(g->prec, g->stream, q.n, src[r][0], src[r][1], src[r][2], src[r][3], src[r][4], src[r][5],
+                           g->dims, rn.n[0], rn.n[1], rn.n[2], P, base);
+    };
+    // every request matches a loaded group of the same size: convert in place
+    bool in_place = true;
+    std::vector<HostGroup *> match(reqs.size(), nullptr);
+    for (size_t r = 0; r < reqs.size(); ++r) {
+        for (auto &h : g->groups)
+            if (h.run == reqs[r].run && h.species == reqs[r].species && h.n == reqs[r].n) match[r] = &h;
+        if (!match[r]) in_place = false;
+    }
+    if (in_place) {
+        for (size_t r = 0; r < reqs.size(); ++r) {
+            match[r]->q = reqs[r].sp.q;
+            match[r]->m = reqs[r].sp.m;
+            match[r]->weight = reqs[r].sp.weight;
+        }
         int rc = upload_groups(g);
         if (rc != PIC_OK) return rc;
-        if (n > 0) {
-            CK(launch_load(g->prec, g->stream, n, xs[0], xs[1], g->dims == 3 ? xs[2] : xs[0], ws[0], ws[1], ws[2],
-                           g->dims, rn.n[0], rn.n[1], rn.n[2], g->pool, h.base),
-               "particle load");
-            launch_count_add(g, 1);
-        }
+        for (size_t r = 0; r < reqs.size(); ++r) CK(convert(r, g->pool, match[r]->base), "particle load");
         rc = do_sort(g);
         if (rc != PIC_OK) return rc;
-        g->have_ref[run] = 0;
+        for (auto &q : reqs) g->have_ref[q.run] = 0;
         if (!on_device) CK(cudaStreamSynchronize(g->stream), "load");
         return PIC_OK;
     }
-    // new group layout: every loaded (run, species), ordered by run then species
+    // new layout: all (run, species) groups ordered by run then species
     std::vector<HostGroup> old = g->groups;
     std::vector<HostGroup> ng;
-    HostGroup nh{};
-    nh.run = run; nh.species = species; nh.q = sp->q; nh.m = sp->m; nh.weight = sp->weight; nh.n = n;
-    bool placed = false;
     for (auto &h : old) {
-        if (h.run == run && h.species == species) continue;
-        if (!placed && group_before(run, species, h.run, h.species)) {
-            ng.push_back(nh);
-            placed = true;
-        }
-        ng.push_back(h);
+        bool replaced = false;
+        for (auto &q : reqs)
+            if (q.run == h.run && q.species == h.species) replaced = true;
+        if (!replaced) ng.push_back(h);
     }
-    if (!placed) ng.push_back(nh);
+    for (auto &q : reqs) {
+        HostGroup nh{};
+        nh.run = q.run;
+        nh.species = q.species;
+        nh.q = q.sp.q;
+        nh.m = q.sp.m;
+        nh.weight = q.sp.weight;
+        nh.n = q.n;
+        nh.base = -1;   // marks a new group
+        ng.push_back(nh);
+    }
+    std::stable_sort(ng.begin(), ng.end(), [](const HostGroup &x, const HostGroup &y) {
+        return group_before(x.run, x.species, y.run, y.species);
+    });
     long long total = 0;
     for (auto &h : ng) total += h.n;
     graph_drop(g);
@@ -629,27 +669,20 @@ int pic_load_particles_run(pic_grid *g, int run, int species, const pic_species_
         free_pool(na);
         return cuda_fail(e, "particle pool");
     }
-    // copy the other groups into their new places
     long long pb = 0;
-    long long new_base = 0;
     for (auto &h : ng) {
-        if (h.run == run && h.species == species) {
-            new_base = pb;
+        if (e != cudaSuccess) break;
+        if (h.base >= 0) {   // an old group keeps its data
+            if (h.n > 0) {
+                e = launch_copy_pool(g->prec, g->stream, g->pool, h.base, np, pb, h.n);
+                launch_count_add(g, 1);
+            }
         } else {
-            for (auto &o : old)
-                if (o.run == h.run && o.species == h.species && o.n > 0) {
-                    e = launch_copy_pool(g->prec, g->stream, g->pool, o.base, np, pb, o.n);
-                    launch_count_add(g, 1);
-                }
-            if (e != cudaSuccess) break;
+            for (size_t r = 0; r < reqs.size(); ++r)
+                if (reqs[r].run == h.run && reqs[r].species == h.species) e = convert(r, np, pb);
         }
         h.base = pb;
         pb += h.n;
-    }
-    if (e == cudaSuccess && n > 0) {
-        e = launch_load(g->prec, g->stream, n, xs[0], xs[1], g->dims == 3 ? xs[2] : xs[0], ws[0], ws[1], ws[2],
-                        g->dims, rn.n[0], rn.n[1], rn.n[2], np, new_base);
-        launch_count_add(g, 1);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) {
@@ -669,9 +702,45 @@ int pic_load_particles_run(pic_grid *g, int run, int species, const pic_species_
     if (rc != PIC_OK) return rc;
     rc = do_sort(g);
     if (rc != PIC_OK) return rc;
-    g->have_ref[run] = 0;
+    for (auto &q : reqs) g->have_ref[q.run] = 0;
     CK(cudaStreamSynchronize(g->stream), "load: sort");
     return PIC_OK;
+}
+
+int pic_load_particles_run(pic_grid *g, int run, int species, const pic_species_desc *sp, long long n,
+                           const double *const x[3], const double *const w[3], int on_device)
+{
+    if (!g || !sp) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    if (n > 0 && (!x || !w)) return fail(PIC_ERR_INVALID_ARG, "null particle arrays");
+    std::vector<LoadReq> reqs(1);
+    reqs[0].run = run;
+    reqs[0].species = species;
+    reqs[0].sp = *sp;
+    reqs[0].n = n;
+    for (int a = 0; a < 3; ++a) {
+        reqs[0].x[a] = n > 0 ? x[a] : nullptr;
+        reqs[0].w[a] = n > 0 ? w[a] : nullptr;
+    }
+    return load_many(g, reqs, on_device);
+}
+
+int pic_load_particles_runs(pic_grid *g, int count, const int *runs, int species, const pic_species_desc *sp,
+                            const long long *n, const double *const *x, const double *const *w, int on_device)
+{
+    if (!g || !runs || !sp || !n || !x || !w) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    if (count <= 0) return fail(PIC_ERR_INVALID_ARG, "count must be positive");
+    std::vector<LoadReq> reqs(count);
+    for (int r = 0; r < count; ++r) {
+        reqs[r].run = runs[r];
+        reqs[r].species = species;
+        reqs[r].sp = sp[r];
+        reqs[r].n = n[r];
+        for (int a = 0; a < 3; ++a) {
+            reqs[r].x[a] = x[3 * r + a];
+            reqs[r].w[a] = w[3 * r + a];
+        }
+    }
+    return load_many(g, reqs, on_device);
 }
 
 int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, long long n, const double *const x[3],

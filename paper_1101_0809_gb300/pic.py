@@ -219,6 +219,8 @@ _lib.pic_set_fields_run.argtypes = [_VP, C.c_int, _VP3, _VP3, C.c_int]
 _lib.pic_get_fields_run.argtypes = [_VP, C.c_int, _VP3, _VP3, _VP3, C.c_int]
 _lib.pic_load_particles_run.argtypes = [_VP, C.c_int, C.c_int, C.POINTER(pic_species_desc), C.c_longlong,
                                         _VP3, _VP3, C.c_int]
+_lib.pic_load_particles_runs.argtypes = [_VP, C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(pic_species_desc),
+                                         C.POINTER(C.c_longlong), C.POINTER(_VP), C.POINTER(_VP), C.c_int]
 _lib.pic_num_particles_run.argtypes = [_VP, C.c_int, C.c_int]
 _lib.pic_num_particles_run.restype = C.c_longlong
 _lib.pic_get_particles_run.argtypes = [_VP, C.c_int, C.c_int, _VP, _VP3, _VP3, _VP, C.c_int]
@@ -264,6 +266,29 @@ def pic_load_particles_run(g, run, species, q, m, weight, x, w):
     if dx != dw:
         raise ValueError("x and w must both be host or both be device arrays")
     _check(_lib.pic_load_particles_run(g, run, species, C.byref(sp), n, xs, ws, dx))
+
+
+def pic_load_particles_runs(g, runs, species, sps, xs, ws):
+    """One species over many runs in one call: runs[r], sps[r] = (q, m, weight),
+    xs[r], ws[r] = sequences of 3 float64 arrays (host or device, not mixed)."""
+    cnt = len(runs)
+    ra = (C.c_int * cnt)(*runs)
+    sa = (pic_species_desc * cnt)(*[pic_species_desc(*t) for t in sps])
+    na = (C.c_longlong * cnt)(*[int(len(w[0])) for w in ws])
+    xp = (_VP * (3 * cnt))()
+    wp = (_VP * (3 * cnt))()
+    devs = set()
+    for r in range(cnt):
+        for a in range(3):
+            p, d = _addr(xs[r][a])
+            xp[3 * r + a] = p
+            q, d2 = _addr(ws[r][a])
+            wp[3 * r + a] = q
+            devs.update({d, d2})
+    devs.discard(None)
+    if len(devs) > 1:
+        raise ValueError("mixing host and device arrays in one call")
+    _check(_lib.pic_load_particles_runs(g, cnt, ra, species, sa, na, xp, wp, devs.pop() if devs else 0))
 
 
 def pic_num_particles_run(g, run, species):

@@ -157,3 +157,32 @@ def test_graph_replay_refuses_the_legacy_default_stream(env):
         P.pic_step_graph(b.h, 8)
     assert e.value.code == P.PIC_ERR_INVALID_ARG
     b.close()
+
+
+def test_bulk_load_equals_run_by_run_loads(env):
+    P, torch = env
+    runs = ensemble2d(4)
+    b1 = make_batch(P, runs, P.PIC_FP64)
+    descs = [P.make_desc(2, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP64, tile=(16, 16, 1), sort_interval=3,
+                         particles_per_block=1024, rho_bg=wl.rho_bg) for wl in runs]
+    b2 = P.Batch(descs)
+    P.pic_load_particles_runs(b2.h, list(range(len(runs))), 0,
+                              [(wl.species[0].q, wl.species[0].m, wl.species[0].weight) for wl in runs],
+                              [list(wl.species[0].x) for wl in runs], [list(wl.species[0].w) for wl in runs])
+    for r in range(len(runs)):
+        for u, v in zip(b1.particles_run(r, 0), b2.particles_run(r, 0)):
+            if isinstance(u, list):
+                for p, q in zip(u, v):
+                    np.testing.assert_array_equal(p, q)
+            else:
+                np.testing.assert_array_equal(u, v)
+    P.pic_step(b1.h, 4)
+    P.pic_step(b2.h, 4)
+    for r, wl in enumerate(runs):
+        E1, B1, J1 = b1.get_fields_run(r)
+        E2, B2, J2 = b2.get_fields_run(r)
+        for a in range(3):
+            close(J2[a], J1[a], FP64_TOL, f"run {r} J[{a}]")
+            close(E2[a], E1[a], FP64_TOL, f"run {r} E[{a}]")
+    b1.close()
+    b2.close()
