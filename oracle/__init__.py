@@ -217,3 +217,22 @@ def sort_perm(key, nkeys):
     if rc != 0:
         raise ValueError(f"orc_sort_perm failed ({rc})")
     return perm
+
+
+def yee_half_B_adj(g: Grid, lamB, lamE):
+    """lamE += (-(1/2) C_B)^T lamB (transpose of the B half step)."""
+    lib().orc_yee_half_B_adj(C.byref(g.cstruct()), _fields(lamB), _fields(lamE))
+
+
+def step_adj(g: Grid, E, Bh, species, lamE, lamB, lam_x, lam_w):
+    """One step of the discrete adjoint at level n (state E^n, B^{n-1/2}, species
+    at n).  lamE, lamB (fields) and lam_x, lam_w (one (3, n) float64 array per
+    species) hold dL/d(state n+1) on entry and dL/d(state n) on return."""
+    arr = _species_array(species)
+    LX = (_P * len(species))(*[_ptr(a) for a in lam_x])
+    LW = (_P * len(species))(*[_ptr(a) for a in lam_w])
+    for a in list(lam_x) + list(lam_w):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().orc_step_adj(C.byref(g.cstruct()), _fields(E), _fields(Bh), C.c_int(len(species)), arr,
+                       _fields(lamE), _fields(lamB), LX, LW)
+

@@ -556,3 +556,367 @@ int orc_sort_perm(long long n, const int *key, int nkeys, long long *perm)
     free(start);
     return 0;
 }
+
+/* ===========================================================================
+ * Discrete adjoint of one time step (hand-derived reverse mode of the
+ * Appendix step above).  State at level n: E^n, B^{n-1/2}, x^n, w^{n-1/2};
+ * the adjoints lam* hold dL/d(state at n+1) on entry and dL/d(state at n) on
+ * return.  The step's intermediate quantities are recomputed from the state at
+ * n.  Forward order: B1 = B - (1/2) C_B E; particles (gather from E, B1; push;
+ * move; deposit into J); B2 = B1 - (1/2) C_B E; E' = E - 4 pi dt J + C_E B2.
+ * Reverse order: transpose of the E step, of the second B half step, of every
+ * particle, of the first B half step.  Cell indices (floor) are piecewise
+ * constant and contribute no derivative.
+ * ========================================================================= */
+
+/* derivatives of the l_a = 1 1/2 values with respect to x_p (d = x_p - i) */
+static void form_factor_deriv(double xp, double df[2], double dS[3])
+{
+    double d = xp - floor(xp);
+    df[0] = -1.0;
+    df[1] = 1.0;
+    dS[0] = -(1.0 - d);
+    dS[1] = 1.0 - 2.0 * d;
+    dS[2] = d;
+}
+
+/* Transpose of B -= (1/2) curl_h E (orc_yee_half_B): lamE += (-(1/2) C_B)^T lamB. */
+void orc_yee_half_B_adj(const orc_grid *g, const double *const lamB[3], double *lamE[3])
+{
+    const double cx = g->c * g->dt / g->dx, cy = g->c * g->dt / g->dy;
+    const double cz = g->dims == 2 ? 0.0 : g->c * g->dt / g->dz;
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                long long p = cell_index(g, i, j, k);
+                /* Bx[p] = ... - 0.5 cy (Ez[p] - Ez[j-1]) + 0.5 cz (Ey[p] - Ey[k-1]) */
+                lamE[2][p] += -0.5 * cy * lamB[0][p];
+                lamE[2][cell_index(g, i, j - 1, k)] += 0.5 * cy * lamB[0][p];
+                lamE[1][p] += 0.5 * cz * lamB[0][p];
+                lamE[1][cell_index(g, i, j, k - 1)] += -0.5 * cz * lamB[0][p];
+                /* By[p] = ... - 0.5 cz (Ex[p] - Ex[k-1]) + 0.5 cx (Ez[p] - Ez[i-1]) */
+                lamE[0][p] += -0.5 * cz * lamB[1][p];
+                lamE[0][cell_index(g, i, j, k - 1)] += 0.5 * cz * lamB[1][p];
+                lamE[2][p] += 0.5 * cx * lamB[1][p];
+                lamE[2][cell_index(g, i - 1, j, k)] += -0.5 * cx * lamB[1][p];
+                /* Bz[p] = ... - 0.5 cx (Ey[p] - Ey[i-1]) + 0.5 cy (Ex[p] - Ex[j-1]) */
+                lamE[1][p] += -0.5 * cx * lamB[2][p];
+                lamE[1][cell_index(g, i - 1, j, k)] += 0.5 * cx * lamB[2][p];
+                lamE[0][p] += 0.5 * cy * lamB[2][p];
+                lamE[0][cell_index(g, i, j - 1, k)] += -0.5 * cy * lamB[2][p];
+            }
+}
+
+/* Transpose of E += -4 pi dt J + C_E B (orc_yee_E): lamE passes through,
+ * lamB += C_E^T lamE, lamJ = -4 pi dt lamE. */
+void orc_yee_E_adj(const orc_grid *g, const double *const lamE[3], double *lamB[3], double *lamJ[3])
+{
+    const double cx = g->c * g->dt / g->dx, cy = g->c * g->dt / g->dy;
+    const double cz = g->dims == 2 ? 0.0 : g->c * g->dt / g->dz;
+    const double fpdt = 4.0 * ORC_PI * g->dt;
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                long long p = cell_index(g, i, j, k);
+                for (int a = 0; a < 3; ++a) lamJ[a][p] = -fpdt * lamE[a][p];
+                /* Ex[p] += cy (Bz[j+1] - Bz[p]) - cz (By[k+1] - By[p]) */
+                lamB[2][cell_index(g, i, j + 1, k)] += cy * lamE[0][p];
+                lamB[2][p] += -cy * lamE[0][p];
+                lamB[1][cell_index(g, i, j, k + 1)] += -cz * lamE[0][p];
+                lamB[1][p] += cz * lamE[0][p];
+                /* Ey[p] += cz (Bx[k+1] - Bx[p]) - cx (Bz[i+1] - Bz[p]) */
+                lamB[0][cell_index(g, i, j, k + 1)] += cz * lamE[1][p];
+                lamB[0][p] += -cz * lamE[1][p];
+                lamB[2][cell_index(g, i + 1, j, k)] += -cx * lamE[1][p];
+                lamB[2][p] += cx * lamE[1][p];
+                /* Ez[p] += cx (By[i+1] - By[p]) - cy (Bx[j+1] - Bx[p]) */
+                lamB[1][cell_index(g, i + 1, j, k)] += cx * lamE[2][p];
+                lamB[1][p] += -cx * lamE[2][p];
+                lamB[0][cell_index(g, i, j + 1, k)] += -cy * lamE[2][p];
+                lamB[0][p] += cy * lamE[2][p];
+            }
+}
+
+/* Transpose of the gather (orc_gather) at x_p: scatter lamEp alpha into lamE and
+ * lamBp beta into lamB, and add sum (d alpha/d x_p) E lamEp + (d beta/d x_p) B lamBp
+ * to lam_x. */
+void orc_gather_adj(const orc_grid *g, const double *const E[3], const double *const B[3], const double xp[3],
+                    const double lamEp[3], const double lamBp[3], double *lamE[3], double *lamB[3], double lam_x[3])
+{
+    orc_weights wt;
+    particle_weights(g, xp, &wt);
+    double dw[3][2][3];   /* [axis][0: d f, 1: d dF][index] */
+    for (int a = 0; a < 3; ++a) {
+        double df[2], dS[3];
+        if (a == 2 && g->dims == 2) {
+            df[0] = df[1] = 0.0;
+            dS[0] = dS[1] = dS[2] = 0.0;
+        } else {
+            form_factor_deriv(xp[a], df, dS);
+        }
+        dw[a][0][0] = df[0]; dw[a][0][1] = df[1]; dw[a][0][2] = 0.0;
+        dw[a][1][0] = dS[0]; dw[a][1][1] = dS[1]; dw[a][1][2] = dS[2];
+    }
+    const long long i0[3] = { wt.i0[0], wt.i0[1], wt.i0[2] };
+    /* per component: which family (0 = f at integer points, 1 = dF at half-integers) per axis */
+    const int famE[3][3] = { { 0, 1, 1 }, { 1, 0, 1 }, { 1, 1, 0 } };
+    const int famB[3][3] = { { 1, 0, 0 }, { 0, 1, 0 }, { 0, 0, 1 } };
+    for (int fld = 0; fld < 2; ++fld)
+        for (int c = 0; c < 3; ++c) {
+            const int *fam = fld == 0 ? famE[c] : famB[c];
+            const double lam = fld == 0 ? lamEp[c] : lamBp[c];
+            const double *F = fld == 0 ? E[c] : B[c];
+            double *LF = fld == 0 ? lamE[c] : lamB[c];
+            int cnt[3], off[3];
+            for (int a = 0; a < 3; ++a) {
+                if (a == 2 && g->dims == 2) { cnt[a] = 1; off[a] = 0; continue; }
+                cnt[a] = fam[a] == 0 ? 2 : 3;
+                off[a] = fam[a] == 0 ? 0 : -1;
+            }
+            for (int s2 = 0; s2 < cnt[2]; ++s2)
+                for (int s1 = 0; s1 < cnt[1]; ++s1)
+                    for (int s0 = 0; s0 < cnt[0]; ++s0) {
+                        const int sidx[3] = { s0, s1, s2 };
+                        double v[3], d[3];
+                        for (int a = 0; a < 3; ++a) {
+                            if (a == 2 && g->dims == 2) { v[a] = 1.0; d[a] = 0.0; continue; }
+                            if (fam[a] == 0) { v[a] = wt.f[a][sidx[a]]; d[a] = dw[a][0][sidx[a]]; }
+                            else { v[a] = wt.dF[a][sidx[a]]; d[a] = dw[a][1][sidx[a]]; }
+                        }
+                        long long idx = cell_index(g, i0[0] + off[0] + s0, i0[1] + off[1] + s1,
+                                                   i0[2] + off[2] + s2);
+                        LF[idx] += v[0] * v[1] * v[2] * lam;
+                        lam_x[0] += d[0] * v[1] * v[2] * F[idx] * lam;
+                        lam_x[1] += v[0] * d[1] * v[2] * F[idx] * lam;
+                        lam_x[2] += v[0] * v[1] * d[2] * F[idx] * lam;
+                    }
+        }
+}
+
+/* Transpose of orc_boris: given the pre-push w, Ep, Bp and lam_w1 = dL/dw^{n+1/2},
+ * return lam_w0 = dL/dw^{n-1/2}, lamEp, lamBp (the push's reverse sweep). */
+void orc_boris_adj(const double w[3], const double Ep[3], const double Bp[3], double qm, double dt, double c,
+                   const double lam_w1[3], double lam_w0[3], double lamEp[3], double lamBp[3])
+{
+    const double h = 0.5 * qm * dt;
+    double e[3], t[3], b[3], n[3], m[3], tb[3];
+    for (int a = 0; a < 3; ++a) e[a] = h * Ep[a];
+    for (int a = 0; a < 3; ++a) t[a] = w[a] + e[a];
+    double gt = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + c * c);
+    double s = h / gt;
+    for (int a = 0; a < 3; ++a) b[a] = s * Bp[a];
+    cross(t, b, tb);
+    for (int a = 0; a < 3; ++a) n[a] = t[a] + tb[a];
+    double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    double F = 2.0 / (1.0 + b2);
+    cross(n, b, m);
+    /* w1 = t + e + F m */
+    double lt[3], le[3], lm[3], ln[3], lb[3], tmp[3];
+    double lF = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        lt[a] = lam_w1[a];
+        le[a] = lam_w1[a];
+        lm[a] = F * lam_w1[a];
+        lF += lam_w1[a] * m[a];
+    }
+    /* m = n x b:  d(lm.(n x b))/dn = b x lm,  /db = lm x n */
+    cross(b, lm, ln);
+    cross(lm, n, lb);
+    /* F = 2/(1+b2), b2 = b.b */
+    double lb2 = lF * (-2.0 / ((1.0 + b2) * (1.0 + b2)));
+    for (int a = 0; a < 3; ++a) lb[a] += 2.0 * b[a] * lb2;
+    /* n = t + t x b */
+    cross(b, ln, tmp);
+    for (int a = 0; a < 3; ++a) lt[a] += ln[a] + tmp[a];
+    cross(ln, t, tmp);
+    for (int a = 0; a < 3; ++a) lb[a] += tmp[a];
+    /* b = s Bp, s = h/gt, gt = sqrt(t.t + c^2) */
+    double ls = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        ls += lb[a] * Bp[a];
+        lamBp[a] = s * lb[a];
+    }
+    double lgt = -ls * h / (gt * gt);
+    for (int a = 0; a < 3; ++a) lt[a] += lgt * t[a] / gt;
+    /* t = w + e, e = h Ep */
+    for (int a = 0; a < 3; ++a) {
+        lam_w0[a] = lt[a];
+        le[a] += lt[a];
+        lamEp[a] = h * le[a];
+    }
+}
+
+/* Window of one axis of the deposit together with the derivatives of the placed
+ * old/new weights with respect to x^n (dold) and x^{n+1} (dnew). */
+typedef struct {
+    orc_axis_current cur;
+    double old_w[ORC_MAXWIN], new_w[ORC_MAXWIN];
+    double dold[ORC_MAXWIN], dnew[ORC_MAXWIN];
+} orc_axis_adj;
+
+static int axis_current_adj(double x0, double x1, orc_axis_adj *ad)
+{
+    if (axis_current(x0, x1, &ad->cur) != 0) return -1;
+    long long i0, i1;
+    double f0[2], f1[2], dF0[3], dF1[3], df[2], dS0[3], dS1[3];
+    orc_form_factor(x0, &i0, f0, dF0);
+    orc_form_factor(x1, &i1, f1, dF1);
+    form_factor_deriv(x0, df, dS0);
+    form_factor_deriv(x1, df, dS1);
+    const long long lo = ad->cur.lo;
+    for (int s = 0; s < ad->cur.len; ++s) {
+        ad->old_w[s] = ad->new_w[s] = ad->dold[s] = ad->dnew[s] = 0.0;
+    }
+    for (int b = 0; b < 3; ++b) {
+        ad->old_w[i0 - 1 + b - lo] = dF0[b];
+        ad->dold[i0 - 1 + b - lo] = dS0[b];
+        ad->new_w[i1 - 1 + b - lo] = dF1[b];
+        ad->dnew[i1 - 1 + b - lo] = dS1[b];
+    }
+    return 0;
+}
+
+/* Transpose of orc_deposit: given lamJ (grid), return the contributions to
+ * lam_x0, lam_x1 and lam_u (u enters the 2D z current only). */
+void orc_deposit_adj(const orc_grid *g, const double x0[3], const double x1[3], const double u[3], double qp,
+                     const double *const lamJ[3], double lam_x0[3], double lam_x1[3], double lam_u[3])
+{
+    orc_axis_adj ax[3];
+    double lPp[3][ORC_MAXWIN], lPm[3][ORC_MAXWIN], lD[3][ORC_MAXWIN];
+    for (int a = 0; a < g->dims; ++a) {
+        if (axis_current_adj(x0[a], x1[a], &ax[a]) != 0) return;
+        for (int s = 0; s < ORC_MAXWIN; ++s) lPp[a][s] = lPm[a][s] = lD[a][s] = 0.0;
+    }
+    const double qV = qp / cell_volume(g);
+    const double dtn = g->dt;
+    if (g->dims == 3) {
+        /* xi^(a) on faces of axis a: k_a D_a(f) [Pp_b Pp_c + Pm_b Pm_c / 3], (b, c) the two other axes */
+        const double dd[3] = { g->dx, g->dy, g->dz };
+        for (int a = 0; a < 3; ++a) {
+            const int b = (a + 1) % 3, cax = (a + 2) % 3;
+            const double ka = -0.25 * (dd[a] / dtn) * qV;
+            const orc_axis_current *A = &ax[a].cur, *Bc = &ax[b].cur, *Cc = &ax[cax].cur;
+            for (int sc = 0; sc < Cc->len; ++sc)
+                for (int sb = 0; sb < Bc->len; ++sb)
+                    for (int sa = 1; sa < A->len; ++sa) {
+                        long long idx[3];
+                        idx[a] = A->lo + sa;
+                        idx[b] = Bc->lo + sb;
+                        idx[cax] = Cc->lo + sc;
+                        const double G = lamJ[a][cell_index(g, idx[0], idx[1], idx[2])] * ka;
+                        const double T = Bc->Pp[sb] * Cc->Pp[sc] + Bc->Pm[sb] * Cc->Pm[sc] / 3.0;
+                        lD[a][sa] += G * T;
+                        lPp[b][sb] += G * A->D[sa] * Cc->Pp[sc];
+                        lPp[cax][sc] += G * A->D[sa] * Bc->Pp[sb];
+                        lPm[b][sb] += G * A->D[sa] * Cc->Pm[sc] / 3.0;
+                        lPm[cax][sc] += G * A->D[sa] * Bc->Pm[sb] / 3.0;
+                    }
+        }
+    } else {
+        const orc_axis_current *X = &ax[0].cur, *Y = &ax[1].cur;
+        const double kx = -0.5 * (g->dx / dtn) * qV, ky = -0.5 * (g->dy / dtn) * qV, kz = 0.25 * qV;
+        for (int sj = 0; sj < Y->len; ++sj)
+            for (int si = 1; si < X->len; ++si) {
+                const double G = lamJ[0][cell_index(g, X->lo + si, Y->lo + sj, 0)] * kx;
+                lD[0][si] += G * Y->Pp[sj];
+                lPp[1][sj] += G * X->D[si];
+            }
+        for (int sj = 1; sj < Y->len; ++sj)
+            for (int si = 0; si < X->len; ++si) {
+                const double G = lamJ[1][cell_index(g, X->lo + si, Y->lo + sj, 0)] * ky;
+                lD[1][sj] += G * X->Pp[si];
+                lPp[0][si] += G * Y->D[sj];
+            }
+        for (int sj = 0; sj < Y->len; ++sj)
+            for (int si = 0; si < X->len; ++si) {
+                const double G = lamJ[2][cell_index(g, X->lo + si, Y->lo + sj, 0)] * kz;
+                lam_u[2] += G * (X->Pp[si] * Y->Pp[sj] + X->Pm[si] * Y->Pm[sj] / 3.0);
+                lPp[0][si] += G * u[2] * Y->Pp[sj];
+                lPp[1][sj] += G * u[2] * X->Pp[si];
+                lPm[0][si] += G * u[2] * Y->Pm[sj] / 3.0;
+                lPm[1][sj] += G * u[2] * X->Pm[si] / 3.0;
+            }
+    }
+    for (int a = 0; a < g->dims; ++a) {
+        const orc_axis_current *A = &ax[a].cur;
+        /* D(f) = sum_{s < f} Pm(s): lam Pm(s) += sum_{f > s} lam D(f) */
+        for (int s = 0; s < A->len; ++s)
+            for (int f = s + 1; f < A->len; ++f) lPm[a][s] += lD[a][f];
+        for (int s = 0; s < A->len; ++s) {
+            const double lnew = lPp[a][s] + lPm[a][s];   /* Pp = new + old, Pm = new - old */
+            const double lold = lPp[a][s] - lPm[a][s];
+            lam_x1[a] += lnew * ax[a].dnew[s];
+            lam_x0[a] += lold * ax[a].dold[s];
+        }
+    }
+}
+
+/* One step of the adjoint (see the block comment above).  The species' x and w
+ * are the state at level n and are not modified; lam_x[s][a], lam_w[s][a] are the
+ * per-particle adjoints of species s. */
+void orc_step_adj(const orc_grid *g, const double *const E[3], const double *const Bh[3], int nsp,
+                  const orc_species *sp, double *lamE[3], double *lamB[3], double *const *lam_x,
+                  double *const *lam_w)
+{
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    double *B1[3], *lamJ[3], *lamB1[3];
+    for (int a = 0; a < 3; ++a) {
+        B1[a] = (double *)malloc(sizeof(double) * N);
+        lamJ[a] = (double *)calloc(N, sizeof(double));
+        lamB1[a] = (double *)calloc(N, sizeof(double));
+        memcpy(B1[a], Bh[a], sizeof(double) * N);
+    }
+    orc_yee_half_B(g, E, B1);
+    /* (E step)^T: lamE unchanged, lamB (= lam B2) += C_E^T lamE, lamJ */
+    orc_yee_E_adj(g, (const double *const *)lamE, lamB, lamJ);
+    /* (second B half step)^T: lam B1 = lam B2, lamE += (-C_B/2)^T lam B2 */
+    orc_yee_half_B_adj(g, (const double *const *)lamB, lamE);
+    for (int a = 0; a < 3; ++a) memcpy(lamB1[a], lamB[a], sizeof(double) * N);
+    /* particles^T */
+    const double cN[3] = { g->c * g->dt / g->dx, g->c * g->dt / g->dy, g->c * g->dt / g->dz };
+    for (int s = 0; s < nsp; ++s) {
+        const double qm = sp[s].q / sp[s].m, qp = sp[s].q * sp[s].weight;
+        for (long long p = 0; p < sp[s].n; ++p) {
+            double x0[3] = { sp[s].x[0][p], sp[s].x[1][p], g->dims == 3 ? sp[s].x[2][p] : 0.0 };
+            double w0[3] = { sp[s].w[0][p], sp[s].w[1][p], sp[s].w[2][p] };
+            double Ep[3], Bp[3], w1[3], x1[3], u[3];
+            orc_gather(g, E, (const double *const *)B1, x0, Ep, Bp);
+            for (int a = 0; a < 3; ++a) w1[a] = w0[a];
+            orc_boris(w1, Ep, Bp, qm, g->dt, g->c);
+            orc_move(g, w1, x0, x1, u);
+            double lx0[3] = { 0, 0, 0 }, lx1[3], lu[3] = { 0, 0, 0 }, lw1[3];
+            for (int a = 0; a < 3; ++a) {
+                lx1[a] = a < g->dims ? lam_x[s][a * sp[s].n + p] : 0.0;
+                lw1[a] = lam_w[s][a * sp[s].n + p];
+            }
+            orc_deposit_adj(g, x0, x1, u, qp, (const double *const *)lamJ, lx0, lx1, lu);
+            /* x1 = x0 + cN w1/gamma1;  u = c w1/gamma1 */
+            const double gam = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2] + g->c * g->c);
+            for (int a = 0; a < g->dims; ++a) lx0[a] += lx1[a];
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double jac = ((a == b ? 1.0 : 0.0) / gam - w1[a] * w1[b] / (gam * gam * gam));
+                    if (a < g->dims) acc += lx1[a] * cN[a] * jac;
+                    acc += lu[a] * g->c * jac;
+                }
+                lw1[b] += acc;
+            }
+            double lw0[3], lEp[3], lBp[3];
+            orc_boris_adj(w0, Ep, Bp, qm, g->dt, g->c, lw1, lw0, lEp, lBp);
+            orc_gather_adj(g, E, (const double *const *)B1, x0, lEp, lBp, lamE, lamB1, lx0);
+            for (int a = 0; a < 3; ++a) {
+                if (a < g->dims) lam_x[s][a * sp[s].n + p] = lx0[a];
+                lam_w[s][a * sp[s].n + p] = lw0[a];
+            }
+        }
+    }
+    /* (first B half step)^T: lam B = lam B1, lamE += (-C_B/2)^T lam B1 */
+    orc_yee_half_B_adj(g, (const double *const *)lamB1, lamE);
+    for (int a = 0; a < 3; ++a) {
+        memcpy(lamB[a], lamB1[a], sizeof(double) * N);
+        free(B1[a]);
+        free(lamJ[a]);
+        free(lamB1[a]);
+    }
+}
