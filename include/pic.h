@@ -231,6 +231,38 @@ enum {
 int pic_profile(pic_grid *g, int enable);
 int pic_profile_read(pic_grid *g, double ms[PIC_PROF_N], long long count[PIC_PROF_N]);
 
+/* ---- State snapshots ------------------------------------------------------------
+ * A snapshot is one contiguous blob: a 48-byte header ("PICS", version 1,
+ * dims, precision, group count, particle and cell counts, sort phase, and a
+ * checksum of the header) followed by the particle arrays (cell, id, offsets,
+ * momenta, in storage order) and the fields E^n, B^{n-1/2}.  pic_state_bytes
+ * gives its size.  pic_state_save writes it to dst (device memory if on_device,
+ * else host memory); pic_state_restore reads one taken from a grid with the same
+ * layout (same runs, species and particle counts), re-sorts the particles by
+ * tile and clears the residual references.  Used for checkpoints, for restart
+ * from a file written by the caller, and by the adjoint's recompute. */
+long long pic_state_bytes(pic_grid *g);
+int pic_state_save(pic_grid *g, void *dst, int on_device);
+int pic_state_restore(pic_grid *g, const void *src, int on_device);
+
+/* ---- Discrete adjoint of the step -----------------------------------------------
+ * pic_adjoint_step takes the grid's current state as level n (E^n, B^{n-1/2},
+ * x^n, w^{n-1/2}) and maps the adjoints of level n+1 to those of level n, in
+ * place: lamE, lamB are field arrays (nx*ny*nz values of the grid's precision
+ * per component, runs concatenated like the fields); lamx, lamw are particle
+ * arrays of the grid's precision, one value per particle, indexed by the
+ * species' position in the pool plus the particle id, i.e. for one species in
+ * its load order (lamx[2] is unused in 2D).  All are device pointers.  The
+ * step is the reverse of pic_step: transposes of the E step and of both B half
+ * steps, and for every particle the gather of lamJ over its current window, the
+ * hand-derived reverse of the deposit (Eq. current), move (Eq. coordscheme),
+ * push (Eq. 1) and gather (Eqs. alphax, betax), with the transposed gather
+ * scattered into lamE and lamB by atomics.
+ * pic_adjoint_yee_half_B adds (-(1/2) C_B)^T lamB to lamE (the transpose of one
+ * B half step), e.g. to seed a loss that uses B^n = B^{n-1/2} - (1/2) c curl E^n. */
+int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], void *lamw[3]);
+int pic_adjoint_yee_half_B(pic_grid *g, void *const lamB[3], void *lamE[3]);
+
 /* ---- Tile sort without device allocation -----------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot
  * allocate device memory: code running inside a memory budget that another

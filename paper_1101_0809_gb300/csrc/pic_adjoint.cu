@@ -1,0 +1,465 @@
+// pic_adjoint.cu -- discrete adjoint of one time step (reverse mode of the step
+// of the paper's Appendix), for gradients of a loss of the final state with
+// respect to the initial positions and momenta.
+//
+// Forward step at level n: B1 = B - (1/2) C_B E; per particle: gather E and B1
+// at x^n, push, move, deposit J; B2 = B1 - (1/2) C_B E; E' = E - 4 pi dt J + C_E B2.
+// Reverse: transpose of the E step (lamJ = -4 pi dt lamE, lamB += C_E^T lamE),
+// of the second B half step (lamE += (-(1/2) C_B)^T lamB), of every particle
+// (gather of lamJ over the particle's current window, hand-derived reverse of the
+// deposit, move and push, scatter of the gather's transpose into lamE and lamB1),
+// and of the first B half step.  The particle's intermediate quantities are
+// recomputed from the state at level n, in the same arithmetic as the forward
+// kernel (including the offset renormalization).  The particle adjoints are
+// indexed by group base + particle id, i.e. in each species' load order.
+#include "pic_internal.h"
+
+namespace pic {
+
+template <typename R>
+struct AdjArgs {
+    const RunDev *runs;
+    const GroupDev *groups;
+    const long long *group_base;
+    int ngroups;
+    long long total;
+    Pool<R> P;
+    const R *E[3];
+    const R *B1[3];
+    const R *lamJ[3];
+    R *lamE[3];
+    R *lamB1[3];
+    R *lamx[3];
+    R *lamw[3];
+};
+
+template <typename R>
+__device__ __forceinline__ void form_factor_d(R d, R df[2], R dS[3])
+{
+    df[0] = R(-1);
+    df[1] = R(1);
+    dS[0] = d - R(1);
+    dS[1] = R(1) - R(2) * d;
+    dS[2] = d;
+}
+
+// Placed old/new weights of one axis on the deposit's 4-cell window (same
+// placement as axis_window) and their derivatives with respect to the old and
+// new offsets.
+template <typename R>
+struct AxisWinAdj {
+    R o[4], n[4], dO[4], dN[4];
+};
+
+template <typename R>
+__device__ __forceinline__ void axis_window_adj(R d0, R d1, int s, AxisWinAdj<R> &a)
+{
+    R f[2], S0[3], S1[3], df[2], dS0[3], dS1[3];
+    form_factor(d0, f, S0);
+    form_factor(d1, f, S1);
+    form_factor_d(d0, df, dS0);
+    form_factor_d(d1, df, dS1);
+    const bool neg = s < 0, pos = s > 0;
+    a.o[0] = neg ? R(0) : S0[0];  a.dO[0] = neg ? R(0) : dS0[0];
+    a.o[1] = neg ? S0[0] : S0[1]; a.dO[1] = neg ? dS0[0] : dS0[1];
+    a.o[2] = neg ? S0[1] : S0[2]; a.dO[2] = neg ? dS0[1] : dS0[2];
+    a.o[3] = neg ? S0[2] : R(0);  a.dO[3] = neg ? dS0[2] : R(0);
+    a.n[0] = pos ? R(0) : S1[0];  a.dN[0] = pos ? R(0) : dS1[0];
+    a.n[1] = pos ? S1[0] : S1[1]; a.dN[1] = pos ? dS1[0] : dS1[1];
+    a.n[2] = pos ? S1[1] : S1[2]; a.dN[2] = pos ? dS1[1] : dS1[2];
+    a.n[3] = pos ? S1[2] : R(0);  a.dN[3] = pos ? dS1[2] : R(0);
+}
+
+template <int DIM, typename R>
+__global__ void __launch_bounds__(256) k_particles_adj(const AdjArgs<R> a)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < a.total; p += stride) {
+        int lo = 0, hi = a.ngroups;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.group_base[mid] <= p) lo = mid; else hi = mid;
+        }
+        const GroupDev gr = a.groups[lo];
+        const RunDev &rn = a.runs[gr.run];
+        const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
+        const long long cb = rn.cell_base;
+        const long long L = gr.base + a.P.id[p];
+        const int cell0 = a.P.cell[p];
+        const int i = cell0 % nx, rest = cell0 / nx, j = rest % ny, k = DIM == 3 ? rest / ny : 0;
+        R o[3] = {a.P.off[0][p], a.P.off[1][p], DIM == 3 ? a.P.off[2][p] : R(0)};
+        const R w0[3] = {a.P.w[0][p], a.P.w[1][p], a.P.w[2][p]};
+        // ---- recompute the forward quantities --------------------------------
+        R f[3][2], S[3][3], df[3][2], dS[3][3];
+        for (int ax = 0; ax < 3; ++ax) {
+            if (ax == 2 && DIM == 2) {
+                f[2][0] = R(1); f[2][1] = R(0); S[2][0] = R(0); S[2][1] = R(1); S[2][2] = R(0);
+                df[2][0] = df[2][1] = R(0); dS[2][0] = dS[2][1] = dS[2][2] = R(0);
+                continue;
+            }
+            form_factor(o[ax], f[ax], S[ax]);
+            form_factor_d(o[ax], df[ax], dS[ax]);
+        }
+        long long xi[4], yj[4], zk[4];
+        for (int q = 0; q < 4; ++q) {
+            xi[q] = cb + wrapi(i - 1 + q, nx);
+            yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
+            zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
+        }
+        // alternating-order weights: E_c uses f along axis c and S along the
+        // others, B_c uses S along c and f along the others (Eqs. alphax, betax)
+        const int nz_pts = DIM == 3 ? 1 : 0;   // in 2D the z factor is the single weight 1
+        R Ep[3] = {0, 0, 0}, Bp[3] = {0, 0, 0};
+        for (int fld = 0; fld < 2; ++fld)
+            for (int c = 0; c < 3; ++c) {
+                const bool intx = (fld == 0) == (c == 0), inty = (fld == 0) == (c == 1), intz = (fld == 0) == (c == 2);
+                const int cx = intx ? 2 : 3, cy = inty ? 2 : 3, cz = DIM == 3 ? (intz ? 2 : 3) : 1;
+                const int ox = intx ? 0 : -1, oy = inty ? 0 : -1, oz = DIM == 3 ? (intz ? 0 : -1) : 0;
+                const R *F = fld == 0 ? a.E[c] : a.B1[c];
+                R acc = 0;
+                for (int sz = 0; sz < cz; ++sz)
+                    for (int sy = 0; sy < cy; ++sy)
+                        for (int sx = 0; sx < cx; ++sx) {
+                            const R wx = intx ? f[0][sx] : S[0][sx];
+                            const R wy = inty ? f[1][sy] : S[1][sy];
+                            const R wz = DIM == 3 ? (intz ? f[2][sz] : S[2][sz]) : R(1);
+                            acc += wx * wy * wz * F[xi[ox + sx + 1] + yj[oy + sy + 1] + zk[oz + sz + nz_pts]];
+                        }
+                if (fld == 0) Ep[c] = acc; else Bp[c] = acc;
+            }
+        const R hq = R(0.5 * gr.qm * rn.dt);
+        const R cl = R(rn.c), c2 = cl * cl;
+        const R cN[3] = {R(rn.cN[0]), R(rn.cN[1]), R(rn.cN[2])};
+        R w1[3] = {w0[0], w0[1], w0[2]};
+        boris(w1, Ep, Bp, hq, c2);
+        const R g1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2] + c2);
+        const R ig = R(1) / g1;
+        R n1[3] = {o[0], o[1], o[2]};
+        int sh[3] = {0, 0, 0};
+        for (int ax = 0; ax < DIM; ++ax) sh[ax] = renormalize(o[ax], w1[ax] * ig * cN[ax], n1[ax]);
+        const R uz = cl * w1[2] * ig;
+        // ---- reverse of the deposit ------------------------------------------
+        AxisWin<R> W[3];
+        AxisWinAdj<R> WA[3];
+        for (int ax = 0; ax < DIM; ++ax) {
+            axis_window(o[ax], n1[ax], sh[ax], W[ax]);
+            axis_window_adj(o[ax], n1[ax], sh[ax], WA[ax]);
+        }
+        R lPp[3][4] = {{0}}, lPm[3][4] = {{0}}, lD[3][3] = {{0}};
+        R luz = 0;
+        const int base[3] = {i, j, k};
+        const int nn[3] = {nx, ny, nz};
+        auto gidx = [&](int c0, int c1, int c2i) -> long long {
+            return cb + (long long)wrapi(base[0] + c0, nn[0]) +
+                   (long long)nx * ((long long)wrapi(base[1] + c1, nn[1]) + (long long)ny * (DIM == 3 ? wrapi(base[2] + c2i, nn[2]) : 0));
+        };
+        if (DIM == 3) {
+            for (int cmp = 0; cmp < 3; ++cmp) {
+                const int b = (cmp + 1) % 3, cc = (cmp + 2) % 3;
+                const R ka = R(-0.25 * rn.d[cmp] / rn.dt * gr.qp / rn.V);
+                for (int wc = 0; wc < 4; ++wc)
+                    for (int wb = 0; wb < 4; ++wb) {
+                        const R T = W[b].Pp[wb] * W[cc].Pp[wc] + W[b].Pm[wb] * W[cc].Pm[wc] / R(3);
+                        for (int q = 0; q < 3; ++q) {
+                            int off[3];
+                            off[cmp] = W[cmp].lo + 1 + q;
+                            off[b] = W[b].lo + wb;
+                            off[cc] = W[cc].lo + wc;
+                            const R G = a.lamJ[cmp][gidx(off[0], off[1], off[2])] * ka;
+                            lD[cmp][q] += G * T;
+                            lPp[b][wb] += G * W[cmp].D[q] * W[cc].Pp[wc];
+                            lPp[cc][wc] += G * W[cmp].D[q] * W[b].Pp[wb];
+                            lPm[b][wb] += G * W[cmp].D[q] * W[cc].Pm[wc] / R(3);
+                            lPm[cc][wc] += G * W[cmp].D[q] * W[b].Pm[wb] / R(3);
+                        }
+                    }
+            }
+        } else {
+            const R kx = R(-0.5 * rn.d[0] / rn.dt * gr.qp / rn.V);
+            const R ky = R(-0.5 * rn.d[1] / rn.dt * gr.qp / rn.V);
+            const R kz = R(0.25 * gr.qp / rn.V);
+            for (int wy = 0; wy < 4; ++wy)
+                for (int q = 0; q < 3; ++q) {
+                    const R G = a.lamJ[0][gidx(W[0].lo + 1 + q, W[1].lo + wy, 0)] * kx;
+                    lD[0][q] += G * W[1].Pp[wy];
+                    lPp[1][wy] += G * W[0].D[q];
+                }
+            for (int wx = 0; wx < 4; ++wx)
+                for (int q = 0; q < 3; ++q) {
+                    const R G = a.lamJ[1][gidx(W[0].lo + wx, W[1].lo + 1 + q, 0)] * ky;
+                    lD[1][q] += G * W[0].Pp[wx];
+                    lPp[0][wx] += G * W[1].D[q];
+                }
+            for (int wy = 0; wy < 4; ++wy)
+                for (int wx = 0; wx < 4; ++wx) {
+                    const R G = a.lamJ[2][gidx(W[0].lo + wx, W[1].lo + wy, 0)] * kz;
+                    luz += G * (W[0].Pp[wx] * W[1].Pp[wy] + W[0].Pm[wx] * W[1].Pm[wy] / R(3));
+                    lPp[0][wx] += G * uz * W[1].Pp[wy];
+                    lPp[1][wy] += G * uz * W[0].Pp[wx];
+                    lPm[0][wx] += G * uz * W[1].Pm[wy] / R(3);
+                    lPm[1][wy] += G * uz * W[0].Pm[wx] / R(3);
+                }
+        }
+        R lx1[3], lx0[3];
+        for (int ax = 0; ax < 3; ++ax) {
+            lx1[ax] = ax < DIM ? a.lamx[ax][L] : R(0);
+            lx0[ax] = 0;
+        }
+        for (int ax = 0; ax < DIM; ++ax) {
+            // D[q] = sum_{w <= q} Pm[w]
+            lPm[ax][0] += lD[ax][0] + lD[ax][1] + lD[ax][2];
+            lPm[ax][1] += lD[ax][1] + lD[ax][2];
+            lPm[ax][2] += lD[ax][2];
+            R ln = 0, lo2 = 0;
+            for (int w4 = 0; w4 < 4; ++w4) {
+                ln += (lPp[ax][w4] + lPm[ax][w4]) * WA[ax].dN[w4];
+                lo2 += (lPp[ax][w4] - lPm[ax][w4]) * WA[ax].dO[w4];
+            }
+            lx1[ax] += ln;
+            lx0[ax] += lo2 + lx1[ax];   // x^{n+1} = x^n + delta
+        }
+        // ---- reverse of the move: delta_a = cN_a w1_a / gamma1, u_z = c w1_z / gamma1
+        R lw1[3] = {a.lamw[0][L], a.lamw[1][L], a.lamw[2][L]};
+        const R ig3 = ig * ig * ig;
+        for (int bb = 0; bb < 3; ++bb) {
+            R acc = 0;
+            for (int ax = 0; ax < 3; ++ax) {
+                const R jac = (ax == bb ? ig : R(0)) - w1[ax] * w1[bb] * ig3;
+                if (ax < DIM) acc += lx1[ax] * cN[ax] * jac;
+                if (ax == 2 && DIM == 2) acc += luz * cl * jac;
+            }
+            lw1[bb] += acc;
+        }
+        // ---- reverse of the push (Appendix): t = w + e, b = s B, n = t + t x b,
+        // F = 2/(1 + b.b), w1 = t + e + F (n x b)
+        R lEp[3], lBp[3], lw0[3];
+        {
+            R e[3], t[3], b[3], nn3[3], m[3];
+            for (int ax = 0; ax < 3; ++ax) {
+                e[ax] = hq * Ep[ax];
+                t[ax] = w0[ax] + e[ax];
+            }
+            const R gt = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + c2);
+            const R s = hq / gt;
+            for (int ax = 0; ax < 3; ++ax) b[ax] = s * Bp[ax];
+            nn3[0] = t[0] + (t[1] * b[2] - t[2] * b[1]);
+            nn3[1] = t[1] + (t[2] * b[0] - t[0] * b[2]);
+            nn3[2] = t[2] + (t[0] * b[1] - t[1] * b[0]);
+            const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+            const R Fq = R(2) / (R(1) + b2);
+            m[0] = nn3[1] * b[2] - nn3[2] * b[1];
+            m[1] = nn3[2] * b[0] - nn3[0] * b[2];
+            m[2] = nn3[0] * b[1] - nn3[1] * b[0];
+            R lt[3], le[3], lm[3], ln3[3], lb[3];
+            R lF = 0;
+            for (int ax = 0; ax < 3; ++ax) {
+                lt[ax] = lw1[ax];
+                le[ax] = lw1[ax];
+                lm[ax] = Fq * lw1[ax];
+                lF += lw1[ax] * m[ax];
+            }
+            // m = n x b: ln = b x lm, lb = lm x n
+            ln3[0] = b[1] * lm[2] - b[2] * lm[1];
+            ln3[1] = b[2] * lm[0] - b[0] * lm[2];
+            ln3[2] = b[0] * lm[1] - b[1] * lm[0];
+            lb[0] = lm[1] * nn3[2] - lm[2] * nn3[1];
+            lb[1] = lm[2] * nn3[0] - lm[0] * nn3[2];
+            lb[2] = lm[0] * nn3[1] - lm[1] * nn3[0];
+            const R lb2 = lF * (-R(2) / ((R(1) + b2) * (R(1) + b2)));
+            for (int ax = 0; ax < 3; ++ax) lb[ax] += R(2) * b[ax] * lb2;
+            // n = t + t x b: lt += ln + b x ln, lb += ln x t
+            lt[0] += ln3[0] + (b[1] * ln3[2] - b[2] * ln3[1]);
+            lt[1] += ln3[1] + (b[2] * ln3[0] - b[0] * ln3[2]);
+            lt[2] += ln3[2] + (b[0] * ln3[1] - b[1] * ln3[0]);
+            lb[0] += ln3[1] * t[2] - ln3[2] * t[1];
+            lb[1] += ln3[2] * t[0] - ln3[0] * t[2];
+            lb[2] += ln3[0] * t[1] - ln3[1] * t[0];
+            R ls = 0;
+            for (int ax = 0; ax < 3; ++ax) {
+                ls += lb[ax] * Bp[ax];
+                lBp[ax] = s * lb[ax];
+            }
+            const R lgt = -ls * hq / (gt * gt);
+            for (int ax = 0; ax < 3; ++ax) {
+                lt[ax] += lgt * t[ax] / gt;
+                lw0[ax] = lt[ax];
+                lEp[ax] = hq * (le[ax] + lt[ax]);
+            }
+        }
+        // ---- reverse of the gather: scatter into lamE, lamB1; derivatives into lx0
+        for (int fld = 0; fld < 2; ++fld)
+            for (int c = 0; c < 3; ++c) {
+                const bool intx = (fld == 0) == (c == 0), inty = (fld == 0) == (c == 1), intz = (fld == 0) == (c == 2);
+                const int cx = intx ? 2 : 3, cy = inty ? 2 : 3, cz = DIM == 3 ? (intz ? 2 : 3) : 1;
+                const int ox = intx ? 0 : -1, oy = inty ? 0 : -1, oz = DIM == 3 ? (intz ? 0 : -1) : 0;
+                const R *F = fld == 0 ? a.E[c] : a.B1[c];
+                R *LF = fld == 0 ? a.lamE[c] : a.lamB1[c];
+                const R lam = fld == 0 ? lEp[c] : lBp[c];
+                for (int sz = 0; sz < cz; ++sz)
+                    for (int sy = 0; sy < cy; ++sy)
+                        for (int sx = 0; sx < cx; ++sx) {
+                            const R vx = intx ? f[0][sx] : S[0][sx], dx = intx ? df[0][sx] : dS[0][sx];
+                            const R vy = inty ? f[1][sy] : S[1][sy], dy = inty ? df[1][sy] : dS[1][sy];
+                            const R vz = DIM == 3 ? (intz ? f[2][sz] : S[2][sz]) : R(1);
+                            const R dz = DIM == 3 ? (intz ? df[2][sz] : dS[2][sz]) : R(0);
+                            const long long idx = xi[ox + sx + 1] + yj[oy + sy + 1] + zk[oz + sz + nz_pts];
+                            atomicAdd(&LF[idx], vx * vy * vz * lam);
+                            const R fl = F[idx] * lam;
+                            lx0[0] += dx * vy * vz * fl;
+                            lx0[1] += vx * dy * vz * fl;
+                            lx0[2] += vx * vy * dz * fl;
+                        }
+            }
+        for (int ax = 0; ax < 3; ++ax) {
+            if (ax < DIM) a.lamx[ax][L] = lx0[ax];
+            a.lamw[ax][L] = lw0[ax];
+        }
+    }
+}
+
+// Transpose of the E step at one cell: lamJ = -4 pi dt lamE; lamB += C_E^T lamE,
+// i.e. lamBx += c_y(lamEz[p] - lamEz[j-1]) - c_z(lamEy[p] - lamEy[k-1]) and cyclically.
+template <int DIM, typename R>
+__global__ void k_adj_yee_e(const RunDev *runs, const R *lamE0, const R *lamE1, const R *lamE2, R *lB0, R *lB1,
+                            R *lB2, R *lJ0, R *lJ1, R *lJ2)
+{
+    const RunDev &rn = runs[blockIdx.y];
+    const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
+    const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (l >= (long long)nx * ny * nz) return;
+    const int i = (int)(l % nx);
+    const long long r = l / nx;
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const long long p = rn.cell_base + l;
+    const long long pim = p + (i == 0 ? nx - 1 : -1);
+    const long long pjm = p + (long long)nx * (j == 0 ? ny - 1 : -1);
+    const R cx = R(rn.cN[0]), cy = R(rn.cN[1]);
+    const R fp = R(4.0 * 3.14159265358979323846 * rn.dt);
+    lJ0[p] = -fp * lamE0[p];
+    lJ1[p] = -fp * lamE1[p];
+    lJ2[p] = -fp * lamE2[p];
+    R bx = cy * (lamE2[p] - lamE2[pjm]);
+    R by = -cx * (lamE2[p] - lamE2[pim]);
+    R bz = cx * (lamE1[p] - lamE1[pim]) - cy * (lamE0[p] - lamE0[pjm]);
+    if (DIM == 3) {
+        const long long pkm = p + (long long)nx * ny * (k == 0 ? nz - 1 : -1);
+        const R cz = R(rn.cN[2]);
+        bx -= cz * (lamE1[p] - lamE1[pkm]);
+        by += cz * (lamE0[p] - lamE0[pkm]);
+    }
+    lB0[p] += bx;
+    lB1[p] += by;
+    lB2[p] += bz;
+}
+
+// Transpose of the B half step at one cell: lamE += (-(1/2) C_B)^T lamB, i.e.
+// lamEx += -(1/2)[c_y(lamBz[j+1] - lamBz[p]) - c_z(lamBy[k+1] - lamBy[p])] and cyclically.
+template <int DIM, typename R>
+__global__ void k_adj_yee_b(const RunDev *runs, const R *lB0, const R *lB1, const R *lB2, R *lE0, R *lE1, R *lE2)
+{
+    const RunDev &rn = runs[blockIdx.y];
+    const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
+    const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (l >= (long long)nx * ny * nz) return;
+    const int i = (int)(l % nx);
+    const long long r = l / nx;
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const long long p = rn.cell_base + l;
+    const long long pip = p + (i == nx - 1 ? -(nx - 1) : 1);
+    const long long pjp = p + (long long)nx * (j == ny - 1 ? -(ny - 1) : 1);
+    const R hx = R(0.5 * rn.cN[0]), hy = R(0.5 * rn.cN[1]);
+    R ex = -hy * (lB2[pjp] - lB2[p]);
+    R ey = hx * (lB2[pip] - lB2[p]);
+    R ez = -hx * (lB1[pip] - lB1[p]) + hy * (lB0[pjp] - lB0[p]);
+    if (DIM == 3) {
+        const long long pkp = p + (long long)nx * ny * (k == nz - 1 ? -(nz - 1) : 1);
+        const R hz = R(0.5 * rn.cN[2]);
+        ex += hz * (lB1[pkp] - lB1[p]);
+        ey -= hz * (lB0[pkp] - lB0[p]);
+    }
+    lE0[p] += ex;
+    lE1[p] += ey;
+    lE2[p] += ez;
+}
+
+template <int DIM, typename R>
+static cudaError_t adj_yee_t(int which, cudaStream_t st, const RunDev *runs, int nruns, long long max_cells,
+                             void *const lamE[3], void *const lamB[3], void *const lamJ[3])
+{
+    const int nt = 256;
+    dim3 grid((unsigned)((max_cells + nt - 1) / nt), (unsigned)nruns);
+    R *e[3], *b[3], *j[3];
+    for (int c = 0; c < 3; ++c) {
+        e[c] = (R *)lamE[c];
+        b[c] = (R *)lamB[c];
+        j[c] = lamJ ? (R *)lamJ[c] : nullptr;
+    }
+    if (which == 2)
+        k_adj_yee_e<DIM, R><<<grid, nt, 0, st>>>(runs, e[0], e[1], e[2], b[0], b[1], b[2], j[0], j[1], j[2]);
+    else
+        k_adj_yee_b<DIM, R><<<grid, nt, 0, st>>>(runs, b[0], b[1], b[2], e[0], e[1], e[2]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_yee(int dims, int prec, int which, cudaStream_t st, const RunDev *runs, int nruns,
+                           long long max_cells, void *const lamE[3], void *const lamB[3], void *const lamJ[3])
+{
+    if (dims == 3)
+        return prec == 0 ? adj_yee_t<3, double>(which, st, runs, nruns, max_cells, lamE, lamB, lamJ)
+                         : adj_yee_t<3, float>(which, st, runs, nruns, max_cells, lamE, lamB, lamJ);
+    return prec == 0 ? adj_yee_t<2, double>(which, st, runs, nruns, max_cells, lamE, lamB, lamJ)
+                     : adj_yee_t<2, float>(which, st, runs, nruns, max_cells, lamE, lamB, lamJ);
+}
+
+template <int DIM, typename R>
+static cudaError_t adj_part_t(cudaStream_t st, const RunDev *runs, const GroupDev *groups, const long long *gbase,
+                              int ngroups, long long total, const PoolBuf &P, void *const E[3], void *const B1[3],
+                              void *const lamJ[3], void *const lamE[3], void *const lamB1[3], void *const lamx[3],
+                              void *const lamw[3])
+{
+    AdjArgs<R> a;
+    a.runs = runs;
+    a.groups = groups;
+    a.group_base = gbase;
+    a.ngroups = ngroups;
+    a.total = total;
+    a.P.cell = P.cell;
+    a.P.id = P.id;
+    for (int c = 0; c < 3; ++c) {
+        a.P.off[c] = (R *)P.off[c];
+        a.P.w[c] = (R *)P.w[c];
+        a.E[c] = (const R *)E[c];
+        a.B1[c] = (const R *)B1[c];
+        a.lamJ[c] = (const R *)lamJ[c];
+        a.lamE[c] = (R *)lamE[c];
+        a.lamB1[c] = (R *)lamB1[c];
+        a.lamx[c] = (R *)lamx[c];
+        a.lamw[c] = (R *)lamw[c];
+    }
+    if (total <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (total + 255) / 256;
+    if (blocks > 16LL * sms) blocks = 16LL * sms;
+    k_particles_adj<DIM, R><<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_particles_adj(int dims, int prec, cudaStream_t st, const RunDev *runs, const GroupDev *groups,
+                                 const long long *gbase, int ngroups, long long total, const PoolBuf &P,
+                                 void *const E[3], void *const B1[3], void *const lamJ[3], void *const lamE[3],
+                                 void *const lamB1[3], void *const lamx[3], void *const lamw[3])
+{
+    if (dims == 3)
+        return prec == 0 ? adj_part_t<3, double>(st, runs, groups, gbase, ngroups, total, P, E, B1, lamJ, lamE, lamB1,
+                                                 lamx, lamw)
+                         : adj_part_t<3, float>(st, runs, groups, gbase, ngroups, total, P, E, B1, lamJ, lamE, lamB1,
+                                                lamx, lamw);
+    return prec == 0 ? adj_part_t<2, double>(st, runs, groups, gbase, ngroups, total, P, E, B1, lamJ, lamE, lamB1,
+                                             lamx, lamw)
+                     : adj_part_t<2, float>(st, runs, groups, gbase, ngroups, total, P, E, B1, lamJ, lamE, lamB1, lamx,
+                                            lamw);
+}
+
+}  // namespace pic

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstddef>
 #include <algorithm>
 #include <array>
 #include <new>
@@ -371,6 +372,11 @@ void destroy_grid(pic_grid *g)
     dfree(g->d_err);
     dfree(g->stage);
     dfree(g->d_run_cell_base);
+    for (int c = 0; c < 3; ++c) {
+        dfree(g->adj_B1[c]);
+        dfree(g->adj_lamJ[c]);
+        dfree(g->adj_lamB1[c]);
+    }
     graph_drop(g);
     prof_clear(g);
     for (auto e : g->prof_free) cudaEventDestroy(e);
@@ -1005,5 +1011,166 @@ int pic_diagnostics_run(pic_grid *g, int run, pic_diag *out)
 }
 
 int pic_diagnostics(pic_grid *g, pic_diag *out) { return pic_diagnostics_run(g, 0, out); }
+
+// ---- state snapshots -----------------------------------------------------------
+struct StateHeader {
+    char magic[4];            // "PICS"
+    int version;              // 1
+    int dims, prec, ngroups, steps_since_sort;
+    long long total, total_cells;
+    unsigned checksum;        // FNV-1a of the bytes before this field
+    int pad;
+};
+
+static unsigned fnv1a(const void *p, size_t n)
+{
+    const unsigned char *b = (const unsigned char *)p;
+    unsigned h = 2166136261u;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 16777619u;
+    }
+    return h;
+}
+
+static void fill_header(const pic_grid *g, StateHeader &h)
+{
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "PICS", 4);
+    h.version = 1;
+    h.dims = g->dims;
+    h.prec = g->prec;
+    h.ngroups = (int)g->groups.size();
+    h.steps_since_sort = g->steps_since_sort;
+    h.total = g->total;
+    h.total_cells = g->total_cells;
+    h.checksum = fnv1a(&h, offsetof(StateHeader, checksum));
+}
+
+long long pic_state_bytes(pic_grid *g)
+{
+    if (!g) return 0;
+    const long long es = (long long)elem(g);
+    return (long long)sizeof(StateHeader) + g->total * (8 + es * (g->dims + 3)) + g->total_cells * es * 6;
+}
+
+int pic_state_save(pic_grid *g, void *dst, int on_device)
+{
+    if (!g || !dst) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    StateHeader h;
+    fill_header(g, h);
+    const cudaMemcpyKind k = kind_out(on_device);
+    const size_t es = elem(g);
+    char *o = (char *)dst;
+    CK(cudaMemcpyAsync(o, &h, sizeof(h), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, g->stream),
+       "state header");
+    o += sizeof(h);
+    auto put = [&](const void *src, size_t bytes) -> cudaError_t {
+        cudaError_t e = bytes ? cudaMemcpyAsync(o, src, bytes, k, g->stream) : cudaSuccess;
+        o += bytes;
+        return e;
+    };
+    CK(put(g->pool.cell, sizeof(int) * g->total), "state cells");
+    CK(put(g->pool.id, sizeof(int) * g->total), "state ids");
+    for (int a = 0; a < g->dims; ++a) CK(put(g->pool.off[a], es * g->total), "state offsets");
+    for (int a = 0; a < 3; ++a) CK(put(g->pool.w[a], es * g->total), "state momenta");
+    for (int a = 0; a < 3; ++a) CK(put(g->E[a], es * g->total_cells), "state E");
+    for (int a = 0; a < 3; ++a) CK(put(g->B[a], es * g->total_cells), "state B");
+    CK(cudaStreamSynchronize(g->stream), "state save");
+    return PIC_OK;
+}
+
+int pic_state_restore(pic_grid *g, const void *src, int on_device)
+{
+    if (!g || !src) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    StateHeader h;
+    CK(cudaMemcpy(&h, src, sizeof(h), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "state header");
+    if (memcmp(h.magic, "PICS", 4) != 0 || h.version != 1 || h.checksum != fnv1a(&h, offsetof(StateHeader, checksum)))
+        return fail(PIC_ERR_INVALID_ARG, "not a libpic state snapshot (bad magic, version or header checksum)");
+    if (h.dims != g->dims || h.prec != g->prec || h.total != g->total || h.total_cells != g->total_cells ||
+        h.ngroups != (int)g->groups.size())
+        return fail(PIC_ERR_INVALID_ARG, "state snapshot does not match this grid's layout");
+    const cudaMemcpyKind k = kind_in(on_device);
+    const size_t es = elem(g);
+    const char *o = (const char *)src + sizeof(h);
+    auto get = [&](void *dstp, size_t bytes) -> cudaError_t {
+        cudaError_t e = bytes ? cudaMemcpyAsync(dstp, o, bytes, k, g->stream) : cudaSuccess;
+        o += bytes;
+        return e;
+    };
+    CK(get(g->pool.cell, sizeof(int) * g->total), "state cells");
+    CK(get(g->pool.id, sizeof(int) * g->total), "state ids");
+    for (int a = 0; a < g->dims; ++a) CK(get(g->pool.off[a], es * g->total), "state offsets");
+    for (int a = 0; a < 3; ++a) CK(get(g->pool.w[a], es * g->total), "state momenta");
+    for (int a = 0; a < 3; ++a) CK(get(g->E[a], es * g->total_cells), "state E");
+    for (int a = 0; a < 3; ++a) CK(get(g->B[a], es * g->total_cells), "state B");
+    int rc = do_sort(g);
+    if (rc != PIC_OK) return rc;
+    for (auto &r : g->have_ref) r = 0;
+    CK(cudaStreamSynchronize(g->stream), "state restore");
+    return PIC_OK;
+}
+
+// ---- adjoint ---------------------------------------------------------------------
+static int adj_scratch(pic_grid *g)
+{
+    if (g->adj_B1[0]) return PIC_OK;
+    for (int c = 0; c < 3; ++c) {
+        CK(dalloc_bytes(&g->adj_B1[c], g->total_cells * elem(g)), "adjoint scratch");
+        CK(dalloc_bytes(&g->adj_lamJ[c], g->total_cells * elem(g)), "adjoint scratch");
+        CK(dalloc_bytes(&g->adj_lamB1[c], g->total_cells * elem(g)), "adjoint scratch");
+    }
+    return PIC_OK;
+}
+
+static long long max_run_cells(const pic_grid *g)
+{
+    long long m = 0;
+    for (auto &r : g->runs) m = std::max(m, (long long)r.dev.n[0] * r.dev.n[1] * r.dev.n[2]);
+    return m;
+}
+
+int pic_adjoint_yee_half_B(pic_grid *g, void *const lamB[3], void *lamE[3])
+{
+    if (!g || !lamB || !lamE) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    CK(launch_adj_yee(g->dims, g->prec, 1, g->stream, g->d_runs, (int)g->runs.size(), max_run_cells(g), lamE, lamB,
+                      nullptr),
+       "adjoint B half step");
+    launch_count_add(g, 1);
+    return PIC_OK;
+}
+
+int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], void *lamw[3])
+{
+    if (!g || !lamE || !lamB || !lamx || !lamw) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    for (int c = 0; c < 3; ++c)
+        if (!lamE[c] || !lamB[c] || !lamw[c] || (c < g->dims && !lamx[c]))
+            return fail(PIC_ERR_INVALID_ARG, "null adjoint component");
+    int rc = adj_scratch(g);
+    if (rc != PIC_OK) return rc;
+    const size_t fb = g->total_cells * elem(g);
+    const long long mc = max_run_cells(g);
+    const int nr = (int)g->runs.size();
+    // B^n = B^{n-1/2} - (1/2) C_B E^n into scratch (the state is not modified)
+    for (int c = 0; c < 3; ++c) CK(cudaMemcpyAsync(g->adj_B1[c], g->B[c], fb, cudaMemcpyDeviceToDevice, g->stream), "B1");
+    CK(launch_yee(g->prec, PIC_B_HALF, 0, g->stream, g->d_runs, nr, mc, g->E, g->adj_B1, g->J, g->dims), "B1");
+    // (E step)^T, (second B half step)^T
+    CK(launch_adj_yee(g->dims, g->prec, 2, g->stream, g->d_runs, nr, mc, lamE, lamB, g->adj_lamJ), "adjoint E step");
+    CK(launch_adj_yee(g->dims, g->prec, 1, g->stream, g->d_runs, nr, mc, lamE, lamB, nullptr), "adjoint B half step");
+    for (int c = 0; c < 3; ++c)
+        CK(cudaMemcpyAsync(g->adj_lamB1[c], lamB[c], fb, cudaMemcpyDeviceToDevice, g->stream), "lam B1");
+    // particles^T
+    CK(launch_particles_adj(g->dims, g->prec, g->stream, g->d_runs, g->d_groups, g->d_group_base,
+                            (int)g->groups.size(), g->total, g->pool, g->E, g->adj_B1, g->adj_lamJ, lamE, g->adj_lamB1,
+                            lamx, lamw),
+       "adjoint particles");
+    // (first B half step)^T
+    CK(launch_adj_yee(g->dims, g->prec, 1, g->stream, g->d_runs, nr, mc, lamE, g->adj_lamB1, nullptr),
+       "adjoint B half step");
+    for (int c = 0; c < 3; ++c)
+        CK(cudaMemcpyAsync(lamB[c], g->adj_lamB1[c], fb, cudaMemcpyDeviceToDevice, g->stream), "lam B");
+    launch_count_add(g, 6);
+    return PIC_OK;
+}
 
 }  // extern "C"

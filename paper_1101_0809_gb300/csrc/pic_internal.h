@@ -103,6 +103,16 @@ constexpr int kDiagResults = 12;
 
 void set_last_error(const char *msg);
 
+// Adjoint kernels (pic_adjoint.cu).  which = 2: transpose of the E step
+// (lamJ = -4 pi dt lamE, lamB += C_E^T lamE); which = 1: transpose of the B half
+// step (lamE += (-(1/2) C_B)^T lamB).
+cudaError_t launch_adj_yee(int dims, int prec, int which, cudaStream_t st, const RunDev *runs, int nruns,
+                           long long max_cells, void *const lamE[3], void *const lamB[3], void *const lamJ[3]);
+cudaError_t launch_particles_adj(int dims, int prec, cudaStream_t st, const RunDev *runs, const GroupDev *groups,
+                                 const long long *gbase, int ngroups, long long total, const PoolBuf &P,
+                                 void *const E[3], void *const B1[3], void *const lamJ[3], void *const lamE[3],
+                                 void *const lamB1[3], void *const lamx[3], void *const lamw[3]);
+
 }  // namespace pic
 
 struct pic_grid {
@@ -165,6 +175,11 @@ struct pic_grid {
     bool profiling = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_marks;
     std::vector<cudaEvent_t> prof_free;
+
+    // adjoint scratch: B^n, lamJ, lam B1 (field-sized, allocated on first use)
+    void *adj_B1[3] = {nullptr, nullptr, nullptr};
+    void *adj_lamJ[3] = {nullptr, nullptr, nullptr};
+    void *adj_lamB1[3] = {nullptr, nullptr, nullptr};
 
     // staging for host-pointer particle loads (grown, never shrunk)
     double *stage = nullptr;

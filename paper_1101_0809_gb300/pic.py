@@ -324,6 +324,38 @@ def pic_step_graph(g, nsteps=1):
     _check(_lib.pic_step_graph(g, nsteps))
 
 
+_lib.pic_state_bytes.argtypes = [_VP]
+_lib.pic_state_bytes.restype = C.c_longlong
+_lib.pic_state_save.argtypes = [_VP, _VP, C.c_int]
+_lib.pic_state_restore.argtypes = [_VP, _VP, C.c_int]
+_lib.pic_adjoint_step.argtypes = [_VP, _VP3, _VP3, _VP3, _VP3]
+_lib.pic_adjoint_yee_half_B.argtypes = [_VP, _VP3, _VP3]
+
+
+def pic_state_bytes(g):
+    return int(_lib.pic_state_bytes(g))
+
+
+def pic_state_save(g, dst):
+    """dst: a uint8 numpy array (host) or CUDA tensor of pic_state_bytes(g) bytes."""
+    p, d = _addr(dst)
+    _check(_lib.pic_state_save(g, p, d))
+
+
+def pic_state_restore(g, src):
+    p, d = _addr(src)
+    _check(_lib.pic_state_restore(g, p, d))
+
+
+def pic_adjoint_step(g, lamE, lamB, lamx, lamw):
+    """All arguments are sequences of 3 CUDA tensors of the grid's precision."""
+    _check(_lib.pic_adjoint_step(g, _triple(lamE)[0], _triple(lamB)[0], _triple(lamx)[0], _triple(lamw)[0]))
+
+
+def pic_adjoint_yee_half_B(g, lamB, lamE):
+    _check(_lib.pic_adjoint_yee_half_B(g, _triple(lamB)[0], _triple(lamE)[0]))
+
+
 PIC_NOALLOC_MAX_PARTICLES = 1048576
 _lib.pic_tile_sort_perm_noalloc.argtypes = [_VP, C.c_longlong, C.c_int, C.c_int * 3, C.c_int * 3, _VP, _VP, _VP]
 

@@ -1,0 +1,188 @@
+"""GPU discrete adjoint: one adjoint step against the oracle's hand-derived
+adjoint on the same state, the gradient of a window field energy after 20 steps
+with respect to the density-perturbation amplitude against the oracle adjoint
+and against central finite differences of the GPU forward run, and state
+snapshots (checkpoint/restart)."""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1101_0809_gb300 import workloads as W
+from pichelpers import close, fp64_field_tol, oracle_grid
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1101_0809_gb300 import build as B
+    B.build()
+    from paper_1101_0809_gb300 import pic
+    return pic, torch
+
+
+def _state_after(wl, steps):
+    g = oracle_grid(wl)
+    sp = [O.Species(s.q, s.m, s.weight, s.x.copy(), s.w.copy()) for s in wl.species]
+    E, B, J = g.zeros(), g.zeros(), g.zeros()
+    for _ in range(steps):
+        O.step(g, E, B, J, sp)
+    return g, sp, E, B
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_adjoint_step_matches_oracle(env, which):
+    P, torch = env
+    if which == "2d":
+        wl = W.c4_perturbed2d(n=32, ppc=8, steps=3)
+    else:
+        wl = W.thermal_plasma("3D small", 3, (20, 18, 22), 2, 0.1, 3, W.SEED_BASE + 11, ions=1836.0,
+                              tile=(8, 8, 8), dt_courant=0.45)
+    g, sp, E, B = _state_after(wl, 3)
+    desc = P.make_desc(wl.dims, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP64, tile=wl.tile, rho_bg=wl.rho_bg)
+    grid = P.Grid(desc)
+    grid.set_fields(E, B)
+    for s, o in enumerate(sp):
+        grid.load(s, o.q, o.m, o.weight, o.x, o.w)
+    rng = np.random.default_rng(77)
+    lamE = [rng.normal(size=g.shape) for _ in range(3)]
+    lamB = [rng.normal(size=g.shape) for _ in range(3)]
+    lx = [rng.normal(size=(3, o.x.shape[1])) for o in sp]
+    lw = [rng.normal(size=(3, o.x.shape[1])) for o in sp]
+    if wl.dims == 2:
+        for a in lx:
+            a[2] = 0.0
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    gE = [dev(a) for a in lamE]
+    gB = [dev(a) for a in lamB]
+    gx = [dev(np.concatenate([a[c] for a in lx])) for c in range(3)]
+    gw = [dev(np.concatenate([a[c] for a in lw])) for c in range(3)]
+    torch.cuda.synchronize()
+    P.pic_adjoint_step(grid.h, gE, gB, gx, gw)
+    torch.cuda.synchronize()
+    O.step_adj(g, E, B, sp, lamE, lamB, lx, lw)
+    tol = 1e-11
+    for a in range(3):
+        close(gE[a].cpu().numpy(), lamE[a], tol, f"lamE[{a}]")
+        close(gB[a].cpu().numpy(), lamB[a], tol, f"lamB[{a}]")
+        close(gw[a].cpu().numpy(), np.concatenate([v[a] for v in lw]), tol, f"lamw[{a}]")
+        if a < wl.dims:
+            close(gx[a].cpu().numpy(), np.concatenate([v[a] for v in lx]), tol, f"lamx[{a}]")
+    grid.close()
+
+
+N_CELLS, PPC, STEPS, AMP, WIN = 32, 16, 20, 0.05, ((12, 20), (12, 20))
+
+
+def _run(P, torch, precision):
+    from paper_1101_0809_gb300.adjoint import DifferentiableRun
+    wl = W.c4_perturbed2d(n=N_CELLS, ppc=PPC, amplitude=AMP, steps=STEPS)
+    desc = P.make_desc(2, wl.n, wl.d, wl.dt, wl.c, precision, tile=(16, 16, 1), rho_bg=wl.rho_bg)
+    sp = wl.species[0]
+    return DifferentiableRun(desc, sp.q, sp.m, sp.weight, STEPS, WIN, checkpoint_every=5)
+
+
+def _xu():
+    wl = W.c4_perturbed2d(n=N_CELLS, ppc=PPC, amplitude=0.0, steps=STEPS)
+    return wl.species[0].x.copy(), wl.species[0].w.copy()
+
+
+def _gpu_grad_A(P, torch, precision):
+    from paper_1101_0809_gb300.adjoint import WindowEnergyLoss
+    run = _run(P, torch, precision)
+    xu, w0 = _xu()
+    k = 2 * math.pi * 2 / N_CELLS
+    A = torch.tensor(AMP, dtype=torch.float64, requires_grad=True)
+    xu_t = torch.from_numpy(xu)
+    x0 = xu_t.clone()
+    x0[0] = torch.remainder(xu_t[0] - (A / k) * torch.sin(k * xu_t[0]), float(N_CELLS))
+    L = WindowEnergyLoss.apply(x0, torch.from_numpy(w0), run)
+    L.backward()
+    return float(L), float(A.grad), run
+
+
+def _oracle_grad_A():
+    import importlib.util
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("adjpins", os.path.join(here, "test_oracle_adjoint.py"))
+    m = importlib.util.module_from_spec(spec)
+    sys.modules["adjpins"] = m
+    spec.loader.exec_module(m)
+    wl, g = m.setup(AMP)
+    wl_u, _ = m.setup(0.0)
+    k = 2 * math.pi * 2 / N_CELLS
+    dxdA = np.zeros_like(wl_u.species[0].x)
+    dxdA[0] = -np.sin(k * wl_u.species[0].x[0]) / k
+    L, lx, lw = m.adjoint(wl, g, wl.species[0].x.copy(), wl.species[0].w.copy())
+    return L, float((lx * dxdA).sum())
+
+
+def test_fp64_gradient_matches_oracle_adjoint_and_central_fd(env):
+    P, torch = env
+    L, dLdA, run = _gpu_grad_A(P, torch, P.PIC_FP64)
+    Lo, go = _oracle_grad_A()
+    assert L == pytest.approx(Lo, rel=1e-10)
+    assert dLdA == pytest.approx(go, rel=1e-9)
+    # central differences of the GPU forward run itself
+    xu, w0 = _xu()
+    k = 2 * math.pi * 2 / N_CELLS
+    h = 1e-7 * AMP
+
+    def loss(A):
+        x0 = xu.copy()
+        x0[0] = np.mod(xu[0] - (A / k) * np.sin(k * xu[0]), float(N_CELLS))
+        return run.forward(torch.from_numpy(x0), torch.from_numpy(w0))
+
+    fd = (loss(AMP + h) - loss(AMP - h)) / (2 * h)
+    assert dLdA == pytest.approx(fd, rel=1e-6)
+    run.grid.close()
+
+
+def test_fp32_gradient_against_fp64(env):
+    P, torch = env
+    L32, g32, r32 = _gpu_grad_A(P, torch, P.PIC_FP32)
+    L64, g64, r64 = _gpu_grad_A(P, torch, P.PIC_FP64)
+    assert L32 == pytest.approx(L64, rel=1e-3)
+    assert g32 == pytest.approx(g64, rel=1e-2)
+    r32.grid.close()
+    r64.grid.close()
+
+
+def test_state_snapshot_restarts_the_same_run(env):
+    P, torch = env
+    wl = W.c0_small2d(steps=6)
+    desc = P.make_desc(2, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP64, tile=wl.tile, rho_bg=wl.rho_bg)
+    grid = P.Grid(desc)
+    sp = wl.species[0]
+    grid.load(0, sp.q, sp.m, sp.weight, sp.x, sp.w)
+    P.pic_step(grid.h, 2)
+    blob = np.empty(P.pic_state_bytes(grid.h), dtype=np.uint8)
+    P.pic_state_save(grid.h, blob)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "state.bin")
+        blob.tofile(path)
+        P.pic_step(grid.h, 4)
+        E1, B1, J1 = grid.get_fields()
+        _, _, w1, id1 = grid.particles(0)
+        back = np.fromfile(path, dtype=np.uint8)
+    P.pic_state_restore(grid.h, back)
+    P.pic_step(grid.h, 4)
+    E2, B2, J2 = grid.get_fields()
+    _, _, w2, id2 = grid.particles(0)
+    for a in range(3):
+        close(E2[a], E1[a], 1e-12, f"E[{a}]")
+        close(B2[a], B1[a], 1e-12, f"B[{a}]")
+        close(w2[a][np.argsort(id2)], w1[a][np.argsort(id1)], 1e-12, f"w[{a}]")
+    bad = back.copy()
+    bad[0] = ord("X")
+    with pytest.raises(P.PicError) as e:
+        P.pic_state_restore(grid.h, bad)
+    assert e.value.code == P.PIC_ERR_INVALID_ARG
+    grid.close()
