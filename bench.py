@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--batch-runs", type=int, default=256)
     return ap.parse_args()
 
@@ -294,6 +296,67 @@ def batched_arm(P, W, torch, args, dist):
             "autotune_table": [[c, t] for c, t, _ in table], "gpu_launches": launches}
 
 
+def adjoint_arm(P, W, torch, args):
+    """Differentiable 2D3V run: 256^2 periodic grid, 16 e-/cell, v_th = 0.05c,
+    density perturbation A = 0.05 in mode k = 2; loss = field energy in a 32x32
+    probe window after `adj_steps` steps; gradient with respect to A and the
+    initial momenta by the discrete adjoint with checkpoints every 20 steps.
+    Forward and forward+adjoint throughput in FP32 and FP64, and the FP32
+    gradient against FP64 central differences of the loss on the GPU."""
+    from paper_1101_0809_gb300.adjoint import DifferentiableRun, WindowEnergyLoss
+    n, ppc, amp, mode = 256, 16, 0.05, 2
+    steps = args.adj_steps
+    win = ((112, 144), (112, 144))
+    wl0 = W.c4_perturbed2d(n=n, ppc=ppc, amplitude=0.0, mode=mode, steps=steps)
+    xu, w0 = wl0.species[0].x.copy(), wl0.species[0].w.copy()
+    k = 2 * math.pi * mode / n
+    sp = wl0.species[0]
+
+    def x_of(A):
+        x = xu.copy()
+        x[0] = np.mod(xu[0] - (A / k) * np.sin(k * xu[0]), float(n))
+        x[0][x[0] >= n] = 0.0
+        return x
+
+    out = {"workload": f"2D3V {n}^2 periodic, {ppc} e-/cell, v_th = 0.05c, perturbation A = {amp} k = {mode}; "
+                       f"loss = field energy in a 32x32 window after {steps} steps; checkpoints every 20 steps",
+           "particles": wl0.n_particles, "steps": steps}
+    for name, prec in (("fp32", P.PIC_FP32), ("fp64", P.PIC_FP64)):
+        desc = P.make_desc(2, wl0.n, wl0.d, wl0.dt, wl0.c, prec, tile=(16, 16, 1), rho_bg=wl0.rho_bg)
+        # warm-up: a short differentiable run loads every kernel and allocator path once
+        warm = DifferentiableRun(desc, sp.q, sp.m, sp.weight, 20, win, checkpoint_every=20)
+        Lw = WindowEnergyLoss.apply(torch.from_numpy(x_of(amp)), torch.from_numpy(w0).requires_grad_(), warm)
+        Lw.backward()
+        torch.cuda.synchronize()
+        warm.grid.close()
+        run = DifferentiableRun(desc, sp.q, sp.m, sp.weight, steps, win, checkpoint_every=20)
+        A = torch.tensor(amp, dtype=torch.float64, requires_grad=True)
+        xu_t = torch.from_numpy(xu)
+        x0 = xu_t.clone()
+        x0[0] = torch.remainder(xu_t[0] - (A / k) * torch.sin(k * xu_t[0]), float(n))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = WindowEnergyLoss.apply(x0, torch.from_numpy(w0), run)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        npart = wl0.n_particles
+        out[name] = {"fwd": npart * steps / (t1 - t0), "fwd_adj": npart * steps / (t2 - t0), "unit": UNIT,
+                     "fwd_s": t1 - t0, "adj_s": t2 - t1, "loss": float(L.detach()), "dL_dA": float(A.grad.item())}
+        if name == "fp64":
+            h = 1e-7 * amp
+            lp = run.forward(torch.from_numpy(x_of(amp + h)), torch.from_numpy(w0))
+            lm = run.forward(torch.from_numpy(x_of(amp - h)), torch.from_numpy(w0))
+            out["fp64_central_fd_dL_dA"] = (lp - lm) / (2 * h)
+        run.grid.close()
+    fd = out["fp64_central_fd_dL_dA"]
+    out["fp32_grad_rel_err_vs_fp64_fd"] = abs(out["fp32"]["dL_dA"] - fd) / abs(fd)
+    out["fp64_grad_rel_err_vs_fp64_fd"] = abs(out["fp64"]["dL_dA"] - fd) / abs(fd)
+    return out
+
+
 def our_arm(args):
     import torch
     rank, local, world = dist_env()
@@ -409,6 +472,9 @@ def our_arm(args):
     batched = None
     if not args.no_batch:
         batched = batched_arm(P, W, torch, args, dist)
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        adjoint = adjoint_arm(P, W, torch, args)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -420,7 +486,7 @@ def our_arm(args):
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                           "l2": "inputs larger than L2 (3.76 GB of particle SoA per replica); no flush"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-               "fp64": fp64, "batched": batched}
+               "fp64": fp64, "batched": batched, "adjoint": adjoint}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
