@@ -75,7 +75,18 @@ typedef struct {
     int particles_per_block;/* particles per thread block work item (0 = default 8192) */
     double rho_bg;          /* uniform immobile background charge density (enters rho only) */
     void *cuda_stream;      /* cudaStream_t to enqueue on; NULL = the legacy default stream */
+    int sort_order;         /* PIC_SORT_BANKED (0, default) or PIC_SORT_STABLE (1), see pic_sort */
 } pic_grid_desc;
+
+/* Order of the tile sort.  Both sort by tile key first.  PIC_SORT_STABLE keeps
+ * the input order inside a tile.  PIC_SORT_BANKED orders a tile's particles by
+ * (r, b): b = base mod 32 with base = (i-ox+h+2) + P0*((j-oy+h+2) + P1*(k-oz+h+2))
+ * (no k term in 2D) the shared-memory bank of the particle's cell in the
+ * current tile of its tile (tile origin (ox, oy, oz), halo h, tile pitches
+ * P0, P1 as reported by pic_tile_layout), and r the number of earlier
+ * particles (input order) of the same tile with the same b; so that 32
+ * consecutive particles fall on 32 different banks. */
+enum { PIC_SORT_BANKED = 0, PIC_SORT_STABLE = 1 };
 
 /* One species.  The macro-particle charge is q_p = weight*q, its mass m_p = weight*m;
  * the push uses q/m (Eq. 1), the deposit q_p/V (Eq. xi). */
@@ -130,6 +141,10 @@ int pic_get_fields(pic_grid *g, void *E[3], void *B[3], void *J[3], int on_devic
 int pic_load_particles(pic_grid *g, int species, const pic_species_desc *sp, long long n,
                        const double *const x[3], const double *const w[3], int on_device);
 
+/* Layout chosen at creation: out[0..2] tile extents, out[3] halo, out[4..5] the
+ * x and y pitch of the shared-memory field and current tiles. */
+int pic_tile_layout(pic_grid *g, int out[6]);
+
 /* Number of particles of a species (0 if not loaded). */
 long long pic_num_particles(pic_grid *g, int species);
 
@@ -161,7 +176,7 @@ int pic_yee_update(pic_grid *g, int which);
  * tile-sorted particles, B half step, E full step. */
 int pic_step(pic_grid *g, int nsteps);
 
-/* Stable counting sort of all particles by tile (ties keep their order). */
+/* Sort all particles by tile (order inside a tile: see PIC_SORT_BANKED). */
 int pic_sort(pic_grid *g);
 
 /* FP64 diagnostics (see pic_diag).  Synchronizes the grid's stream. */

@@ -249,7 +249,8 @@ int do_sort(pic_grid *g)
     int nl = 0;
     cudaError_t e = sort_and_build_items(g->prec, g->dims, g->stream, g->total, g->pool, g->pool_alt, g->d_groups,
                                          g->d_group_base, (int)g->groups.size(), g->d_runs, g->total_tiles, g->sort,
-                                         g->tile_start, g->item_scan, g->items, g->n_items, g->ppi, &nl);
+                                         g->tile_start, g->item_scan, g->items, g->n_items, g->ppi, g->halo,
+                                         g->sort_order == PIC_SORT_BANKED ? 1 : 0, &nl);
     launch_count_add(g, nl);
     if (e != cudaSuccess) return cuda_fail(e, "tile sort");
     if (g->total > 0 && !g->groups.empty()) std::swap(g->pool, g->pool_alt);
@@ -264,7 +265,7 @@ int launch_part(pic_grid *g, int mode)
     ProfScope ps(g, PIC_PROF_PARTICLES);
     cudaError_t e = launch_particles(g->dims, g->prec, mode, g->stream, g->items, g->n_items, g->max_items, g->d_runs,
                                      g->d_groups, g->pool, g->E, g->B, g->J, g->old_cell, g->old_off, g->halo,
-                                     g->tile[0], g->tile[1], g->tile[2], g->d_err);
+                                     g->tile[0], g->tile[1], g->tile[2], g->d_err, g->pitch[0], g->pitch[1]);
     launch_count_add(g, g->max_items > 0 ? 1 : 0);
     if (e != cudaSuccess) return cuda_fail(e, "particle kernel");
     return PIC_OK;
@@ -280,6 +281,45 @@ int launch_fields(pic_grid *g, int which, int zero_j)
     launch_count_add(g, 1);
     if (e != cudaSuccess) return cuda_fail(e, "Yee kernel");
     return PIC_OK;
+}
+
+// Pitches of the shared-memory tiles: the smallest x pitch >= Tx + 2h + 4 and
+// y pitch >= Ty + 2h + 4 (up to 32) that spread the tile's cells most evenly over
+// the 32 shared-memory banks (so that the banked sort order keeps whole rounds
+// of 32 distinct banks), preferring layouts that leave room for two blocks per
+// SM.  In 2D only the x pitch matters.
+static void choose_pitch(pic_grid *g)
+{
+    const int h = g->halo, T0 = g->tile[0], T1 = g->tile[1], T2 = g->dims == 3 ? g->tile[2] : 1;
+    const int je0 = T0 + 2 * h + 4, je1 = T1 + 2 * h + 4;
+    const size_t es = g->prec == PIC_FP64 ? 8 : 4;
+    long long best_key = -1;
+    for (int p0 = je0; p0 <= std::max(je0, 32); ++p0) {
+        for (int p1 = je1; p1 <= (g->dims == 3 ? std::max(je1, 32) : je1); ++p1) {
+            int cnt[32] = {0};
+            for (int k = 0; k < T2; ++k)
+                for (int j = 0; j < T1; ++j)
+                    for (int i = 0; i < T0; ++i) {
+                        const int base = (i + h + 2) + p0 * ((j + h + 2) + (g->dims == 3 ? p1 * (k + h + 2) : 0));
+                        ++cnt[base & 31];
+                    }
+            int mn = cnt[0], mx = cnt[0];
+            for (int b = 1; b < 32; ++b) {
+                mn = std::min(mn, cnt[b]);
+                mx = std::max(mx, cnt[b]);
+            }
+            const long long fe = (long long)p0 * p1 * (g->dims == 3 ? T2 + 2 * h + 2 : 1);
+            const long long je = (long long)p0 * p1 * (g->dims == 3 ? T2 + 2 * h + 4 : 1);
+            const long long smem = 6 * fe * (long long)es + 24 * je;
+            const long long two = smem <= 113 * 1024 ? 0 : 1;
+            const long long key = ((long long)(mx - mn) << 40) | (two << 39) | smem;
+            if (best_key < 0 || key < best_key) {
+                best_key = key;
+                g->pitch[0] = p0;
+                g->pitch[1] = p1;
+            }
+        }
+    }
 }
 
 // Validates one run descriptor.  The first run of a batch fixes the settings
@@ -316,6 +356,10 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
         g->sort_interval = d->sort_interval > 0 ? d->sort_interval : 10;
         g->ppi = d->particles_per_block > 0 ? d->particles_per_block : 8192;
         if (g->ppi > 8192) return fail(PIC_ERR_INVALID_ARG, "particles_per_block must be <= 8192");
+        if (g->ppi % 32 != 0) return fail(PIC_ERR_INVALID_ARG, "particles_per_block must be a multiple of 32");
+        if (d->sort_order != PIC_SORT_BANKED && d->sort_order != PIC_SORT_STABLE)
+            return fail(PIC_ERR_INVALID_ARG, "sort_order must be PIC_SORT_BANKED or PIC_SORT_STABLE");
+        g->sort_order = d->sort_order;
         for (int a = 0; a < 3; ++a) g->tile[a] = d->tile[a] > 0 ? d->tile[a] : (d->dims == 3 ? 8 : 16);
         if (d->dims == 2) g->tile[2] = 1;
     }
@@ -330,7 +374,10 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
                         "axis %d has %d cells; the tile (%d) plus its staged halo (%d) must fit in the grid", a, n[a],
                         t[a], 2 * g->halo + 4);
     }
+    if (first) choose_pitch(g);
     memset(&rd, 0, sizeof(rd));
+    rd.pitch[0] = g->pitch[0];
+    rd.pitch[1] = g->pitch[1];
     for (int a = 0; a < 3; ++a) {
         rd.n[a] = n[a];
         rd.tile[a] = t[a];
@@ -456,7 +503,8 @@ int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     for (int mode = 0; mode < 3; ++mode) {
-        const size_t b = particles_smem_bytes(g->dims, g->prec, mode, g->tile[0], g->tile[1], g->tile[2], g->halo);
+        const size_t b = particles_smem_bytes(g->dims, g->prec, mode, g->tile[0], g->tile[1], g->tile[2], g->halo,
+                                              g->pitch[0], g->pitch[1]);
         if ((long long)b > optin) {
             destroy_grid(g);
             return fail(PIC_ERR_INVALID_ARG, "tile %dx%dx%d with halo %d needs %zu B of shared memory (> %d)",
@@ -475,6 +523,18 @@ int pic_create_grid(const pic_grid_desc *desc, pic_grid **out)
 }
 
 int pic_num_runs(pic_grid *g) { return g ? (int)g->runs.size() : 0; }
+
+int pic_tile_layout(pic_grid *g, int out[6])
+{
+    if (!g || !out) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    out[0] = g->tile[0];
+    out[1] = g->tile[1];
+    out[2] = g->tile[2];
+    out[3] = g->halo;
+    out[4] = g->pitch[0];
+    out[5] = g->pitch[1];
+    return PIC_OK;
+}
 
 int pic_destroy(pic_grid *g)
 {
@@ -850,7 +910,8 @@ static int persistent_step(pic_grid *g)
     ProfScope ps(g, PIC_PROF_PARTICLES);
     cudaError_t e = launch_step_persistent(g->dims, g->prec, g->stream, g->items, g->n_items, g->d_runs, g->d_groups,
                                            g->pool, g->E, g->B, g->J, g->halo, g->tile[0], g->tile[1], g->tile[2],
-                                           g->d_err, (int)g->runs.size(), g->d_run_cell_base, &g->persist_blocks, 1);
+                                           g->d_err, (int)g->runs.size(), g->d_run_cell_base, &g->persist_blocks, 1,
+                                           g->pitch[0], g->pitch[1]);
     launch_count_add(g, 1);
     if (e != cudaSuccess) return cuda_fail(e, "persistent step");
     g->steps_since_sort += 1;
@@ -880,7 +941,7 @@ static int capture_graph(pic_grid *g)
         cudaError_t ep = launch_step_persistent(g->dims, g->prec, g->stream, g->items, g->n_items, g->d_runs,
                                                 g->d_groups, g->pool, g->E, g->B, g->J, g->halo, g->tile[0],
                                                 g->tile[1], g->tile[2], g->d_err, (int)g->runs.size(),
-                                                g->d_run_cell_base, &g->persist_blocks, 0);
+                                                g->d_run_cell_base, &g->persist_blocks, 0, g->pitch[0], g->pitch[1]);
         if (ep != cudaSuccess) return cuda_fail(ep, "persistent kernel set-up");
     }
     const bool prof = g->profiling;

@@ -19,6 +19,7 @@ struct RunDev {
     int n[3];             // cells per axis (n[2] = 1 in 2D)
     int tile[3];          // tile extents (tile[2] = 1 in 2D)
     int ntile[3];         // tiles per axis, ceil(n/tile)
+    int pitch[2];         // x and y pitch of the shared-memory field and current tiles
     long long cell_base;  // first cell of this run in the concatenated field arrays
     double cN[3];         // Courant numbers c*dt/d_a
     double dt, c;
@@ -294,7 +295,8 @@ struct SmemAcc {
 // FP32 form: the shared current tile accumulates in integer fixed point.
 // Shared-memory float atomics run as compare-and-swap loops on this GPU while
 // 32-bit integer atomics are native, so every contribution v is scaled by the
-// power of two `scale` (q = v*scale, exact) and split into hi = rint(q/2^16) and
+// power of two `scale` (q = v*scale, exact; the caller's prefactors carry the
+// scale) and split into hi = rint(q/2^16) and
 // lo = q - hi*2^16 (exact, |lo| <= 2^15), both rounded to integers with the
 // 1.5*2^23 magic-number trick instead of conversion instructions.  The two
 // integer sums are exact; the block converts hi*2^16 + lo back once.  The
@@ -304,11 +306,11 @@ struct FixedAcc {
     int *hi[3];
     int *lo[3];
     int base, s1, s2;
-    float scale;
+    // v arrives already scaled (the caller folds the scale into its prefactors)
     __device__ __forceinline__ void add(int a, int dx, int dy, int dz, float v) const
     {
         const float magic = 12582912.0f;   // 1.5 * 2^23
-        const float q = v * scale;
+        const float q = v;
         const float th = fmaf(q, 1.0f / 65536.0f, magic);
         const float hf = th - magic;
         const float r = fmaf(-hf, 65536.0f, q);
@@ -335,57 +337,88 @@ struct GlobalAcc {
 // Deposit one particle.  kf[a] = -(1/4)(d_a/dt) q_p/V in 3D and -(1/2)(d_a/dt) q_p/V
 // (a = x, y) with kf[2] = (1/4) q_p/V in 2D (reading of Eq. current summed
 // over the ignorable z: xi^x = -(1/2)(dx/dt) D_x Pp_y, xi^z = (1/4) u_z [Pp Pp + Pm Pm/3]).
+// Bit a of `full` is clear when no particle handled by the warp changed cell
+// along axis a: then every window's fourth cell along a carries zero weight and
+// its third face only the closure sum of Pm (zero up to rounding; the window
+// of an unshifted particle has two interior faces), and those contributions are
+// skipped.  The flag is warp-uniform, so the skip is a uniform branch.
 template <int DIM, typename R, class Acc>
 __device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, const AxisWin<R> &Y, const AxisWin<R> &Z,
-                                        const R kf[3], R uz)
+                                        const R kf[3], R uz, int full)
 {
     const R third = R(1) / R(3);
+    const bool fx = full & 1, fy = full & 2, fz = full & 4;
     if (DIM == 3) {
 #pragma unroll
         for (int wz = 0; wz < 4; ++wz) {
+            if (wz == 3 && !fz) continue;
 #pragma unroll
             for (int wy = 0; wy < 4; ++wy) {
+                if (wy == 3 && !fy) continue;
                 const R T = Y.Pp[wy] * Z.Pp[wz] + third * Y.Pm[wy] * Z.Pm[wz];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) acc.add(0, X.lo + 1 + q, Y.lo + wy, Z.lo + wz, kf[0] * X.D[q] * T);
+                for (int q = 0; q < 3; ++q) {
+                    if (q == 2 && !fx) continue;
+                    acc.add(0, X.lo + 1 + q, Y.lo + wy, Z.lo + wz, kf[0] * X.D[q] * T);
+                }
             }
         }
 #pragma unroll
         for (int wz = 0; wz < 4; ++wz) {
+            if (wz == 3 && !fz) continue;
 #pragma unroll
             for (int wx = 0; wx < 4; ++wx) {
+                if (wx == 3 && !fx) continue;
                 const R T = X.Pp[wx] * Z.Pp[wz] + third * X.Pm[wx] * Z.Pm[wz];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) acc.add(1, X.lo + wx, Y.lo + 1 + q, Z.lo + wz, kf[1] * Y.D[q] * T);
+                for (int q = 0; q < 3; ++q) {
+                    if (q == 2 && !fy) continue;
+                    acc.add(1, X.lo + wx, Y.lo + 1 + q, Z.lo + wz, kf[1] * Y.D[q] * T);
+                }
             }
         }
 #pragma unroll
         for (int wy = 0; wy < 4; ++wy) {
+            if (wy == 3 && !fy) continue;
 #pragma unroll
             for (int wx = 0; wx < 4; ++wx) {
+                if (wx == 3 && !fx) continue;
                 const R T = X.Pp[wx] * Y.Pp[wy] + third * X.Pm[wx] * Y.Pm[wy];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) acc.add(2, X.lo + wx, Y.lo + wy, Z.lo + 1 + q, kf[2] * Z.D[q] * T);
+                for (int q = 0; q < 3; ++q) {
+                    if (q == 2 && !fz) continue;
+                    acc.add(2, X.lo + wx, Y.lo + wy, Z.lo + 1 + q, kf[2] * Z.D[q] * T);
+                }
             }
         }
     } else {
 #pragma unroll
         for (int wy = 0; wy < 4; ++wy) {
+            if (wy == 3 && !fy) continue;
             const R t = kf[0] * Y.Pp[wy];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) acc.add(0, X.lo + 1 + q, Y.lo + wy, 0, t * X.D[q]);
+            for (int q = 0; q < 3; ++q) {
+                if (q == 2 && !fx) continue;
+                acc.add(0, X.lo + 1 + q, Y.lo + wy, 0, t * X.D[q]);
+            }
         }
 #pragma unroll
         for (int wx = 0; wx < 4; ++wx) {
+            if (wx == 3 && !fx) continue;
             const R t = kf[1] * X.Pp[wx];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) acc.add(1, X.lo + wx, Y.lo + 1 + q, 0, t * Y.D[q]);
+            for (int q = 0; q < 3; ++q) {
+                if (q == 2 && !fy) continue;
+                acc.add(1, X.lo + wx, Y.lo + 1 + q, 0, t * Y.D[q]);
+            }
         }
         const R kz = kf[2] * uz;
 #pragma unroll
         for (int wy = 0; wy < 4; ++wy) {
+            if (wy == 3 && !fy) continue;
 #pragma unroll
             for (int wx = 0; wx < 4; ++wx) {
+                if (wx == 3 && !fx) continue;
                 const R T = X.Pp[wx] * Y.Pp[wy] + third * X.Pm[wx] * Y.Pm[wy];
                 acc.add(2, X.lo + wx, Y.lo + wy, 0, kz * T);
             }

@@ -42,15 +42,16 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
                              const int *n_items, int max_items, const RunDev *runs, const GroupDev *groups,
                              const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
                              int *old_cell, void *const old_off[3], int halo, int max_tile_x,
-                             int max_tile_y, int max_tile_z, int *err);
-size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo);
+                             int max_tile_y, int max_tile_z, int *err, int p0, int p1);
+size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo, int p0, int p1);
 // One cooperative launch per step over every run (see k_step_persistent);
 // *grid_blocks = 0 asks for the occupancy-derived grid and returns it; launch = 0
 // only prepares (attributes and grid size), which must happen outside a capture.
 cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const WorkItem *items, const int *n_items,
                                    const RunDev *runs, const GroupDev *groups, const PoolBuf &P, void *const E[3],
                                    void *const B[3], void *const J[3], int halo, int tx, int ty, int tz, int *err,
-                                   int nruns, const long long *run_cell_base, int *grid_blocks, int launch);
+                                   int nruns, const long long *run_cell_base, int *grid_blocks, int launch, int p0,
+                                   int p1);
 cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes);
 
 cudaError_t launch_load(int prec, cudaStream_t st, long long n, const double *x0, const double *x1,
@@ -79,7 +80,7 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  const PoolBuf &dst, const GroupDev *groups, const long long *group_base_dev,
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
-                                 int particles_per_item, int *launches);
+                                 int particles_per_item, int halo, int banked, int *launches);
 
 cudaError_t radix_sort_pairs(cudaStream_t st, long long n, int nbits, unsigned *const keys[2], unsigned *const vals[2],
                              unsigned *hist, unsigned *block_sums, int *cur_out);
@@ -117,8 +118,9 @@ cudaError_t launch_particles_adj(int dims, int prec, cudaStream_t st, const RunD
 
 struct pic_grid {
     int dims = 3, prec = 0;
-    int halo = 1, sort_interval = 10, ppi = 8192;
+    int halo = 1, sort_interval = 10, ppi = 8192, sort_order = 0;
     int tile[3] = {8, 8, 8};
+    int pitch[2] = {0, 0};   // x, y pitch of the shared tiles (chosen at create)
     cudaStream_t stream = nullptr;
 
     std::vector<pic::HostRun> runs;

@@ -78,7 +78,7 @@ __device__ __noinline__ void deposit_global(const Fields<R> &F, long long cb, in
     acc.cell_base = cb;
     acc.i = i; acc.j = j; acc.k = k;
     acc.nx = nx; acc.ny = ny; acc.nz = nz;
-    deposit<DIM>(acc, win[0], win[1], win[2], kf, uz);
+    deposit<DIM>(acc, win[0], win[1], win[2], kf, uz, 7);
 }
 
 // MODE 0: fused gather + push + move + deposit (pic_step).
@@ -103,7 +103,11 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     const int ox = tx * T0, oy = ty * T1, oz = tz * T2;
     const int fe0 = T0 + 2 * G + 2, fe1 = T1 + 2 * G + 2, fe2 = DIM == 3 ? T2 + 2 * G + 2 : 1;
     const int je0 = T0 + 2 * G + 4, je1 = T1 + 2 * G + 4, je2 = DIM == 3 ? T2 + 2 * G + 4 : 1;
-    const int nf = fe0 * fe1 * fe2, nj = je0 * je1 * je2;
+    // the field tile is stored with the current tile's x and y pitches, so that
+    // a particle's field and current bases differ by a constant and one bank
+    // order of the particles (set by the tile sort) serves both
+    const int P0 = rn.pitch[0], P1 = rn.pitch[1];   // >= je0, je1 (see the tile layout choice)
+    const int nf = P0 * P1 * fe2, nj = P0 * P1 * je2;
     constexpr bool NEED_F = MODE != 2;
     constexpr bool NEED_J = MODE != 1;
     const long long cb = rn.cell_base;
@@ -129,7 +133,8 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
 
     if (NEED_F) {
         for (int l = threadIdx.x; l < nf; l += blockDim.x) {
-            const int lx = l % fe0, r = l / fe0, ly = r % fe1, lz = r / fe1;
+            const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
+            if (lx >= fe0 || ly >= fe1) continue;   // pitch padding
             const int gx = wrapi(ox - G - 1 + lx, nx);
             const int gy = wrapi(oy - G - 1 + ly, ny);
             const int gz = DIM == 3 ? wrapi(oz - G - 1 + lz, nz) : 0;
@@ -159,6 +164,8 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         kf[1] = R(-0.5 * rn.d[1] / rn.dt * gr.qp / rn.V);
         kf[2] = R(0.25 * gr.qp / rn.V);
     }
+    R kfs[3];   // prefactors with the fixed-point scale of the FP32 current tile folded in
+    for (int c = 0; c < 3; ++c) kfs[c] = kf[c] * R(gr.jscale);
 
     for (long long p = it.begin + threadIdx.x; p < it.end; p += blockDim.x) {
         // ---- the particle's state at x^n (old) -------------------------------
@@ -199,9 +206,9 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             if (inr) {
                 SmemReader<R> rd;
                 for (int c = 0; c < 3; ++c) { rd.E[c] = sE[c]; rd.B[c] = sB[c]; }
-                rd.base = (li + G + 1) + fe0 * ((lj + G + 1) + (DIM == 3 ? fe1 * (lk + G + 1) : 0));
-                rd.s1 = fe0;
-                rd.s2 = fe0 * fe1;
+                rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
+                rd.s1 = P0;
+                rd.s2 = P0 * P1;
                 gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
             } else {
                 R w6[15] = {fx[0], fx[1], Sx[0], Sx[1], Sx[2], fy[0], fy[1], Sy[0], Sy[1], Sy[2],
@@ -255,23 +262,26 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         axis_window(o0, n0, s0, X);
         axis_window(o1, n1, s1, Y);
         if (DIM == 3) axis_window(o2, n2, s2, Z); else Z = X;
+        // axes along which some particle of this warp changed cell (warp-uniform)
+        const unsigned am = __activemask();
+        const int full = (__any_sync(am, s0 != 0) ? 1 : 0) | (__any_sync(am, s1 != 0) ? 2 : 0) |
+                         (DIM == 3 && __any_sync(am, s2 != 0) ? 4 : 0);
         if (inr) {
-            const int base = (li + G + 2) + je0 * ((lj + G + 2) + (DIM == 3 ? je1 * (lk + G + 2) : 0));
+            const int base = (li + G + 2) + P0 * ((lj + G + 2) + (DIM == 3 ? P1 * (lk + G + 2) : 0));
             if constexpr (FIX) {
                 FixedAcc acc;
                 for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
                 acc.base = base;
-                acc.s1 = je0;
-                acc.s2 = je0 * je1;
-                acc.scale = gr.jscale;
-                deposit<DIM>(acc, X, Y, Z, kf, uz);
+                acc.s1 = P0;
+                acc.s2 = P0 * P1;
+                deposit<DIM>(acc, X, Y, Z, kfs, uz, full);
             } else {
                 SmemAcc<R> acc;
                 for (int c = 0; c < 3; ++c) acc.J[c] = sJ[c];
                 acc.base = base;
-                acc.s1 = je0;
-                acc.s2 = je0 * je1;
-                deposit<DIM>(acc, X, Y, Z, kf, uz);
+                acc.s1 = P0;
+                acc.s2 = P0 * P1;
+                deposit<DIM>(acc, X, Y, Z, kf, uz, full);
             }
         } else {
             AxisWin<R> win[3] = {X, Y, Z};
@@ -283,7 +293,8 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         __syncthreads();
         const float jinv = gr.jinv;
         for (int l = threadIdx.x; l < nj; l += blockDim.x) {
-            const int lx = l % je0, r = l / je0, ly = r % je1, lz = r / je1;
+            const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
+            if (lx >= je0 || ly >= je1) continue;   // pitch padding
             const int gx = wrapi(ox - G - 2 + lx, nx);
             const int gy = wrapi(oy - G - 2 + ly, ny);
             const int gz = DIM == 3 ? wrapi(oz - G - 2 + lz, nz) : 0;
@@ -371,11 +382,11 @@ static cudaError_t launch_mode(int mode, cudaStream_t st, int max_items, size_t 
     }
 }
 
-size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo)
+size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo, int p0, int p1)
 {
     const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
-    const long long fe = (long long)(tx + 2 * halo + 2) * (ty + 2 * halo + 2) * (dims == 3 ? tz + 2 * halo + 2 : 1);
-    const long long je = (long long)(tx + 2 * halo + 4) * (ty + 2 * halo + 4) * (dims == 3 ? tz + 2 * halo + 4 : 1);
+    const long long fe = (long long)p0 * p1 * (dims == 3 ? tz + 2 * halo + 2 : 1);
+    const long long je = (long long)p0 * p1 * (dims == 3 ? tz + 2 * halo + 4 : 1);
     size_t b = 0;
     if (mode != 2) b += 6 * fe * es;
     if (mode != 1) b += 24 * je;
@@ -429,9 +440,9 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
                              const int *n_items, int max_items, const RunDev *runs, const GroupDev *groups,
                              const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
                              int *old_cell, void *const old_off[3], int halo, int max_tile_x, int max_tile_y,
-                             int max_tile_z, int *err)
+                             int max_tile_z, int *err, int p0, int p1)
 {
-    const size_t smem = particles_smem_bytes(dims, prec, mode, max_tile_x, max_tile_y, max_tile_z, halo);
+    const size_t smem = particles_smem_bytes(dims, prec, mode, max_tile_x, max_tile_y, max_tile_z, halo, p0, p1);
     if (prec == 0) {
         auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
         return dims == 3 ? launch_mode<3, double>(mode, st, max_items, smem, a)
@@ -468,10 +479,11 @@ static cudaError_t persistent_t(cudaStream_t st, size_t smem, int nruns, const l
 cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const WorkItem *items, const int *n_items,
                                    const RunDev *runs, const GroupDev *groups, const PoolBuf &P, void *const E[3],
                                    void *const B[3], void *const J[3], int halo, int tx, int ty, int tz, int *err,
-                                   int nruns, const long long *run_cell_base, int *grid_blocks, int launch)
+                                   int nruns, const long long *run_cell_base, int *grid_blocks, int launch, int p0,
+                                   int p1)
 {
     void *none[3] = {nullptr, nullptr, nullptr};
-    const size_t smem = particles_smem_bytes(dims, prec, 0, tx, ty, tz, halo);
+    const size_t smem = particles_smem_bytes(dims, prec, 0, tx, ty, tz, halo, p0, p1);
     if (prec == 0) {
         auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, nullptr, none, halo, err);
         return dims == 3 ? persistent_t<3, double>(st, smem, nruns, run_cell_base, a, grid_blocks, launch)

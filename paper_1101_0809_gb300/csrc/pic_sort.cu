@@ -211,6 +211,89 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(const unsigned *keys
     }
 }
 
+// Bank interleave inside every tile.  The particle kernels stage the tile's
+// current in shared memory with x pitch P0 and y pitch P1 (rn.pitch);
+// a particle's accesses are its cell's base address plus offsets common to all
+// particles, so the 32 lanes of a warp hit 32 distinct banks when their cells'
+// base addresses are distinct modulo 32.  Within each tile this kernel keeps the
+// stable tile order per bank b = base(cell) mod 32 and interleaves the banks:
+// the r-th particle (r = its rank among the tile's particles of bank b) goes to
+// slot S(r) + #{b' < b : cnt[b'] > r}, with S(r) = sum_b' min(cnt[b'], r).  The
+// key order (by tile) is unchanged; only the order inside a tile changes.
+__global__ void __launch_bounds__(kSortThreads) k_bank_order(const long long *tile_start, const unsigned *vals_in,
+                                                             unsigned *vals_out, const int *cell, const GroupDev *groups,
+                                                             int ngroups, const RunDev *runs, int halo, int dims)
+{
+    __shared__ unsigned cnt[32];
+    __shared__ unsigned tot[32];
+    __shared__ unsigned wh[kSortThreads / 32][32];
+    __shared__ unsigned pre[kSortThreads / 32][32];
+    const int t = blockIdx.x;
+    const long long b0 = tile_start[t], e0 = tile_start[t + 1];
+    if (e0 - b0 <= 1) {
+        if (threadIdx.x == 0 && e0 > b0) vals_out[b0] = vals_in[b0];
+        return;
+    }
+    int lo = 0, hi = ngroups;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (groups[mid].tile_base <= t) lo = mid; else hi = mid;
+    }
+    const RunDev &rn = runs[groups[lo].run];
+    const int lt = t - groups[lo].tile_base;
+    const int tx = lt % rn.ntile[0], ty = (lt / rn.ntile[0]) % rn.ntile[1], tz = lt / (rn.ntile[0] * rn.ntile[1]);
+    const int ox = tx * rn.tile[0], oy = ty * rn.tile[1], oz = tz * rn.tile[2];
+    const int P0 = rn.pitch[0], P1 = rn.pitch[1];
+    const int nx = rn.n[0], ny = rn.n[1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto bank_of = [&](unsigned v) -> unsigned {
+        const int c = cell[v];
+        const int i = c % nx, r = c / nx, j = r % ny, k = r / ny;
+        const int base = (i - ox + halo + 2) + P0 * ((j - oy + halo + 2) + (dims == 3 ? P1 * (k - oz + halo + 2) : 0));
+        return (unsigned)base & 31u;
+    };
+    if (tid < 32) {
+        cnt[tid] = 0;
+        tot[tid] = 0;
+    }
+    if (tid < kSortThreads / 32 * 32) wh[tid >> 5][tid & 31] = 0;
+    __syncthreads();
+    for (long long o = b0 + tid; o < e0; o += kSortThreads) atomicAdd(&cnt[bank_of(vals_in[o])], 1u);
+    __syncthreads();
+    const unsigned ltm = (1u << lane) - 1u;
+    for (long long r0 = b0; r0 < e0; r0 += kSortThreads) {
+        const long long o = r0 + tid;
+        const bool valid = o < e0;
+        const unsigned v = valid ? vals_in[o] : 0u;
+        const unsigned bk = valid ? bank_of(v) : 32u;
+        const unsigned peers = __match_any_sync(0xffffffffu, bk);
+        const unsigned rk = __popc(peers & ltm);
+        if (valid && (__ffs(peers) - 1) == lane) wh[warp][bk] = __popc(peers);
+        __syncthreads();
+        if (tid < 32) {
+            unsigned run = tot[tid];
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                const unsigned c = wh[w][tid];
+                pre[w][tid] = run;
+                run += c;
+                wh[w][tid] = 0;
+            }
+            tot[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const unsigned rank = pre[warp][bk] + rk;   // rank among the tile's particles of bank bk
+            unsigned S = 0, below = 0;
+            for (int b = 0; b < 32; ++b) {
+                const unsigned cb = cnt[b];
+                S += cb < rank ? cb : rank;
+                if (b < (int)bk && cb > rank) ++below;
+            }
+            vals_out[b0 + S + below] = v;
+        }
+    }
+}
+
 // Permute every particle array: dst[o] = src[perm[o]].
 template <typename R, int DIM>
 __global__ void k_permute(long long n, const unsigned *perm, Pool<R> src, Pool<R> dst)
@@ -276,7 +359,7 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  const PoolBuf &dst, const GroupDev *groups, const long long *group_base_dev,
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
-                                 int particles_per_item, int *launches)
+                                 int particles_per_item, int halo, int banked, int *launches)
 {
     cudaError_t e;
     if (total <= 0 || ngroups <= 0) {
@@ -307,6 +390,18 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
         cur = 1 - cur;
     }
 
+    // tile starts, then the bank interleave inside every tile (into the other value buffer)
+    k_tile_start<<<nbp, nt, 0, st>>>(scr.keys[cur], total, total_tiles, tile_start);
+    *launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (banked) {
+        k_bank_order<<<(unsigned)total_tiles, kSortThreads, 0, st>>>(tile_start, scr.vals[cur], scr.vals[1 - cur],
+                                                                   src.cell, groups, ngroups, runs, halo, dims);
+        *launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cur = 1 - cur;
+    }
+
     if (prec == 0) {
         Pool<double> s, d;
         s.cell = src.cell; s.id = src.id; d.cell = dst.cell; d.id = dst.id;
@@ -329,9 +424,6 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
     *launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-    k_tile_start<<<nbp, nt, 0, st>>>(scr.keys[cur], total, total_tiles, tile_start);
-    *launches += 1;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const unsigned nbt = (unsigned)((total_tiles + nt - 1) / nt);
     k_item_counts<<<nbt, nt, 0, st>>>(tile_start, total_tiles, particles_per_item, item_scan);
     *launches += 1;

@@ -18,6 +18,7 @@ PIC_OK, PIC_ERR_INVALID_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_CUDA = 0, 1, 2, 3
 PIC_ERR_NONFINITE, PIC_ERR_OUT_OF_TILE, PIC_ERR_TIMEOUT, PIC_ERR_STATE = 5, 6, 7, 8
 PIC_FP64, PIC_FP32 = 0, 1
 PIC_B_HALF, PIC_E_FULL = 1, 2
+PIC_SORT_BANKED, PIC_SORT_STABLE = 0, 1
 
 
 class PicError(RuntimeError):
@@ -32,7 +33,7 @@ class pic_grid_desc(C.Structure):
                 ("dt", C.c_double), ("c", C.c_double),
                 ("precision", C.c_int), ("order2", C.c_int), ("tile", C.c_int * 3),
                 ("halo", C.c_int), ("sort_interval", C.c_int), ("particles_per_block", C.c_int),
-                ("rho_bg", C.c_double), ("cuda_stream", C.c_void_p)]
+                ("rho_bg", C.c_double), ("cuda_stream", C.c_void_p), ("sort_order", C.c_int)]
 
 
 class pic_species_desc(C.Structure):
@@ -324,6 +325,16 @@ def pic_step_graph(g, nsteps=1):
     _check(_lib.pic_step_graph(g, nsteps))
 
 
+_lib.pic_tile_layout.argtypes = [_VP, C.c_int * 6]
+
+
+def pic_tile_layout(g):
+    """(tile[3], halo, pitch[2]) of the grid's shared-memory stages."""
+    out = (C.c_int * 6)()
+    _check(_lib.pic_tile_layout(g, out))
+    return tuple(out[0:3]), out[3], tuple(out[4:6])
+
+
 _lib.pic_state_bytes.argtypes = [_VP]
 _lib.pic_state_bytes.restype = C.c_longlong
 _lib.pic_state_save.argtypes = [_VP, _VP, C.c_int]
@@ -371,11 +382,11 @@ def pic_tile_sort_perm_noalloc(cell, n, dims, ncell, tile, perm, tile_start=None
 
 
 def make_desc(dims, n, d, dt, c, precision=PIC_FP64, tile=(0, 0, 0), halo=-1, sort_interval=0,
-              particles_per_block=0, rho_bg=0.0, stream=None):
+              particles_per_block=0, rho_bg=0.0, stream=None, sort_order=PIC_SORT_BANKED):
     """Fill a pic_grid_desc; ``stream`` is a raw cudaStream_t handle (int) or None."""
     return pic_grid_desc(dims, n[0], n[1], n[2] if dims == 3 else 1, d[0], d[1], d[2], dt, c,
                          precision, 3, (C.c_int * 3)(*tile), halo, sort_interval,
-                         particles_per_block, rho_bg, stream)
+                         particles_per_block, rho_bg, stream, sort_order)
 
 
 class Grid:

@@ -93,12 +93,45 @@ def compare_particles(wl, sp_index, grid, osp, tol, check_cells=True):
         close(w[a][order], ref.w[a], tol, f"species {sp_index} w[{a}]")
 
 
-def make_grid(P, wl, precision, stream=None, tile=None, halo=-1, sort_interval=None, ppb=0):
+def make_grid(P, wl, precision, stream=None, tile=None, halo=-1, sort_interval=None, ppb=0, sort_order=0):
     desc = P.make_desc(wl.dims, wl.n, wl.d, wl.dt, wl.c, precision,
                        tile=tile if tile is not None else wl.tile, halo=halo,
                        sort_interval=sort_interval if sort_interval is not None else wl.sort_interval,
-                       particles_per_block=ppb, rho_bg=wl.rho_bg, stream=stream)
+                       particles_per_block=ppb, rho_bg=wl.rho_bg, stream=stream, sort_order=sort_order)
     grid = P.Grid(desc)
     for s, sp in enumerate(wl.species):
         grid.load(s, sp.q, sp.m, sp.weight, sp.x, sp.w)
     return grid
+
+
+def tile_sort_perm(wl, cells, tile, halo=1, banked=True, pitch=None):
+    """The tile sort's permutation written out from its definition (integer work,
+    compared bit-exactly): sort by tile key; with ``banked``, inside a tile by
+    (r, b) where b is the shared-memory bank of the cell's base address in the
+    tile's current stage, base = (i-ox+h+2) + P0*((j-oy+h+2) + P1*(k-oz+h+2)) with
+    the grid's tile pitches (pic_tile_layout), and r the particle's rank among
+    the tile's particles of bank b in input order.  Returns perm[o] = input
+    index at slot o."""
+    nx, ny = wl.n[0], wl.n[1]
+    cells = np.asarray(cells, dtype=np.int64)
+    i, j, k = cells % nx, (cells // nx) % ny, cells // (nx * ny)
+    T = tile
+    ntx, nty = -(-nx // T[0]), -(-ny // T[1])
+    ti, tj, tk = i // T[0], j // T[1], (k // T[2] if wl.dims == 3 else 0 * k)
+    key = (tk * nty + tj) * ntx + ti
+    if not banked:
+        return np.argsort(key, kind="stable")
+    je0, je1 = pitch if pitch is not None else (T[0] + 2 * halo + 4, T[1] + 2 * halo + 4)
+    base = (i - ti * T[0] + halo + 2) + je0 * (j - tj * T[1] + halo + 2)
+    if wl.dims == 3:
+        base = base + je0 * je1 * (k - tk * T[2] + halo + 2)
+    b = base % 32
+    kb = key * 32 + b
+    idx = np.argsort(kb, kind="stable")          # groups (tile, bank), input order inside
+    skb = kb[idx]
+    start = np.r_[0, np.flatnonzero(np.diff(skb)) + 1]
+    grp = np.repeat(start, np.diff(np.r_[start, skb.size]))
+    r = np.empty(cells.size, dtype=np.int64)
+    r[idx] = np.arange(skb.size) - grp
+    return np.lexsort((b, r, key))
+

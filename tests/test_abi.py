@@ -48,7 +48,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(pic_grid_desc), offsetof(pic_grid_desc, precision),
          offsetof(pic_grid_desc, rho_bg), offsetof(pic_grid_desc, cuda_stream),
          sizeof(pic_diag), offsetof(pic_diag, n_particles));
-  printf("%zu\n", sizeof(pic_species_desc));
+  printf("%zu %zu\n", sizeof(pic_species_desc), offsetof(pic_grid_desc, sort_order));
   return 0;
 }
 """
@@ -65,6 +65,7 @@ int main(void) {
     assert vals[4] == C.sizeof(P.pic_diag)
     assert vals[5] == P.pic_diag.n_particles.offset
     assert vals[6] == C.sizeof(P.pic_species_desc)
+    assert vals[7] == P.pic_grid_desc.sort_order.offset
 
 
 def _create(P, **kw):

@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from paper_1101_0809_gb300 import workloads as W
 from pichelpers import (FP32_TOL, FP64_TOL, close, compare_particles, make_grid, oracle_grid,
-                        oracle_species, positions_from_gpu)
+                        oracle_species, positions_from_gpu, tile_sort_perm)
 
 pytestmark = pytest.mark.gpu
 
@@ -77,9 +77,11 @@ def test_yee_updates_match_oracle(P, dims, prec):
 
 # ---------------------------------------------------------------------------- load and sort
 @pytest.mark.parametrize("which", ["2d", "3d"])
-def test_load_cells_offsets_and_stable_tile_sort_are_exact(P, which):
+@pytest.mark.parametrize("order", ["banked", "stable"])
+def test_load_cells_offsets_and_tile_sort_are_exact(P, which, order):
     wl = W.c0_small2d() if which == "2d" else small3d()
-    grid = make_grid(P, wl, P.PIC_FP64)
+    banked = order == "banked"
+    grid = make_grid(P, wl, P.PIC_FP64, sort_order=P.PIC_SORT_BANKED if banked else P.PIC_SORT_STABLE)
     g = oracle_grid(wl)
     for s, sp in enumerate(wl.species):
         cell, off, w, ident = grid.particles(s)
@@ -93,25 +95,35 @@ def test_load_cells_offsets_and_stable_tile_sort_are_exact(P, which):
         for a in range(wl.dims):
             np.testing.assert_array_equal(off[a], x[a] - fl[a])
             np.testing.assert_array_equal(w[a], sp.w[a][ident])
-        # storage order is the stable sort of the load order by tile key
-        keys = O.tile_keys(g, wl.tile, sp.x)
-        nt = [math.ceil(wl.n[a] / wl.tile[a]) for a in range(3)]
-        perm = O.sort_perm(keys, nt[0] * nt[1] * (nt[2] if wl.dims == 3 else 1))
-        np.testing.assert_array_equal(ident, perm)
+        # storage order: the tile sort of the load order
+        fl0 = np.floor(sp.x).astype(np.int64)
+        cells0 = fl0[0] + wl.n[0] * (fl0[1] + wl.n[1] * (fl0[2] if wl.dims == 3 else 0))
+        _, _, pitch = P.pic_tile_layout(grid.h)
+        np.testing.assert_array_equal(ident, tile_sort_perm(wl, cells0, wl.tile, 1, banked, pitch))
+        if not banked:
+            keys = O.tile_keys(g, wl.tile, sp.x)
+            nt = [math.ceil(wl.n[a] / wl.tile[a]) for a in range(3)]
+            perm = O.sort_perm(keys, nt[0] * nt[1] * (nt[2] if wl.dims == 3 else 1))
+            np.testing.assert_array_equal(ident, perm)
     grid.close()
 
 
-def test_sort_after_motion_is_the_stable_permutation(P):
+@pytest.mark.parametrize("order", ["banked", "stable"])
+def test_sort_after_motion_is_the_defined_permutation(P, order):
     wl = ragged2d(vth=0.3)
-    grid = make_grid(P, wl, P.PIC_FP64, sort_interval=1000)
+    banked = order == "banked"
+    grid = make_grid(P, wl, P.PIC_FP64, sort_interval=1000,
+                     sort_order=P.PIC_SORT_BANKED if banked else P.PIC_SORT_STABLE)
     P.pic_step(grid.h, 6)
     cell_b, off_b, w_b, id_b = grid.particles(0)
     P.pic_sort(grid.h)
     cell_a, off_a, w_a, id_a = grid.particles(0)
-    x = positions_from_gpu(wl, cell_b, off_b)
-    keys = O.tile_keys(oracle_grid(wl), wl.tile, x)
-    nt = [math.ceil(wl.n[a] / wl.tile[a]) for a in range(2)]
-    perm = O.sort_perm(keys, nt[0] * nt[1])
+    perm = tile_sort_perm(wl, cell_b, wl.tile, 1, banked, P.pic_tile_layout(grid.h)[2])
+    if not banked:
+        x = positions_from_gpu(wl, cell_b, off_b)
+        keys = O.tile_keys(oracle_grid(wl), wl.tile, x)
+        nt = [math.ceil(wl.n[a] / wl.tile[a]) for a in range(2)]
+        np.testing.assert_array_equal(perm, O.sort_perm(keys, nt[0] * nt[1]))
     np.testing.assert_array_equal(id_a, id_b[perm])
     np.testing.assert_array_equal(cell_a, cell_b[perm])
     for a in range(3):

@@ -65,7 +65,9 @@ def test_noalloc_permutation_equals_the_library_sort_twice_in_a_row(env, which):
     else:
         wl = W.thermal_plasma("3D small", 3, (20, 18, 22), 4, 0.3, 6, W.SEED_BASE + 11,
                               tile=(8, 8, 8), dt_courant=0.45)
-    grid = make_grid(P, wl, P.PIC_FP64, sort_interval=1000)
+    # the library sorts inside a tile in bank order by default; the allocation-free
+    # entry point computes the stable tile order, which the library also offers
+    grid = make_grid(P, wl, P.PIC_FP64, sort_interval=1000, sort_order=P.PIC_SORT_STABLE)
     sp = wl.species[0]
     # call 1: the load order; the library's load sorted the same particles
     fl = np.floor(sp.x).astype(np.int64)
