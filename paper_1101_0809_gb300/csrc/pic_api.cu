@@ -292,7 +292,6 @@ static void choose_pitch(pic_grid *g)
 {
     const int h = g->halo, T0 = g->tile[0], T1 = g->tile[1], T2 = g->dims == 3 ? g->tile[2] : 1;
     const int je0 = T0 + 2 * h + 4, je1 = T1 + 2 * h + 4;
-    const size_t es = g->prec == PIC_FP64 ? 8 : 4;
     long long best_key = -1;
     for (int p0 = je0; p0 <= std::max(je0, 32); ++p0) {
         for (int p1 = je1; p1 <= (g->dims == 3 ? std::max(je1, 32) : je1); ++p1) {
@@ -308,9 +307,7 @@ static void choose_pitch(pic_grid *g)
                 mn = std::min(mn, cnt[b]);
                 mx = std::max(mx, cnt[b]);
             }
-            const long long fe = (long long)p0 * p1 * (g->dims == 3 ? T2 + 2 * h + 2 : 1);
-            const long long je = (long long)p0 * p1 * (g->dims == 3 ? T2 + 2 * h + 4 : 1);
-            const long long smem = 6 * fe * (long long)es + 24 * je;
+            const long long smem = (long long)particles_smem_bytes(g->dims, g->prec, 0, T0, T1, T2, h, p0, p1);
             const long long two = smem <= 113 * 1024 ? 0 : 1;
             const long long key = ((long long)(mx - mn) << 40) | (two << 39) | smem;
             if (best_key < 0 || key < best_key) {

@@ -281,6 +281,29 @@ __device__ __forceinline__ void axis_window(R d0, R d1, int s, AxisWin<R> &a)
     a.lo = neg ? -2 : -1;
 }
 
+// The window of a particle that stayed in its cell along this axis (s = 0):
+// cells -1..1 of the old cell, interior faces 0 and 1.  The fourth cell and the
+// third face carry nothing (zero weight; the closure sum of Pm), and a
+// deposit called with the axis' `full` bit clear never reads them.
+template <typename R>
+__device__ __forceinline__ void axis_window_still(R d0, R d1, AxisWin<R> &a)
+{
+    R f0[2], S0[3], f1[2], S1[3];
+    form_factor(d0, f0, S0);
+    form_factor(d1, f1, S1);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        a.Pp[t] = S1[t] + S0[t];
+        a.Pm[t] = S1[t] - S0[t];
+    }
+    a.Pp[3] = R(0);
+    a.Pm[3] = R(0);
+    a.D[0] = a.Pm[0];
+    a.D[1] = a.D[0] + a.Pm[1];
+    a.D[2] = R(0);
+    a.lo = -1;
+}
+
 // Current accumulators; offsets are relative to the particle's OLD cell.
 template <typename R>
 struct SmemAcc {

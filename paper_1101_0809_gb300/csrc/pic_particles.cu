@@ -36,6 +36,12 @@ struct PartArgs {
 
 extern __shared__ __align__(16) unsigned char g_smem[];
 
+// Per-warp deposit queue of particles that changed cell: capacity (a warp adds
+// at most 32 entries to fewer than 32) and the values kept per entry (old and
+// new offsets, u_z in 2D) besides one packed int (tile base << 8 | shifts + 1).
+constexpr int kQueueCap = 64;
+constexpr int kQueueVals = 7;
+
 __device__ __forceinline__ bool finite3(float a, float b, float c) { return isfinite(a) && isfinite(b) && isfinite(c); }
 __device__ __forceinline__ bool finite3(double a, double b, double c) { return isfinite(a) && isfinite(b) && isfinite(c); }
 
@@ -167,126 +173,216 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     R kfs[3];   // prefactors with the fixed-point scale of the FP32 current tile folded in
     for (int c = 0; c < 3; ++c) kfs[c] = kf[c] * R(gr.jscale);
 
-    for (long long p = it.begin + threadIdx.x; p < it.end; p += blockDim.x) {
-        // ---- the particle's state at x^n (old) -------------------------------
-        const int cell0 = MODE == 2 ? a.old_cell[p] : a.P.cell[p];
-        const R o0 = MODE == 2 ? a.old_off[0][p] : a.P.off[0][p];
-        const R o1 = MODE == 2 ? a.old_off[1][p] : a.P.off[1][p];
-        const R o2 = DIM == 3 ? (MODE == 2 ? a.old_off[2][p] : a.P.off[2][p]) : R(0);
-        R w[3] = {R(0), R(0), R(0)};
-        if (MODE != 2 || DIM == 2) {
-            w[0] = a.P.w[0][p];
-            w[1] = a.P.w[1][p];
-            w[2] = a.P.w[2][p];
-        }
-        const int i = cell0 % nx;
-        const int rest = cell0 / nx;
-        const int j = rest % ny;
-        const int k = DIM == 3 ? rest / ny : 0;
-        const int li = local_coord(i, ox, T0, G, nx);
-        const int lj = local_coord(j, oy, T1, G, ny);
-        const int lk = DIM == 3 ? local_coord(k, oz, T2, G, nz) : 0;
-        const bool inr = li >= -G && li < T0 + G && lj >= -G && lj < T1 + G &&
-                         (DIM == 2 || (lk >= -G && lk < T2 + G));
+    // Deposit queue of this warp (MODES 0, 2).  A particle that stayed in its
+    // cell along every axis deposits at once with three-cell windows (54
+    // contributions in 3D, 21 in 2D), where its lane's bank is the one the tile
+    // sort gave it.  A particle that changed cell needs four-cell windows along
+    // the axes it crossed; it is queued and deposited later together with 31
+    // other such particles, so that the wider windows are paid only by warps
+    // of moved particles.  The integer current sums do not depend on the order.
+    R *qv = nullptr;
+    int *qs = nullptr;
+    if (NEED_J) {
+        unsigned char *qb = g_smem + (NEED_F ? 6 * (size_t)nf * sizeof(R) : 0) + 24 * (size_t)nj;
+        const int warp = threadIdx.x >> 5;
+        qv = reinterpret_cast<R *>(qb) + (size_t)warp * kQueueCap * kQueueVals;
+        qs = reinterpret_cast<int *>(qb + (size_t)(kThreads / 32) * kQueueCap * kQueueVals * sizeof(R)) +
+             warp * kQueueCap;
+    }
+    const int lane = threadIdx.x & 31;
+    int qn = 0;   // entries in this warp's queue (warp-uniform)
 
-        R n0 = o0, n1 = o1, n2 = o2;
-        int s0 = 0, s1 = 0, s2 = 0;
-        R uz = R(0);
-        if (MODE != 2) {
-            R fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
-            form_factor(o0, fx, Sx);
-            form_factor(o1, fy, Sy);
-            if (DIM == 3) {
-                form_factor(o2, fz, Sz);
-            } else {
-                fz[0] = R(1); fz[1] = R(0);
-                Sz[0] = R(0); Sz[1] = R(1); Sz[2] = R(0);
-            }
-            R Ep[3], Bp[3];
-            if (inr) {
-                SmemReader<R> rd;
-                for (int c = 0; c < 3; ++c) { rd.E[c] = sE[c]; rd.B[c] = sB[c]; }
-                rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
-                rd.s1 = P0;
-                rd.s2 = P0 * P1;
-                gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
-            } else {
-                R w6[15] = {fx[0], fx[1], Sx[0], Sx[1], Sx[2], fy[0], fy[1], Sy[0], Sy[1], Sy[2],
-                            fz[0], fz[1], Sz[0], Sz[1], Sz[2]};
-                gather_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, w6, Ep, Bp);
-            }
-            boris(w, Ep, Bp, hq, c2);
-            if (!finite3(w[0], w[1], w[2])) {
-                atomicOr(a.err, ERR_NONFINITE);
-                continue;   // the particle keeps x^n and contributes no current
-            }
-            const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
-            s0 = renormalize(o0, w[0] * ig * cN0, n0);
-            s1 = renormalize(o1, w[1] * ig * cN1, n1);
-            if (DIM == 3) s2 = renormalize(o2, w[2] * ig * cN2, n2);
-            uz = cl * w[2] * ig;
-            const int i1 = wrapi(i + s0, nx), j1 = wrapi(j + s1, ny), k1 = DIM == 3 ? wrapi(k + s2, nz) : 0;
-            const int cell1 = i1 + nx * (j1 + ny * k1);
-            if (MODE == 1) {
-                a.old_cell[p] = cell0;
-                a.old_off[0][p] = o0;
-                a.old_off[1][p] = o1;
-                if (DIM == 3) a.old_off[2][p] = o2;
-            }
-            a.P.cell[p] = cell1;
-            a.P.off[0][p] = n0;
-            a.P.off[1][p] = n1;
-            if (DIM == 3) a.P.off[2][p] = n2;
-            a.P.w[0][p] = w[0];
-            a.P.w[1][p] = w[1];
-            a.P.w[2][p] = w[2];
+
+    auto deposit_local = [&](int base, const AxisWin<R> &X, const AxisWin<R> &Y, const AxisWin<R> &Z, R uz,
+                             int full) {
+        if constexpr (FIX) {
+            FixedAcc acc;
+            for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
+            acc.base = base;
+            acc.s1 = P0;
+            acc.s2 = P0 * P1;
+            deposit<DIM>(acc, X, Y, Z, kfs, uz, full);
         } else {
-            // deposit-only: x^{n+1} is the stored state, the shift follows from the cells
-            const int cell1 = a.P.cell[p];
-            n0 = a.P.off[0][p];
-            n1 = a.P.off[1][p];
-            if (DIM == 3) n2 = a.P.off[2][p];
-            const int i1 = cell1 % nx, r1 = cell1 / nx, j1 = r1 % ny, k1 = DIM == 3 ? r1 / ny : 0;
-            s0 = i1 - i; if (s0 > 1) s0 -= nx; if (s0 < -1) s0 += nx;
-            s1 = j1 - j; if (s1 > 1) s1 -= ny; if (s1 < -1) s1 += ny;
-            if (DIM == 3) { s2 = k1 - k; if (s2 > 1) s2 -= nz; if (s2 < -1) s2 += nz; }
-            if (DIM == 2) {
-                const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
-                uz = cl * w[2] * ig;
+            SmemAcc<R> acc;
+            for (int c = 0; c < 3; ++c) acc.J[c] = sJ[c];
+            acc.base = base;
+            acc.s1 = P0;
+            acc.s2 = P0 * P1;
+            deposit<DIM>(acc, X, Y, Z, kf, uz, full);
+        }
+    };
+    // deposits the queue entries [first, first + 32) whose lanes have `on`
+    auto drain = [&](int first, bool on) {
+        const int slot = first + lane;
+        R d0 = R(0), d1 = R(0), d2 = R(0), e0 = R(0), e1 = R(0), e2 = R(0), u = R(0);
+        int code = 1 | (1 << 2) | (1 << 4);
+        if (on) {
+            d0 = qv[0 * kQueueCap + slot];
+            d1 = qv[1 * kQueueCap + slot];
+            e0 = qv[3 * kQueueCap + slot];
+            e1 = qv[4 * kQueueCap + slot];
+            if (DIM == 3) {
+                d2 = qv[2 * kQueueCap + slot];
+                e2 = qv[5 * kQueueCap + slot];
+            } else {
+                u = qv[6 * kQueueCap + slot];
+            }
+            code = qs[slot];
+        }
+        const int q0 = (code & 3) - 1, q1 = ((code >> 2) & 3) - 1, q2 = ((code >> 4) & 3) - 1;
+        const int full = (__any_sync(0xffffffffu, q0 != 0) ? 1 : 0) | (__any_sync(0xffffffffu, q1 != 0) ? 2 : 0) |
+                         (DIM == 3 && __any_sync(0xffffffffu, q2 != 0) ? 4 : 0);
+        if (on) {
+            AxisWin<R> X, Y, Z;
+            axis_window(d0, e0, q0, X);
+            axis_window(d1, e1, q1, Y);
+            if (DIM == 3) axis_window(d2, e2, q2, Z); else Z = X;
+            deposit_local(code >> 8, X, Y, Z, u, full);
+        }
+    };
+
+    // warps run whole rounds of 32 consecutive particles (the last one partial)
+    for (long long pw = it.begin + (threadIdx.x & ~31); pw < it.end; pw += blockDim.x) {
+        const long long p = pw + lane;
+        const bool valid = p < it.end;
+        bool live = false;   // the particle moves and deposits this step
+        bool inr = false;
+        int i = 0, j = 0, k = 0, li = 0, lj = 0, lk = 0;
+        R o0 = R(0), o1 = R(0), o2 = R(0), n0 = R(0), n1 = R(0), n2 = R(0), uz = R(0);
+        int s0 = 0, s1 = 0, s2 = 0;
+        if (valid) {
+            // ---- the particle's state at x^n (old) -------------------------------
+            const int cell0 = MODE == 2 ? a.old_cell[p] : a.P.cell[p];
+            o0 = MODE == 2 ? a.old_off[0][p] : a.P.off[0][p];
+            o1 = MODE == 2 ? a.old_off[1][p] : a.P.off[1][p];
+            o2 = DIM == 3 ? (MODE == 2 ? a.old_off[2][p] : a.P.off[2][p]) : R(0);
+            R w[3] = {R(0), R(0), R(0)};
+            if (MODE != 2 || DIM == 2) {
+                w[0] = a.P.w[0][p];
+                w[1] = a.P.w[1][p];
+                w[2] = a.P.w[2][p];
+            }
+            i = cell0 % nx;
+            const int rest = cell0 / nx;
+            j = rest % ny;
+            k = DIM == 3 ? rest / ny : 0;
+            li = local_coord(i, ox, T0, G, nx);
+            lj = local_coord(j, oy, T1, G, ny);
+            lk = DIM == 3 ? local_coord(k, oz, T2, G, nz) : 0;
+            inr = li >= -G && li < T0 + G && lj >= -G && lj < T1 + G && (DIM == 2 || (lk >= -G && lk < T2 + G));
+
+            n0 = o0; n1 = o1; n2 = o2;
+            live = true;
+            if (MODE != 2) {
+                R fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
+                form_factor(o0, fx, Sx);
+                form_factor(o1, fy, Sy);
+                if (DIM == 3) {
+                    form_factor(o2, fz, Sz);
+                } else {
+                    fz[0] = R(1); fz[1] = R(0);
+                    Sz[0] = R(0); Sz[1] = R(1); Sz[2] = R(0);
+                }
+                R Ep[3], Bp[3];
+                if (inr) {
+                    SmemReader<R> rd;
+                    for (int c = 0; c < 3; ++c) { rd.E[c] = sE[c]; rd.B[c] = sB[c]; }
+                    rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
+                    rd.s1 = P0;
+                    rd.s2 = P0 * P1;
+                    gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                } else {
+                    R w6[15] = {fx[0], fx[1], Sx[0], Sx[1], Sx[2], fy[0], fy[1], Sy[0], Sy[1], Sy[2],
+                                fz[0], fz[1], Sz[0], Sz[1], Sz[2]};
+                    gather_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, w6, Ep, Bp);
+                }
+                boris(w, Ep, Bp, hq, c2);
+                if (!finite3(w[0], w[1], w[2])) {
+                    atomicOr(a.err, ERR_NONFINITE);
+                    live = false;   // the particle keeps x^n and contributes no current
+                } else {
+                    const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
+                    s0 = renormalize(o0, w[0] * ig * cN0, n0);
+                    s1 = renormalize(o1, w[1] * ig * cN1, n1);
+                    if (DIM == 3) s2 = renormalize(o2, w[2] * ig * cN2, n2);
+                    uz = cl * w[2] * ig;
+                    const int i1 = wrapi(i + s0, nx), j1 = wrapi(j + s1, ny), k1 = DIM == 3 ? wrapi(k + s2, nz) : 0;
+                    const int cell1 = i1 + nx * (j1 + ny * k1);
+                    if (MODE == 1) {
+                        a.old_cell[p] = cell0;
+                        a.old_off[0][p] = o0;
+                        a.old_off[1][p] = o1;
+                        if (DIM == 3) a.old_off[2][p] = o2;
+                    }
+                    a.P.cell[p] = cell1;
+                    a.P.off[0][p] = n0;
+                    a.P.off[1][p] = n1;
+                    if (DIM == 3) a.P.off[2][p] = n2;
+                    a.P.w[0][p] = w[0];
+                    a.P.w[1][p] = w[1];
+                    a.P.w[2][p] = w[2];
+                }
+            } else {
+                // deposit-only: x^{n+1} is the stored state, the shift follows from the cells
+                const int cell1 = a.P.cell[p];
+                n0 = a.P.off[0][p];
+                n1 = a.P.off[1][p];
+                if (DIM == 3) n2 = a.P.off[2][p];
+                const int i1 = cell1 % nx, r1 = cell1 / nx, j1 = r1 % ny, k1 = DIM == 3 ? r1 / ny : 0;
+                s0 = i1 - i; if (s0 > 1) s0 -= nx; if (s0 < -1) s0 += nx;
+                s1 = j1 - j; if (s1 > 1) s1 -= ny; if (s1 < -1) s1 += ny;
+                if (DIM == 3) { s2 = k1 - k; if (s2 > 1) s2 -= nz; if (s2 < -1) s2 += nz; }
+                if (DIM == 2) {
+                    const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
+                    uz = cl * w[2] * ig;
+                }
             }
         }
         if (MODE == 1) continue;
 
         // ---- virtual-path current (Eq. current) -------------------------------
-        AxisWin<R> X, Y, Z;
-        axis_window(o0, n0, s0, X);
-        axis_window(o1, n1, s1, Y);
-        if (DIM == 3) axis_window(o2, n2, s2, Z); else Z = X;
-        // axes along which some particle of this warp changed cell (warp-uniform)
-        const unsigned am = __activemask();
-        const int full = (__any_sync(am, s0 != 0) ? 1 : 0) | (__any_sync(am, s1 != 0) ? 2 : 0) |
-                         (DIM == 3 && __any_sync(am, s2 != 0) ? 4 : 0);
-        if (inr) {
-            const int base = (li + G + 2) + P0 * ((lj + G + 2) + (DIM == 3 ? P1 * (lk + G + 2) : 0));
-            if constexpr (FIX) {
-                FixedAcc acc;
-                for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
-                acc.base = base;
-                acc.s1 = P0;
-                acc.s2 = P0 * P1;
-                deposit<DIM>(acc, X, Y, Z, kfs, uz, full);
-            } else {
-                SmemAcc<R> acc;
-                for (int c = 0; c < 3; ++c) acc.J[c] = sJ[c];
-                acc.base = base;
-                acc.s1 = P0;
-                acc.s2 = P0 * P1;
-                deposit<DIM>(acc, X, Y, Z, kf, uz, full);
-            }
-        } else {
-            AxisWin<R> win[3] = {X, Y, Z};
+        const bool moved = (s0 | s1 | s2) != 0;
+        const int base = (li + G + 2) + P0 * ((lj + G + 2) + (DIM == 3 ? P1 * (lk + G + 2) : 0));
+        if (live && inr && !moved) {
+            AxisWin<R> X, Y, Z;
+            axis_window_still(o0, n0, X);
+            axis_window_still(o1, n1, Y);
+            if (DIM == 3) axis_window_still(o2, n2, Z); else Z = X;
+            deposit_local(base, X, Y, Z, uz, 0);
+        } else if (live && !inr) {
+            AxisWin<R> win[3];
+            axis_window(o0, n0, s0, win[0]);
+            axis_window(o1, n1, s1, win[1]);
+            if (DIM == 3) axis_window(o2, n2, s2, win[2]); else win[2] = win[0];
             deposit_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, win, kf, uz);
         }
+        const bool enq = live && inr && moved;
+        const unsigned qm = __ballot_sync(0xffffffffu, enq);
+        if (enq) {
+            const int slot = qn + __popc(qm & ((1u << lane) - 1u));
+            qv[0 * kQueueCap + slot] = o0;
+            qv[1 * kQueueCap + slot] = o1;
+            qv[3 * kQueueCap + slot] = n0;
+            qv[4 * kQueueCap + slot] = n1;
+            if (DIM == 3) {
+                qv[2 * kQueueCap + slot] = o2;
+                qv[5 * kQueueCap + slot] = n2;
+            } else {
+                qv[6 * kQueueCap + slot] = uz;
+            }
+            qs[slot] = (base << 8) | (s0 + 1) | ((s1 + 1) << 2) | ((s2 + 1) << 4);
+        }
+        qn += __popc(qm);
+        if (qn >= 32) {   // warp-uniform
+            __syncwarp();
+            qn -= 32;
+            drain(qn, true);
+            __syncwarp();   // the drained slots are free again
+        }
+    }
+    if (NEED_J && qn > 0) {
+        __syncwarp();
+        drain(0, lane < qn);
     }
 
     if (NEED_J) {
@@ -389,7 +485,7 @@ size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz
     const long long je = (long long)p0 * p1 * (dims == 3 ? tz + 2 * halo + 4 : 1);
     size_t b = 0;
     if (mode != 2) b += 6 * fe * es;
-    if (mode != 1) b += 24 * je;
+    if (mode != 1) b += 24 * je + (size_t)(kThreads / 32) * kQueueCap * (kQueueVals * es + sizeof(int));
     return b;
 }
 
