@@ -309,35 +309,32 @@ template <typename R>
 struct SmemAcc {
     R *J[3];
     int base, s1, s2;
-    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, R v) const
+    // adds kp * t
+    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, R kp, R t) const
     {
-        atomicAdd(&J[a][base + dx + s1 * dy + s2 * dz], v);
+        atomicAdd(&J[a][base + dx + s1 * dy + s2 * dz], kp * t);
     }
 };
 
 // FP32 form: the shared current tile accumulates in integer fixed point.
 // Shared-memory float atomics run as compare-and-swap loops on this GPU while
-// 32-bit integer atomics are native, so every contribution v is scaled by the
-// power of two `scale` (q = v*scale, exact; the caller's prefactors carry the
-// scale) and split into hi = rint(q/2^16) and
-// lo = q - hi*2^16 (exact, |lo| <= 2^15), both rounded to integers with the
-// 1.5*2^23 magic-number trick instead of conversion instructions.  The two
-// integer sums are exact; the block converts hi*2^16 + lo back once.  The
-// scale keeps |q| <= 2^33 for every possible contribution and the sums below
-// 2^31 for up to 2^13 particles per block (set on the host).
+// 32-bit integer atomics are native.  A contribution is the product kp*t, where
+// the caller's prefactor kp carries a power-of-two scale: q = kp*t (|q| <= 2^33
+// for every possible contribution; the host sets the scale).  It is split into
+// hi = rint(q/2^16) and lo = rint(q - hi*2^16) (|lo| <= 2^15), both taken from
+// the 1.5*2^23 magic-number addition, with the product formed inside the fused
+// multiply-adds.  The two integer sums are exact and stay below 2^31 for up to
+// 2^13 particles per block; the block converts hi*2^16 + lo back once.
 struct FixedAcc {
     int *hi[3];
     int *lo[3];
     int base, s1, s2;
-    // v arrives already scaled (the caller folds the scale into its prefactors)
-    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, float v) const
+    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, float kp, float t) const
     {
         const float magic = 12582912.0f;   // 1.5 * 2^23
-        const float q = v;
-        const float th = fmaf(q, 1.0f / 65536.0f, magic);
-        const float hf = th - magic;
-        const float r = fmaf(-hf, 65536.0f, q);
-        const float tl = r + magic;
+        const float th = fmaf(kp * (1.0f / 65536.0f), t, magic);   // magic + hi
+        const float mh = fmaf(th, -65536.0f, magic * 65536.0f);      // -hi * 2^16, exact
+        const float tl = fmaf(kp, t, mh) + magic;                    // magic + lo
         const int idx = base + dx + s1 * dy + s2 * dz;
         atomicAdd(&hi[a][idx], __float_as_int(th) - 0x4B400000);
         atomicAdd(&lo[a][idx], __float_as_int(tl) - 0x4B400000);
@@ -349,8 +346,9 @@ struct GlobalAcc {
     R *J[3];
     long long cell_base;
     int i, j, k, nx, ny, nz;
-    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, R v) const
+    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, R kp, R t) const
     {
+        const R v = kp * t;
         const long long idx = cell_base + (long long)wrapi(i + dx, nx) +
                               (long long)nx * ((long long)wrapi(j + dy, ny) + (long long)ny * wrapi(k + dz, nz));
         atomicAdd(&J[a][idx], v);
@@ -382,7 +380,7 @@ __device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, con
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     if (q == 2 && !fx) continue;
-                    acc.add(0, X.lo + 1 + q, Y.lo + wy, Z.lo + wz, kf[0] * X.D[q] * T);
+                    acc.add(0, X.lo + 1 + q, Y.lo + wy, Z.lo + wz, kf[0] * X.D[q], T);
                 }
             }
         }
@@ -396,7 +394,7 @@ __device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, con
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     if (q == 2 && !fy) continue;
-                    acc.add(1, X.lo + wx, Y.lo + 1 + q, Z.lo + wz, kf[1] * Y.D[q] * T);
+                    acc.add(1, X.lo + wx, Y.lo + 1 + q, Z.lo + wz, kf[1] * Y.D[q], T);
                 }
             }
         }
@@ -410,7 +408,7 @@ __device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, con
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     if (q == 2 && !fz) continue;
-                    acc.add(2, X.lo + wx, Y.lo + wy, Z.lo + 1 + q, kf[2] * Z.D[q] * T);
+                    acc.add(2, X.lo + wx, Y.lo + wy, Z.lo + 1 + q, kf[2] * Z.D[q], T);
                 }
             }
         }
@@ -422,7 +420,7 @@ __device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, con
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 if (q == 2 && !fx) continue;
-                acc.add(0, X.lo + 1 + q, Y.lo + wy, 0, t * X.D[q]);
+                acc.add(0, X.lo + 1 + q, Y.lo + wy, 0, t, X.D[q]);
             }
         }
 #pragma unroll
@@ -432,7 +430,7 @@ __device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, con
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 if (q == 2 && !fy) continue;
-                acc.add(1, X.lo + wx, Y.lo + 1 + q, 0, t * Y.D[q]);
+                acc.add(1, X.lo + wx, Y.lo + 1 + q, 0, t, Y.D[q]);
             }
         }
         const R kz = kf[2] * uz;
@@ -443,7 +441,7 @@ __device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, con
             for (int wx = 0; wx < 4; ++wx) {
                 if (wx == 3 && !fx) continue;
                 const R T = X.Pp[wx] * Y.Pp[wy] + third * X.Pm[wx] * Y.Pm[wy];
-                acc.add(2, X.lo + wx, Y.lo + wy, 0, kz * T);
+                acc.add(2, X.lo + wx, Y.lo + wy, 0, kz, T);
             }
         }
     }

@@ -1,472 +1,9 @@
-// pic_particles.cu -- per-particle kernels of the charge-conserving PIC step
-// (Sokolov, arXiv:1101.0809, Appendix step 2): alternating-order gather, push,
-// move and virtual-path deposit, run over tile-sorted particles.
-//
-// One thread block takes one work item: a contiguous range of particles that
-// the last sort put in one tile.  The block stages E and B of the tile plus a
-// halo of (halo + 1) cells in shared memory, and a current tile with a halo of
-// (halo + 2) cells.  Each thread streams particles (coalesced SoA loads),
-// gathers from shared memory, pushes, renormalizes offset and cell, writes the
-// particle back and scatters its 144 (3D) or 40 (2D) face currents into the
-// shared current tile with shared-memory atomics.  A particle that has drifted
-// more than `halo` cells outside the tile since the last sort takes the same
-// arithmetic on the global arrays instead (periodic indices, global atomics).
-// At the end the block adds its current tile to the global J with atomics.
-#include <cooperative_groups.h>
-
-#include "pic_internal.h"
-
-namespace cg = cooperative_groups;
+// pic_particles.cu -- launchers of the per-particle kernels (pic_particles.cuh)
+// with the tile geometry read at run time, the shared-memory sizing, and the
+// particle loader and pool copy.
+#include "pic_particles.cuh"
 
 namespace pic {
-
-template <typename R>
-struct PartArgs {
-    const WorkItem *items;
-    const int *n_items;
-    const RunDev *runs;
-    const GroupDev *groups;
-    Pool<R> P;
-    Fields<R> F;
-    int *old_cell;
-    R *old_off[3];
-    int halo;
-    int *err;
-};
-
-extern __shared__ __align__(16) unsigned char g_smem[];
-
-// Per-warp deposit queue of particles that changed cell: capacity (a warp adds
-// at most 32 entries to fewer than 32) and the values kept per entry (old and
-// new offsets, u_z in 2D) besides one packed int (tile base << 8 | shifts + 1).
-constexpr int kQueueCap = 64;
-constexpr int kQueueVals = 7;
-
-__device__ __forceinline__ bool finite3(float a, float b, float c) { return isfinite(a) && isfinite(b) && isfinite(c); }
-__device__ __forceinline__ bool finite3(double a, double b, double c) { return isfinite(a) && isfinite(b) && isfinite(c); }
-
-// Tile-local coordinate of global index i for a tile starting at o with extent T:
-// the periodic image in [-G, T+G) if there is one (the grid is wider than the
-// staged region, so at most one image lies there), else a value outside it.
-__device__ __forceinline__ int local_coord(int i, int o, int T, int G, int n)
-{
-    int l = i - o;
-    if (l >= T + G) l -= n;
-    if (l < -G) l += n;
-    return l;
-}
-
-// Rare path: a particle more than `halo` cells outside its tile since the
-// last sort.  Same arithmetic on the periodic global arrays; kept out of line
-// so that it does not raise the register count of the tiled path.
-template <int DIM, typename R>
-__device__ __noinline__ void gather_global(const Fields<R> &F, long long cb, int i, int j, int k, int nx, int ny,
-                                           int nz, const R *w6, R *Ep, R *Bp)
-{
-    GlobalReader<R> rd;
-    for (int c = 0; c < 3; ++c) { rd.E[c] = F.E[c]; rd.B[c] = F.B[c]; }
-    for (int q = 0; q < 4; ++q) {
-        rd.xi[q] = cb + wrapi(i - 1 + q, nx);
-        rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
-        rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
-    }
-    R fx[2] = {w6[0], w6[1]}, fy[2] = {w6[5], w6[6]}, fz[2] = {w6[10], w6[11]};
-    R Sx[3] = {w6[2], w6[3], w6[4]}, Sy[3] = {w6[7], w6[8], w6[9]}, Sz[3] = {w6[12], w6[13], w6[14]};
-    gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
-}
-
-template <int DIM, typename R>
-__device__ __noinline__ void deposit_global(const Fields<R> &F, long long cb, int i, int j, int k, int nx, int ny,
-                                            int nz, const AxisWin<R> *win, const R *kf, R uz)
-{
-    GlobalAcc<R> acc;
-    for (int c = 0; c < 3; ++c) acc.J[c] = F.J[c];
-    acc.cell_base = cb;
-    acc.i = i; acc.j = j; acc.k = k;
-    acc.nx = nx; acc.ny = ny; acc.nz = nz;
-    deposit<DIM>(acc, win[0], win[1], win[2], kf, uz, 7);
-}
-
-// MODE 0: fused gather + push + move + deposit (pic_step).
-// MODE 1: gather + push + move, keeping x^n (pic_gather_push).
-// MODE 2: deposit from the kept x^n and the current x^{n+1} (pic_deposit_current).
-// Shared memory: E and B tiles (6 * nf values of R) for MODES 0, 1; the current
-// tile for MODES 0, 2: in FP32 two int32 fixed-point words per value, in FP64
-// one double -- 24 * nj bytes either way.
-template <int DIM, typename R, int MODE>
-__device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
-{
-    constexpr bool FIX = sizeof(R) == 4;
-    const WorkItem it = a.items[item];
-    const GroupDev gr = a.groups[it.group];
-    const RunDev rn = a.runs[gr.run];
-    const int G = a.halo;
-    const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
-    const int T0 = rn.tile[0], T1 = rn.tile[1], T2 = DIM == 3 ? rn.tile[2] : 1;
-    const int tx = it.tile % rn.ntile[0];
-    const int ty = (it.tile / rn.ntile[0]) % rn.ntile[1];
-    const int tz = DIM == 3 ? it.tile / (rn.ntile[0] * rn.ntile[1]) : 0;
-    const int ox = tx * T0, oy = ty * T1, oz = tz * T2;
-    const int fe0 = T0 + 2 * G + 2, fe1 = T1 + 2 * G + 2, fe2 = DIM == 3 ? T2 + 2 * G + 2 : 1;
-    const int je0 = T0 + 2 * G + 4, je1 = T1 + 2 * G + 4, je2 = DIM == 3 ? T2 + 2 * G + 4 : 1;
-    // the field tile is stored with the current tile's x and y pitches, so that
-    // a particle's field and current bases differ by a constant and one bank
-    // order of the particles (set by the tile sort) serves both
-    const int P0 = rn.pitch[0], P1 = rn.pitch[1];   // >= je0, je1 (see the tile layout choice)
-    const int nf = P0 * P1 * fe2, nj = P0 * P1 * je2;
-    constexpr bool NEED_F = MODE != 2;
-    constexpr bool NEED_J = MODE != 1;
-    const long long cb = rn.cell_base;
-
-    R *sE[3], *sB[3];
-    R *sJ[3];          // FP64 current tile
-    int *sJh[3], *sJl[3];   // FP32 fixed-point current tile
-    {
-        unsigned char *sp = g_smem;
-        if (NEED_F) {
-            R *f = reinterpret_cast<R *>(sp);
-            for (int c = 0; c < 3; ++c) { sE[c] = f + c * nf; sB[c] = f + (3 + c) * nf; }
-            sp += 6 * (size_t)nf * sizeof(R);
-        }
-        if (NEED_J) {
-            for (int c = 0; c < 3; ++c) {
-                sJ[c] = reinterpret_cast<R *>(sp) + c * nj;
-                sJh[c] = reinterpret_cast<int *>(sp) + c * nj;
-                sJl[c] = reinterpret_cast<int *>(sp) + (3 + c) * nj;
-            }
-        }
-    }
-
-    if (NEED_F) {
-        for (int l = threadIdx.x; l < nf; l += blockDim.x) {
-            const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
-            if (lx >= fe0 || ly >= fe1) continue;   // pitch padding
-            const int gx = wrapi(ox - G - 1 + lx, nx);
-            const int gy = wrapi(oy - G - 1 + ly, ny);
-            const int gz = DIM == 3 ? wrapi(oz - G - 1 + lz, nz) : 0;
-            const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                sE[c][l] = a.F.E[c][gi];
-                sB[c][l] = a.F.B[c][gi];
-            }
-        }
-    }
-    if (NEED_J) {
-        int *z = sJh[0];   // 24 * nj bytes = 6 * nj words in both precisions
-        for (int l = threadIdx.x; l < 6 * nj; l += blockDim.x) z[l] = 0;
-    }
-    __syncthreads();
-
-    const R hq = R(0.5 * gr.qm * rn.dt);
-    const R cl = R(rn.c);
-    const R c2 = cl * cl;
-    const R cN0 = R(rn.cN[0]), cN1 = R(rn.cN[1]), cN2 = R(rn.cN[2]);
-    R kf[3];
-    if (DIM == 3) {
-        for (int c = 0; c < 3; ++c) kf[c] = R(-0.25 * rn.d[c] / rn.dt * gr.qp / rn.V);
-    } else {
-        kf[0] = R(-0.5 * rn.d[0] / rn.dt * gr.qp / rn.V);
-        kf[1] = R(-0.5 * rn.d[1] / rn.dt * gr.qp / rn.V);
-        kf[2] = R(0.25 * gr.qp / rn.V);
-    }
-    R kfs[3];   // prefactors with the fixed-point scale of the FP32 current tile folded in
-    for (int c = 0; c < 3; ++c) kfs[c] = kf[c] * R(gr.jscale);
-
-    // Deposit queue of this warp (MODES 0, 2).  A particle that stayed in its
-    // cell along every axis deposits at once with three-cell windows (54
-    // contributions in 3D, 21 in 2D), where its lane's bank is the one the tile
-    // sort gave it.  A particle that changed cell needs four-cell windows along
-    // the axes it crossed; it is queued and deposited later together with 31
-    // other such particles, so that the wider windows are paid only by warps
-    // of moved particles.  The integer current sums do not depend on the order.
-    R *qv = nullptr;
-    int *qs = nullptr;
-    if (NEED_J) {
-        unsigned char *qb = g_smem + (NEED_F ? 6 * (size_t)nf * sizeof(R) : 0) + 24 * (size_t)nj;
-        const int warp = threadIdx.x >> 5;
-        qv = reinterpret_cast<R *>(qb) + (size_t)warp * kQueueCap * kQueueVals;
-        qs = reinterpret_cast<int *>(qb + (size_t)(kThreads / 32) * kQueueCap * kQueueVals * sizeof(R)) +
-             warp * kQueueCap;
-    }
-    const int lane = threadIdx.x & 31;
-    int qn = 0;   // entries in this warp's queue (warp-uniform)
-
-
-    auto deposit_local = [&](int base, const AxisWin<R> &X, const AxisWin<R> &Y, const AxisWin<R> &Z, R uz,
-                             int full) {
-        if constexpr (FIX) {
-            FixedAcc acc;
-            for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
-            acc.base = base;
-            acc.s1 = P0;
-            acc.s2 = P0 * P1;
-            deposit<DIM>(acc, X, Y, Z, kfs, uz, full);
-        } else {
-            SmemAcc<R> acc;
-            for (int c = 0; c < 3; ++c) acc.J[c] = sJ[c];
-            acc.base = base;
-            acc.s1 = P0;
-            acc.s2 = P0 * P1;
-            deposit<DIM>(acc, X, Y, Z, kf, uz, full);
-        }
-    };
-    // deposits the queue entries [first, first + 32) whose lanes have `on`
-    auto drain = [&](int first, bool on) {
-        const int slot = first + lane;
-        R d0 = R(0), d1 = R(0), d2 = R(0), e0 = R(0), e1 = R(0), e2 = R(0), u = R(0);
-        int code = 1 | (1 << 2) | (1 << 4);
-        if (on) {
-            d0 = qv[0 * kQueueCap + slot];
-            d1 = qv[1 * kQueueCap + slot];
-            e0 = qv[3 * kQueueCap + slot];
-            e1 = qv[4 * kQueueCap + slot];
-            if (DIM == 3) {
-                d2 = qv[2 * kQueueCap + slot];
-                e2 = qv[5 * kQueueCap + slot];
-            } else {
-                u = qv[6 * kQueueCap + slot];
-            }
-            code = qs[slot];
-        }
-        const int q0 = (code & 3) - 1, q1 = ((code >> 2) & 3) - 1, q2 = ((code >> 4) & 3) - 1;
-        const int full = (__any_sync(0xffffffffu, q0 != 0) ? 1 : 0) | (__any_sync(0xffffffffu, q1 != 0) ? 2 : 0) |
-                         (DIM == 3 && __any_sync(0xffffffffu, q2 != 0) ? 4 : 0);
-        if (on) {
-            AxisWin<R> X, Y, Z;
-            axis_window(d0, e0, q0, X);
-            axis_window(d1, e1, q1, Y);
-            if (DIM == 3) axis_window(d2, e2, q2, Z); else Z = X;
-            deposit_local(code >> 8, X, Y, Z, u, full);
-        }
-    };
-
-    // warps run whole rounds of 32 consecutive particles (the last one partial)
-    for (long long pw = it.begin + (threadIdx.x & ~31); pw < it.end; pw += blockDim.x) {
-        const long long p = pw + lane;
-        const bool valid = p < it.end;
-        bool live = false;   // the particle moves and deposits this step
-        bool inr = false;
-        int i = 0, j = 0, k = 0, li = 0, lj = 0, lk = 0;
-        R o0 = R(0), o1 = R(0), o2 = R(0), n0 = R(0), n1 = R(0), n2 = R(0), uz = R(0);
-        int s0 = 0, s1 = 0, s2 = 0;
-        if (valid) {
-            // ---- the particle's state at x^n (old) -------------------------------
-            const int cell0 = MODE == 2 ? a.old_cell[p] : a.P.cell[p];
-            o0 = MODE == 2 ? a.old_off[0][p] : a.P.off[0][p];
-            o1 = MODE == 2 ? a.old_off[1][p] : a.P.off[1][p];
-            o2 = DIM == 3 ? (MODE == 2 ? a.old_off[2][p] : a.P.off[2][p]) : R(0);
-            R w[3] = {R(0), R(0), R(0)};
-            if (MODE != 2 || DIM == 2) {
-                w[0] = a.P.w[0][p];
-                w[1] = a.P.w[1][p];
-                w[2] = a.P.w[2][p];
-            }
-            i = cell0 % nx;
-            const int rest = cell0 / nx;
-            j = rest % ny;
-            k = DIM == 3 ? rest / ny : 0;
-            li = local_coord(i, ox, T0, G, nx);
-            lj = local_coord(j, oy, T1, G, ny);
-            lk = DIM == 3 ? local_coord(k, oz, T2, G, nz) : 0;
-            inr = li >= -G && li < T0 + G && lj >= -G && lj < T1 + G && (DIM == 2 || (lk >= -G && lk < T2 + G));
-
-            n0 = o0; n1 = o1; n2 = o2;
-            live = true;
-            if (MODE != 2) {
-                R fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
-                form_factor(o0, fx, Sx);
-                form_factor(o1, fy, Sy);
-                if (DIM == 3) {
-                    form_factor(o2, fz, Sz);
-                } else {
-                    fz[0] = R(1); fz[1] = R(0);
-                    Sz[0] = R(0); Sz[1] = R(1); Sz[2] = R(0);
-                }
-                R Ep[3], Bp[3];
-                if (inr) {
-                    SmemReader<R> rd;
-                    for (int c = 0; c < 3; ++c) { rd.E[c] = sE[c]; rd.B[c] = sB[c]; }
-                    rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
-                    rd.s1 = P0;
-                    rd.s2 = P0 * P1;
-                    gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
-                } else {
-                    R w6[15] = {fx[0], fx[1], Sx[0], Sx[1], Sx[2], fy[0], fy[1], Sy[0], Sy[1], Sy[2],
-                                fz[0], fz[1], Sz[0], Sz[1], Sz[2]};
-                    gather_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, w6, Ep, Bp);
-                }
-                boris(w, Ep, Bp, hq, c2);
-                if (!finite3(w[0], w[1], w[2])) {
-                    atomicOr(a.err, ERR_NONFINITE);
-                    live = false;   // the particle keeps x^n and contributes no current
-                } else {
-                    const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
-                    s0 = renormalize(o0, w[0] * ig * cN0, n0);
-                    s1 = renormalize(o1, w[1] * ig * cN1, n1);
-                    if (DIM == 3) s2 = renormalize(o2, w[2] * ig * cN2, n2);
-                    uz = cl * w[2] * ig;
-                    const int i1 = wrapi(i + s0, nx), j1 = wrapi(j + s1, ny), k1 = DIM == 3 ? wrapi(k + s2, nz) : 0;
-                    const int cell1 = i1 + nx * (j1 + ny * k1);
-                    if (MODE == 1) {
-                        a.old_cell[p] = cell0;
-                        a.old_off[0][p] = o0;
-                        a.old_off[1][p] = o1;
-                        if (DIM == 3) a.old_off[2][p] = o2;
-                    }
-                    a.P.cell[p] = cell1;
-                    a.P.off[0][p] = n0;
-                    a.P.off[1][p] = n1;
-                    if (DIM == 3) a.P.off[2][p] = n2;
-                    a.P.w[0][p] = w[0];
-                    a.P.w[1][p] = w[1];
-                    a.P.w[2][p] = w[2];
-                }
-            } else {
-                // deposit-only: x^{n+1} is the stored state, the shift follows from the cells
-                const int cell1 = a.P.cell[p];
-                n0 = a.P.off[0][p];
-                n1 = a.P.off[1][p];
-                if (DIM == 3) n2 = a.P.off[2][p];
-                const int i1 = cell1 % nx, r1 = cell1 / nx, j1 = r1 % ny, k1 = DIM == 3 ? r1 / ny : 0;
-                s0 = i1 - i; if (s0 > 1) s0 -= nx; if (s0 < -1) s0 += nx;
-                s1 = j1 - j; if (s1 > 1) s1 -= ny; if (s1 < -1) s1 += ny;
-                if (DIM == 3) { s2 = k1 - k; if (s2 > 1) s2 -= nz; if (s2 < -1) s2 += nz; }
-                if (DIM == 2) {
-                    const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
-                    uz = cl * w[2] * ig;
-                }
-            }
-        }
-        if (MODE == 1) continue;
-
-        // ---- virtual-path current (Eq. current) -------------------------------
-        const bool moved = (s0 | s1 | s2) != 0;
-        const int base = (li + G + 2) + P0 * ((lj + G + 2) + (DIM == 3 ? P1 * (lk + G + 2) : 0));
-        if (live && inr && !moved) {
-            AxisWin<R> X, Y, Z;
-            axis_window_still(o0, n0, X);
-            axis_window_still(o1, n1, Y);
-            if (DIM == 3) axis_window_still(o2, n2, Z); else Z = X;
-            deposit_local(base, X, Y, Z, uz, 0);
-        } else if (live && !inr) {
-            AxisWin<R> win[3];
-            axis_window(o0, n0, s0, win[0]);
-            axis_window(o1, n1, s1, win[1]);
-            if (DIM == 3) axis_window(o2, n2, s2, win[2]); else win[2] = win[0];
-            deposit_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, win, kf, uz);
-        }
-        const bool enq = live && inr && moved;
-        const unsigned qm = __ballot_sync(0xffffffffu, enq);
-        if (enq) {
-            const int slot = qn + __popc(qm & ((1u << lane) - 1u));
-            qv[0 * kQueueCap + slot] = o0;
-            qv[1 * kQueueCap + slot] = o1;
-            qv[3 * kQueueCap + slot] = n0;
-            qv[4 * kQueueCap + slot] = n1;
-            if (DIM == 3) {
-                qv[2 * kQueueCap + slot] = o2;
-                qv[5 * kQueueCap + slot] = n2;
-            } else {
-                qv[6 * kQueueCap + slot] = uz;
-            }
-            qs[slot] = (base << 8) | (s0 + 1) | ((s1 + 1) << 2) | ((s2 + 1) << 4);
-        }
-        qn += __popc(qm);
-        if (qn >= 32) {   // warp-uniform
-            __syncwarp();
-            qn -= 32;
-            drain(qn, true);
-            __syncwarp();   // the drained slots are free again
-        }
-    }
-    if (NEED_J && qn > 0) {
-        __syncwarp();
-        drain(0, lane < qn);
-    }
-
-    if (NEED_J) {
-        __syncthreads();
-        const float jinv = gr.jinv;
-        for (int l = threadIdx.x; l < nj; l += blockDim.x) {
-            const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
-            if (lx >= je0 || ly >= je1) continue;   // pitch padding
-            const int gx = wrapi(ox - G - 2 + lx, nx);
-            const int gy = wrapi(oy - G - 2 + ly, ny);
-            const int gz = DIM == 3 ? wrapi(oz - G - 2 + lz, nz) : 0;
-            const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if constexpr (FIX) {
-                    const int h = sJh[c][l], lo = sJl[c][l];
-                    if ((h | lo) != 0)
-                        atomicAdd(&a.F.J[c][gi], (R)(fmaf((float)h, 65536.0f, (float)lo) * jinv));
-                } else {
-                    const R v = sJ[c][l];
-                    if (v != R(0)) atomicAdd(&a.F.J[c][gi], v);
-                }
-            }
-        }
-    }
-    __syncthreads();   // the shared tiles are free for the block's next item
-}
-
-template <int DIM, typename R, int MODE>
-__global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
-{
-    if ((int)blockIdx.x >= *a.n_items) return;
-    process_item<DIM, R, MODE>(a, blockIdx.x);
-}
-
-// Run of a batch that owns concatenated cell l (run_cell_base has nruns + 1 entries).
-__device__ __forceinline__ int find_run(const long long *run_cell_base, int nruns, long long l)
-{
-    int lo = 0, hi = nruns;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (run_cell_base[mid] <= l) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-// One whole step of every run of a batch in one cooperative launch: B half
-// step (+ J clear) over all cells, grid barrier, the fused particle work items,
-// grid barrier, B half step, grid barrier, E full step.  The grid is sized so
-// that all blocks are resident (cooperative launch), which the barriers need.
-template <int DIM, typename R>
-__global__ void __launch_bounds__(kThreads) k_step_persistent(const PartArgs<R> a, int nruns,
-                                                              const long long *run_cell_base)
-{
-    cg::grid_group grid = cg::this_grid();
-    const long long total = run_cell_base[nruns];
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    for (long long l = t0; l < total; l += stride) {
-        const int r = find_run(run_cell_base, nruns, l);
-        yee_b_half_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r], 1);
-    }
-    grid.sync();
-    const int ni = *a.n_items;
-    for (int it = blockIdx.x; it < ni; it += gridDim.x) process_item<DIM, R, 0>(a, it);
-    grid.sync();
-    for (long long l = t0; l < total; l += stride) {
-        const int r = find_run(run_cell_base, nruns, l);
-        yee_b_half_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r], 0);
-    }
-    grid.sync();
-    for (long long l = t0; l < total; l += stride) {
-        const int r = find_run(run_cell_base, nruns, l);
-        yee_e_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r]);
-    }
-}
-
-template <int DIM, typename R, int MODE>
-static cudaError_t launch_t(cudaStream_t st, int max_items, size_t smem, const PartArgs<R> &a)
-{
-    if (max_items <= 0) return cudaSuccess;
-    k_particles<DIM, R, MODE><<<max_items, kThreads, smem, st>>>(a);
-    return cudaGetLastError();
-}
 
 template <int DIM, typename R>
 static cudaError_t launch_mode(int mode, cudaStream_t st, int max_items, size_t smem, const PartArgs<R> &a)
@@ -502,6 +39,10 @@ static cudaError_t set_limit_t(int mode, size_t bytes)
 
 cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes)
 {
+    if (prec != 0 && mode == 0) {
+        const cudaError_t e = fixed_set_smem_limit(dims, bytes);
+        if (e != cudaSuccess) return e;
+    }
     if (dims == 3) return prec == 0 ? set_limit_t<3, double>(mode, bytes) : set_limit_t<3, float>(mode, bytes);
     return prec == 0 ? set_limit_t<2, double>(mode, bytes) : set_limit_t<2, float>(mode, bytes);
 }
@@ -545,31 +86,13 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
                          : launch_mode<2, double>(mode, st, max_items, smem, a);
     }
     auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
+    if (mode == 0) {
+        const int tile[3] = {max_tile_x, max_tile_y, max_tile_z};
+        cudaError_t e = cudaSuccess;
+        if (launch_particles_fixed(dims, st, max_items, smem, a, tile, halo, p0, p1, &e)) return e;
+    }
     return dims == 3 ? launch_mode<3, float>(mode, st, max_items, smem, a)
                      : launch_mode<2, float>(mode, st, max_items, smem, a);
-}
-
-template <int DIM, typename R>
-static cudaError_t persistent_t(cudaStream_t st, size_t smem, int nruns, const long long *run_cell_base,
-                                PartArgs<R> a, int *grid_blocks, int launch)
-{
-    auto fn = k_step_persistent<DIM, R>;
-    cudaError_t e;
-    if (*grid_blocks <= 0) {
-        // first use (outside any stream capture): shared-memory limit and grid size
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem);
-        if (e != cudaSuccess) return e;
-        if (per <= 0) return cudaErrorInvalidConfiguration;
-        *grid_blocks = sms * per;
-    }
-    if (!launch) return cudaSuccess;
-    void *args[] = {(void *)&a, (void *)&nruns, (void *)&run_cell_base};
-    return cudaLaunchCooperativeKernel((const void *)fn, dim3(*grid_blocks), dim3(kThreads), args, smem, st);
 }
 
 cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const WorkItem *items, const int *n_items,
@@ -586,6 +109,10 @@ cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const Wo
                          : persistent_t<2, double>(st, smem, nruns, run_cell_base, a, grid_blocks, launch);
     }
     auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, nullptr, none, halo, err);
+    const int tile[3] = {tx, ty, tz};
+    cudaError_t e = cudaSuccess;
+    if (launch_persistent_fixed(dims, st, smem, nruns, run_cell_base, a, grid_blocks, launch, tile, halo, p0, p1, &e))
+        return e;
     return dims == 3 ? persistent_t<3, float>(st, smem, nruns, run_cell_base, a, grid_blocks, launch)
                      : persistent_t<2, float>(st, smem, nruns, run_cell_base, a, grid_blocks, launch);
 }

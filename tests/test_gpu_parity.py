@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 from paper_1101_0809_gb300 import workloads as W
-from pichelpers import (FP32_TOL, FP64_TOL, close, compare_particles, make_grid, oracle_grid,
+from pichelpers import (FP32_TOL, FP64_TOL, close, compare_particles, fp64_field_tol, make_grid, oracle_grid,
                         oracle_species, positions_from_gpu, tile_sort_perm)
 
 pytestmark = pytest.mark.gpu
@@ -183,6 +183,17 @@ def test_fp64_particles_far_outside_their_tile_take_the_global_path(P, halo):
     P.pic_step(grid.h, wl.steps)
     g, osp, E, B, J = run_oracle(wl, wl.steps)
     _check_state(P, wl, grid, osp, E, B, J, FP64_TOL)
+    grid.close()
+
+
+@pytest.mark.parametrize("halo", [0, 1])
+def test_fp64_3d_particles_far_outside_their_tile_take_the_global_path(P, halo):
+    wl = small3d(vth=0.3, steps=8, ions=False)     # fast electrons, no sort for 8 steps
+    grid = make_grid(P, wl, P.PIC_FP64, tile=(8, 4, 4), halo=halo, sort_interval=1000, ppb=512)
+    P.pic_step(grid.h, wl.steps)
+    g, osp, E, B, J = run_oracle(wl, wl.steps)
+    tol = fp64_field_tol(wl, osp)
+    _check_state(P, wl, grid, osp, E, B, J, tol)
     grid.close()
 
 
