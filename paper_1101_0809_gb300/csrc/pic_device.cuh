@@ -325,7 +325,15 @@ struct SmemAcc {
 // the 1.5*2^23 magic-number addition, with the product formed inside the fused
 // multiply-adds.  The two integer sums are exact and stay below 2^31 for up to
 // 2^13 particles per block; the block converts hi*2^16 + lo back once.
-struct FixedAcc {
+// The words added are the bit patterns of magic + hi and magic + lo, i.e.
+// kFixBias + hi and kFixBias + lo.  With SUB the bias is taken off before each
+// atomic; without it the block takes N * kFixBias off each word once before the
+// flush, N being the number of contributions the word received (known for the
+// fixed stencil of a particle that stayed in its cell; integer sums wrap
+// modulo 2^32, so the order does not matter).
+constexpr unsigned kFixBias = 0x4B400000u;
+template <bool SUB>
+struct FixedAccT {
     int *hi[3];
     int *lo[3];
     int base, s1, s2;
@@ -336,10 +344,11 @@ struct FixedAcc {
         const float mh = fmaf(th, -65536.0f, magic * 65536.0f);      // -hi * 2^16, exact
         const float tl = fmaf(kp, t, mh) + magic;                    // magic + lo
         const int idx = base + dx + s1 * dy + s2 * dz;
-        atomicAdd(&hi[a][idx], __float_as_int(th) - 0x4B400000);
-        atomicAdd(&lo[a][idx], __float_as_int(tl) - 0x4B400000);
+        atomicAdd(&hi[a][idx], SUB ? __float_as_int(th) - (int)kFixBias : __float_as_int(th));
+        atomicAdd(&lo[a][idx], SUB ? __float_as_int(tl) - (int)kFixBias : __float_as_int(tl));
     }
 };
+using FixedAcc = FixedAccT<true>;
 
 template <typename R>
 struct GlobalAcc {

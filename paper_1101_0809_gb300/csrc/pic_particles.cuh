@@ -141,6 +141,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     R *sE[3], *sB[3];
     R *sJ[3];          // FP64 current tile
     int *sJh[3], *sJl[3];   // FP32 fixed-point current tile
+    int *scnt = nullptr;    // FP32: particles that stayed in their cell, per base cell
     {
         unsigned char *sp = g_smem;
         if (NEED_F) {
@@ -154,6 +155,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                 sJh[c] = reinterpret_cast<int *>(sp) + c * nj;
                 sJl[c] = reinterpret_cast<int *>(sp) + (3 + c) * nj;
             }
+            if (FIX) scnt = reinterpret_cast<int *>(sp) + 6 * nj;
         }
     }
 
@@ -173,8 +175,8 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         }
     }
     if (NEED_J) {
-        int *z = sJh[0];   // 24 * nj bytes = 6 * nj words in both precisions
-        for (int l = threadIdx.x; l < 6 * nj; l += blockDim.x) z[l] = 0;
+        int *z = sJh[0];   // 24 * nj bytes = 6 * nj words in both precisions, + nj counts in FP32
+        for (int l = threadIdx.x; l < (FIX ? 7 : 6) * nj; l += blockDim.x) z[l] = 0;
     }
     __syncthreads();
 
@@ -203,7 +205,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     R *qv = nullptr;
     int *qs = nullptr;
     if (NEED_J) {
-        unsigned char *qb = g_smem + (NEED_F ? 6 * (size_t)nf * sizeof(R) : 0) + 24 * (size_t)nj;
+        unsigned char *qb = g_smem + (NEED_F ? 6 * (size_t)nf * sizeof(R) : 0) + (FIX ? 28 : 24) * (size_t)nj;
         const int warp = threadIdx.x >> 5;
         qv = reinterpret_cast<R *>(qb) + (size_t)warp * kQueueCap * kQueueVals;
         qs = reinterpret_cast<int *>(qb + (size_t)(kThreads / 32) * kQueueCap * kQueueVals * sizeof(R)) +
@@ -216,7 +218,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     auto deposit_local = [&](int base, const AxisWin<R> &X, const AxisWin<R> &Y, const AxisWin<R> &Z, R uz,
                              int full) {
         if constexpr (FIX) {
-            FixedAcc acc;
+            FixedAcc acc;   // bias taken off per contribution (variable stencil)
             for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
             acc.base = base;
             acc.s1 = P0;
@@ -368,7 +370,18 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             axis_window_still(o0, n0, X);
             axis_window_still(o1, n1, Y);
             if (DIM == 3) axis_window_still(o2, n2, Z); else Z = X;
-            deposit_local(base, X, Y, Z, uz, 0);
+            if constexpr (FIX) {
+                // fixed stencil: the bias comes off once per word at the flush
+                FixedAccT<false> acc;
+                for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
+                acc.base = base;
+                acc.s1 = P0;
+                acc.s2 = P0 * P1;
+                deposit<DIM>(acc, X, Y, Z, kfs, uz, 0);
+                atomicAdd(&scnt[base], 1);
+            } else {
+                deposit_local(base, X, Y, Z, uz, 0);
+            }
         } else if (live && !inr) {
             AxisWin<R> win[3];
             axis_window(o0, n0, s0, win[0]);
@@ -415,10 +428,53 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             const int gy = wrapi(oy - G - 2 + ly, ny);
             const int gz = DIM == 3 ? wrapi(oz - G - 2 + lz, nz) : 0;
             const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
+            // FP32: contributions of particles that stayed in their cell, per
+            // component: the stencil of such a particle with base b covers the
+            // cells b + (dx, dy, dz) with dx in {0, 1} and dy, dz in {-1, 0, 1}
+            // for J^x (faces 0, 1; cells -1..1), likewise for J^y and J^z, so a
+            // cell l received sum_{b in l - stencil} cnt[b] of them
+            unsigned nst[3] = {0u, 0u, 0u};
+            if constexpr (FIX) {
+                if (lx >= 1 && lx < je0 - 1 && ly >= 1 && ly < je1 - 1 && (DIM == 2 || (lz >= 1 && lz < je2 - 1))) {
+                    if (DIM == 3) {
+                        unsigned tot = 0, px = 0, py = 0, pz = 0;   // all 27, and the +1 planes
+#pragma unroll
+                        for (int oz = -1; oz <= 1; ++oz)
+#pragma unroll
+                            for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+                                for (int ox = -1; ox <= 1; ++ox) {
+                                    const unsigned v = (unsigned)scnt[l + ox + P0 * (oy + P1 * oz)];
+                                    tot += v;
+                                    if (ox == 1) px += v;
+                                    if (oy == 1) py += v;
+                                    if (oz == 1) pz += v;
+                                }
+                        nst[0] = tot - px;
+                        nst[1] = tot - py;
+                        nst[2] = tot - pz;
+                    } else {
+                        unsigned tot = 0, px = 0, py = 0;
+#pragma unroll
+                        for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+                            for (int ox = -1; ox <= 1; ++ox) {
+                                const unsigned v = (unsigned)scnt[l + ox + P0 * oy];
+                                tot += v;
+                                if (ox == 1) px += v;
+                                if (oy == 1) py += v;
+                            }
+                        nst[0] = tot - px;
+                        nst[1] = tot - py;
+                        nst[2] = tot;
+                    }
+                }
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 if constexpr (FIX) {
-                    const int h = sJh[c][l], lo = sJl[c][l];
+                    const unsigned off = nst[c] * kFixBias;
+                    const int h = (int)((unsigned)sJh[c][l] - off), lo = (int)((unsigned)sJl[c][l] - off);
                     if ((h | lo) != 0)
                         atomicAdd(&a.F.J[c][gi], (R)(fmaf((float)h, 65536.0f, (float)lo) * jinv));
                 } else {
