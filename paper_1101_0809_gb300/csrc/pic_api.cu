@@ -231,6 +231,19 @@ int upload_groups(pic_grid *g)
         const int e = bound > 0.0 ? R - (int)std::ceil(std::log2(bound)) : 0;
         gd[q].jscale = (float)std::ldexp(1.0, e);
         gd[q].jinv = (float)std::ldexp(1.0, -e);
+        gd[q].hq = 0.5 * gd[q].qm * rn.dt;
+        if (g->dims == 3) {
+            for (int a = 0; a < 3; ++a) gd[q].kf[a] = -0.25 * rn.d[a] / rn.dt * gd[q].qp / rn.V;
+        } else {
+            gd[q].kf[0] = -0.5 * rn.d[0] / rn.dt * gd[q].qp / rn.V;
+            gd[q].kf[1] = -0.5 * rn.d[1] / rn.dt * gd[q].qp / rn.V;
+            gd[q].kf[2] = 0.25 * gd[q].qp / rn.V;
+        }
+        gd[q].hqf = (float)gd[q].hq;
+        for (int a = 0; a < 3; ++a) {
+            gd[q].kff[a] = (float)gd[q].kf[a];
+            gd[q].kfsf[a] = gd[q].kff[a] * gd[q].jscale;
+        }
         base[q] = h.base;
     }
     base[ng] = pb;
@@ -388,6 +401,10 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
     rd.V = d->dims == 3 ? dd[0] * dd[1] * dd[2] : dd[0] * dd[1];
     rd.rho_bg = d->rho_bg;
     rd.cell_base = 0;
+    rd.div_nx = make_divu31(n[0]);
+    rd.div_ny = make_divu31(n[1]);
+    rd.cf = (float)rd.c;
+    for (int a = 0; a < 3; ++a) rd.cNf[a] = (float)rd.cN[a];
     return PIC_OK;
 }
 

@@ -15,6 +15,30 @@ namespace pic {
 // pool.  Tiles of all groups share one global numbering (group tile_base + the
 // tile's linear index inside its run) that is the sort key.
 // ---------------------------------------------------------------------------
+// Division of a non-negative int below 2^31 by a fixed divisor d >= 1 as a
+// multiply and shift (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994, Thm. 4.2): with L = 31 + ceil(log2 d) and
+// m = ceil(2^L / d) (at most 2^32), floor(n / d) = (n * m) >> L exactly, and
+// n * m < 2^63.
+struct DivU31 {
+    unsigned long long m;
+    int L;
+};
+inline DivU31 make_divu31(int d)
+{
+    int c = 0;
+    while ((1LL << c) < (long long)d) ++c;
+    const int L = 31 + c;
+    DivU31 v;
+    v.m = (unsigned long long)(((unsigned __int128)1 << L) + (unsigned)d - 1) / (unsigned)d;
+    v.L = L;
+    return v;
+}
+__device__ __forceinline__ int divu31(int n, const DivU31 &v)
+{
+    return (int)(((unsigned long long)(unsigned)n * v.m) >> v.L);
+}
+
 struct RunDev {
     int n[3];             // cells per axis (n[2] = 1 in 2D)
     int tile[3];          // tile extents (tile[2] = 1 in 2D)
@@ -26,6 +50,8 @@ struct RunDev {
     double d[3];
     double V;             // cell volume (dx*dy in 2D)
     double rho_bg;        // uniform background charge density
+    DivU31 div_nx, div_ny;  // division by n[0] and n[1]
+    float cf, cNf[3];     // c and the Courant numbers in FP32
 };
 
 struct GroupDev {
@@ -37,6 +63,11 @@ struct GroupDev {
     double mp;            // macro mass m_p = weight*m
     float jscale;         // fixed-point scale of the FP32 shared current tile (a power of two)
     float jinv;           // 1 / jscale
+    // push and deposit prefactors of the group in its run, from the host:
+    // hq = (1/2)(q/m) dt; kf[a] = -(1/4)(d_a/dt) q_p/V in 3D, and in 2D
+    // kf[0,1] = -(1/2)(d_a/dt) q_p/V, kf[2] = (1/4) q_p/V (see deposit)
+    double hq, kf[3];
+    float hqf, kff[3], kfsf[3];   // FP32: the same, and kf * jscale
 };
 
 struct WorkItem {

@@ -180,20 +180,22 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     }
     __syncthreads();
 
-    const R hq = R(0.5 * gr.qm * rn.dt);
-    const R cl = R(rn.c);
-    const R c2 = cl * cl;
-    const R cN0 = R(rn.cN[0]), cN1 = R(rn.cN[1]), cN2 = R(rn.cN[2]);
-    R kf[3];
-    if (DIM == 3) {
-        for (int c = 0; c < 3; ++c) kf[c] = R(-0.25 * rn.d[c] / rn.dt * gr.qp / rn.V);
+    // constants of the group and run, prepared on the host (no FP64 arithmetic
+    // runs in the FP32 kernels)
+    R hq, cl, cN0, cN1, cN2;
+    R kf[3], kfs[3];   // kfs: prefactors with the fixed-point scale of the FP32 current tile folded in
+    if constexpr (FIX) {
+        hq = gr.hqf;
+        cl = rn.cf;
+        cN0 = rn.cNf[0]; cN1 = rn.cNf[1]; cN2 = rn.cNf[2];
+        for (int c = 0; c < 3; ++c) { kf[c] = gr.kff[c]; kfs[c] = gr.kfsf[c]; }
     } else {
-        kf[0] = R(-0.5 * rn.d[0] / rn.dt * gr.qp / rn.V);
-        kf[1] = R(-0.5 * rn.d[1] / rn.dt * gr.qp / rn.V);
-        kf[2] = R(0.25 * gr.qp / rn.V);
+        hq = gr.hq;
+        cl = rn.c;
+        cN0 = rn.cN[0]; cN1 = rn.cN[1]; cN2 = rn.cN[2];
+        for (int c = 0; c < 3; ++c) { kf[c] = gr.kf[c]; kfs[c] = gr.kf[c]; }
     }
-    R kfs[3];   // prefactors with the fixed-point scale of the FP32 current tile folded in
-    for (int c = 0; c < 3; ++c) kfs[c] = kf[c] * R(gr.jscale);
+    const R c2 = cl * cl;
 
     // Deposit queue of this warp (MODES 0, 2).  A particle that stayed in its
     // cell along every axis deposits at once with three-cell windows (54
@@ -284,10 +286,14 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                 w[1] = a.P.w[1][p];
                 w[2] = a.P.w[2][p];
             }
-            i = cell0 % nx;
-            const int rest = cell0 / nx;
-            j = rest % ny;
-            k = DIM == 3 ? rest / ny : 0;
+            const int rest = divu31(cell0, rn.div_nx);
+            i = cell0 - rest * nx;
+            if (DIM == 3) {
+                k = divu31(rest, rn.div_ny);
+                j = rest - k * ny;
+            } else {
+                j = rest;
+            }
             li = local_coord(i, ox, T0, G, nx);
             lj = local_coord(j, oy, T1, G, ny);
             lk = DIM == 3 ? local_coord(k, oz, T2, G, nz) : 0;
@@ -350,7 +356,10 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                 n0 = a.P.off[0][p];
                 n1 = a.P.off[1][p];
                 if (DIM == 3) n2 = a.P.off[2][p];
-                const int i1 = cell1 % nx, r1 = cell1 / nx, j1 = r1 % ny, k1 = DIM == 3 ? r1 / ny : 0;
+                const int r1 = divu31(cell1, rn.div_nx);
+                const int i1 = cell1 - r1 * nx;
+                const int k1 = DIM == 3 ? divu31(r1, rn.div_ny) : 0;
+                const int j1 = r1 - k1 * ny;
                 s0 = i1 - i; if (s0 > 1) s0 -= nx; if (s0 < -1) s0 += nx;
                 s1 = j1 - j; if (s1 > 1) s1 -= ny; if (s1 < -1) s1 += ny;
                 if (DIM == 3) { s2 = k1 - k; if (s2 > 1) s2 -= nz; if (s2 < -1) s2 += nz; }
