@@ -164,7 +164,7 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- our arm
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("pic_device.cuh", "pic_particles.cu"):
+    for f in ("pic_device.cuh", "pic_particles.cuh", "pic_particles.cu", "pic_particles_fixed.cu"):
         h.update(open(os.path.join(ROOT, "paper_1101_0809_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
