@@ -403,6 +403,7 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
     rd.cell_base = 0;
     rd.div_nx = make_divu31(n[0]);
     rd.div_ny = make_divu31(n[1]);
+    for (int a = 0; a < 3; ++a) rd.div_t[a] = make_divu31(t[a]);
     rd.cf = (float)rd.c;
     for (int a = 0; a < 3; ++a) rd.cNf[a] = (float)rd.cN[a];
     return PIC_OK;

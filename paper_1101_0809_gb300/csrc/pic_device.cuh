@@ -51,6 +51,7 @@ struct RunDev {
     double V;             // cell volume (dx*dy in 2D)
     double rho_bg;        // uniform background charge density
     DivU31 div_nx, div_ny;  // division by n[0] and n[1]
+    DivU31 div_t[3];        // division by the tile extents
     float cf, cNf[3];     // c and the Courant numbers in FP32
 };
 

@@ -138,15 +138,14 @@ __global__ void k_keys(long long total, const int *cell, const long long *group_
         const int mid = (lo + hi) >> 1;
         if (group_base[mid] <= p) lo = mid; else hi = mid;
     }
-    const GroupDev g = groups[lo];
-    const RunDev &r = runs[g.run];
+    const RunDev &r = runs[groups[lo].run];
     const int c = cell[p];
-    const int i = c % r.n[0];
-    const int rest = c / r.n[0];
-    const int j = rest % r.n[1];
-    const int k = rest / r.n[1];
-    const int t = ((k / r.tile[2]) * r.ntile[1] + j / r.tile[1]) * r.ntile[0] + i / r.tile[0];
-    keys[p] = (unsigned)(g.tile_base + t);
+    const int rest = divu31(c, r.div_nx);
+    const int i = c - rest * r.n[0];
+    const int k = divu31(rest, r.div_ny);
+    const int j = rest - k * r.n[1];
+    const int t = (divu31(k, r.div_t[2]) * r.ntile[1] + divu31(j, r.div_t[1])) * r.ntile[0] + divu31(i, r.div_t[0]);
+    keys[p] = (unsigned)(groups[lo].tile_base + t);
     vals[p] = (unsigned)p;
 }
 
@@ -224,10 +223,14 @@ __global__ void __launch_bounds__(kSortThreads) k_bank_order(const long long *ti
                                                              unsigned *vals_out, const int *cell, const GroupDev *groups,
                                                              int ngroups, const RunDev *runs, int halo, int dims)
 {
+    constexpr int kRankTab = 1024;   // ranks with a precomputed slot table
     __shared__ unsigned cnt[32];
     __shared__ unsigned tot[32];
     __shared__ unsigned wh[kSortThreads / 32][32];
     __shared__ unsigned pre[kSortThreads / 32][32];
+    __shared__ unsigned gmask[kRankTab];   // banks b with cnt[b] > r
+    __shared__ unsigned gS[kRankTab];      // S(r)
+    __shared__ unsigned ntab;
     const int t = blockIdx.x;
     const long long b0 = tile_start[t], e0 = tile_start[t + 1];
     if (e0 - b0 <= 1) {
@@ -248,7 +251,10 @@ __global__ void __launch_bounds__(kSortThreads) k_bank_order(const long long *ti
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     auto bank_of = [&](unsigned v) -> unsigned {
         const int c = cell[v];
-        const int i = c % nx, r = c / nx, j = r % ny, k = r / ny;
+        const int r = divu31(c, rn.div_nx);
+        const int i = c - r * nx;
+        const int k = dims == 3 ? divu31(r, rn.div_ny) : 0;
+        const int j = r - k * ny;
         const int base = (i - ox + halo + 2) + P0 * ((j - oy + halo + 2) + (dims == 3 ? P1 * (k - oz + halo + 2) : 0));
         return (unsigned)base & 31u;
     };
@@ -259,6 +265,37 @@ __global__ void __launch_bounds__(kSortThreads) k_bank_order(const long long *ti
     if (tid < kSortThreads / 32 * 32) wh[tid >> 5][tid & 31] = 0;
     __syncthreads();
     for (long long o = b0 + tid; o < e0; o += kSortThreads) atomicAdd(&cnt[bank_of(vals_in[o])], 1u);
+    __syncthreads();
+    // slot tables for ranks below min(max cnt, kRankTab): the mask of banks that
+    // still have a particle of rank r, and S(r) = sum_b min(cnt[b], r), the
+    // number of slots taken by lower ranks
+    if (warp == 0) {
+        unsigned m = cnt[lane];
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) ntab = m < (unsigned)kRankTab ? m : (unsigned)kRankTab;
+    }
+    __syncthreads();
+    const unsigned nt = ntab;
+    for (unsigned r = tid; r < nt; r += kSortThreads) {
+        unsigned m = 0;
+        for (int b = 0; b < 32; ++b) m |= (cnt[b] > r ? 1u : 0u) << b;
+        gmask[r] = m;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        unsigned run = 0;
+        for (unsigned r0 = 0; r0 < nt; r0 += 32) {
+            const unsigned r = r0 + lane;
+            const unsigned g = r < nt ? __popc(gmask[r]) : 0u;
+            unsigned inc = g;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (r < nt) gS[r] = run + inc - g;
+            run += __shfl_sync(0xffffffffu, inc, 31);
+        }
+    }
     __syncthreads();
     const unsigned ltm = (1u << lane) - 1u;
     for (long long r0 = b0; r0 < e0; r0 += kSortThreads) {
@@ -284,10 +321,15 @@ __global__ void __launch_bounds__(kSortThreads) k_bank_order(const long long *ti
         if (valid) {
             const unsigned rank = pre[warp][bk] + rk;   // rank among the tile's particles of bank bk
             unsigned S = 0, below = 0;
-            for (int b = 0; b < 32; ++b) {
-                const unsigned cb = cnt[b];
-                S += cb < rank ? cb : rank;
-                if (b < (int)bk && cb > rank) ++below;
+            if (rank < nt) {
+                S = gS[rank];
+                below = __popc(gmask[rank] & ((1u << bk) - 1u));
+            } else {
+                for (int b = 0; b < 32; ++b) {
+                    const unsigned cb = cnt[b];
+                    S += cb < rank ? cb : rank;
+                    if (b < (int)bk && cb > rank) ++below;
+                }
             }
             vals_out[b0 + S + below] = v;
         }
