@@ -231,6 +231,10 @@ int upload_groups(pic_grid *g)
         const int e = bound > 0.0 ? R - (int)std::ceil(std::log2(bound)) : 0;
         gd[q].jscale = (float)std::ldexp(1.0, e);
         gd[q].jinv = (float)std::ldexp(1.0, -e);
+        // charge of one particle on one cell: (q_p/V) Sx Sy Sz <= q_p/V
+        const int er = qV > 0.0 ? R - (int)std::ceil(std::log2(qV)) : 0;
+        gd[q].rscale = (float)std::ldexp(1.0, er);
+        gd[q].rinv = (float)std::ldexp(1.0, -er);
         gd[q].hq = 0.5 * gd[q].qm * rn.dt;
         if (g->dims == 3) {
             for (int a = 0; a < 3; ++a) gd[q].kf[a] = -0.25 * rn.d[a] / rn.dt * gd[q].qp / rn.V;
@@ -527,6 +531,9 @@ int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out)
         }
         if ((e = particles_set_smem_limit(g->dims, g->prec, mode, b)) != cudaSuccess) return bail(e, "smem limit");
     }
+    if (g->prec == PIC_FP32 && (e = diag_set_smem_limit(g->dims, diag_items_smem_bytes(g->dims, g->tile, g->halo,
+                                                                                      g->pitch))) != cudaSuccess)
+        return bail(e, "smem limit");
     if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return bail(e, "create");
     *out = g;
     return PIC_OK;
@@ -1060,7 +1067,8 @@ int pic_diagnostics_run(pic_grid *g, int run, pic_diag *out)
     cudaError_t e = launch_diagnostics_run(g->dims, g->prec, g->stream, g->d_runs, run,
                                            (long long)rn.n[0] * rn.n[1] * rn.n[2], rn.cell_base, g->d_groups,
                                            g->d_group_base, (int)g->groups.size(), g->total, g->pool, g->E, g->B,
-                                           g->diag, g->have_ref[run] ? 0 : 1, kDiagBlocks, kDiagBlocks, &nl);
+                                           g->diag, g->have_ref[run] ? 0 : 1, kDiagBlocks, kDiagBlocks, &nl,
+                                           g->items, g->n_items, g->halo, g->tile, g->pitch);
     launch_count_add(g, nl);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
     double r[kDiagResults];

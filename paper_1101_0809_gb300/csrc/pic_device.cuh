@@ -69,6 +69,7 @@ struct GroupDev {
     // kf[0,1] = -(1/2)(d_a/dt) q_p/V, kf[2] = (1/4) q_p/V (see deposit)
     double hq, kf[3];
     float hqf, kff[3], kfsf[3];   // FP32: the same, and kf * jscale
+    float rscale, rinv;   // fixed-point scale of the FP32 diagnostics' shared charge tile, 1/rscale
 };
 
 struct WorkItem {

@@ -116,6 +116,156 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_particles(int run, long l
     block_reduce_store(v, -1, partials + (long long)blockIdx.x * kPartVals);
 }
 
+// FP32 state: the same particle sums over the tile-sorted work items.  A block
+// stages the item's E tile (halo + 1) in shared memory and accumulates rho on a
+// shared tile in integer fixed point (the current tile's scheme of the
+// particle kernels, scale rscale per group), then adds it to the FP64 rho.  The
+// per-particle terms are FP32 (kinetic energy in the cancellation-free form
+// m c w^2 / (gamma + c)), every sum FP64.  Particles more than `halo` cells
+// outside their tile read E and add rho on the global arrays.  Blocks take
+// items round-robin, so the partial slot of a block sums a fixed set of items.
+struct ZeroB {   // gather reader for E only: B reads as 0
+    const float *E[3];
+    int base, s1, s2;
+    __device__ __forceinline__ float e(int a, int dx, int dy, int dz) const { return E[a][base + dx + s1 * dy + s2 * dz]; }
+    __device__ __forceinline__ float b(int, int, int, int) const { return 0.0f; }
+};
+struct GlobalZeroB {
+    const float *E[3];
+    long long xi[4], yj[4], zk[4];
+    __device__ __forceinline__ float e(int a, int dx, int dy, int dz) const { return E[a][xi[dx + 1] + yj[dy + 1] + zk[dz + 1]]; }
+    __device__ __forceinline__ float b(int, int, int, int) const { return 0.0f; }
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_items(int run, const WorkItem *items, const int *n_items,
+                                                             const GroupDev *groups, const RunDev *runs, Pool<float> P,
+                                                             Fields<float> F, int halo, double *rho, double *partials)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    double v[kPartVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int ni = *n_items;
+    const RunDev &rn = runs[run];
+    const int G = halo;
+    const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
+    const int T0 = rn.tile[0], T1 = rn.tile[1], T2 = DIM == 3 ? rn.tile[2] : 1;
+    const int P0 = rn.pitch[0], P1 = rn.pitch[1];
+    const int fe0 = T0 + 2 * G + 2, fe1 = T1 + 2 * G + 2, fe2 = DIM == 3 ? T2 + 2 * G + 2 : 1;
+    const int nf = P0 * P1 * fe2;
+    float *sE[3];
+    for (int c = 0; c < 3; ++c) sE[c] = reinterpret_cast<float *>(dsm) + c * nf;
+    int *rh = reinterpret_cast<int *>(dsm) + 3 * nf;
+    int *rl = rh + nf;
+    const long long cb = rn.cell_base;
+    const float cl = rn.cf, c2 = cl * cl;
+    for (int item = blockIdx.x; item < ni; item += gridDim.x) {
+        const WorkItem it = items[item];
+        const GroupDev &gr = groups[it.group];
+        if (gr.run != run) continue;   // the same for the whole block
+        const int tx = it.tile % rn.ntile[0];
+        const int ty = (it.tile / rn.ntile[0]) % rn.ntile[1];
+        const int tz = DIM == 3 ? it.tile / (rn.ntile[0] * rn.ntile[1]) : 0;
+        const int ox = tx * T0, oy = ty * T1, oz = tz * T2;
+        for (int l = threadIdx.x; l < nf; l += blockDim.x) {
+            const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
+            rh[l] = 0;
+            rl[l] = 0;
+            if (lx >= fe0 || ly >= fe1) continue;   // pitch padding
+            const int gx = wrapi(ox - G - 1 + lx, nx);
+            const int gy = wrapi(oy - G - 1 + ly, ny);
+            const int gz = DIM == 3 ? wrapi(oz - G - 1 + lz, nz) : 0;
+            const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
+            for (int c = 0; c < 3; ++c) sE[c][l] = F.E[c][gi];
+        }
+        __syncthreads();
+        const float qV = (float)(gr.qp / rn.V);
+        const float kq = qV * gr.rscale;
+        const float mp = (float)gr.mp;
+        const float hqdt = (float)(0.5 * gr.qp * rn.dt * rn.c);
+        FixedAcc acc;
+        acc.hi[0] = rh;
+        acc.lo[0] = rl;
+        acc.s1 = P0;
+        acc.s2 = P0 * P1;
+        for (long long p = it.begin + threadIdx.x; p < it.end; p += blockDim.x) {
+            const int c0 = P.cell[p];
+            const int rest = divu31(c0, rn.div_nx);
+            const int i = c0 - rest * nx;
+            const int k = DIM == 3 ? divu31(rest, rn.div_ny) : 0;
+            const int j = rest - k * ny;
+            int li = i - ox, lj = j - oy, lk = k - oz;
+            if (li >= T0 + G) li -= nx; if (li < -G) li += nx;
+            if (lj >= T1 + G) lj -= ny; if (lj < -G) lj += ny;
+            if (DIM == 3) { if (lk >= T2 + G) lk -= nz; if (lk < -G) lk += nz; }
+            const bool inr = li >= -G && li < T0 + G && lj >= -G && lj < T1 + G && (DIM == 2 || (lk >= -G && lk < T2 + G));
+            float fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
+            form_factor(P.off[0][p], fx, Sx);
+            form_factor(P.off[1][p], fy, Sy);
+            if (DIM == 3) {
+                form_factor(P.off[2][p], fz, Sz);
+            } else {
+                fz[0] = 1.0f; fz[1] = 0.0f; Sz[0] = 0.0f; Sz[1] = 1.0f; Sz[2] = 0.0f;
+            }
+            float Ep[3], Bp[3];
+            if (inr) {
+                ZeroB rd;
+                for (int c = 0; c < 3; ++c) rd.E[c] = sE[c];
+                rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
+                rd.s1 = P0;
+                rd.s2 = P0 * P1;
+                gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                acc.base = rd.base;
+                const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
+#pragma unroll
+                for (int dz = kz0; dz <= kz1; ++dz)
+#pragma unroll
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const float t = Sy[dy + 1] * Sz[dz + 1];
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) acc.add(0, dx, dy, dz, kq * Sx[dx + 1], t);
+                    }
+            } else {
+                GlobalZeroB rd;
+                for (int c = 0; c < 3; ++c) rd.E[c] = F.E[c];
+                for (int q = 0; q < 4; ++q) {
+                    rd.xi[q] = cb + wrapi(i - 1 + q, nx);
+                    rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
+                    rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
+                }
+                gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
+                for (int dz = kz0; dz <= kz1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx)
+                            atomicAdd(&rho[rd.xi[dx + 1] + rd.yj[dy + 1] + rd.zk[dz + 1]],
+                                      (double)qV * Sx[dx + 1] * Sy[dy + 1] * Sz[dz + 1]);
+            }
+            const float w0 = P.w[0][p], w1 = P.w[1][p], w2 = P.w[2][p];
+            const float ww = w0 * w0 + w1 * w1 + w2 * w2;
+            const float gam = sqrtf(ww + c2);
+            v[0] += (double)(mp * cl * ww / (gam + cl));
+            v[1] += (double)(mp * w0);
+            v[2] += (double)(mp * w1);
+            v[3] += (double)(mp * w2);
+            v[4] += (double)(hqdt * (w0 * Ep[0] + w1 * Ep[1] + w2 * Ep[2]) / gam);
+            v[5] += 1.0;
+        }
+        __syncthreads();
+        const double rinv = gr.rinv;
+        for (int l = threadIdx.x; l < nf; l += blockDim.x) {
+            const int h = rh[l], lo = rl[l];
+            if ((h | lo) == 0) continue;
+            const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
+            const int gx = wrapi(ox - G - 1 + lx, nx);
+            const int gy = wrapi(oy - G - 1 + ly, ny);
+            const int gz = DIM == 3 ? wrapi(oz - G - 1 + lz, nz) : 0;
+            atomicAdd(&rho[cb + gx + (long long)nx * (gy + (long long)ny * gz)], ((double)h * 65536.0 + (double)lo) * rinv);
+        }
+        __syncthreads();
+    }
+    block_reduce_store(v, -1, partials + (long long)blockIdx.x * kPartVals);
+}
+
 // Cells: residual against the reference, charge, field energies.
 // Partial slots: 0 max |r - r_ref|, 1 sum (r - r_ref)^2, 2 charge, 3 sum E^2, 4 sum B^2.
 template <int DIM, typename R>
@@ -200,7 +350,8 @@ template <int DIM, typename R>
 static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run, long long run_cells,
                           const GroupDev *groups, const long long *group_base, int ngroups, long long total,
                           const PoolBuf &P, void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
-                          int np_blocks, int nc_blocks, int *launches)
+                          int np_blocks, int nc_blocks, int *launches, const WorkItem *items, const int *n_items,
+                          int halo, size_t items_smem)
 {
     Pool<R> pool;
     pool.cell = P.cell;
@@ -213,8 +364,24 @@ static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run, long lon
         F.B[c] = (R *)B[c];
         F.J[c] = nullptr;
     }
-    k_diag_particles<DIM, R><<<np_blocks, kDiagThreads, 0, st>>>(run, total, group_base, ngroups, groups, runs, pool,
-                                                                 F, scr.rho, scr.partials);
+    if (sizeof(R) == 4 && items) {
+        Pool<float> pf;
+        Fields<float> ff;
+        pf.cell = P.cell;
+        pf.id = P.id;
+        for (int c = 0; c < 3; ++c) {
+            pf.off[c] = (float *)P.off[c];
+            pf.w[c] = (float *)P.w[c];
+            ff.E[c] = (float *)E[c];
+            ff.B[c] = (float *)B[c];
+            ff.J[c] = nullptr;
+        }
+        k_diag_items<DIM><<<np_blocks, kDiagThreads, items_smem, st>>>(run, items, n_items, groups, runs, pf, ff, halo,
+                                                                       scr.rho, scr.partials);
+    } else {
+        k_diag_particles<DIM, R><<<np_blocks, kDiagThreads, 0, st>>>(run, total, group_base, ngroups, groups, runs,
+                                                                     pool, F, scr.rho, scr.partials);
+    }
     k_diag_cells<DIM, R><<<nc_blocks, kDiagThreads, 0, st>>>(runs, run, F, scr.rho, scr.resid_ref, set_ref,
                                                              scr.partials + (long long)np_blocks * kPartVals);
     k_diag_final<<<1, 32, 0, st>>>(scr.partials, np_blocks, scr.partials + (long long)np_blocks * kPartVals,
@@ -227,19 +394,34 @@ cudaError_t launch_diagnostics_run(int dims, int prec, cudaStream_t st, const Ru
                                    long long run_cells, long long cell_base, const GroupDev *groups,
                                    const long long *group_base, int ngroups, long long total, const PoolBuf &P,
                                    void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
-                                   int np_blocks, int nc_blocks, int *launches)
+                                   int np_blocks, int nc_blocks, int *launches, const WorkItem *items,
+                                   const int *n_items, int halo, const int tile[3], const int pitch[2])
 {
     cudaError_t e = cudaMemsetAsync(scr.rho + cell_base, 0, sizeof(double) * run_cells, st);
     if (e != cudaSuccess) return e;
+    const size_t items_smem = diag_items_smem_bytes(dims, tile, halo, pitch);
     if (dims == 3)
         return prec == 0 ? diag_t<3, double>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
-                                             scr, set_ref, np_blocks, nc_blocks, launches)
+                                             scr, set_ref, np_blocks, nc_blocks, launches, nullptr, nullptr, halo, 0)
                          : diag_t<3, float>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
-                                            scr, set_ref, np_blocks, nc_blocks, launches);
+                                            scr, set_ref, np_blocks, nc_blocks, launches, items, n_items, halo,
+                                            items_smem);
     return prec == 0 ? diag_t<2, double>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
-                                         set_ref, np_blocks, nc_blocks, launches)
+                                         set_ref, np_blocks, nc_blocks, launches, nullptr, nullptr, halo, 0)
                      : diag_t<2, float>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
-                                        set_ref, np_blocks, nc_blocks, launches);
+                                        set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
+}
+
+size_t diag_items_smem_bytes(int dims, const int tile[3], int halo, const int pitch[2])
+{
+    const long long fe2 = dims == 3 ? tile[2] + 2 * halo + 2 : 1;
+    return (size_t)5 * pitch[0] * pitch[1] * fe2 * sizeof(float);
+}
+
+cudaError_t diag_set_smem_limit(int dims, size_t bytes)
+{
+    return dims == 3 ? cudaFuncSetAttribute(k_diag_items<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
+                     : cudaFuncSetAttribute(k_diag_items<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace pic

@@ -99,7 +99,10 @@ cudaError_t launch_diagnostics_run(int dims, int prec, cudaStream_t st, const Ru
                                    long long run_cells, long long cell_base, const GroupDev *groups,
                                    const long long *group_base, int ngroups, long long total, const PoolBuf &P,
                                    void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
-                                   int np_blocks, int nc_blocks, int *launches);
+                                   int np_blocks, int nc_blocks, int *launches, const WorkItem *items,
+                                   const int *n_items, int halo, const int tile[3], const int pitch[2]);
+size_t diag_items_smem_bytes(int dims, const int tile[3], int halo, const int pitch[2]);
+cudaError_t diag_set_smem_limit(int dims, size_t bytes);
 constexpr int kDiagResults = 12;
 
 void set_last_error(const char *msg);

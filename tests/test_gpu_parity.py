@@ -275,6 +275,36 @@ def test_diagnostics_match_oracle(P, which):
     grid.close()
 
 
+@pytest.mark.parametrize("which", ["2d", "3d", "3d-8x4x4"])
+def test_fp32_diagnostics_match_oracle_on_the_same_state(P, which):
+    """The FP32 state's diagnostics (FP32 per-particle terms over the work
+    items, FP64 sums) against the oracle's FP64 diagnostics of the very state
+    the GPU holds, read back.  The field terms are FP64 on both sides; the
+    particle terms carry FP32 rounding per particle."""
+    wl = W.c0_small2d() if which == "2d" else small3d()
+    tile = (8, 4, 4) if which == "3d-8x4x4" else None
+    grid = make_grid(P, wl, P.PIC_FP32, tile=tile)
+    P.pic_step(grid.h, 4)
+    d = P.pic_diagnostics(grid.h)
+    gE, gB, gJ = grid.get_fields()
+    osp = []
+    for s, sp in enumerate(wl.species):
+        cell, off, w, ident = grid.particles(s)
+        x = positions_from_gpu(wl, cell, off)
+        osp.append(O.Species(sp.q, sp.m, sp.weight, x, np.array(w, dtype=np.float64)))
+    od, rho, res = O.diagnostics(oracle_grid(wl), [np.asarray(a, np.float64) for a in gE],
+                                 [np.asarray(a, np.float64) for a in gB], osp, wl.rho_bg)
+    for k in ("field_E", "field_B"):
+        assert d[k] == pytest.approx(od[k], rel=1e-12), k
+    for k in ("kinetic", "half_step_corr", "total"):
+        assert d[k] == pytest.approx(od[k], rel=2e-6, abs=1e-6 * abs(od["total"])), k
+    pabs = sum(float(np.abs(sp.m * sp.weight * sp.w).sum()) for sp in osp)
+    np.testing.assert_allclose(d["momentum"], od["momentum"], rtol=0, atol=1e-6 * pabs)
+    assert d["total_charge"] == pytest.approx(od["charge"], abs=1e-9 * max(1.0, wl.n_particles))
+    assert d["n_particles"] == wl.n_particles
+    grid.close()
+
+
 # ---------------------------------------------------------------------------- edge cases
 def test_edge_positions_empty_species_and_reload(P):
     wl = W.c0_small2d()
