@@ -250,11 +250,14 @@ int pic_profile_read(pic_grid *g, double ms[PIC_PROF_N], long long count[PIC_PRO
  * A snapshot is one contiguous blob: a 48-byte header ("PICS", version 1,
  * dims, precision, group count, particle and cell counts, sort phase, and a
  * checksum of the header) followed by the particle arrays (cell, id, offsets,
- * momenta, in storage order) and the fields E^n, B^{n-1/2}.  pic_state_bytes
- * gives its size.  pic_state_save writes it to dst (device memory if on_device,
- * else host memory); pic_state_restore reads one taken from a grid with the same
- * layout (same runs, species and particle counts), re-sorts the particles by
- * tile and clears the residual references.  Used for checkpoints, for restart
+ * momenta, in storage order), the fields E^n, B^{n-1/2} and the tile starts of
+ * the particle order (from the last tile sort).  pic_state_bytes gives its
+ * size.  pic_state_save writes it to dst (device memory if on_device, else host
+ * memory); pic_state_restore reads one taken from a grid with the same layout
+ * (same runs, species, particle counts and tiles), rebuilds the work items from
+ * the saved tile starts, continues the saved sort schedule (steps since the
+ * last sort) and clears the residual references, so that a restored grid steps
+ * on exactly as the saved one would have.  Used for checkpoints, for restart
  * from a file written by the caller, and by the adjoint's recompute. */
 long long pic_state_bytes(pic_grid *g);
 int pic_state_save(pic_grid *g, void *dst, int on_device);

@@ -1099,9 +1099,10 @@ int pic_diagnostics(pic_grid *g, pic_diag *out) { return pic_diagnostics_run(g, 
 // ---- state snapshots -----------------------------------------------------------
 struct StateHeader {
     char magic[4];            // "PICS"
-    int version;              // 1
+    int version;              // 2
     int dims, prec, ngroups, steps_since_sort;
     long long total, total_cells;
+    long long total_tiles;    // tile starts of the particle order follow the fields
     unsigned checksum;        // FNV-1a of the bytes before this field
     int pad;
 };
@@ -1121,13 +1122,14 @@ static void fill_header(const pic_grid *g, StateHeader &h)
 {
     memset(&h, 0, sizeof(h));
     memcpy(h.magic, "PICS", 4);
-    h.version = 1;
+    h.version = 2;
     h.dims = g->dims;
     h.prec = g->prec;
     h.ngroups = (int)g->groups.size();
     h.steps_since_sort = g->steps_since_sort;
     h.total = g->total;
     h.total_cells = g->total_cells;
+    h.total_tiles = g->total_tiles;
     h.checksum = fnv1a(&h, offsetof(StateHeader, checksum));
 }
 
@@ -1135,7 +1137,8 @@ long long pic_state_bytes(pic_grid *g)
 {
     if (!g) return 0;
     const long long es = (long long)elem(g);
-    return (long long)sizeof(StateHeader) + g->total * (8 + es * (g->dims + 3)) + g->total_cells * es * 6;
+    return (long long)sizeof(StateHeader) + g->total * (8 + es * (g->dims + 3)) + g->total_cells * es * 6 +
+           (long long)sizeof(long long) * (g->total_tiles + 1);
 }
 
 int pic_state_save(pic_grid *g, void *dst, int on_device)
@@ -1160,6 +1163,7 @@ int pic_state_save(pic_grid *g, void *dst, int on_device)
     for (int a = 0; a < 3; ++a) CK(put(g->pool.w[a], es * g->total), "state momenta");
     for (int a = 0; a < 3; ++a) CK(put(g->E[a], es * g->total_cells), "state E");
     for (int a = 0; a < 3; ++a) CK(put(g->B[a], es * g->total_cells), "state B");
+    CK(put(g->tile_start, sizeof(long long) * (g->total_tiles + 1)), "state tile starts");
     CK(cudaStreamSynchronize(g->stream), "state save");
     return PIC_OK;
 }
@@ -1169,10 +1173,10 @@ int pic_state_restore(pic_grid *g, const void *src, int on_device)
     if (!g || !src) return fail(PIC_ERR_INVALID_ARG, "null argument");
     StateHeader h;
     CK(cudaMemcpy(&h, src, sizeof(h), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "state header");
-    if (memcmp(h.magic, "PICS", 4) != 0 || h.version != 1 || h.checksum != fnv1a(&h, offsetof(StateHeader, checksum)))
+    if (memcmp(h.magic, "PICS", 4) != 0 || h.version != 2 || h.checksum != fnv1a(&h, offsetof(StateHeader, checksum)))
         return fail(PIC_ERR_INVALID_ARG, "not a libpic state snapshot (bad magic, version or header checksum)");
     if (h.dims != g->dims || h.prec != g->prec || h.total != g->total || h.total_cells != g->total_cells ||
-        h.ngroups != (int)g->groups.size())
+        h.ngroups != (int)g->groups.size() || h.total_tiles != g->total_tiles)
         return fail(PIC_ERR_INVALID_ARG, "state snapshot does not match this grid's layout");
     const cudaMemcpyKind k = kind_in(on_device);
     const size_t es = elem(g);
@@ -1188,8 +1192,19 @@ int pic_state_restore(pic_grid *g, const void *src, int on_device)
     for (int a = 0; a < 3; ++a) CK(get(g->pool.w[a], es * g->total), "state momenta");
     for (int a = 0; a < 3; ++a) CK(get(g->E[a], es * g->total_cells), "state E");
     for (int a = 0; a < 3; ++a) CK(get(g->B[a], es * g->total_cells), "state B");
-    int rc = do_sort(g);
-    if (rc != PIC_OK) return rc;
+    // the particles are in the order of the sort before the save: its tile
+    // starts give the work items back, and the sort schedule continues
+    CK(get(g->tile_start, sizeof(long long) * (g->total_tiles + 1)), "state tile starts");
+    if (g->total > 0 && !g->groups.empty()) {
+        int nl = 0;
+        cudaError_t e = build_items(g->stream, g->tile_start, g->total_tiles, g->ppi, g->d_groups,
+                                    (int)g->groups.size(), g->sort, g->item_scan, g->items, g->n_items, &nl);
+        launch_count_add(g, nl);
+        if (e != cudaSuccess) return cuda_fail(e, "work items");
+    }
+    g->steps_since_sort = h.steps_since_sort;
+    g->have_old = false;
+    if (!g->capturing) graph_drop(g);
     for (auto &r : g->have_ref) r = 0;
     CK(cudaStreamSynchronize(g->stream), "state restore");
     return PIC_OK;

@@ -81,6 +81,11 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
                                  int particles_per_item, int halo, int banked, int *launches);
+// Work items (ranges of at most particles_per_item particles of one tile) from
+// the tile starts of the current particle order.
+cudaError_t build_items(cudaStream_t st, const long long *tile_start, int total_tiles, int particles_per_item,
+                        const GroupDev *groups, int ngroups, SortScratch &scr, unsigned *item_scan, WorkItem *items,
+                        int *n_items, int *launches);
 
 cudaError_t radix_sort_pairs(cudaStream_t st, long long n, int nbits, unsigned *const keys[2], unsigned *const vals[2],
                              unsigned *hist, unsigned *block_sums, int *cur_out);

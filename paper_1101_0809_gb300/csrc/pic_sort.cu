@@ -466,6 +466,16 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
     *launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
+    return build_items(st, tile_start, total_tiles, particles_per_item, groups, ngroups, scr, item_scan, items, n_items,
+                       launches);
+}
+
+cudaError_t build_items(cudaStream_t st, const long long *tile_start, int total_tiles, int particles_per_item,
+                        const GroupDev *groups, int ngroups, SortScratch &scr, unsigned *item_scan, WorkItem *items,
+                        int *n_items, int *launches)
+{
+    cudaError_t e;
+    const int nt = 256;
     const unsigned nbt = (unsigned)((total_tiles + nt - 1) / nt);
     k_item_counts<<<nbt, nt, 0, st>>>(tile_start, total_tiles, particles_per_item, item_scan);
     *launches += 1;
