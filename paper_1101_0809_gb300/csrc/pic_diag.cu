@@ -138,7 +138,7 @@ struct GlobalZeroB {
 };
 
 template <int DIM>
-__global__ void __launch_bounds__(kDiagThreads) k_diag_items(int run, const WorkItem *items, const int *n_items,
+__global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const WorkItem *items, const int *n_items,
                                                              const GroupDev *groups, const RunDev *runs, Pool<float> P,
                                                              Fields<float> F, int halo, double *rho, double *partials)
 {
@@ -187,6 +187,16 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_items(int run, const Work
         acc.lo[0] = rl;
         acc.s1 = P0;
         acc.s2 = P0 * P1;
+        // the item's share of this thread (at most particles per item / threads
+        // values) is summed in FP32 with Kahan compensation, then added in FP64
+        float ks[5] = {0, 0, 0, 0, 0}, kc[5] = {0, 0, 0, 0, 0};
+        int count = 0;
+        auto kahan = [&](int q, float x) {
+            const float y = x - kc[q];
+            const float t = ks[q] + y;
+            kc[q] = (t - ks[q]) - y;
+            ks[q] = t;
+        };
         for (long long p = it.begin + threadIdx.x; p < it.end; p += blockDim.x) {
             const int c0 = P.cell[p];
             const int rest = divu31(c0, rn.div_nx);
@@ -243,13 +253,15 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_items(int run, const Work
             const float w0 = P.w[0][p], w1 = P.w[1][p], w2 = P.w[2][p];
             const float ww = w0 * w0 + w1 * w1 + w2 * w2;
             const float gam = sqrtf(ww + c2);
-            v[0] += (double)(mp * cl * ww / (gam + cl));
-            v[1] += (double)(mp * w0);
-            v[2] += (double)(mp * w1);
-            v[3] += (double)(mp * w2);
-            v[4] += (double)(hqdt * (w0 * Ep[0] + w1 * Ep[1] + w2 * Ep[2]) / gam);
-            v[5] += 1.0;
+            kahan(0, mp * cl * ww / (gam + cl));
+            kahan(1, mp * w0);
+            kahan(2, mp * w1);
+            kahan(3, mp * w2);
+            kahan(4, hqdt * (w0 * Ep[0] + w1 * Ep[1] + w2 * Ep[2]) / gam);
+            ++count;
         }
+        for (int q = 0; q < 5; ++q) v[q] += (double)ks[q] - (double)kc[q];
+        v[5] += (double)count;
         __syncthreads();
         const double rinv = gr.rinv;
         for (int l = threadIdx.x; l < nf; l += blockDim.x) {
