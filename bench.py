@@ -448,7 +448,7 @@ def our_arm(args):
         el = timed_host(e2e_step, e2e_steps)
         e2e = {"value": world * npart * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": 136, "steps": e2e_steps,
-               "step": "pic_state_restore (pinned host snapshot: cells, ids, offsets, momenta, E, B; re-sort) + "
+               "step": "pic_state_restore (pinned host snapshot: cells, ids, offsets, momenta, E, B, tile starts) + "
                        "pic_step + pic_diagnostics"}
         del host_state
 
