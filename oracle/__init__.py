@@ -24,6 +24,11 @@ class _Grid(C.Structure):
                 ("dt", C.c_double), ("c", C.c_double)]
 
 
+class _Antenna(C.Structure):
+    _fields_ = [("pol", C.c_int), ("i0", C.c_int), ("E0", C.c_double), ("omega", C.c_double),
+                ("ramp", C.c_double)]
+
+
 class _Species(C.Structure):
     _fields_ = [("q", C.c_double), ("m", C.c_double), ("weight", C.c_double),
                 ("n", C.c_longlong), ("x", C.POINTER(C.c_double) * 3),
@@ -46,6 +51,7 @@ def lib():
         _lib = C.CDLL(build_oracle())
         _lib.orc_deposit.restype = C.c_double
         _lib.orc_step.restype = C.c_double
+        _lib.orc_step_antenna.restype = C.c_double
         _lib.orc_push_deposit.restype = C.c_double
         _lib.orc_sort_perm.restype = C.c_int
     return _lib
@@ -180,11 +186,27 @@ def push_deposit(g: Grid, E, B, J, sp: Species):
                                   C.byref(arr[0]))
 
 
-def step(g: Grid, E, B, J, species):
-    """One full time step of the Appendix, in place; returns the worst closure."""
+@dataclass
+class Antenna:
+    """Plane-wave antenna (one-way source on the plane x = i0): pol 1 = E_y/B_z,
+    pol 2 = E_z/B_y; amplitude E0, angular frequency omega, sin^2 rise time ramp."""
+    pol: int
+    i0: int
+    E0: float
+    omega: float
+    ramp: float = 0.0
+
+
+def step(g: Grid, E, B, J, species, antenna: Antenna = None, n: int = 0):
+    """One full time step of the Appendix, in place; returns the worst closure.
+    With an antenna, n is the step's index on the antenna's clock."""
     arr = _species_array(species)
-    return lib().orc_step(C.byref(g.cstruct()), _fields(E), _fields(B), _fields(J),
-                          C.c_int(len(species)), arr)
+    if antenna is None:
+        return lib().orc_step(C.byref(g.cstruct()), _fields(E), _fields(B), _fields(J),
+                              C.c_int(len(species)), arr)
+    a = _Antenna(antenna.pol, antenna.i0, antenna.E0, antenna.omega, antenna.ramp)
+    return lib().orc_step_antenna(C.byref(g.cstruct()), C.byref(a), C.c_longlong(n), _fields(E), _fields(B),
+                                  _fields(J), C.c_int(len(species)), arr)
 
 
 def diagnostics(g: Grid, E, Bh, species, rho_bg=0.0):

@@ -463,6 +463,86 @@ double orc_step(const orc_grid *g, double *E[3], double *B[3], double *J[3], int
 }
 
 /* ---------------------------------------------------------------------------
+ * Plane-wave antenna.  The paper motivates laser-plasma runs but gives no
+ * injection (reading of the laser setup: a one-way source on a plane of
+ * constant x, uniform in y and z).  It is a total-field / scattered-field
+ * plane: the incident wave E_inc travels in +x,
+ *   E_inc(x, t) = E0 g(tau) sin(omega tau),  tau = t - (x - i0) dx / c,
+ *   g(tau) = sin^2(pi tau / (2 ramp)) for 0 < tau < ramp, 1 after, 0 before,
+ * with E_y = E_inc, B_z = E_inc (pol 1) or E_z = E_inc, B_y = -E_inc (pol 2).
+ * Cells i >= i0 of the B components and i >= i0 of the E components hold the
+ * total field, the rest the scattered field.  A B node at x = i0 differences
+ * the E node at x = i0 - 1/2, which lacks the incident wave; the E node at
+ * x = i0 - 1/2 differences the B node at x = i0, which carries it.  So every
+ * B half step of step n (with E at time t^n = n dt) adds, on the plane i = i0,
+ *   +(c_x/2) E_inc(i0 - 1/2, t^n) to B_z (pol 1),  -(c_x/2) E_inc(i0 - 1/2, t^n) to B_y (pol 2),
+ * and the E step (with B at t^n + dt/2) adds, on the plane i = i0 - 1,
+ *   +c_x E_inc(i0, t^n + dt/2) to E_y (pol 1) or to E_z (pol 2)
+ * (in both cases minus c_x times the incident B of the B node).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int pol;                /* 1: E_y with B_z; 2: E_z with B_y */
+    int i0;                 /* first total-field B node along x */
+    double E0, omega, ramp; /* amplitude, angular frequency, rise time */
+} orc_antenna;
+
+static double orc_incident(const orc_grid *g, const orc_antenna *a, double x, double t)
+{
+    double tau = t - (x - a->i0) * g->dx / g->c;
+    if (tau <= 0.0) return 0.0;
+    double env = 1.0;
+    if (tau < a->ramp) {
+        double s = sin(0.5 * ORC_PI * tau / a->ramp);
+        env = s * s;
+    }
+    return a->E0 * env * sin(a->omega * tau);
+}
+
+static void orc_antenna_B(const orc_grid *g, const orc_antenna *a, double t, double *B[3])
+{
+    const double cx = g->c * g->dt / g->dx;
+    const double v = 0.5 * cx * orc_incident(g, a, a->i0 - 0.5, t);
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j) {
+            long long p = cell_index(g, a->i0, j, k);
+            if (a->pol == 1) B[2][p] += v; else B[1][p] -= v;
+        }
+}
+
+static void orc_antenna_E(const orc_grid *g, const orc_antenna *a, double t, double *E[3])
+{
+    const double cx = g->c * g->dt / g->dx;
+    const double v = cx * orc_incident(g, a, a->i0, t);
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j) {
+            long long p = cell_index(g, a->i0 - 1, j, k);
+            if (a->pol == 1) E[1][p] += v; else E[2][p] += v;
+        }
+}
+
+/* Step n of a run with an antenna (n counts the steps since the antenna was
+ * set): the plain step's sequence with the antenna's sheet terms. */
+double orc_step_antenna(const orc_grid *g, const orc_antenna *a, long long n, double *E[3], double *B[3],
+                        double *J[3], int nsp, orc_species *sp)
+{
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    const double tn = n * g->dt;
+    for (int q = 0; q < 3; ++q) memset(J[q], 0, sizeof(double) * N);
+    orc_yee_half_B(g, (const double *const *)E, B);
+    orc_antenna_B(g, a, tn, B);
+    double worst = 0.0;
+    for (int s = 0; s < nsp; ++s) {
+        double cl = orc_push_deposit(g, (const double *const *)E, (const double *const *)B, J, &sp[s]);
+        if (cl > worst) worst = cl;
+    }
+    orc_yee_half_B(g, (const double *const *)E, B);
+    orc_antenna_B(g, a, tn, B);
+    orc_yee_E(g, (const double *const *)B, (const double *const *)J, E);
+    orc_antenna_E(g, a, tn + 0.5 * g->dt, E);
+    return worst;
+}
+
+/* ---------------------------------------------------------------------------
  * Diagnostics at time level n (state E^n, B^{n-1/2}, x^n, w^{n-1/2}):
  *   rho^n from the stored positions (Eq. rho) plus a uniform background;
  *   the Gauss residual r = div_h E - 4 pi rho (Eq. chargelaw; Sec. 2 Poisson form),
