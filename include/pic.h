@@ -171,6 +171,51 @@ int pic_deposit_current(pic_grid *g);
  * PIC_E_FULL: E += -4 pi dt J + c curl_h B (Eq. escheme). */
 int pic_yee_update(pic_grid *g, int which);
 
+/* ---- Plane-wave antenna ------------------------------------------------------
+ * The paper motivates laser-plasma runs but gives no injection; this antenna is
+ * a one-way source on a plane of constant x (a total-field / scattered-field
+ * boundary), uniform in y and z, so it adds no charge and leaves the discrete
+ * continuity equation untouched.  The incident wave travels in +x:
+ *   E_inc(x, t) = amplitude * g(tau) * sin(omega * tau),  tau = t - (x - plane) dx / c,
+ *   g = sin^2(pi tau / (2 ramp)) for 0 < tau < ramp, 1 after, 0 before;
+ * polarization PIC_POL_Y: E_y = E_inc, B_z = E_inc; PIC_POL_Z: E_z = E_inc, B_y = -E_inc.
+ * The total field starts at the B node x = plane.  Each B half step of step n
+ * adds (c_x/2) E_inc(plane - 1/2, t^n) to B_z (PIC_POL_Y) or subtracts it from
+ * B_y (PIC_POL_Z) on the cells i = plane; the E step adds
+ * c_x E_inc(plane, t^n + dt/2) to E_y or E_z on the cells i = plane - 1.  t^n =
+ * n dt counts the E steps since the antenna was set, plus `start` (the
+ * antenna's clock, kept on the device, saved in state snapshots).  The box stays periodic: the wave
+ * must not reach the plane again from the other side.  a == NULL removes the
+ * antenna.  Errors: PIC_ERR_INVALID_ARG for a bad run, polarization or plane
+ * (1 <= plane < nx required). */
+enum { PIC_POL_Y = 1, PIC_POL_Z = 2 };
+typedef struct {
+    int polarization;   /* PIC_POL_Y or PIC_POL_Z */
+    int plane;          /* x index of the first total-field B node */
+    double amplitude;   /* E_0 */
+    double omega;       /* angular frequency */
+    double ramp;        /* rise time of the sin^2 envelope (0: none) */
+    long long start;    /* initial value of the antenna's clock (E steps already taken) */
+} pic_antenna_desc;
+int pic_set_antenna(pic_grid *g, int run, const pic_antenna_desc *a);
+
+/* Sort policy of pic_step.  By default particles are re-sorted by tile every
+ * sort_interval steps.  With adaptive != 0, pic_step times every step's
+ * particle kernel and counts the particles that ran more than `halo` cells
+ * past their tile since the last sort (they take the slower global-memory
+ * path).  While there are such particles it sums the kernel's time above that
+ * of the first step after the last sort, and sorts before the next step once
+ * the sum, plus the last step's excess again (the next step costs at least as
+ * much), exceeds the measured time of a sort.  A sort so triggered after k
+ * steps sets the interval to k - 1 (drift that builds up coherently, as in a
+ * laser-driven plasma, arrives all at once); after a growing number of cycles
+ * without drift the interval is tried one step longer.  sort_interval stays
+ * the longest interval.  The measurement costs one stream synchronization per step, so the
+ * adaptive policy applies to pic_step only (pic_step_persistent and
+ * pic_step_graph keep the fixed interval), and the sort schedule follows the
+ * timings.  Errors: PIC_ERR_INVALID_ARG for a null grid. */
+int pic_set_sort_policy(pic_grid *g, int adaptive);
+
 /* nsteps full steps of the Appendix: B half step, [tile sort every
  * sort_interval steps], gather + push + deposit fused in one pass over the
  * tile-sorted particles, B half step, E full step. */

@@ -294,9 +294,14 @@ int launch_fields(pic_grid *g, int which, int zero_j)
     for (auto &r : g->runs) maxc = std::max(maxc, (long long)r.dev.n[0] * r.dev.n[1] * r.dev.n[2]);
     ProfScope ps(g, which == PIC_B_HALF ? PIC_PROF_YEE_B : PIC_PROF_YEE_E);
     cudaError_t e = launch_yee(g->prec, which, zero_j, g->stream, g->d_runs, (int)g->runs.size(), maxc, g->E, g->B,
-                               g->J, g->dims);
+                               g->J, g->dims, g->d_ant_n);
     launch_count_add(g, 1);
     if (e != cudaSuccess) return cuda_fail(e, "Yee kernel");
+    if (which == PIC_E_FULL && g->antennas > 0) {   // the E step ends a step of the antenna clock
+        e = launch_antenna_tick(g->stream, g->d_ant_n, (int)g->runs.size());
+        launch_count_add(g, 1);
+        if (e != cudaSuccess) return cuda_fail(e, "antenna clock");
+    }
     return PIC_OK;
 }
 
@@ -405,6 +410,8 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
     rd.V = d->dims == 3 ? dd[0] * dd[1] * dd[2] : dd[0] * dd[1];
     rd.rho_bg = d->rho_bg;
     rd.cell_base = 0;
+    rd.fpdt = 4.0 * 3.14159265358979323846 * rd.dt;
+    rd.fpdtf = (float)rd.fpdt;
     rd.div_nx = make_divu31(n[0]);
     rd.div_ny = make_divu31(n[1]);
     for (int a = 0; a < 3; ++a) rd.div_t[a] = make_divu31(t[a]);
@@ -438,6 +445,10 @@ void destroy_grid(pic_grid *g)
     dfree(g->d_err);
     dfree(g->stage);
     dfree(g->d_run_cell_base);
+    dfree(g->d_ant_n);
+    if (g->h_drift) cudaFreeHost(g->h_drift);
+    for (auto &ev : g->ad_ev)
+        if (ev) cudaEventDestroy(ev);
     for (int c = 0; c < 3; ++c) {
         dfree(g->adj_B1[c]);
         dfree(g->adj_lamJ[c]);
@@ -509,8 +520,13 @@ int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out)
     if ((e = cudaMemcpy(g->d_run_cell_base, base.data(), sizeof(long long) * base.size(), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return bail(e, "run bases");
-    if ((e = dalloc(&g->d_err, 1)) != cudaSuccess) return bail(e, "error word");
-    if ((e = cudaMemset(g->d_err, 0, sizeof(int))) != cudaSuccess) return bail(e, "error word");
+    if ((e = dalloc(&g->d_ant_n, g->runs.size())) != cudaSuccess) return bail(e, "antenna clocks");
+    if ((e = cudaMemset(g->d_ant_n, 0, sizeof(long long) * g->runs.size())) != cudaSuccess)
+        return bail(e, "antenna clocks");
+    if ((e = dalloc(&g->d_err, 2)) != cudaSuccess) return bail(e, "error word");
+    if ((e = cudaMemset(g->d_err, 0, 2 * sizeof(int))) != cudaSuccess) return bail(e, "error word");
+    if ((e = cudaHostAlloc((void **)&g->h_drift, sizeof(unsigned), cudaHostAllocDefault)) != cudaSuccess)
+        return bail(e, "drift count");
     if ((e = dalloc(&g->n_items, 1)) != cudaSuccess) return bail(e, "item count");
     if ((e = cudaMemset(g->n_items, 0, sizeof(int))) != cudaSuccess) return bail(e, "item count");
     if ((e = dalloc(&g->diag.rho, g->total_cells)) != cudaSuccess) return bail(e, "rho");
@@ -573,6 +589,52 @@ static int check_run_index(pic_grid *g, int run)
 {
     if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
     if (run < 0 || run >= (int)g->runs.size()) return fail(PIC_ERR_INVALID_ARG, "run %d is not in the batch", run);
+    return PIC_OK;
+}
+
+int pic_set_sort_policy(pic_grid *g, int adaptive)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    g->adaptive_sort = adaptive ? 1 : 0;
+    g->sort_due = false;
+    g->ad_excess = 0.f;
+    g->ad_sort = -1.f;
+    g->ad_limit = 0;
+    g->ad_clean = 0;
+    g->ad_backoff = 2;
+    g->ad_drifted = false;
+    return PIC_OK;
+}
+
+int pic_set_antenna(pic_grid *g, int run, const pic_antenna_desc *a)
+{
+    int rc = check_run_index(g, run);
+    if (rc != PIC_OK) return rc;
+    RunDev &rd = g->runs[run].dev;
+    const int was = rd.ant_pol != 0;
+    if (a) {
+        if (a->polarization != PIC_POL_Y && a->polarization != PIC_POL_Z)
+            return fail(PIC_ERR_INVALID_ARG, "antenna polarization must be PIC_POL_Y or PIC_POL_Z");
+        if (a->plane < 1 || a->plane >= rd.n[0])
+            return fail(PIC_ERR_INVALID_ARG, "antenna plane %d outside 1..nx-1 (nx = %d)", a->plane, rd.n[0]);
+        if (!std::isfinite(a->amplitude) || !std::isfinite(a->omega) || !std::isfinite(a->ramp) || a->ramp < 0.0 ||
+            a->start < 0)
+            return fail(PIC_ERR_INVALID_ARG, "antenna amplitude, frequency and ramp must be finite, ramp and start >= 0");
+        rd.ant_pol = a->polarization;
+        rd.ant_i0 = a->plane;
+        rd.ant_E0 = a->amplitude;
+        rd.ant_omega = a->omega;
+        rd.ant_ramp = a->ramp;
+    } else {
+        rd.ant_pol = 0;
+    }
+    g->antennas += (rd.ant_pol != 0) - was;
+    CK(cudaMemcpyAsync(g->d_runs + run, &rd, sizeof(RunDev), cudaMemcpyHostToDevice, g->stream), "antenna");
+    const long long start = a ? a->start : 0;
+    CK(cudaMemcpyAsync(g->d_ant_n + run, &start, sizeof(long long), cudaMemcpyHostToDevice, g->stream),
+       "antenna clock");
+    CK(cudaStreamSynchronize(g->stream), "antenna");
+    if (!g->capturing) graph_drop(g);   // the graph's step has one launch more or less
     return PIC_OK;
 }
 
@@ -910,15 +972,72 @@ int pic_step(pic_grid *g, int nsteps)
 {
     if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
     if (nsteps < 0) return fail(PIC_ERR_INVALID_ARG, "negative step count");
+    const bool measure = g->adaptive_sort && g->total > 0;
+    if (measure && !g->ad_ev[0])
+        for (auto &ev : g->ad_ev) CK(cudaEventCreate(&ev), "sort policy events");
     for (int s = 0; s < nsteps; ++s) {
         int rc;
-        if (g->steps_since_sort >= g->sort_interval && (rc = do_sort(g)) != PIC_OK) return rc;
+        bool timed_sort = false;
+        const int limit = measure && g->ad_limit > 0 ? std::min(g->ad_limit, g->sort_interval) : g->sort_interval;
+        if (measure && g->steps_since_sort >= limit && !g->sort_due && g->steps_since_sort > 0) {
+            // a cycle that reached the learned interval without drift: after
+            // ad_backoff of them, try one step longer
+            if (!g->ad_drifted && ++g->ad_clean >= g->ad_backoff && limit < g->sort_interval) {
+                g->ad_limit = limit + 1;
+                g->ad_clean = 0;
+            }
+        }
+        if (g->steps_since_sort >= limit || g->sort_due) {
+            if (measure) CK(cudaEventRecord(g->ad_ev[2], g->stream), "sort policy events");
+            if ((rc = do_sort(g)) != PIC_OK) return rc;
+            if (measure) CK(cudaEventRecord(g->ad_ev[3], g->stream), "sort policy events");
+            timed_sort = measure;
+        }
+        const bool sorted = g->steps_since_sort == 0;
+        g->sort_due = false;
+        if (measure) CK(cudaMemsetAsync(g->d_err + 1, 0, sizeof(int), g->stream), "drift count");
         if ((rc = launch_fields(g, PIC_B_HALF, 1)) != PIC_OK) return rc;
+        if (measure) CK(cudaEventRecord(g->ad_ev[0], g->stream), "sort policy events");
         if (g->total > 0 && (rc = launch_part(g, 0)) != PIC_OK) return rc;
+        if (measure) CK(cudaEventRecord(g->ad_ev[1], g->stream), "sort policy events");
         if ((rc = launch_fields(g, PIC_B_HALF, 0)) != PIC_OK) return rc;
         if ((rc = launch_fields(g, PIC_E_FULL, 0)) != PIC_OK) return rc;
         g->steps_since_sort += 1;
         g->have_old = false;
+        if (measure) {
+            // Particles past their tile's halo take the global-memory path; the
+            // slowdown they cause since the last sort is summed, and the next
+            // step sorts once it exceeds what a sort costs.
+            CK(cudaMemcpyAsync(g->h_drift, g->d_err + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream),
+               "drift count");
+            CK(cudaStreamSynchronize(g->stream), "sort policy");
+            float tp = 0.f;
+            CK(cudaEventElapsedTime(&tp, g->ad_ev[0], g->ad_ev[1]), "sort policy events");
+            if (sorted) {
+                if (timed_sort) CK(cudaEventElapsedTime(&g->ad_sort, g->ad_ev[2], g->ad_ev[3]), "sort policy events");
+                g->ad_base = tp;
+                g->ad_excess = 0.f;
+                g->ad_drifted = false;
+            }
+            float last = 0.f;
+            if (*g->h_drift > 0u) g->ad_drifted = true;
+            if (!sorted && *g->h_drift > 0u) {
+                last = std::max(0.f, tp - g->ad_base);
+                g->ad_excess += last;
+            }
+            // the next step will cost at least as much extra as this one did
+            const float cost = g->ad_sort > 0.f ? g->ad_sort : g->ad_base;
+            g->sort_due = g->ad_excess + last > cost;
+            if (g->sort_due) {
+                // drift got costly after steps_since_sort steps: from now on sort
+                // one step earlier; a failed attempt at a longer interval doubles
+                // the clean cycles needed before the next attempt
+                const int learned = std::max(1, g->steps_since_sort - 1);
+                if (g->ad_limit > 0 && learned < g->ad_limit) g->ad_backoff = std::min(64, 2 * g->ad_backoff);
+                g->ad_limit = learned;
+                g->ad_clean = 0;
+            }
+        }
     }
     return PIC_OK;
 }
@@ -933,7 +1052,7 @@ static int persistent_step(pic_grid *g)
     cudaError_t e = launch_step_persistent(g->dims, g->prec, g->stream, g->items, g->n_items, g->d_runs, g->d_groups,
                                            g->pool, g->E, g->B, g->J, g->halo, g->tile[0], g->tile[1], g->tile[2],
                                            g->d_err, (int)g->runs.size(), g->d_run_cell_base, &g->persist_blocks, 1,
-                                           g->pitch[0], g->pitch[1]);
+                                           g->pitch[0], g->pitch[1], g->d_ant_n, g->antennas);
     launch_count_add(g, 1);
     if (e != cudaSuccess) return cuda_fail(e, "persistent step");
     g->steps_since_sort += 1;
@@ -963,7 +1082,8 @@ static int capture_graph(pic_grid *g)
         cudaError_t ep = launch_step_persistent(g->dims, g->prec, g->stream, g->items, g->n_items, g->d_runs,
                                                 g->d_groups, g->pool, g->E, g->B, g->J, g->halo, g->tile[0],
                                                 g->tile[1], g->tile[2], g->d_err, (int)g->runs.size(),
-                                                g->d_run_cell_base, &g->persist_blocks, 0, g->pitch[0], g->pitch[1]);
+                                                g->d_run_cell_base, &g->persist_blocks, 0, g->pitch[0], g->pitch[1],
+                                                g->d_ant_n, g->antennas);
         if (ep != cudaSuccess) return cuda_fail(ep, "persistent kernel set-up");
     }
     const bool prof = g->profiling;
@@ -1138,7 +1258,7 @@ long long pic_state_bytes(pic_grid *g)
     if (!g) return 0;
     const long long es = (long long)elem(g);
     return (long long)sizeof(StateHeader) + g->total * (8 + es * (g->dims + 3)) + g->total_cells * es * 6 +
-           (long long)sizeof(long long) * (g->total_tiles + 1);
+           (long long)sizeof(long long) * (g->total_tiles + 1 + (long long)g->runs.size());
 }
 
 int pic_state_save(pic_grid *g, void *dst, int on_device)
@@ -1164,6 +1284,7 @@ int pic_state_save(pic_grid *g, void *dst, int on_device)
     for (int a = 0; a < 3; ++a) CK(put(g->E[a], es * g->total_cells), "state E");
     for (int a = 0; a < 3; ++a) CK(put(g->B[a], es * g->total_cells), "state B");
     CK(put(g->tile_start, sizeof(long long) * (g->total_tiles + 1)), "state tile starts");
+    CK(put(g->d_ant_n, sizeof(long long) * g->runs.size()), "state antenna clocks");
     CK(cudaStreamSynchronize(g->stream), "state save");
     return PIC_OK;
 }
@@ -1195,6 +1316,7 @@ int pic_state_restore(pic_grid *g, const void *src, int on_device)
     // the particles are in the order of the sort before the save: its tile
     // starts give the work items back, and the sort schedule continues
     CK(get(g->tile_start, sizeof(long long) * (g->total_tiles + 1)), "state tile starts");
+    CK(get(g->d_ant_n, sizeof(long long) * g->runs.size()), "state antenna clocks");
     if (g->total > 0 && !g->groups.empty()) {
         int nl = 0;
         cudaError_t e = build_items(g->stream, g->tile_start, g->total_tiles, g->ppi, g->d_groups,
@@ -1252,7 +1374,8 @@ int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], v
     const int nr = (int)g->runs.size();
     // B^n = B^{n-1/2} - (1/2) C_B E^n into scratch (the state is not modified)
     for (int c = 0; c < 3; ++c) CK(cudaMemcpyAsync(g->adj_B1[c], g->B[c], fb, cudaMemcpyDeviceToDevice, g->stream), "B1");
-    CK(launch_yee(g->prec, PIC_B_HALF, 0, g->stream, g->d_runs, nr, mc, g->E, g->adj_B1, g->J, g->dims), "B1");
+    CK(launch_yee(g->prec, PIC_B_HALF, 0, g->stream, g->d_runs, nr, mc, g->E, g->adj_B1, g->J, g->dims, g->d_ant_n),
+       "B1");
     // (E step)^T, (second B half step)^T
     CK(launch_adj_yee(g->dims, g->prec, 2, g->stream, g->d_runs, nr, mc, lamE, lamB, g->adj_lamJ), "adjoint E step");
     CK(launch_adj_yee(g->dims, g->prec, 1, g->stream, g->d_runs, nr, mc, lamE, lamB, nullptr), "adjoint B half step");

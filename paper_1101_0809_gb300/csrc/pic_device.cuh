@@ -50,6 +50,12 @@ struct RunDev {
     double d[3];
     double V;             // cell volume (dx*dy in 2D)
     double rho_bg;        // uniform background charge density
+    // plane-wave antenna (include/pic.h): pol 0 none, 1 E_y/B_z, 2 E_z/B_y;
+    // the total field starts at the B node x = ant_i0
+    int ant_pol, ant_i0;
+    double ant_E0, ant_omega, ant_ramp;
+    double fpdt;            // 4 pi dt
+    float fpdtf;            // 4 pi dt in FP32
     DivU31 div_nx, div_ny;  // division by n[0] and n[1]
     DivU31 div_t[3];        // division by the tile extents
     float cf, cNf[3];     // c and the Courant numbers in FP32
@@ -289,6 +295,24 @@ struct AxisWin {
     int lo;
 };
 
+// Pm = dF(x^{n+1}) - dF(x^n) on the cells -1..1 of a particle that stayed in
+// its cell along this axis (offsets d0 -> d1), in the factored form of the
+// differences of the l_a = 1 1/2 weights,
+//   (1-d1)^2/2 - (1-d0)^2/2 = -(1/2) dl (2 - d0 - d1),
+//   (1/2-d0)^2 - (1/2-d1)^2 =  dl (1 - d0 - d1),
+//   d1^2/2 - d0^2/2          =  (1/2) dl (d0 + d1),       dl = d1 - d0,
+// which vanishes exactly for a particle at rest and keeps its relative accuracy
+// for small displacements (the plain differences cancel).
+template <typename R>
+__device__ __forceinline__ void still_pm(R d0, R d1, R pm[3])
+{
+    const R dl = d1 - d0;
+    const R sm = d0 + d1;
+    pm[0] = R(-0.5) * dl * (R(2) - sm);
+    pm[1] = dl * (R(1) - sm);
+    pm[2] = R(0.5) * dl * sm;
+}
+
 template <typename R>
 __device__ __forceinline__ void axis_window(R d0, R d1, int s, AxisWin<R> &a)
 {
@@ -308,6 +332,13 @@ __device__ __forceinline__ void axis_window(R d0, R d1, int s, AxisWin<R> &a)
     a.Pp[1] = n1 + o1; a.Pm[1] = n1 - o1;
     a.Pp[2] = n2 + o2; a.Pm[2] = n2 - o2;
     a.Pp[3] = n3 + o3; a.Pm[3] = n3 - o3;
+    if (s == 0) {   // no shift along this axis: the factored differences
+        R pm[3];
+        still_pm(d0, d1, pm);
+        a.Pm[0] = pm[0];
+        a.Pm[1] = pm[1];
+        a.Pm[2] = pm[2];
+    }
     a.D[0] = a.Pm[0];
     a.D[1] = a.D[0] + a.Pm[1];
     a.D[2] = a.D[1] + a.Pm[2];
@@ -324,10 +355,12 @@ __device__ __forceinline__ void axis_window_still(R d0, R d1, AxisWin<R> &a)
     R f0[2], S0[3], f1[2], S1[3];
     form_factor(d0, f0, S0);
     form_factor(d1, f1, S1);
+    R pm[3];
+    still_pm(d0, d1, pm);
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
         a.Pp[t] = S1[t] + S0[t];
-        a.Pm[t] = S1[t] - S0[t];
+        a.Pm[t] = pm[t];
     }
     a.Pp[3] = R(0);
     a.Pm[3] = R(0);
@@ -500,8 +533,23 @@ __device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, con
 //                 Ez += -4 pi dt Jz + c_x(By[i+1,j,k]-By[i,j,k]) - c_y(Bx[i,j+1,k]-Bx[i,j,k])
 // With zero_j the B pass also clears J for the coming deposit.
 // ---------------------------------------------------------------------------
+// The antenna's incident field at x (cell units) and time t (include/pic.h).
+__device__ __forceinline__ double antenna_field(const RunDev &rn, double x, double t)
+{
+    const double tau = t - (x - rn.ant_i0) * rn.d[0] / rn.c;
+    if (tau <= 0.0) return 0.0;
+    double g = 1.0;
+    if (tau < rn.ant_ramp) {
+        const double s = sin(1.5707963267948966 * tau / rn.ant_ramp);
+        g = s * s;
+    }
+    return rn.ant_E0 * g * sin(rn.ant_omega * tau);
+}
+
+// ant_n: the antenna clock of the run (E steps since the antenna was set).
 template <int DIM, typename R>
-__device__ __forceinline__ void yee_b_half_cell(const RunDev &rn, const Fields<R> &F, long long l, int zero_j)
+__device__ __forceinline__ void yee_b_half_cell(const RunDev &rn, const Fields<R> &F, long long l, int zero_j,
+                                                long long ant_n)
 {
     const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
     const int i = (int)(l % nx);
@@ -511,16 +559,22 @@ __device__ __forceinline__ void yee_b_half_cell(const RunDev &rn, const Fields<R
     const long long p = rn.cell_base + l;
     const long long pim = p + (i == 0 ? nx - 1 : -1);
     const long long pjm = p + (long long)nx * (j == 0 ? ny - 1 : -1);
-    const R hx = R(0.5 * rn.cN[0]), hy = R(0.5 * rn.cN[1]);
+    const bool f32 = sizeof(R) == 4;
+    const R hx = f32 ? R(0.5f * rn.cNf[0]) : R(0.5 * rn.cN[0]), hy = f32 ? R(0.5f * rn.cNf[1]) : R(0.5 * rn.cN[1]);
     const R ex = F.E[0][p], ey = F.E[1][p], ez = F.E[2][p];
     R bx = F.B[0][p] - hy * (ez - F.E[2][pjm]);
     R by = F.B[1][p] + hx * (ez - F.E[2][pim]);
     R bz = F.B[2][p] - hx * (ey - F.E[1][pim]) + hy * (ex - F.E[0][pjm]);
     if (DIM == 3) {
         const long long pkm = p + (long long)nx * ny * (k == 0 ? nz - 1 : -1);
-        const R hz = R(0.5 * rn.cN[2]);
+        const R hz = f32 ? R(0.5f * rn.cNf[2]) : R(0.5 * rn.cN[2]);
         bx += hz * (ey - F.E[1][pkm]);
         by -= hz * (ex - F.E[0][pkm]);
+    }
+    if (rn.ant_pol != 0 && i == rn.ant_i0) {
+        // the scattered-field E node at x = i0 - 1/2 lacks the incident wave
+        const R a = R(0.5 * rn.cN[0] * antenna_field(rn, rn.ant_i0 - 0.5, ant_n * rn.dt));
+        if (rn.ant_pol == 1) bz += a; else by -= a;
     }
     F.B[0][p] = bx;
     F.B[1][p] = by;
@@ -533,7 +587,7 @@ __device__ __forceinline__ void yee_b_half_cell(const RunDev &rn, const Fields<R
 }
 
 template <int DIM, typename R>
-__device__ __forceinline__ void yee_e_cell(const RunDev &rn, const Fields<R> &F, long long l)
+__device__ __forceinline__ void yee_e_cell(const RunDev &rn, const Fields<R> &F, long long l, long long ant_n)
 {
     const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
     const int i = (int)(l % nx);
@@ -543,17 +597,24 @@ __device__ __forceinline__ void yee_e_cell(const RunDev &rn, const Fields<R> &F,
     const long long p = rn.cell_base + l;
     const long long pip = p + (i == nx - 1 ? -(nx - 1) : 1);
     const long long pjp = p + (long long)nx * (j == ny - 1 ? -(ny - 1) : 1);
-    const R cx = R(rn.cN[0]), cy = R(rn.cN[1]);
-    const R fp = R(4.0 * 3.14159265358979323846 * rn.dt);
+    const bool f32 = sizeof(R) == 4;
+    const R cx = f32 ? R(rn.cNf[0]) : R(rn.cN[0]), cy = f32 ? R(rn.cNf[1]) : R(rn.cN[1]);
+    const R fp = f32 ? R(rn.fpdtf) : R(rn.fpdt);
     const R bx = F.B[0][p], by = F.B[1][p], bz = F.B[2][p];
     R ex = F.E[0][p] - fp * F.J[0][p] + cy * (F.B[2][pjp] - bz);
     R ey = F.E[1][p] - fp * F.J[1][p] - cx * (F.B[2][pip] - bz);
     R ez = F.E[2][p] - fp * F.J[2][p] + cx * (F.B[1][pip] - by) - cy * (F.B[0][pjp] - bx);
     if (DIM == 3) {
         const long long pkp = p + (long long)nx * ny * (k == nz - 1 ? -(nz - 1) : 1);
-        const R cz = R(rn.cN[2]);
+        const R cz = f32 ? R(rn.cNf[2]) : R(rn.cN[2]);
         ex -= cz * (F.B[1][pkp] - by);
         ey += cz * (F.B[0][pkp] - bx);
+    }
+    if (rn.ant_pol != 0 && i == rn.ant_i0 - 1) {
+        // the scattered-field E node at x = i0 - 1/2 sees the total-field B node at
+        // x = i0, whose incident part (B_z = E_inc, B_y = -E_inc) comes off
+        const R a = R(rn.cN[0] * antenna_field(rn, rn.ant_i0, (ant_n + 0.5) * rn.dt));
+        if (rn.ant_pol == 1) ey += a; else ez += a;
     }
     F.E[0][p] = ex;
     F.E[1][p] = ey;

@@ -51,7 +51,7 @@ cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const Wo
                                    const RunDev *runs, const GroupDev *groups, const PoolBuf &P, void *const E[3],
                                    void *const B[3], void *const J[3], int halo, int tx, int ty, int tz, int *err,
                                    int nruns, const long long *run_cell_base, int *grid_blocks, int launch, int p0,
-                                   int p1);
+                                   int p1, long long *ant_n, int antennas);
 cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes);
 
 cudaError_t launch_load(int prec, cudaStream_t st, long long n, const double *x0, const double *x1,
@@ -59,7 +59,10 @@ cudaError_t launch_load(int prec, cudaStream_t st, long long n, const double *x0
                         int dims, int nx, int ny, int nz, const PoolBuf &P, long long base);
 
 cudaError_t launch_yee(int prec, int which, int zero_j, cudaStream_t st, const RunDev *runs, int nruns,
-                       long long max_cells, void *const E[3], void *const B[3], void *const J[3], int dims);
+                       long long max_cells, void *const E[3], void *const B[3], void *const J[3], int dims,
+                       const long long *ant_n);
+// Advances every run's antenna clock (E steps since its antenna was set) by one.
+cudaError_t launch_antenna_tick(cudaStream_t st, long long *ant_n, int nruns);
 
 cudaError_t launch_copy_pool(int prec, cudaStream_t st, const PoolBuf &src, long long src_base,
                              const PoolBuf &dst, long long dst_base, long long n);
@@ -160,6 +163,15 @@ struct pic_grid {
     long long *tile_start = nullptr;
     unsigned *item_scan = nullptr;
     pic::WorkItem *items = nullptr;
+    long long *d_ant_n = nullptr;   // antenna clock per run (device)
+    unsigned *h_drift = nullptr;    // pinned host copy of the drift count (d_err[1])
+    int adaptive_sort = 0;          // sort when the particle kernel's accumulated slowdown exceeds a sort
+    bool sort_due = false;
+    cudaEvent_t ad_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // particle kernel, sort
+    float ad_base = 0.f, ad_excess = 0.f, ad_sort = -1.f;          // ms
+    int ad_limit = 0, ad_clean = 0, ad_backoff = 2;                // learned interval (steps)
+    bool ad_drifted = false;                                       // drift seen since the last sort
+    int antennas = 0;               // number of runs with an antenna
     int *n_items = nullptr;
     int max_items = 0;
     int steps_since_sort = 0;

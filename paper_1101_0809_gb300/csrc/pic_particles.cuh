@@ -33,7 +33,7 @@ struct PartArgs {
     int *old_cell;
     R *old_off[3];
     int halo;
-    int *err;
+    int *err;   // err[0]: error word; err[1]: particles that ran past their tile's halo (counted by MODES 0, 1)
 };
 
 extern __shared__ __align__(16) unsigned char g_smem[];
@@ -369,6 +369,10 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                 }
             }
         }
+        if (MODE != 2) {   // particles on the global path: the sort policy's measure of drift
+            const unsigned dm = __ballot_sync(0xffffffffu, valid && !inr);
+            if (lane == 0 && dm != 0u) atomicAdd(reinterpret_cast<unsigned *>(a.err) + 1, (unsigned)__popc(dm));
+        }
         if (MODE == 1) continue;
 
         // ---- virtual-path current (Eq. current) -------------------------------
@@ -520,7 +524,8 @@ __device__ __forceinline__ int find_run(const long long *run_cell_base, int nrun
 // that all blocks are resident (cooperative launch), which the barriers need.
 template <int DIM, typename R, class GEO = GeoDyn>
 __global__ void __launch_bounds__(kThreads) k_step_persistent(const PartArgs<R> a, int nruns,
-                                                              const long long *run_cell_base)
+                                                              const long long *run_cell_base, long long *ant_n,
+                                                              int antennas)
 {
     cg::grid_group grid = cg::this_grid();
     const long long total = run_cell_base[nruns];
@@ -528,7 +533,7 @@ __global__ void __launch_bounds__(kThreads) k_step_persistent(const PartArgs<R> 
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     for (long long l = t0; l < total; l += stride) {
         const int r = find_run(run_cell_base, nruns, l);
-        yee_b_half_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r], 1);
+        yee_b_half_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r], 1, ant_n[r]);
     }
     grid.sync();
     const int ni = *a.n_items;
@@ -536,12 +541,17 @@ __global__ void __launch_bounds__(kThreads) k_step_persistent(const PartArgs<R> 
     grid.sync();
     for (long long l = t0; l < total; l += stride) {
         const int r = find_run(run_cell_base, nruns, l);
-        yee_b_half_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r], 0);
+        yee_b_half_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r], 0, ant_n[r]);
     }
     grid.sync();
     for (long long l = t0; l < total; l += stride) {
         const int r = find_run(run_cell_base, nruns, l);
-        yee_e_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r]);
+        yee_e_cell<DIM, R>(a.runs[r], a.F, l - run_cell_base[r], ant_n[r]);
+    }
+    if (antennas) {   // the antenna clocks advance once every block has read them
+        grid.sync();
+        if (blockIdx.x == 0)
+            for (int r = threadIdx.x; r < nruns; r += blockDim.x) ant_n[r] += 1;
     }
 }
 
@@ -555,7 +565,7 @@ static cudaError_t launch_t(cudaStream_t st, int max_items, size_t smem, const P
 
 template <int DIM, typename R, class GEO = GeoDyn>
 static cudaError_t persistent_t(cudaStream_t st, size_t smem, int nruns, const long long *run_cell_base,
-                                PartArgs<R> a, int *grid_blocks, int launch)
+                                PartArgs<R> a, int *grid_blocks, int launch, long long *ant_n, int antennas)
 {
     auto fn = k_step_persistent<DIM, R, GEO>;
     cudaError_t e;
@@ -572,7 +582,7 @@ static cudaError_t persistent_t(cudaStream_t st, size_t smem, int nruns, const l
         *grid_blocks = sms * per;
     }
     if (!launch) return cudaSuccess;
-    void *args[] = {(void *)&a, (void *)&nruns, (void *)&run_cell_base};
+    void *args[] = {(void *)&a, (void *)&nruns, (void *)&run_cell_base, (void *)&ant_n, (void *)&antennas};
     return cudaLaunchCooperativeKernel((const void *)fn, dim3(*grid_blocks), dim3(kThreads), args, smem, st);
 }
 
@@ -583,7 +593,7 @@ bool launch_particles_fixed(int dims, cudaStream_t st, int max_items, size_t sme
                             const int tile[3], int halo, int p0, int p1, cudaError_t *err);
 bool launch_persistent_fixed(int dims, cudaStream_t st, size_t smem, int nruns, const long long *run_cell_base,
                              const PartArgs<float> &a, int *grid_blocks, int launch, const int tile[3], int halo,
-                             int p0, int p1, cudaError_t *err);
+                             int p0, int p1, long long *ant_n, int antennas, cudaError_t *err);
 cudaError_t fixed_set_smem_limit(int dims, size_t bytes);
 
 }  // namespace pic

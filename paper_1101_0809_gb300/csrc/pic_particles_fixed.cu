@@ -40,14 +40,16 @@ bool launch_particles_fixed(int dims, cudaStream_t st, int max_items, size_t sme
 
 bool launch_persistent_fixed(int dims, cudaStream_t st, size_t smem, int nruns, const long long *run_cell_base,
                              const PartArgs<float> &a, int *grid_blocks, int launch, const int tile[3], int halo,
-                             int p0, int p1, cudaError_t *err)
+                             int p0, int p1, long long *ant_n, int antennas, cudaError_t *err)
 {
     if (dims == 2 && matches<Geo2_16>(2, tile, halo, p0, p1)) {
-        *err = persistent_t<2, float, Geo2_16>(st, smem, nruns, run_cell_base, a, grid_blocks, launch);
+        *err = persistent_t<2, float, Geo2_16>(st, smem, nruns, run_cell_base, a, grid_blocks, launch, ant_n,
+                                                antennas);
         return true;
     }
     if (dims == 2 && matches<Geo2_8>(2, tile, halo, p0, p1)) {
-        *err = persistent_t<2, float, Geo2_8>(st, smem, nruns, run_cell_base, a, grid_blocks, launch);
+        *err = persistent_t<2, float, Geo2_8>(st, smem, nruns, run_cell_base, a, grid_blocks, launch, ant_n,
+                                               antennas);
         return true;
     }
     return false;

@@ -40,6 +40,14 @@ class pic_species_desc(C.Structure):
     _fields_ = [("q", C.c_double), ("m", C.c_double), ("weight", C.c_double)]
 
 
+class pic_antenna_desc(C.Structure):
+    _fields_ = [("polarization", C.c_int), ("plane", C.c_int), ("amplitude", C.c_double),
+                ("omega", C.c_double), ("ramp", C.c_double), ("start", C.c_longlong)]
+
+
+PIC_POL_Y, PIC_POL_Z = 1, 2
+
+
 class pic_diag(C.Structure):
     _fields_ = [("kinetic", C.c_double), ("field_E", C.c_double), ("field_B", C.c_double),
                 ("half_step_corr", C.c_double), ("total", C.c_double),
@@ -228,6 +236,8 @@ _lib.pic_get_particles_run.argtypes = [_VP, C.c_int, C.c_int, _VP, _VP3, _VP3, _
 _lib.pic_diagnostics_run.argtypes = [_VP, C.c_int, C.POINTER(pic_diag)]
 _lib.pic_step_persistent.argtypes = [_VP, C.c_int]
 _lib.pic_step_graph.argtypes = [_VP, C.c_int]
+_lib.pic_set_antenna.argtypes = [_VP, C.c_int, C.POINTER(pic_antenna_desc)]
+_lib.pic_set_sort_policy.argtypes = [_VP, C.c_int]
 
 
 def pic_create_batch(descs):
@@ -323,6 +333,19 @@ def pic_step_persistent(g, nsteps=1):
 
 def pic_step_graph(g, nsteps=1):
     _check(_lib.pic_step_graph(g, nsteps))
+
+
+def pic_set_sort_policy(g, adaptive):
+    _check(_lib.pic_set_sort_policy(g, 1 if adaptive else 0))
+
+
+def pic_set_antenna(g, run, polarization=None, plane=0, amplitude=0.0, omega=0.0, ramp=0.0, start=0):
+    """Sets (or, with polarization None, removes) the plane-wave antenna of a run."""
+    if polarization is None:
+        _check(_lib.pic_set_antenna(g, run, None))
+        return
+    a = pic_antenna_desc(polarization, plane, amplitude, omega, ramp, start)
+    _check(_lib.pic_set_antenna(g, run, C.byref(a)))
 
 
 _lib.pic_tile_layout.argtypes = [_VP, C.c_int * 6]

@@ -47,6 +47,7 @@ class Workload:
     steps: int = 1
     tile: tuple = (8, 8, 8)
     sort_interval: int = 10
+    antenna: dict = None   # plane-wave antenna: pol, plane, amplitude, omega, ramp
 
     @property
     def n_particles(self):
@@ -117,6 +118,50 @@ def c1_thermal3d(n=128, ppc=32, steps=200, fraction=1.0, tile=(8, 4, 4), sort_in
     return thermal_plasma(f"3D3V {n}^3 e+i {ppc}ppc each vth=0.1c", 3, (n, n, n), ppc, 0.1,
                           steps, SEED_BASE + 1, ions=1836.0, tile=tile,
                           sort_interval=sort_interval, dt_courant=0.45, fraction=fraction)
+
+
+def c2_laser_slab(n=(512, 128, 128), ppc=16, a0=5.0, wavelength=20.0, steps=1000, dims=3,
+                  slab=(128.0, 178.0, 384.0), plane=8, tile=(8, 4, 4), sort_interval=10, dt_courant=0.45,
+                  seed_offset=2, ramp_periods=2.0):
+    """3D relativistic laser-plasma.  Periodic box, c = 1, dx = 1, dt = 0.45;
+    a linearly polarized (E_y) plane wave of wavelength 20 cells and a0 = 5
+    (E_0 = a0 m omega c / e = a0 omega) from a one-way antenna plane at x = 8
+    with a sin^2 rise over two periods; cold electrons in a slab, density
+    rising linearly over x in [128, 178), plateau at 0.01 n_c (n_c = m omega^2 /
+    (4 pi e^2)) up to x = 384, vacuum elsewhere.  16 candidates per cell, one
+    at x kept with probability n(x)/n_plateau, so all weights are equal.  The
+    immobile ions enter only rho and are left out: Gauss's residual is tracked
+    against its initial value.  ``dims`` = 2 gives the same slab in 2D (test
+    sizes; they also take a shorter rise, ``ramp_periods``)."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_offset))
+    nn = (n[0], n[1], n[2] if dims == 3 else 1)
+    c = 1.0
+    dt = dt_courant / c
+    omega = 2.0 * math.pi * c / wavelength
+    n_c = omega * omega / (4.0 * math.pi)
+    V = 1.0
+    W = 0.01 * n_c * V / ppc
+    x0, x1, x2 = slab
+    i_lo, i_hi = int(math.floor(x0)), int(math.ceil(x2))
+    ncand = (i_hi - i_lo) * nn[1] * nn[2] * ppc
+    x = np.zeros((3, ncand))
+    x[0] = rng.uniform(float(i_lo), float(i_hi), size=ncand)
+    x[1] = rng.uniform(0.0, float(nn[1]), size=ncand)
+    if dims == 3:
+        x[2] = rng.uniform(0.0, float(nn[2]), size=ncand)
+    keep_p = np.clip((x[0] - x0) / (x1 - x0), 0.0, 1.0)
+    keep_p[x[0] >= x2] = 0.0
+    keep = rng.uniform(0.0, 1.0, size=ncand) < keep_p
+    x = np.ascontiguousarray(x[:, keep])
+    for a in range(dims):
+        x[a][x[a] >= nn[a]] = 0.0
+    w = np.zeros_like(x)
+    sp = SpeciesInit("electrons", -1.0, 1.0, W, x, w)
+    ant = {"pol": 1, "plane": plane, "amplitude": a0 * omega * c, "omega": omega,
+           "ramp": ramp_periods * wavelength / c}
+    name = f"{dims}D laser slab {n[0]}x{n[1]}" + (f"x{n[2]}" if dims == 3 else "") + f" a0={a0}"
+    return Workload(name, dims, nn, (1.0, 1.0, 1.0), dt, c, [sp], 0.0, steps,
+                    tuple(tile) if dims == 3 else (tile[0], tile[1], 1), sort_interval, ant)
 
 
 def c4_perturbed2d(n=256, ppc=16, amplitude=0.05, mode=2, steps=200, seed_offset=4):

@@ -49,6 +49,8 @@ int main(void) {
          offsetof(pic_grid_desc, rho_bg), offsetof(pic_grid_desc, cuda_stream),
          sizeof(pic_diag), offsetof(pic_diag, n_particles));
   printf("%zu %zu\n", sizeof(pic_species_desc), offsetof(pic_grid_desc, sort_order));
+  printf("%zu %zu %zu %zu\n", sizeof(pic_antenna_desc), offsetof(pic_antenna_desc, amplitude),
+         offsetof(pic_antenna_desc, ramp), offsetof(pic_antenna_desc, start));
   return 0;
 }
 """
@@ -66,6 +68,10 @@ int main(void) {
     assert vals[5] == P.pic_diag.n_particles.offset
     assert vals[6] == C.sizeof(P.pic_species_desc)
     assert vals[7] == P.pic_grid_desc.sort_order.offset
+    assert vals[8] == C.sizeof(P.pic_antenna_desc)
+    assert vals[9] == P.pic_antenna_desc.amplitude.offset
+    assert vals[10] == P.pic_antenna_desc.ramp.offset
+    assert vals[11] == P.pic_antenna_desc.start.offset
 
 
 def _create(P, **kw):
@@ -107,3 +113,5 @@ def test_null_arguments_return_errors(P):
     assert lib.pic_diagnostics(None, None) == P.PIC_ERR_INVALID_ARG
     assert lib.pic_destroy(None) == P.PIC_OK
     assert lib.pic_num_particles(None, 0) == 0
+    assert lib.pic_set_sort_policy(None, 1) == P.PIC_ERR_INVALID_ARG
+    assert lib.pic_set_antenna(None, 0, None) == P.PIC_ERR_INVALID_ARG

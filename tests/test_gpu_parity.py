@@ -186,6 +186,32 @@ def test_fp64_particles_far_outside_their_tile_take_the_global_path(P, halo):
     grid.close()
 
 
+def test_adaptive_sort_policy_sorts_when_particles_drift_and_not_before(P):
+    """pic_set_sort_policy: with a long fixed interval and the adaptive
+    policy, a fast plasma is re-sorted as its particles leave their tiles' halos
+    (and still equals the oracle; the schedule does not change the arithmetic),
+    and a plasma at rest is never re-sorted."""
+    wl = ragged2d(vth=0.3, steps=40)
+    grid = make_grid(P, wl, P.PIC_FP64, halo=1, sort_interval=1000, ppb=512)
+    P.pic_set_sort_policy(grid.h, True)
+    P.pic_profile(grid.h, True)
+    P.pic_step(grid.h, wl.steps)
+    prof = P.pic_profile_read(grid.h)
+    assert prof["sort"][1] >= 1
+    g, osp, E, B, J = run_oracle(wl, wl.steps)
+    _check_state(P, wl, grid, osp, E, B, J, FP64_TOL)
+    grid.close()
+    cold = ragged2d(vth=0.3, steps=8)
+    for sp in cold.species:
+        sp.w[:] = 0.0
+    grid = make_grid(P, cold, P.PIC_FP32, halo=1, sort_interval=1000)
+    P.pic_set_sort_policy(grid.h, True)
+    P.pic_profile(grid.h, True)
+    P.pic_step(grid.h, cold.steps)
+    assert P.pic_profile_read(grid.h)["sort"][1] == 0
+    grid.close()
+
+
 @pytest.mark.parametrize("halo", [0, 1])
 def test_fp64_3d_particles_far_outside_their_tile_take_the_global_path(P, halo):
     wl = small3d(vth=0.3, steps=8, ions=False)     # fast electrons, no sort for 8 steps
