@@ -80,13 +80,18 @@ __global__ void __launch_bounds__(256) k_particles_adj(const AdjArgs<R> a)
             const int mid = (lo + hi) >> 1;
             if (a.group_base[mid] <= p) lo = mid; else hi = mid;
         }
-        const GroupDev gr = a.groups[lo];
+        const GroupDev &gr = a.groups[lo];
         const RunDev &rn = a.runs[gr.run];
         const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
         const long long cb = rn.cell_base;
         const long long L = gr.base + a.P.id[p];
         const int cell0 = a.P.cell[p];
-        const int i = cell0 % nx, rest = cell0 / nx, j = rest % ny, k = DIM == 3 ? rest / ny : 0;
+        const int rest = divu31(cell0, rn.div_nx);
+        const int i = cell0 - rest * nx;
+        const int k = DIM == 3 ? divu31(rest, rn.div_ny) : 0;
+        const int j = rest - k * ny;
+        constexpr bool F32 = sizeof(R) == 4;
+        const R third = R(1) / R(3);
         R o[3] = {a.P.off[0][p], a.P.off[1][p], DIM == 3 ? a.P.off[2][p] : R(0)};
         const R w0[3] = {a.P.w[0][p], a.P.w[1][p], a.P.w[2][p]};
         // ---- recompute the forward quantities --------------------------------
@@ -127,9 +132,11 @@ __global__ void __launch_bounds__(256) k_particles_adj(const AdjArgs<R> a)
                         }
                 if (fld == 0) Ep[c] = acc; else Bp[c] = acc;
             }
-        const R hq = R(0.5 * gr.qm * rn.dt);
-        const R cl = R(rn.c), c2 = cl * cl;
-        const R cN[3] = {R(rn.cN[0]), R(rn.cN[1]), R(rn.cN[2])};
+        // group and run constants prepared on the host (no FP64 arithmetic in FP32)
+        const R hq = F32 ? R(gr.hqf) : R(gr.hq);
+        const R cl = F32 ? R(rn.cf) : R(rn.c), c2 = cl * cl;
+        const R cN[3] = {F32 ? R(rn.cNf[0]) : R(rn.cN[0]), F32 ? R(rn.cNf[1]) : R(rn.cN[1]),
+                         F32 ? R(rn.cNf[2]) : R(rn.cN[2])};
         R w1[3] = {w0[0], w0[1], w0[2]};
         boris(w1, Ep, Bp, hq, c2);
         const R g1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2] + c2);
@@ -147,19 +154,21 @@ __global__ void __launch_bounds__(256) k_particles_adj(const AdjArgs<R> a)
         }
         R lPp[3][4] = {{0}}, lPm[3][4] = {{0}}, lD[3][3] = {{0}};
         R luz = 0;
-        const int base[3] = {i, j, k};
-        const int nn[3] = {nx, ny, nz};
-        auto gidx = [&](int c0, int c1, int c2i) -> long long {
-            return cb + (long long)wrapi(base[0] + c0, nn[0]) +
-                   (long long)nx * ((long long)wrapi(base[1] + c1, nn[1]) + (long long)ny * (DIM == 3 ? wrapi(base[2] + c2i, nn[2]) : 0));
-        };
+        // wrapped offsets of the deposit window cells -2..2 around the old cell
+        long long wx5[5], wy5[5], wz5[5];
+        for (int q = 0; q < 5; ++q) {
+            wx5[q] = cb + wrapi(i - 2 + q, nx);
+            wy5[q] = (long long)nx * wrapi(j - 2 + q, ny);
+            wz5[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 2 + q, nz) : 0;
+        }
+        auto gidx = [&](int c0, int c1, int c2i) -> long long { return wx5[c0 + 2] + wy5[c1 + 2] + wz5[c2i + 2]; };
         if (DIM == 3) {
             for (int cmp = 0; cmp < 3; ++cmp) {
                 const int b = (cmp + 1) % 3, cc = (cmp + 2) % 3;
-                const R ka = R(-0.25 * rn.d[cmp] / rn.dt * gr.qp / rn.V);
+                const R ka = F32 ? R(gr.kff[cmp]) : R(gr.kf[cmp]);
                 for (int wc = 0; wc < 4; ++wc)
                     for (int wb = 0; wb < 4; ++wb) {
-                        const R T = W[b].Pp[wb] * W[cc].Pp[wc] + W[b].Pm[wb] * W[cc].Pm[wc] / R(3);
+                        const R T = W[b].Pp[wb] * W[cc].Pp[wc] + W[b].Pm[wb] * W[cc].Pm[wc] * third;
                         for (int q = 0; q < 3; ++q) {
                             int off[3];
                             off[cmp] = W[cmp].lo + 1 + q;
@@ -169,15 +178,15 @@ __global__ void __launch_bounds__(256) k_particles_adj(const AdjArgs<R> a)
                             lD[cmp][q] += G * T;
                             lPp[b][wb] += G * W[cmp].D[q] * W[cc].Pp[wc];
                             lPp[cc][wc] += G * W[cmp].D[q] * W[b].Pp[wb];
-                            lPm[b][wb] += G * W[cmp].D[q] * W[cc].Pm[wc] / R(3);
-                            lPm[cc][wc] += G * W[cmp].D[q] * W[b].Pm[wb] / R(3);
+                            lPm[b][wb] += G * W[cmp].D[q] * W[cc].Pm[wc] * third;
+                            lPm[cc][wc] += G * W[cmp].D[q] * W[b].Pm[wb] * third;
                         }
                     }
             }
         } else {
-            const R kx = R(-0.5 * rn.d[0] / rn.dt * gr.qp / rn.V);
-            const R ky = R(-0.5 * rn.d[1] / rn.dt * gr.qp / rn.V);
-            const R kz = R(0.25 * gr.qp / rn.V);
+            const R kx = F32 ? R(gr.kff[0]) : R(gr.kf[0]);
+            const R ky = F32 ? R(gr.kff[1]) : R(gr.kf[1]);
+            const R kz = F32 ? R(gr.kff[2]) : R(gr.kf[2]);
             for (int wy = 0; wy < 4; ++wy)
                 for (int q = 0; q < 3; ++q) {
                     const R G = a.lamJ[0][gidx(W[0].lo + 1 + q, W[1].lo + wy, 0)] * kx;
@@ -193,11 +202,11 @@ __global__ void __launch_bounds__(256) k_particles_adj(const AdjArgs<R> a)
             for (int wy = 0; wy < 4; ++wy)
                 for (int wx = 0; wx < 4; ++wx) {
                     const R G = a.lamJ[2][gidx(W[0].lo + wx, W[1].lo + wy, 0)] * kz;
-                    luz += G * (W[0].Pp[wx] * W[1].Pp[wy] + W[0].Pm[wx] * W[1].Pm[wy] / R(3));
+                    luz += G * (W[0].Pp[wx] * W[1].Pp[wy] + W[0].Pm[wx] * W[1].Pm[wy] * third);
                     lPp[0][wx] += G * uz * W[1].Pp[wy];
                     lPp[1][wy] += G * uz * W[0].Pp[wx];
-                    lPm[0][wx] += G * uz * W[1].Pm[wy] / R(3);
-                    lPm[1][wy] += G * uz * W[0].Pm[wx] / R(3);
+                    lPm[0][wx] += G * uz * W[1].Pm[wy] * third;
+                    lPm[1][wy] += G * uz * W[0].Pm[wx] * third;
                 }
         }
         R lx1[3], lx0[3];
