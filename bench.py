@@ -269,7 +269,7 @@ def batched_arm(P, W, torch, args, dist):
         finally:
             b.close()
 
-    cands = [dict(tile=t, ppb=p, K=k) for t in (8, 16) for p in (2048, 8192) for k in (5, 10, 20)]
+    cands = [dict(tile=t, ppb=p, K=k) for t in (8, 16) for p in (8192,) for k in (2, 3, 5, 8)]
     key = AT.workload_key("ensemble2d", [(r["n"], r["ppc"], round(r["vth"], 6)) for r in params[::8]])
     best, table, cached = AT.tune(key, torch.cuda.get_device_name(), cands, time_candidate)
     b = build(runs, best)
