@@ -171,9 +171,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_particle(precision):
-    """Bytes of DRAM traffic per particle of the fused particle kernel from the
-    committed ncu summary, if it was taken on the current kernel source."""
+def ncu_per_particle(precision, key):
+    """A per-particle figure (DRAM bytes, warp instructions) of the fused
+    particle kernel from the committed ncu summary, if it was taken on the
+    current kernel source."""
     path = os.path.join(ROOT, "profiles", f"k_particles_fused_3d_{precision}.md")
     if not os.path.exists(path):
         return None
@@ -185,9 +186,13 @@ def ncu_traffic_per_particle(precision):
     if vals.get("source_sha") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_particle"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def ncu_traffic_per_particle(precision):
+    return ncu_per_particle(precision, "dram_bytes_per_particle")
 
 
 def build_grid(P, wl, precision, stream):
@@ -452,6 +457,18 @@ def our_arm(args):
             "kernel": "k_particles<3,float,fused>", "peak_source": peak_note,
             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": pk_ms / pk_n,
             "step_share": {k: v[0] / ms for k, v in prof.items()}}
+    # the unit that binds the kernel: instruction issue (warp instructions per
+    # particle from the committed ncu summary, 4 per SM per clock at the clock
+    # sampled during the timed steps)
+    ipp = ncu_per_particle("fp32", "warp_instructions_per_particle")
+    sm_mhz = (clocks or {}).get("sm_mhz") or (peaks["sm_max_mhz"] if peaks else 2070.0)
+    if ipp:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        issue_peak = 4.0 * sms * sm_mhz * 1e6
+        issue_ach = ipp * npart / (pk_ms / pk_n * 1e-3)
+        roof["issue"] = {"achieved": issue_ach, "peak": issue_peak, "unit": "warp instructions/s",
+                         "frac": issue_ach / issue_peak, "warp_instructions_per_particle": ipp,
+                         "peak_source": f"4 per SM per clock x {sms} SMs x {sm_mhz:.0f} MHz (sampled)"}
 
     # ---- end to end through the public API with host buffers ---------------------------
     # Each step uploads its whole input state from pinned host memory and reads
