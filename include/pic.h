@@ -292,11 +292,12 @@ int pic_profile(pic_grid *g, int enable);
 int pic_profile_read(pic_grid *g, double ms[PIC_PROF_N], long long count[PIC_PROF_N]);
 
 /* ---- State snapshots ------------------------------------------------------------
- * A snapshot is one contiguous blob: a 48-byte header ("PICS", version 1,
- * dims, precision, group count, particle and cell counts, sort phase, and a
- * checksum of the header) followed by the particle arrays (cell, id, offsets,
- * momenta, in storage order), the fields E^n, B^{n-1/2} and the tile starts of
- * the particle order (from the last tile sort).  pic_state_bytes gives its
+ * A snapshot is one contiguous blob: a 56-byte header ("PICS", version 2,
+ * dims, precision, group count, sort phase, particle, cell and tile counts, and
+ * a checksum of the header) followed by the particle arrays (cell, id, offsets,
+ * momenta, in storage order), the fields E^n, B^{n-1/2}, the tile starts of
+ * the particle order (from the last tile sort) and the antenna clock of every
+ * run (pic_set_antenna).  pic_state_bytes gives its
  * size.  pic_state_save writes it to dst (device memory if on_device, else host
  * memory); pic_state_restore reads one taken from a grid with the same layout
  * (same runs, species, particle counts and tiles), rebuilds the work items from
@@ -307,6 +308,15 @@ int pic_profile_read(pic_grid *g, double ms[PIC_PROF_N], long long count[PIC_PRO
 long long pic_state_bytes(pic_grid *g);
 int pic_state_save(pic_grid *g, void *dst, int on_device);
 int pic_state_restore(pic_grid *g, const void *src, int on_device);
+
+/* The recompute pass of a checkpointed adjoint: nsteps steps as
+ * pic_step(g, 1) each, with a device snapshot of the state before step s
+ * written to states[s] (nsteps device buffers of pic_state_bytes(g) bytes,
+ * owned by the caller).  Everything is enqueued on the grid's stream; unlike
+ * pic_state_save the call does not wait for the copies (pic_sync does).
+ * Errors: PIC_ERR_INVALID_ARG for a null grid, a null list or buffer, or a
+ * negative count; the errors of pic_step. */
+int pic_step_saving(pic_grid *g, int nsteps, void *const *states);
 
 /* ---- Discrete adjoint of the step -----------------------------------------------
  * pic_adjoint_step takes the grid's current state as level n (E^n, B^{n-1/2},
@@ -320,10 +330,29 @@ int pic_state_restore(pic_grid *g, const void *src, int on_device);
  * steps, and for every particle the gather of lamJ over its current window, the
  * hand-derived reverse of the deposit (Eq. current), move (Eq. coordscheme),
  * push (Eq. 1) and gather (Eqs. alphax, betax), with the transposed gather
- * scattered into lamE and lamB by atomics.
+ * scattered into lamE and lamB by atomics.  The particle part runs over the
+ * last tile sort's work items with each item's E, B and lamJ staged in shared
+ * memory (particles that drifted past their tile's halo read the global
+ * arrays); pic_set_adjoint_tiled(g, 0) selects the untiled form instead (one
+ * thread per particle, all reads global; the same arithmetic).
  * pic_adjoint_yee_half_B adds (-(1/2) C_B)^T lamB to lamE (the transpose of one
  * B half step), e.g. to seed a loss that uses B^n = B^{n-1/2} - (1/2) c curl E^n. */
 int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], void *lamw[3]);
+/* Adjoint steps back through nstates device snapshots of consecutive levels
+ * (states[s] holds level n0 + s, e.g. from pic_step_saving): for
+ * s = nstates-1 ... 0, restore states[s] as pic_state_restore does, then
+ * pic_adjoint_step with the same adjoint arrays.  The headers of all snapshots
+ * are read and checked first, with one host synchronization; nothing else
+ * waits.  On return the grid holds the state of states[0].  Errors: those of
+ * pic_state_restore (checked for every snapshot before any is restored) and
+ * of pic_adjoint_step; PIC_ERR_INVALID_ARG for a null list or buffer or a
+ * negative count. */
+int pic_adjoint_steps(pic_grid *g, void *const *states, int nstates, void *lamE[3], void *lamB[3], void *lamx[3],
+                      void *lamw[3]);
+
+/* tiled != 0 (the default): the tiled particle adjoint; 0: the untiled one.
+ * Errors: PIC_ERR_INVALID_ARG for a null grid. */
+int pic_set_adjoint_tiled(pic_grid *g, int tiled);
 int pic_adjoint_yee_half_B(pic_grid *g, void *const lamB[3], void *lamE[3]);
 
 /* ---- Tile sort without device allocation -----------------------------------

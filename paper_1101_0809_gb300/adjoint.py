@@ -10,8 +10,9 @@ over the staggered points whose integer indices lie in the window.  Its gradient
 with respect to x0 and w0 comes from libpic's discrete adjoint
 (pic_adjoint_step): the forward run keeps a state snapshot every
 `checkpoint_every` steps; the backward pass restores each checkpoint in reverse
-order, recomputes that segment keeping one snapshot per step, and runs the
-adjoint steps through it backwards.  Everything numerical runs in libpic; torch
+order, recomputes that segment keeping one device snapshot per step
+(pic_step_saving), and runs the adjoint steps back through it
+(pic_adjoint_steps), with one host synchronization per segment.  Everything numerical runs in libpic; torch
 only holds device buffers and the window mask, and chains the gradient to the
 caller's parameters (e.g. a density-perturbation amplitude) through
 torch.autograd.
@@ -103,17 +104,18 @@ class DifferentiableRun:
         lamE, lamB = self.lamE, self.lamB
         lamx = [torch.zeros(self.n, dtype=self.dtype, device="cuda") for _ in range(3)]
         lamw = [torch.zeros(self.n, dtype=self.dtype, device="cuda") for _ in range(3)]
+        nbytes = P.pic_state_bytes(self.grid.h)
+        bufs = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(min(self.ce, self.steps))]
+        torch.cuda.synchronize()
         for start in sorted(self.checkpoints, reverse=True):
             self.restore(self.checkpoints[start])
-            states = []
-            for s in range(start, min(start + self.ce, self.steps)):
-                states.append(self.snapshot())
-                P.pic_step(self.grid.h, 1)
-            for st in reversed(states):
-                self.restore(st)
-                P.pic_adjoint_step(self.grid.h, lamE, lamB, lamx, lamw)
-        torch.cuda.synchronize()
+            states = bufs[:min(start + self.ce, self.steps) - start]
+            # recompute the segment keeping the state of every level, then run
+            # the adjoint back through it; both calls only enqueue work
+            P.pic_step_saving(self.grid.h, states)
+            P.pic_adjoint_steps(self.grid.h, states, lamE, lamB, lamx, lamw)
         P.pic_sync(self.grid.h)
+        torch.cuda.synchronize()
         gx = torch.stack(lamx).to(torch.float64)
         if self.dims == 2:
             gx[2] = 0

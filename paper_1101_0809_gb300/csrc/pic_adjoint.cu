@@ -12,7 +12,10 @@
 // recomputed from the state at level n, in the same arithmetic as the forward
 // kernel (including the offset renormalization).  The particle adjoints are
 // indexed by group base + particle id, i.e. in each species' load order.
-#include "pic_internal.h"
+// The particle part runs over the last tile sort's work items with the item's
+// E, B1 and lambda_J in shared memory (k_particles_adj_tiled), or untiled over
+// the pool with every read global (k_particles_adj); the arithmetic is the same.
+#include "pic_particles.cuh"
 
 namespace pic {
 
@@ -70,6 +73,300 @@ __device__ __forceinline__ void axis_window_adj(R d0, R d1, int s, AxisWinAdj<R>
     a.n[3] = pos ? S1[2] : R(0);  a.dN[3] = pos ? dS1[2] : R(0);
 }
 
+// Wrapped run-local offsets of the cells -2..2 around a particle's old cell
+// per axis (x: i, y: nx j, z: nx ny k; a run has fewer than 2^31 cells) and the
+// run's first cell.  They index the scatter into lambda_E and lambda_B on every
+// path, and every read on the global-memory path.
+struct AdjWrap {
+    long long cb;
+    int x[5], y[5], z[5];
+    __device__ __forceinline__ long long at(int dx, int dy, int dz) const
+    {
+        return cb + (long long)(x[dx + 2] + y[dy + 2] + z[dz + 2]);
+    }
+};
+
+template <int DIM>
+__device__ __forceinline__ void adj_wrap(AdjWrap &w, const RunDev &rn, int i, int j, int k)
+{
+    const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
+    w.cb = rn.cell_base;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        w.x[q] = wrapi(i - 2 + q, nx);
+        w.y[q] = nx * wrapi(j - 2 + q, ny);
+        w.z[q] = DIM == 3 ? nx * ny * wrapi(k - 2 + q, nz) : 0;
+    }
+}
+
+// Readers of the particle adjoint: E and B1 at offsets -1..1 and lambda_J at
+// offsets -2..2 from the particle's old cell, from the periodic global arrays
+// or from a work item's shared-memory tiles.
+template <typename R>
+struct AdjGlobalRd {
+    const R *E[3];
+    const R *B[3];
+    const R *LJ[3];
+    const AdjWrap *w;
+    __device__ __forceinline__ R e(int c, int dx, int dy, int dz) const { return E[c][w->at(dx, dy, dz)]; }
+    __device__ __forceinline__ R b(int c, int dx, int dy, int dz) const { return B[c][w->at(dx, dy, dz)]; }
+    __device__ __forceinline__ R lj(int c, int dx, int dy, int dz) const { return LJ[c][w->at(dx, dy, dz)]; }
+};
+
+template <typename R>
+struct AdjSmemRd {
+    const R *E[3];
+    const R *B[3];
+    const R *LJ[3];
+    int fb, jb, s1, s2;   // the old cell in the field tile and in the lambda_J tile; y and z strides
+    __device__ __forceinline__ R e(int c, int dx, int dy, int dz) const { return E[c][fb + dx + s1 * dy + s2 * dz]; }
+    __device__ __forceinline__ R b(int c, int dx, int dy, int dz) const { return B[c][fb + dx + s1 * dy + s2 * dz]; }
+    __device__ __forceinline__ R lj(int c, int dx, int dy, int dz) const
+    {
+        return LJ[c][jb + dx + s1 * dy + s2 * dz];
+    }
+};
+
+// Reverse of one particle's step: from lambda_x, lambda_w at level n+1 (index
+// L) to level n, adding the transposed gather into lambda_E and lambda_B1.
+template <int DIM, typename R, class Rd>
+__device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev &gr, const RunDev &rn, long long p,
+                                             long long L, const Rd &rd, const AdjWrap &wr)
+{
+    constexpr bool F32 = sizeof(R) == 4;
+    const R third = R(1) / R(3);
+    // the particle's adjoints at level n+1, loaded first so that their latency
+    // overlaps the recomputation
+    R lx1[3], lw1[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        lx1[ax] = ax < DIM ? a.lamx[ax][L] : R(0);
+        lw1[ax] = a.lamw[ax][L];
+    }
+    R o[3] = {a.P.off[0][p], a.P.off[1][p], DIM == 3 ? a.P.off[2][p] : R(0)};
+    const R w0[3] = {a.P.w[0][p], a.P.w[1][p], a.P.w[2][p]};
+    // ---- recompute the forward quantities ------------------------------------
+    R f[3][2], S[3][3], df[3][2], dS[3][3];
+    for (int ax = 0; ax < 3; ++ax) {
+        if (ax == 2 && DIM == 2) {
+            f[2][0] = R(1); f[2][1] = R(0); S[2][0] = R(0); S[2][1] = R(1); S[2][2] = R(0);
+            df[2][0] = df[2][1] = R(0); dS[2][0] = dS[2][1] = dS[2][2] = R(0);
+            continue;
+        }
+        form_factor(o[ax], f[ax], S[ax]);
+        form_factor_d(o[ax], df[ax], dS[ax]);
+    }
+    // alternating-order gather (Eqs. alphax, betax), the forward kernel's sums
+    R Ep[3], Bp[3];
+    gather<DIM>(rd, f[0], S[0], f[1], S[1], f[2], S[2], Ep, Bp);
+    // group and run constants prepared on the host (no FP64 arithmetic in FP32)
+    const R hq = F32 ? R(gr.hqf) : R(gr.hq);
+    const R cl = F32 ? R(rn.cf) : R(rn.c), c2 = cl * cl;
+    const R cN[3] = {F32 ? R(rn.cNf[0]) : R(rn.cN[0]), F32 ? R(rn.cNf[1]) : R(rn.cN[1]),
+                     F32 ? R(rn.cNf[2]) : R(rn.cN[2])};
+    R w1[3] = {w0[0], w0[1], w0[2]};
+    boris(w1, Ep, Bp, hq, c2);
+    const R g1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2] + c2);
+    const R ig = R(1) / g1;
+    R n1[3] = {o[0], o[1], o[2]};
+    int sh[3] = {0, 0, 0};
+    for (int ax = 0; ax < DIM; ++ax) sh[ax] = renormalize(o[ax], w1[ax] * ig * cN[ax], n1[ax]);
+    const R uz = cl * w1[2] * ig;
+    // ---- reverse of the deposit ----------------------------------------------
+    AxisWin<R> W[3];
+    AxisWinAdj<R> WA[3];
+    for (int ax = 0; ax < DIM; ++ax) {
+        axis_window(o[ax], n1[ax], sh[ax], W[ax]);
+        axis_window_adj(o[ax], n1[ax], sh[ax], WA[ax]);
+    }
+    R lPp[3][4] = {{0}}, lPm[3][4] = {{0}}, lD[3][3] = {{0}};
+    R luz = 0;
+    if (DIM == 3) {
+        for (int cmp = 0; cmp < 3; ++cmp) {
+            const int b = (cmp + 1) % 3, cc = (cmp + 2) % 3;
+            const R ka = F32 ? R(gr.kff[cmp]) : R(gr.kf[cmp]);
+            for (int wc = 0; wc < 4; ++wc)
+                for (int wb = 0; wb < 4; ++wb) {
+                    const R T = W[b].Pp[wb] * W[cc].Pp[wc] + W[b].Pm[wb] * W[cc].Pm[wc] * third;
+                    for (int q = 0; q < 3; ++q) {
+                        int off[3];
+                        off[cmp] = W[cmp].lo + 1 + q;
+                        off[b] = W[b].lo + wb;
+                        off[cc] = W[cc].lo + wc;
+                        const R G = rd.lj(cmp, off[0], off[1], off[2]) * ka;
+                        lD[cmp][q] += G * T;
+                        lPp[b][wb] += G * W[cmp].D[q] * W[cc].Pp[wc];
+                        lPp[cc][wc] += G * W[cmp].D[q] * W[b].Pp[wb];
+                        lPm[b][wb] += G * W[cmp].D[q] * W[cc].Pm[wc] * third;
+                        lPm[cc][wc] += G * W[cmp].D[q] * W[b].Pm[wb] * third;
+                    }
+                }
+        }
+    } else {
+        const R kx = F32 ? R(gr.kff[0]) : R(gr.kf[0]);
+        const R ky = F32 ? R(gr.kff[1]) : R(gr.kf[1]);
+        const R kz = F32 ? R(gr.kff[2]) : R(gr.kf[2]);
+        for (int wy = 0; wy < 4; ++wy)
+            for (int q = 0; q < 3; ++q) {
+                const R G = rd.lj(0, W[0].lo + 1 + q, W[1].lo + wy, 0) * kx;
+                lD[0][q] += G * W[1].Pp[wy];
+                lPp[1][wy] += G * W[0].D[q];
+            }
+        for (int wx = 0; wx < 4; ++wx)
+            for (int q = 0; q < 3; ++q) {
+                const R G = rd.lj(1, W[0].lo + wx, W[1].lo + 1 + q, 0) * ky;
+                lD[1][q] += G * W[0].Pp[wx];
+                lPp[0][wx] += G * W[1].D[q];
+            }
+        for (int wy = 0; wy < 4; ++wy)
+            for (int wx = 0; wx < 4; ++wx) {
+                const R G = rd.lj(2, W[0].lo + wx, W[1].lo + wy, 0) * kz;
+                luz += G * (W[0].Pp[wx] * W[1].Pp[wy] + W[0].Pm[wx] * W[1].Pm[wy] * third);
+                lPp[0][wx] += G * uz * W[1].Pp[wy];
+                lPp[1][wy] += G * uz * W[0].Pp[wx];
+                lPm[0][wx] += G * uz * W[1].Pm[wy] * third;
+                lPm[1][wy] += G * uz * W[0].Pm[wx] * third;
+            }
+    }
+    R lx0[3] = {R(0), R(0), R(0)};
+    for (int ax = 0; ax < DIM; ++ax) {
+        // D[q] = sum_{w <= q} Pm[w]
+        lPm[ax][0] += lD[ax][0] + lD[ax][1] + lD[ax][2];
+        lPm[ax][1] += lD[ax][1] + lD[ax][2];
+        lPm[ax][2] += lD[ax][2];
+        R ln = 0, lo2 = 0;
+        for (int w4 = 0; w4 < 4; ++w4) {
+            ln += (lPp[ax][w4] + lPm[ax][w4]) * WA[ax].dN[w4];
+            lo2 += (lPp[ax][w4] - lPm[ax][w4]) * WA[ax].dO[w4];
+        }
+        lx1[ax] += ln;
+        lx0[ax] += lo2 + lx1[ax];   // x^{n+1} = x^n + delta
+    }
+    // ---- reverse of the move: delta_a = cN_a w1_a / gamma1, u_z = c w1_z / gamma1
+    const R ig3 = ig * ig * ig;
+    for (int bb = 0; bb < 3; ++bb) {
+        R acc = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+            const R jac = (ax == bb ? ig : R(0)) - w1[ax] * w1[bb] * ig3;
+            if (ax < DIM) acc += lx1[ax] * cN[ax] * jac;
+            if (ax == 2 && DIM == 2) acc += luz * cl * jac;
+        }
+        lw1[bb] += acc;
+    }
+    // ---- reverse of the push (Appendix): t = w + e, b = s B, n = t + t x b,
+    // F = 2/(1 + b.b), w1 = t + e + F (n x b)
+    R lEp[3], lBp[3], lw0[3];
+    {
+        R e[3], t[3], b[3], nn3[3], m[3];
+        for (int ax = 0; ax < 3; ++ax) {
+            e[ax] = hq * Ep[ax];
+            t[ax] = w0[ax] + e[ax];
+        }
+        const R gt = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + c2);
+        const R s = hq / gt;
+        for (int ax = 0; ax < 3; ++ax) b[ax] = s * Bp[ax];
+        nn3[0] = t[0] + (t[1] * b[2] - t[2] * b[1]);
+        nn3[1] = t[1] + (t[2] * b[0] - t[0] * b[2]);
+        nn3[2] = t[2] + (t[0] * b[1] - t[1] * b[0]);
+        const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        const R Fq = R(2) / (R(1) + b2);
+        m[0] = nn3[1] * b[2] - nn3[2] * b[1];
+        m[1] = nn3[2] * b[0] - nn3[0] * b[2];
+        m[2] = nn3[0] * b[1] - nn3[1] * b[0];
+        R lt[3], le[3], lm[3], ln3[3], lb[3];
+        R lF = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+            lt[ax] = lw1[ax];
+            le[ax] = lw1[ax];
+            lm[ax] = Fq * lw1[ax];
+            lF += lw1[ax] * m[ax];
+        }
+        // m = n x b: ln = b x lm, lb = lm x n
+        ln3[0] = b[1] * lm[2] - b[2] * lm[1];
+        ln3[1] = b[2] * lm[0] - b[0] * lm[2];
+        ln3[2] = b[0] * lm[1] - b[1] * lm[0];
+        lb[0] = lm[1] * nn3[2] - lm[2] * nn3[1];
+        lb[1] = lm[2] * nn3[0] - lm[0] * nn3[2];
+        lb[2] = lm[0] * nn3[1] - lm[1] * nn3[0];
+        const R lb2 = lF * (-R(2) / ((R(1) + b2) * (R(1) + b2)));
+        for (int ax = 0; ax < 3; ++ax) lb[ax] += R(2) * b[ax] * lb2;
+        // n = t + t x b: lt += ln + b x ln, lb += ln x t
+        lt[0] += ln3[0] + (b[1] * ln3[2] - b[2] * ln3[1]);
+        lt[1] += ln3[1] + (b[2] * ln3[0] - b[0] * ln3[2]);
+        lt[2] += ln3[2] + (b[0] * ln3[1] - b[1] * ln3[0]);
+        lb[0] += ln3[1] * t[2] - ln3[2] * t[1];
+        lb[1] += ln3[2] * t[0] - ln3[0] * t[2];
+        lb[2] += ln3[0] * t[1] - ln3[1] * t[0];
+        R ls = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+            ls += lb[ax] * Bp[ax];
+            lBp[ax] = s * lb[ax];
+        }
+        const R lgt = -ls * hq / (gt * gt);
+        for (int ax = 0; ax < 3; ++ax) {
+            lt[ax] += lgt * t[ax] / gt;
+            lw0[ax] = lt[ax];
+            lEp[ax] = hq * (le[ax] + lt[ax]);
+        }
+    }
+    // ---- reverse of the gather: scatter into lamE, lamB1 (one global reduction
+    // per tap); derivatives of the weights into lx0
+    for (int fld = 0; fld < 2; ++fld)
+        for (int c = 0; c < 3; ++c) {
+            const bool intx = (fld == 0) == (c == 0), inty = (fld == 0) == (c == 1), intz = (fld == 0) == (c == 2);
+            const int cx = intx ? 2 : 3, cy = inty ? 2 : 3, cz = DIM == 3 ? (intz ? 2 : 3) : 1;
+            const int ox = intx ? 0 : -1, oy = inty ? 0 : -1, oz = DIM == 3 ? (intz ? 0 : -1) : 0;
+            R *LF = fld == 0 ? a.lamE[c] : a.lamB1[c];
+            const R lam = fld == 0 ? lEp[c] : lBp[c];
+            for (int sz = 0; sz < cz; ++sz)
+                for (int sy = 0; sy < cy; ++sy)
+                    for (int sx = 0; sx < cx; ++sx) {
+                        const int dx = ox + sx, dy = oy + sy, dz = DIM == 3 ? oz + sz : 0;
+                        const R vx = intx ? f[0][sx] : S[0][sx], ddx = intx ? df[0][sx] : dS[0][sx];
+                        const R vy = inty ? f[1][sy] : S[1][sy], ddy = inty ? df[1][sy] : dS[1][sy];
+                        const R vz = DIM == 3 ? (intz ? f[2][sz] : S[2][sz]) : R(1);
+                        const R ddz = DIM == 3 ? (intz ? df[2][sz] : dS[2][sz]) : R(0);
+                        atomicAdd(&LF[wr.at(dx, dy, dz)], vx * vy * vz * lam);
+                        const R fl = (fld == 0 ? rd.e(c, dx, dy, dz) : rd.b(c, dx, dy, dz)) * lam;
+                        lx0[0] += ddx * vy * vz * fl;
+                        lx0[1] += vx * ddy * vz * fl;
+                        lx0[2] += vx * vy * ddz * fl;
+                    }
+        }
+    for (int ax = 0; ax < 3; ++ax) {
+        if (ax < DIM) a.lamx[ax][L] = lx0[ax];
+        a.lamw[ax][L] = lw0[ax];
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ void split_cell(const RunDev &rn, int cell, int &i, int &j, int &k)
+{
+    const int rest = divu31(cell, rn.div_nx);
+    i = cell - rest * rn.n[0];
+    k = DIM == 3 ? divu31(rest, rn.div_ny) : 0;
+    j = rest - k * rn.n[1];
+}
+
+// A particle on the periodic global arrays (the untiled kernel, and particles
+// that drifted past their tile's halo since the last sort).  The wrapped
+// offsets are indexed at run time here, so they live in local memory.
+template <int DIM, typename R>
+__device__ __forceinline__ void adj_particle_global_body(const AdjArgs<R> &a, const GroupDev &gr, const RunDev &rn,
+                                                         long long p, long long L, int i, int j, int k)
+{
+    AdjWrap wr;
+    adj_wrap<DIM>(wr, rn, i, j, k);
+    AdjGlobalRd<R> rd;
+    for (int c = 0; c < 3; ++c) {
+        rd.E[c] = a.E[c];
+        rd.B[c] = a.B1[c];
+        rd.LJ[c] = a.lamJ[c];
+    }
+    rd.w = &wr;
+    adj_particle<DIM, R>(a, gr, rn, p, L, rd, wr);
+}
+
+// Untiled form: one thread per particle in pool order, all reads global.
 template <int DIM, typename R>
 __global__ void __launch_bounds__(256) k_particles_adj(const AdjArgs<R> a)
 {
@@ -82,246 +379,99 @@ __global__ void __launch_bounds__(256) k_particles_adj(const AdjArgs<R> a)
         }
         const GroupDev &gr = a.groups[lo];
         const RunDev &rn = a.runs[gr.run];
-        const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
-        const long long cb = rn.cell_base;
+        int i, j, k;
+        split_cell<DIM>(rn, a.P.cell[p], i, j, k);
+        adj_particle_global_body<DIM, R>(a, gr, rn, p, gr.base + a.P.id[p], i, j, k);
+    }
+}
+
+// Tiled form over the last sort's work items: `nsplit` blocks share one item,
+// each stages the item's E and B1 with a halo of (halo + 1) cells and lambda_J
+// with a halo of (halo + 2) cells in shared memory, in the particle kernels'
+// tile pitches, then takes every nsplit-th round of 256 particles of the item.
+// Reads come from the tiles; the transposed gather is scattered into the global
+// lambda_E and lambda_B1 with reductions.  A particle that drifted past the
+// tile's halo takes the global-memory form.
+template <int DIM, typename R>
+__global__ void __launch_bounds__(kThreads) k_particles_adj_tiled(const AdjArgs<R> a, const WorkItem *items,
+                                                                  const int *n_items, int halo, int nsplit)
+{
+    const int item = blockIdx.x / nsplit, part = blockIdx.x - item * nsplit;
+    if (item >= *n_items) return;
+    const WorkItem it = items[item];
+    const GroupDev gr = a.groups[it.group];
+    const RunDev rn = a.runs[gr.run];
+    const int G = halo;
+    const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
+    const int T0 = rn.tile[0], T1 = rn.tile[1], T2 = DIM == 3 ? rn.tile[2] : 1;
+    const int tx = it.tile % rn.ntile[0];
+    const int ty = (it.tile / rn.ntile[0]) % rn.ntile[1];
+    const int tz = DIM == 3 ? it.tile / (rn.ntile[0] * rn.ntile[1]) : 0;
+    const int ox = tx * T0, oy = ty * T1, oz = tz * T2;
+    const int fe0 = T0 + 2 * G + 2, fe1 = T1 + 2 * G + 2, fe2 = DIM == 3 ? T2 + 2 * G + 2 : 1;
+    const int je0 = T0 + 2 * G + 4, je1 = T1 + 2 * G + 4, je2 = DIM == 3 ? T2 + 2 * G + 4 : 1;
+    const int P0 = rn.pitch[0], P1 = rn.pitch[1];   // >= je0, je1
+    const int nf = P0 * P1 * fe2, nj = P0 * P1 * je2;
+    const long long cb = rn.cell_base;
+    R *sE[3], *sB[3], *sL[3];
+    {
+        R *s = reinterpret_cast<R *>(g_smem);
+        for (int c = 0; c < 3; ++c) {
+            sE[c] = s + c * nf;
+            sB[c] = s + (3 + c) * nf;
+            sL[c] = s + 6 * nf + c * nj;
+        }
+    }
+    for (int l = threadIdx.x; l < nf; l += blockDim.x) {
+        const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
+        if (lx >= fe0 || ly >= fe1) continue;   // pitch padding
+        const int gx = wrapi(ox - G - 1 + lx, nx);
+        const int gy = wrapi(oy - G - 1 + ly, ny);
+        const int gz = DIM == 3 ? wrapi(oz - G - 1 + lz, nz) : 0;
+        const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sE[c][l] = a.E[c][gi];
+            sB[c][l] = a.B1[c][gi];
+        }
+    }
+    for (int l = threadIdx.x; l < nj; l += blockDim.x) {
+        const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
+        if (lx >= je0 || ly >= je1) continue;
+        const int gx = wrapi(ox - G - 2 + lx, nx);
+        const int gy = wrapi(oy - G - 2 + ly, ny);
+        const int gz = DIM == 3 ? wrapi(oz - G - 2 + lz, nz) : 0;
+        const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sL[c][l] = a.lamJ[c][gi];
+    }
+    __syncthreads();
+    const long long step = (long long)nsplit * blockDim.x;
+    for (long long p = it.begin + (long long)part * blockDim.x + threadIdx.x; p < it.end; p += step) {
         const long long L = gr.base + a.P.id[p];
-        const int cell0 = a.P.cell[p];
-        const int rest = divu31(cell0, rn.div_nx);
-        const int i = cell0 - rest * nx;
-        const int k = DIM == 3 ? divu31(rest, rn.div_ny) : 0;
-        const int j = rest - k * ny;
-        constexpr bool F32 = sizeof(R) == 4;
-        const R third = R(1) / R(3);
-        R o[3] = {a.P.off[0][p], a.P.off[1][p], DIM == 3 ? a.P.off[2][p] : R(0)};
-        const R w0[3] = {a.P.w[0][p], a.P.w[1][p], a.P.w[2][p]};
-        // ---- recompute the forward quantities --------------------------------
-        R f[3][2], S[3][3], df[3][2], dS[3][3];
-        for (int ax = 0; ax < 3; ++ax) {
-            if (ax == 2 && DIM == 2) {
-                f[2][0] = R(1); f[2][1] = R(0); S[2][0] = R(0); S[2][1] = R(1); S[2][2] = R(0);
-                df[2][0] = df[2][1] = R(0); dS[2][0] = dS[2][1] = dS[2][2] = R(0);
-                continue;
-            }
-            form_factor(o[ax], f[ax], S[ax]);
-            form_factor_d(o[ax], df[ax], dS[ax]);
-        }
-        long long xi[4], yj[4], zk[4];
-        for (int q = 0; q < 4; ++q) {
-            xi[q] = cb + wrapi(i - 1 + q, nx);
-            yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
-            zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
-        }
-        // alternating-order weights: E_c uses f along axis c and S along the
-        // others, B_c uses S along c and f along the others (Eqs. alphax, betax)
-        const int nz_pts = DIM == 3 ? 1 : 0;   // in 2D the z factor is the single weight 1
-        R Ep[3] = {0, 0, 0}, Bp[3] = {0, 0, 0};
-        for (int fld = 0; fld < 2; ++fld)
+        int i, j, k;
+        split_cell<DIM>(rn, a.P.cell[p], i, j, k);
+        const int li = local_coord(i, ox, T0, G, nx);
+        const int lj = local_coord(j, oy, T1, G, ny);
+        const int lk = DIM == 3 ? local_coord(k, oz, T2, G, nz) : 0;
+        const bool inr =
+            li >= -G && li < T0 + G && lj >= -G && lj < T1 + G && (DIM == 2 || (lk >= -G && lk < T2 + G));
+        if (inr) {
+            AdjWrap wr;
+            adj_wrap<DIM>(wr, rn, i, j, k);
+            AdjSmemRd<R> rd;
             for (int c = 0; c < 3; ++c) {
-                const bool intx = (fld == 0) == (c == 0), inty = (fld == 0) == (c == 1), intz = (fld == 0) == (c == 2);
-                const int cx = intx ? 2 : 3, cy = inty ? 2 : 3, cz = DIM == 3 ? (intz ? 2 : 3) : 1;
-                const int ox = intx ? 0 : -1, oy = inty ? 0 : -1, oz = DIM == 3 ? (intz ? 0 : -1) : 0;
-                const R *F = fld == 0 ? a.E[c] : a.B1[c];
-                R acc = 0;
-                for (int sz = 0; sz < cz; ++sz)
-                    for (int sy = 0; sy < cy; ++sy)
-                        for (int sx = 0; sx < cx; ++sx) {
-                            const R wx = intx ? f[0][sx] : S[0][sx];
-                            const R wy = inty ? f[1][sy] : S[1][sy];
-                            const R wz = DIM == 3 ? (intz ? f[2][sz] : S[2][sz]) : R(1);
-                            acc += wx * wy * wz * F[xi[ox + sx + 1] + yj[oy + sy + 1] + zk[oz + sz + nz_pts]];
-                        }
-                if (fld == 0) Ep[c] = acc; else Bp[c] = acc;
+                rd.E[c] = sE[c];
+                rd.B[c] = sB[c];
+                rd.LJ[c] = sL[c];
             }
-        // group and run constants prepared on the host (no FP64 arithmetic in FP32)
-        const R hq = F32 ? R(gr.hqf) : R(gr.hq);
-        const R cl = F32 ? R(rn.cf) : R(rn.c), c2 = cl * cl;
-        const R cN[3] = {F32 ? R(rn.cNf[0]) : R(rn.cN[0]), F32 ? R(rn.cNf[1]) : R(rn.cN[1]),
-                         F32 ? R(rn.cNf[2]) : R(rn.cN[2])};
-        R w1[3] = {w0[0], w0[1], w0[2]};
-        boris(w1, Ep, Bp, hq, c2);
-        const R g1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2] + c2);
-        const R ig = R(1) / g1;
-        R n1[3] = {o[0], o[1], o[2]};
-        int sh[3] = {0, 0, 0};
-        for (int ax = 0; ax < DIM; ++ax) sh[ax] = renormalize(o[ax], w1[ax] * ig * cN[ax], n1[ax]);
-        const R uz = cl * w1[2] * ig;
-        // ---- reverse of the deposit ------------------------------------------
-        AxisWin<R> W[3];
-        AxisWinAdj<R> WA[3];
-        for (int ax = 0; ax < DIM; ++ax) {
-            axis_window(o[ax], n1[ax], sh[ax], W[ax]);
-            axis_window_adj(o[ax], n1[ax], sh[ax], WA[ax]);
-        }
-        R lPp[3][4] = {{0}}, lPm[3][4] = {{0}}, lD[3][3] = {{0}};
-        R luz = 0;
-        // wrapped offsets of the deposit window cells -2..2 around the old cell
-        long long wx5[5], wy5[5], wz5[5];
-        for (int q = 0; q < 5; ++q) {
-            wx5[q] = cb + wrapi(i - 2 + q, nx);
-            wy5[q] = (long long)nx * wrapi(j - 2 + q, ny);
-            wz5[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 2 + q, nz) : 0;
-        }
-        auto gidx = [&](int c0, int c1, int c2i) -> long long { return wx5[c0 + 2] + wy5[c1 + 2] + wz5[c2i + 2]; };
-        if (DIM == 3) {
-            for (int cmp = 0; cmp < 3; ++cmp) {
-                const int b = (cmp + 1) % 3, cc = (cmp + 2) % 3;
-                const R ka = F32 ? R(gr.kff[cmp]) : R(gr.kf[cmp]);
-                for (int wc = 0; wc < 4; ++wc)
-                    for (int wb = 0; wb < 4; ++wb) {
-                        const R T = W[b].Pp[wb] * W[cc].Pp[wc] + W[b].Pm[wb] * W[cc].Pm[wc] * third;
-                        for (int q = 0; q < 3; ++q) {
-                            int off[3];
-                            off[cmp] = W[cmp].lo + 1 + q;
-                            off[b] = W[b].lo + wb;
-                            off[cc] = W[cc].lo + wc;
-                            const R G = a.lamJ[cmp][gidx(off[0], off[1], off[2])] * ka;
-                            lD[cmp][q] += G * T;
-                            lPp[b][wb] += G * W[cmp].D[q] * W[cc].Pp[wc];
-                            lPp[cc][wc] += G * W[cmp].D[q] * W[b].Pp[wb];
-                            lPm[b][wb] += G * W[cmp].D[q] * W[cc].Pm[wc] * third;
-                            lPm[cc][wc] += G * W[cmp].D[q] * W[b].Pm[wb] * third;
-                        }
-                    }
-            }
+            rd.s1 = P0;
+            rd.s2 = P0 * P1;
+            rd.fb = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
+            rd.jb = (li + G + 2) + P0 * ((lj + G + 2) + (DIM == 3 ? P1 * (lk + G + 2) : 0));
+            adj_particle<DIM, R>(a, gr, rn, p, L, rd, wr);
         } else {
-            const R kx = F32 ? R(gr.kff[0]) : R(gr.kf[0]);
-            const R ky = F32 ? R(gr.kff[1]) : R(gr.kf[1]);
-            const R kz = F32 ? R(gr.kff[2]) : R(gr.kf[2]);
-            for (int wy = 0; wy < 4; ++wy)
-                for (int q = 0; q < 3; ++q) {
-                    const R G = a.lamJ[0][gidx(W[0].lo + 1 + q, W[1].lo + wy, 0)] * kx;
-                    lD[0][q] += G * W[1].Pp[wy];
-                    lPp[1][wy] += G * W[0].D[q];
-                }
-            for (int wx = 0; wx < 4; ++wx)
-                for (int q = 0; q < 3; ++q) {
-                    const R G = a.lamJ[1][gidx(W[0].lo + wx, W[1].lo + 1 + q, 0)] * ky;
-                    lD[1][q] += G * W[0].Pp[wx];
-                    lPp[0][wx] += G * W[1].D[q];
-                }
-            for (int wy = 0; wy < 4; ++wy)
-                for (int wx = 0; wx < 4; ++wx) {
-                    const R G = a.lamJ[2][gidx(W[0].lo + wx, W[1].lo + wy, 0)] * kz;
-                    luz += G * (W[0].Pp[wx] * W[1].Pp[wy] + W[0].Pm[wx] * W[1].Pm[wy] * third);
-                    lPp[0][wx] += G * uz * W[1].Pp[wy];
-                    lPp[1][wy] += G * uz * W[0].Pp[wx];
-                    lPm[0][wx] += G * uz * W[1].Pm[wy] * third;
-                    lPm[1][wy] += G * uz * W[0].Pm[wx] * third;
-                }
-        }
-        R lx1[3], lx0[3];
-        for (int ax = 0; ax < 3; ++ax) {
-            lx1[ax] = ax < DIM ? a.lamx[ax][L] : R(0);
-            lx0[ax] = 0;
-        }
-        for (int ax = 0; ax < DIM; ++ax) {
-            // D[q] = sum_{w <= q} Pm[w]
-            lPm[ax][0] += lD[ax][0] + lD[ax][1] + lD[ax][2];
-            lPm[ax][1] += lD[ax][1] + lD[ax][2];
-            lPm[ax][2] += lD[ax][2];
-            R ln = 0, lo2 = 0;
-            for (int w4 = 0; w4 < 4; ++w4) {
-                ln += (lPp[ax][w4] + lPm[ax][w4]) * WA[ax].dN[w4];
-                lo2 += (lPp[ax][w4] - lPm[ax][w4]) * WA[ax].dO[w4];
-            }
-            lx1[ax] += ln;
-            lx0[ax] += lo2 + lx1[ax];   // x^{n+1} = x^n + delta
-        }
-        // ---- reverse of the move: delta_a = cN_a w1_a / gamma1, u_z = c w1_z / gamma1
-        R lw1[3] = {a.lamw[0][L], a.lamw[1][L], a.lamw[2][L]};
-        const R ig3 = ig * ig * ig;
-        for (int bb = 0; bb < 3; ++bb) {
-            R acc = 0;
-            for (int ax = 0; ax < 3; ++ax) {
-                const R jac = (ax == bb ? ig : R(0)) - w1[ax] * w1[bb] * ig3;
-                if (ax < DIM) acc += lx1[ax] * cN[ax] * jac;
-                if (ax == 2 && DIM == 2) acc += luz * cl * jac;
-            }
-            lw1[bb] += acc;
-        }
-        // ---- reverse of the push (Appendix): t = w + e, b = s B, n = t + t x b,
-        // F = 2/(1 + b.b), w1 = t + e + F (n x b)
-        R lEp[3], lBp[3], lw0[3];
-        {
-            R e[3], t[3], b[3], nn3[3], m[3];
-            for (int ax = 0; ax < 3; ++ax) {
-                e[ax] = hq * Ep[ax];
-                t[ax] = w0[ax] + e[ax];
-            }
-            const R gt = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + c2);
-            const R s = hq / gt;
-            for (int ax = 0; ax < 3; ++ax) b[ax] = s * Bp[ax];
-            nn3[0] = t[0] + (t[1] * b[2] - t[2] * b[1]);
-            nn3[1] = t[1] + (t[2] * b[0] - t[0] * b[2]);
-            nn3[2] = t[2] + (t[0] * b[1] - t[1] * b[0]);
-            const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-            const R Fq = R(2) / (R(1) + b2);
-            m[0] = nn3[1] * b[2] - nn3[2] * b[1];
-            m[1] = nn3[2] * b[0] - nn3[0] * b[2];
-            m[2] = nn3[0] * b[1] - nn3[1] * b[0];
-            R lt[3], le[3], lm[3], ln3[3], lb[3];
-            R lF = 0;
-            for (int ax = 0; ax < 3; ++ax) {
-                lt[ax] = lw1[ax];
-                le[ax] = lw1[ax];
-                lm[ax] = Fq * lw1[ax];
-                lF += lw1[ax] * m[ax];
-            }
-            // m = n x b: ln = b x lm, lb = lm x n
-            ln3[0] = b[1] * lm[2] - b[2] * lm[1];
-            ln3[1] = b[2] * lm[0] - b[0] * lm[2];
-            ln3[2] = b[0] * lm[1] - b[1] * lm[0];
-            lb[0] = lm[1] * nn3[2] - lm[2] * nn3[1];
-            lb[1] = lm[2] * nn3[0] - lm[0] * nn3[2];
-            lb[2] = lm[0] * nn3[1] - lm[1] * nn3[0];
-            const R lb2 = lF * (-R(2) / ((R(1) + b2) * (R(1) + b2)));
-            for (int ax = 0; ax < 3; ++ax) lb[ax] += R(2) * b[ax] * lb2;
-            // n = t + t x b: lt += ln + b x ln, lb += ln x t
-            lt[0] += ln3[0] + (b[1] * ln3[2] - b[2] * ln3[1]);
-            lt[1] += ln3[1] + (b[2] * ln3[0] - b[0] * ln3[2]);
-            lt[2] += ln3[2] + (b[0] * ln3[1] - b[1] * ln3[0]);
-            lb[0] += ln3[1] * t[2] - ln3[2] * t[1];
-            lb[1] += ln3[2] * t[0] - ln3[0] * t[2];
-            lb[2] += ln3[0] * t[1] - ln3[1] * t[0];
-            R ls = 0;
-            for (int ax = 0; ax < 3; ++ax) {
-                ls += lb[ax] * Bp[ax];
-                lBp[ax] = s * lb[ax];
-            }
-            const R lgt = -ls * hq / (gt * gt);
-            for (int ax = 0; ax < 3; ++ax) {
-                lt[ax] += lgt * t[ax] / gt;
-                lw0[ax] = lt[ax];
-                lEp[ax] = hq * (le[ax] + lt[ax]);
-            }
-        }
-        // ---- reverse of the gather: scatter into lamE, lamB1; derivatives into lx0
-        for (int fld = 0; fld < 2; ++fld)
-            for (int c = 0; c < 3; ++c) {
-                const bool intx = (fld == 0) == (c == 0), inty = (fld == 0) == (c == 1), intz = (fld == 0) == (c == 2);
-                const int cx = intx ? 2 : 3, cy = inty ? 2 : 3, cz = DIM == 3 ? (intz ? 2 : 3) : 1;
-                const int ox = intx ? 0 : -1, oy = inty ? 0 : -1, oz = DIM == 3 ? (intz ? 0 : -1) : 0;
-                const R *F = fld == 0 ? a.E[c] : a.B1[c];
-                R *LF = fld == 0 ? a.lamE[c] : a.lamB1[c];
-                const R lam = fld == 0 ? lEp[c] : lBp[c];
-                for (int sz = 0; sz < cz; ++sz)
-                    for (int sy = 0; sy < cy; ++sy)
-                        for (int sx = 0; sx < cx; ++sx) {
-                            const R vx = intx ? f[0][sx] : S[0][sx], dx = intx ? df[0][sx] : dS[0][sx];
-                            const R vy = inty ? f[1][sy] : S[1][sy], dy = inty ? df[1][sy] : dS[1][sy];
-                            const R vz = DIM == 3 ? (intz ? f[2][sz] : S[2][sz]) : R(1);
-                            const R dz = DIM == 3 ? (intz ? df[2][sz] : dS[2][sz]) : R(0);
-                            const long long idx = xi[ox + sx + 1] + yj[oy + sy + 1] + zk[oz + sz + nz_pts];
-                            atomicAdd(&LF[idx], vx * vy * vz * lam);
-                            const R fl = F[idx] * lam;
-                            lx0[0] += dx * vy * vz * fl;
-                            lx0[1] += vx * dy * vz * fl;
-                            lx0[2] += vx * vy * dz * fl;
-                        }
-            }
-        for (int ax = 0; ax < 3; ++ax) {
-            if (ax < DIM) a.lamx[ax][L] = lx0[ax];
-            a.lamw[ax][L] = lw0[ax];
+            adj_particle_global_body<DIM, R>(a, gr, rn, p, L, i, j, k);
         }
     }
 }
@@ -421,17 +571,16 @@ cudaError_t launch_adj_yee(int dims, int prec, int which, cudaStream_t st, const
 }
 
 template <int DIM, typename R>
-static cudaError_t adj_part_t(cudaStream_t st, const RunDev *runs, const GroupDev *groups, const long long *gbase,
-                              int ngroups, long long total, const PoolBuf &P, void *const E[3], void *const B1[3],
-                              void *const lamJ[3], void *const lamE[3], void *const lamB1[3], void *const lamx[3],
-                              void *const lamw[3])
+static cudaError_t adj_part_t(cudaStream_t st, const AdjLaunch &lc, const PoolBuf &P, void *const E[3],
+                              void *const B1[3], void *const lamJ[3], void *const lamE[3], void *const lamB1[3],
+                              void *const lamx[3], void *const lamw[3])
 {
     AdjArgs<R> a;
-    a.runs = runs;
-    a.groups = groups;
-    a.group_base = gbase;
-    a.ngroups = ngroups;
-    a.total = total;
+    a.runs = lc.runs;
+    a.groups = lc.groups;
+    a.group_base = lc.group_base;
+    a.ngroups = lc.ngroups;
+    a.total = lc.total;
     a.P.cell = P.cell;
     a.P.id = P.id;
     for (int c = 0; c < 3; ++c) {
@@ -445,30 +594,54 @@ static cudaError_t adj_part_t(cudaStream_t st, const RunDev *runs, const GroupDe
         a.lamx[c] = (R *)lamx[c];
         a.lamw[c] = (R *)lamw[c];
     }
-    if (total <= 0) return cudaSuccess;
+    if (lc.total <= 0) return cudaSuccess;
+    if (lc.items && lc.max_items > 0) {
+        // blocks per work item: about 512 particles or more per block on average
+        long long ns = lc.total / ((long long)lc.max_items * 512);
+        const int nsplit = (int)(ns < 1 ? 1 : ns > 8 ? 8 : ns);
+        const size_t smem = adjoint_smem_bytes(DIM, sizeof(R) == 8 ? 0 : 1, lc.tile, lc.halo, lc.pitch);
+        k_particles_adj_tiled<DIM, R><<<(unsigned)((long long)lc.max_items * nsplit), kThreads, smem, st>>>(
+            a, lc.items, lc.n_items, lc.halo, nsplit);
+        return cudaGetLastError();
+    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long blocks = (total + 255) / 256;
+    long long blocks = (lc.total + 255) / 256;
     if (blocks > 16LL * sms) blocks = 16LL * sms;
     k_particles_adj<DIM, R><<<(unsigned)blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_particles_adj(int dims, int prec, cudaStream_t st, const RunDev *runs, const GroupDev *groups,
-                                 const long long *gbase, int ngroups, long long total, const PoolBuf &P,
+size_t adjoint_smem_bytes(int dims, int prec, const int tile[3], int halo, const int pitch[2])
+{
+    const size_t fe2 = dims == 3 ? (size_t)tile[2] + 2 * halo + 2 : 1;
+    const size_t je2 = dims == 3 ? (size_t)tile[2] + 2 * halo + 4 : 1;
+    const size_t plane = (size_t)pitch[0] * pitch[1];
+    return (6 * plane * fe2 + 3 * plane * je2) * (prec == 0 ? sizeof(double) : sizeof(float));
+}
+
+cudaError_t adjoint_set_smem_limit(int dims, int prec, size_t bytes)
+{
+    const int b = (int)bytes;
+    if (dims == 3)
+        return prec == 0
+                   ? cudaFuncSetAttribute(k_particles_adj_tiled<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)
+                   : cudaFuncSetAttribute(k_particles_adj_tiled<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return prec == 0
+               ? cudaFuncSetAttribute(k_particles_adj_tiled<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)
+               : cudaFuncSetAttribute(k_particles_adj_tiled<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
+cudaError_t launch_particles_adj(int dims, int prec, cudaStream_t st, const AdjLaunch &lc, const PoolBuf &P,
                                  void *const E[3], void *const B1[3], void *const lamJ[3], void *const lamE[3],
                                  void *const lamB1[3], void *const lamx[3], void *const lamw[3])
 {
     if (dims == 3)
-        return prec == 0 ? adj_part_t<3, double>(st, runs, groups, gbase, ngroups, total, P, E, B1, lamJ, lamE, lamB1,
-                                                 lamx, lamw)
-                         : adj_part_t<3, float>(st, runs, groups, gbase, ngroups, total, P, E, B1, lamJ, lamE, lamB1,
-                                                lamx, lamw);
-    return prec == 0 ? adj_part_t<2, double>(st, runs, groups, gbase, ngroups, total, P, E, B1, lamJ, lamE, lamB1,
-                                             lamx, lamw)
-                     : adj_part_t<2, float>(st, runs, groups, gbase, ngroups, total, P, E, B1, lamJ, lamE, lamB1, lamx,
-                                            lamw);
+        return prec == 0 ? adj_part_t<3, double>(st, lc, P, E, B1, lamJ, lamE, lamB1, lamx, lamw)
+                         : adj_part_t<3, float>(st, lc, P, E, B1, lamJ, lamE, lamB1, lamx, lamw);
+    return prec == 0 ? adj_part_t<2, double>(st, lc, P, E, B1, lamJ, lamE, lamB1, lamx, lamw)
+                     : adj_part_t<2, float>(st, lc, P, E, B1, lamJ, lamE, lamB1, lamx, lamw);
 }
 
 }  // namespace pic

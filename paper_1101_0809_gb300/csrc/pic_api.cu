@@ -41,6 +41,16 @@ int cuda_fail(cudaError_t e, const char *what)
 
 constexpr int kDiagBlocks = 1024;
 
+// A snapshot header written into device memory by a kernel, so that a device
+// snapshot is taken in stream order without a host copy or synchronization.
+struct HeaderBytes {
+    unsigned char b[64];
+};
+__global__ void k_put_bytes(const HeaderBytes h, unsigned char *dst, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = h.b[i];
+}
+
 size_t elem(const pic_grid *g) { return g->prec == PIC_FP64 ? sizeof(double) : sizeof(float); }
 
 template <typename T>
@@ -447,6 +457,7 @@ void destroy_grid(pic_grid *g)
     dfree(g->d_run_cell_base);
     dfree(g->d_ant_n);
     if (g->h_drift) cudaFreeHost(g->h_drift);
+    if (g->h_hdr) cudaFreeHost(g->h_hdr);
     for (auto &ev : g->ad_ev)
         if (ev) cudaEventDestroy(ev);
     for (int c = 0; c < 3; ++c) {
@@ -547,6 +558,9 @@ int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out)
         }
         if ((e = particles_set_smem_limit(g->dims, g->prec, mode, b)) != cudaSuccess) return bail(e, "smem limit");
     }
+    if ((e = adjoint_set_smem_limit(g->dims, g->prec, adjoint_smem_bytes(g->dims, g->prec, g->tile, g->halo,
+                                                                          g->pitch))) != cudaSuccess)
+        return bail(e, "smem limit");
     if (g->prec == PIC_FP32 && (e = diag_set_smem_limit(g->dims, diag_items_smem_bytes(g->dims, g->tile, g->halo,
                                                                                       g->pitch))) != cudaSuccess)
         return bail(e, "smem limit");
@@ -1261,16 +1275,25 @@ long long pic_state_bytes(pic_grid *g)
            (long long)sizeof(long long) * (g->total_tiles + 1 + (long long)g->runs.size());
 }
 
-int pic_state_save(pic_grid *g, void *dst, int on_device)
+// Enqueues a snapshot of the grid's state into dst on the grid's stream.
+static int save_body(pic_grid *g, void *dst, int on_device)
 {
-    if (!g || !dst) return fail(PIC_ERR_INVALID_ARG, "null argument");
     StateHeader h;
     fill_header(g, h);
     const cudaMemcpyKind k = kind_out(on_device);
     const size_t es = elem(g);
     char *o = (char *)dst;
-    CK(cudaMemcpyAsync(o, &h, sizeof(h), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, g->stream),
-       "state header");
+    if (on_device) {
+        static_assert(sizeof(StateHeader) <= sizeof(HeaderBytes), "header size");
+        HeaderBytes hb;
+        memset(&hb, 0, sizeof(hb));
+        memcpy(hb.b, &h, sizeof(h));
+        k_put_bytes<<<1, 64, 0, g->stream>>>(hb, (unsigned char *)o, (int)sizeof(h));
+        CK(cudaGetLastError(), "state header");
+        launch_count_add(g, 1);
+    } else {
+        memcpy(o, &h, sizeof(h));
+    }
     o += sizeof(h);
     auto put = [&](const void *src, size_t bytes) -> cudaError_t {
         cudaError_t e = bytes ? cudaMemcpyAsync(o, src, bytes, k, g->stream) : cudaSuccess;
@@ -1285,20 +1308,22 @@ int pic_state_save(pic_grid *g, void *dst, int on_device)
     for (int a = 0; a < 3; ++a) CK(put(g->B[a], es * g->total_cells), "state B");
     CK(put(g->tile_start, sizeof(long long) * (g->total_tiles + 1)), "state tile starts");
     CK(put(g->d_ant_n, sizeof(long long) * g->runs.size()), "state antenna clocks");
-    CK(cudaStreamSynchronize(g->stream), "state save");
     return PIC_OK;
 }
 
-int pic_state_restore(pic_grid *g, const void *src, int on_device)
+static int check_header(const pic_grid *g, const StateHeader &h)
 {
-    if (!g || !src) return fail(PIC_ERR_INVALID_ARG, "null argument");
-    StateHeader h;
-    CK(cudaMemcpy(&h, src, sizeof(h), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "state header");
     if (memcmp(h.magic, "PICS", 4) != 0 || h.version != 2 || h.checksum != fnv1a(&h, offsetof(StateHeader, checksum)))
         return fail(PIC_ERR_INVALID_ARG, "not a libpic state snapshot (bad magic, version or header checksum)");
     if (h.dims != g->dims || h.prec != g->prec || h.total != g->total || h.total_cells != g->total_cells ||
         h.ngroups != (int)g->groups.size() || h.total_tiles != g->total_tiles)
         return fail(PIC_ERR_INVALID_ARG, "state snapshot does not match this grid's layout");
+    return PIC_OK;
+}
+
+// Enqueues the restore of a snapshot whose header h has been checked.
+static int restore_body(pic_grid *g, const void *src, int on_device, const StateHeader &h)
+{
     const cudaMemcpyKind k = kind_in(on_device);
     const size_t es = elem(g);
     const char *o = (const char *)src + sizeof(h);
@@ -1328,7 +1353,42 @@ int pic_state_restore(pic_grid *g, const void *src, int on_device)
     g->have_old = false;
     if (!g->capturing) graph_drop(g);
     for (auto &r : g->have_ref) r = 0;
+    return PIC_OK;
+}
+
+int pic_state_save(pic_grid *g, void *dst, int on_device)
+{
+    if (!g || !dst) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    const int rc = save_body(g, dst, on_device);
+    if (rc != PIC_OK) return rc;
+    CK(cudaStreamSynchronize(g->stream), "state save");
+    return PIC_OK;
+}
+
+int pic_state_restore(pic_grid *g, const void *src, int on_device)
+{
+    if (!g || !src) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    StateHeader h;
+    CK(cudaStreamSynchronize(g->stream), "state header");   // a device snapshot may still be in flight
+    CK(cudaMemcpy(&h, src, sizeof(h), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "state header");
+    int rc = check_header(g, h);
+    if (rc == PIC_OK) rc = restore_body(g, src, on_device, h);
+    if (rc != PIC_OK) return rc;
     CK(cudaStreamSynchronize(g->stream), "state restore");
+    return PIC_OK;
+}
+
+int pic_step_saving(pic_grid *g, int nsteps, void *const *states)
+{
+    if (!g || (nsteps > 0 && !states)) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    if (nsteps < 0) return fail(PIC_ERR_INVALID_ARG, "negative step count");
+    for (int s = 0; s < nsteps; ++s)
+        if (!states[s]) return fail(PIC_ERR_INVALID_ARG, "null state buffer %d", s);
+    for (int s = 0; s < nsteps; ++s) {
+        int rc = save_body(g, states[s], 1);
+        if (rc == PIC_OK) rc = pic_step(g, 1);
+        if (rc != PIC_OK) return rc;
+    }
     return PIC_OK;
 }
 
@@ -1349,6 +1409,13 @@ static long long max_run_cells(const pic_grid *g)
     long long m = 0;
     for (auto &r : g->runs) m = std::max(m, (long long)r.dev.n[0] * r.dev.n[1] * r.dev.n[2]);
     return m;
+}
+
+int pic_set_adjoint_tiled(pic_grid *g, int tiled)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    g->adj_tiled = tiled ? 1 : 0;
+    return PIC_OK;
 }
 
 int pic_adjoint_yee_half_B(pic_grid *g, void *const lamB[3], void *lamE[3])
@@ -1382,9 +1449,21 @@ int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], v
     for (int c = 0; c < 3; ++c)
         CK(cudaMemcpyAsync(g->adj_lamB1[c], lamB[c], fb, cudaMemcpyDeviceToDevice, g->stream), "lam B1");
     // particles^T
-    CK(launch_particles_adj(g->dims, g->prec, g->stream, g->d_runs, g->d_groups, g->d_group_base,
-                            (int)g->groups.size(), g->total, g->pool, g->E, g->adj_B1, g->adj_lamJ, lamE, g->adj_lamB1,
-                            lamx, lamw),
+    AdjLaunch lc;
+    lc.runs = g->d_runs;
+    lc.groups = g->d_groups;
+    lc.group_base = g->d_group_base;
+    lc.ngroups = (int)g->groups.size();
+    lc.total = g->total;
+    lc.items = g->adj_tiled ? g->items : nullptr;
+    lc.n_items = g->n_items;
+    lc.max_items = g->max_items;
+    lc.halo = g->halo;
+    for (int a = 0; a < 3; ++a) lc.tile[a] = g->tile[a];
+    lc.pitch[0] = g->pitch[0];
+    lc.pitch[1] = g->pitch[1];
+    CK(launch_particles_adj(g->dims, g->prec, g->stream, lc, g->pool, g->E, g->adj_B1, g->adj_lamJ, lamE,
+                            g->adj_lamB1, lamx, lamw),
        "adjoint particles");
     // (first B half step)^T
     CK(launch_adj_yee(g->dims, g->prec, 1, g->stream, g->d_runs, nr, mc, lamE, g->adj_lamB1, nullptr),
@@ -1392,6 +1471,38 @@ int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], v
     for (int c = 0; c < 3; ++c)
         CK(cudaMemcpyAsync(lamB[c], g->adj_lamB1[c], fb, cudaMemcpyDeviceToDevice, g->stream), "lam B");
     launch_count_add(g, 6);
+    return PIC_OK;
+}
+
+int pic_adjoint_steps(pic_grid *g, void *const *states, int nstates, void *lamE[3], void *lamB[3], void *lamx[3],
+                      void *lamw[3])
+{
+    if (!g || (nstates > 0 && !states)) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    if (nstates < 0) return fail(PIC_ERR_INVALID_ARG, "negative state count");
+    if (nstates == 0) return PIC_OK;
+    for (int s = 0; s < nstates; ++s)
+        if (!states[s]) return fail(PIC_ERR_INVALID_ARG, "null state buffer %d", s);
+    // every header in one pass: the only host synchronization of the call
+    if ((size_t)nstates > g->h_hdr_cap) {
+        if (g->h_hdr) cudaFreeHost(g->h_hdr);
+        g->h_hdr = nullptr;
+        g->h_hdr_cap = 0;
+        CK(cudaHostAlloc(&g->h_hdr, sizeof(StateHeader) * (size_t)nstates, cudaHostAllocDefault), "state headers");
+        g->h_hdr_cap = (size_t)nstates;
+    }
+    StateHeader *hh = (StateHeader *)g->h_hdr;
+    for (int s = 0; s < nstates; ++s)
+        CK(cudaMemcpyAsync(&hh[s], states[s], sizeof(StateHeader), cudaMemcpyDeviceToHost, g->stream), "state header");
+    CK(cudaStreamSynchronize(g->stream), "state headers");
+    for (int s = 0; s < nstates; ++s) {
+        const int rc = check_header(g, hh[s]);
+        if (rc != PIC_OK) return rc;
+    }
+    for (int s = nstates - 1; s >= 0; --s) {
+        int rc = restore_body(g, states[s], 1, hh[s]);
+        if (rc == PIC_OK) rc = pic_adjoint_step(g, lamE, lamB, lamx, lamw);
+        if (rc != PIC_OK) return rc;
+    }
     return PIC_OK;
 }
 

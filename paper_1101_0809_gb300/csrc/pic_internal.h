@@ -120,10 +120,27 @@ void set_last_error(const char *msg);
 // step (lamE += (-(1/2) C_B)^T lamB).
 cudaError_t launch_adj_yee(int dims, int prec, int which, cudaStream_t st, const RunDev *runs, int nruns,
                            long long max_cells, void *const lamE[3], void *const lamB[3], void *const lamJ[3]);
-cudaError_t launch_particles_adj(int dims, int prec, cudaStream_t st, const RunDev *runs, const GroupDev *groups,
-                                 const long long *gbase, int ngroups, long long total, const PoolBuf &P,
+// Particle part of the adjoint.  With work items (items != nullptr) the tiled
+// kernel runs over them (shared-memory tiles in the particle kernels' pitches);
+// without, the untiled kernel runs over the pool in group order.
+struct AdjLaunch {
+    const RunDev *runs;
+    const GroupDev *groups;
+    const long long *group_base;
+    int ngroups;
+    long long total;
+    const WorkItem *items;
+    const int *n_items;
+    int max_items;
+    int halo;
+    int tile[3];
+    int pitch[2];
+};
+cudaError_t launch_particles_adj(int dims, int prec, cudaStream_t st, const AdjLaunch &lc, const PoolBuf &P,
                                  void *const E[3], void *const B1[3], void *const lamJ[3], void *const lamE[3],
                                  void *const lamB1[3], void *const lamx[3], void *const lamw[3]);
+size_t adjoint_smem_bytes(int dims, int prec, const int tile[3], int halo, const int pitch[2]);
+cudaError_t adjoint_set_smem_limit(int dims, int prec, size_t bytes);
 
 }  // namespace pic
 
@@ -165,6 +182,9 @@ struct pic_grid {
     pic::WorkItem *items = nullptr;
     long long *d_ant_n = nullptr;   // antenna clock per run (device)
     unsigned *h_drift = nullptr;    // pinned host copy of the drift count (d_err[1])
+    void *h_hdr = nullptr;          // pinned host copies of snapshot headers (pic_adjoint_steps)
+    size_t h_hdr_cap = 0;
+    int adj_tiled = 1;              // adjoint particle kernel over work items with shared-memory tiles
     int adaptive_sort = 0;          // sort when the particle kernel's accumulated slowdown exceeds a sort
     bool sort_due = false;
     cudaEvent_t ad_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // particle kernel, sort

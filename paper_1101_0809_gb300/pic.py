@@ -238,6 +238,7 @@ _lib.pic_step_persistent.argtypes = [_VP, C.c_int]
 _lib.pic_step_graph.argtypes = [_VP, C.c_int]
 _lib.pic_set_antenna.argtypes = [_VP, C.c_int, C.POINTER(pic_antenna_desc)]
 _lib.pic_set_sort_policy.argtypes = [_VP, C.c_int]
+_lib.pic_set_adjoint_tiled.argtypes = [_VP, C.c_int]
 
 
 def pic_create_batch(descs):
@@ -364,6 +365,18 @@ _lib.pic_state_save.argtypes = [_VP, _VP, C.c_int]
 _lib.pic_state_restore.argtypes = [_VP, _VP, C.c_int]
 _lib.pic_adjoint_step.argtypes = [_VP, _VP3, _VP3, _VP3, _VP3]
 _lib.pic_adjoint_yee_half_B.argtypes = [_VP, _VP3, _VP3]
+_lib.pic_step_saving.argtypes = [_VP, C.c_int, C.POINTER(_VP)]
+_lib.pic_adjoint_steps.argtypes = [_VP, C.POINTER(_VP), C.c_int, _VP3, _VP3, _VP3, _VP3]
+
+
+def _device_list(bufs):
+    ptrs = []
+    for b in bufs:
+        p, d = _addr(b)
+        if d != 1:
+            raise ValueError("state buffers must be CUDA tensors")
+        ptrs.append(p)
+    return (_VP * max(1, len(ptrs)))(*ptrs)
 
 
 def pic_state_bytes(g):
@@ -384,6 +397,23 @@ def pic_state_restore(g, src):
 def pic_adjoint_step(g, lamE, lamB, lamx, lamw):
     """All arguments are sequences of 3 CUDA tensors of the grid's precision."""
     _check(_lib.pic_adjoint_step(g, _triple(lamE)[0], _triple(lamB)[0], _triple(lamx)[0], _triple(lamw)[0]))
+
+
+def pic_step_saving(g, states):
+    """len(states) steps, with a device snapshot of the state before each step
+    written to the matching CUDA uint8 tensor (pic_state_bytes(g) bytes each)."""
+    _check(_lib.pic_step_saving(g, len(states), _device_list(states)))
+
+
+def pic_adjoint_steps(g, states, lamE, lamB, lamx, lamw):
+    """Adjoint steps back through the device snapshots `states` (consecutive
+    levels, the last one first); the adjoint arrays as for pic_adjoint_step."""
+    _check(_lib.pic_adjoint_steps(g, _device_list(states), len(states), _triple(lamE)[0], _triple(lamB)[0],
+                                  _triple(lamx)[0], _triple(lamw)[0]))
+
+
+def pic_set_adjoint_tiled(g, tiled):
+    _check(_lib.pic_set_adjoint_tiled(g, 1 if tiled else 0))
 
 
 def pic_adjoint_yee_half_B(g, lamB, lamE):

@@ -114,4 +114,8 @@ def test_null_arguments_return_errors(P):
     assert lib.pic_destroy(None) == P.PIC_OK
     assert lib.pic_num_particles(None, 0) == 0
     assert lib.pic_set_sort_policy(None, 1) == P.PIC_ERR_INVALID_ARG
+    assert lib.pic_set_adjoint_tiled(None, 1) == P.PIC_ERR_INVALID_ARG
+    assert lib.pic_step_saving(None, 1, None) == P.PIC_ERR_INVALID_ARG
+    z = P._VP3()
+    assert lib.pic_adjoint_steps(None, None, 1, z, z, z, z) == P.PIC_ERR_INVALID_ARG
     assert lib.pic_set_antenna(None, 0, None) == P.PIC_ERR_INVALID_ARG

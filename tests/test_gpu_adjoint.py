@@ -12,7 +12,7 @@ import pytest
 
 import oracle as O
 from paper_1101_0809_gb300 import workloads as W
-from pichelpers import close, fp64_field_tol, oracle_grid
+from pichelpers import close, fp64_field_tol, oracle_grid, positions_from_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -36,8 +36,9 @@ def _state_after(wl, steps):
     return g, sp, E, B
 
 
+@pytest.mark.parametrize("tiled", [True, False])
 @pytest.mark.parametrize("which", ["2d", "3d"])
-def test_adjoint_step_matches_oracle(env, which):
+def test_adjoint_step_matches_oracle(env, which, tiled):
     P, torch = env
     if which == "2d":
         wl = W.c4_perturbed2d(n=32, ppc=8, steps=3)
@@ -47,6 +48,7 @@ def test_adjoint_step_matches_oracle(env, which):
     g, sp, E, B = _state_after(wl, 3)
     desc = P.make_desc(wl.dims, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP64, tile=wl.tile, rho_bg=wl.rho_bg)
     grid = P.Grid(desc)
+    P.pic_set_adjoint_tiled(grid.h, tiled)
     grid.set_fields(E, B)
     for s, o in enumerate(sp):
         grid.load(s, o.q, o.m, o.weight, o.x, o.w)
@@ -74,6 +76,71 @@ def test_adjoint_step_matches_oracle(env, which):
         close(gw[a].cpu().numpy(), np.concatenate([v[a] for v in lw]), tol, f"lamw[{a}]")
         if a < wl.dims:
             close(gx[a].cpu().numpy(), np.concatenate([v[a] for v in lx]), tol, f"lamx[{a}]")
+    grid.close()
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_tiled_adjoint_with_particles_past_their_tiles(env, which):
+    """Halo 0 and no sort for 4 steps: every particle that left its tile since
+    the load takes the global-memory form inside the tiled kernel.  Both forms
+    against the oracle's adjoint on the state the GPU reached."""
+    P, torch = env
+    if which == "2d":
+        wl = W.c4_perturbed2d(n=32, ppc=8, steps=4)
+        tile = (8, 8, 1)
+    else:
+        wl = W.thermal_plasma("3D small", 3, (20, 18, 22), 2, 0.1, 4, W.SEED_BASE + 11, ions=1836.0,
+                              tile=(8, 8, 8), dt_courant=0.45)
+        tile = (8, 8, 8)
+    desc = P.make_desc(wl.dims, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP64, tile=tile, halo=0, sort_interval=1000,
+                       rho_bg=wl.rho_bg)
+    grid = P.Grid(desc)
+    for s, o in enumerate(wl.species):
+        grid.load(s, o.q, o.m, o.weight, o.x, o.w)
+    P.pic_step(grid.h, 4)
+    P.pic_sync(grid.h)
+    g = oracle_grid(wl)
+    E, B, _ = grid.get_fields()
+    sp = []
+    left = 0
+    for s, o in enumerate(wl.species):
+        cell, off, w, ident = grid.particles(s)
+        order = np.argsort(ident)
+        x = positions_from_gpu(wl, cell[order], [a[order] for a in off])
+        sp.append(O.Species(o.q, o.m, o.weight, x, np.array([a[order] for a in w])))
+        t = [np.floor(x[a] / tile[a]) != np.floor(o.x[a] / tile[a]) for a in range(wl.dims)]
+        left += int(np.any(t, axis=0).sum())
+    assert left > 20            # particles outside their tiles since the load
+    rng = np.random.default_rng(78)
+    lamE = [rng.normal(size=g.shape) for _ in range(3)]
+    lamB = [rng.normal(size=g.shape) for _ in range(3)]
+    lx = [rng.normal(size=(3, o.x.shape[1])) for o in sp]
+    lw = [rng.normal(size=(3, o.x.shape[1])) for o in sp]
+    if wl.dims == 2:
+        for a in lx:
+            a[2] = 0.0
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    got = {}
+    for tiled in (True, False):
+        gE = [dev(a) for a in lamE]
+        gB = [dev(a) for a in lamB]
+        gx = [dev(np.concatenate([a[c] for a in lx])) for c in range(3)]
+        gw = [dev(np.concatenate([a[c] for a in lw])) for c in range(3)]
+        torch.cuda.synchronize()
+        P.pic_set_adjoint_tiled(grid.h, tiled)
+        P.pic_adjoint_step(grid.h, gE, gB, gx, gw)
+        torch.cuda.synchronize()
+        got[tiled] = [[t.cpu().numpy() for t in v] for v in (gE, gB, gx, gw)]
+    O.step_adj(g, E, B, sp, lamE, lamB, lx, lw)
+    want = (lamE, lamB, [np.concatenate([v[a] for v in lx]) for a in range(3)],
+            [np.concatenate([v[a] for v in lw]) for a in range(3)])
+    tol = 1e-11
+    for tiled in (True, False):
+        for name, gv, wv in zip(("lamE", "lamB", "lamx", "lamw"), got[tiled], want):
+            for a in range(3):
+                if name == "lamx" and a >= wl.dims:
+                    continue
+                close(gv[a], wv[a], tol, f"{name}[{a}] tiled={tiled}")
     grid.close()
 
 
@@ -186,3 +253,69 @@ def test_state_snapshot_restarts_the_same_run(env):
         P.pic_state_restore(grid.h, bad)
     assert e.value.code == P.PIC_ERR_INVALID_ARG
     grid.close()
+
+
+def test_batched_segment_calls_match_step_by_step(env):
+    """pic_step_saving + pic_adjoint_steps (one host synchronization per
+    segment) against pic_state_save / pic_step / pic_state_restore /
+    pic_adjoint_step one step at a time, on the same FP64 run with a sort inside
+    the segment; and a corrupt snapshot anywhere in the list is refused before
+    anything is restored."""
+    P, torch = env
+    wl = W.c4_perturbed2d(n=32, ppc=8, steps=7)
+    desc = P.make_desc(2, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP64, tile=(8, 8, 1), sort_interval=3, rho_bg=wl.rho_bg)
+    nbytes = None
+    out = []
+    for batched in (True, False):
+        grid = P.Grid(desc)
+        sp = wl.species[0]
+        grid.load(0, sp.q, sp.m, sp.weight, sp.x, sp.w)
+        P.pic_step(grid.h, 2)
+        nbytes = P.pic_state_bytes(grid.h)
+        states = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(wl.steps)]
+        torch.cuda.synchronize()
+        if batched:
+            P.pic_step_saving(grid.h, states)
+        else:
+            for st in states:
+                P.pic_state_save(grid.h, st)
+                P.pic_step(grid.h, 1)
+        P.pic_sync(grid.h)
+        E1, B1, _ = grid.get_fields()
+        rng = np.random.default_rng(79)
+        n = sp.x.shape[1]
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        lam = ([dev(rng.normal(size=grid.shape)) for _ in range(3)], [dev(rng.normal(size=grid.shape)) for _ in range(3)],
+               [dev(rng.normal(size=n)) for _ in range(3)], [dev(rng.normal(size=n)) for _ in range(3)])
+        torch.cuda.synchronize()
+        if batched:
+            P.pic_adjoint_steps(grid.h, states, *lam)
+        else:
+            for st in reversed(states):
+                P.pic_state_restore(grid.h, st)
+                P.pic_adjoint_step(grid.h, *lam)
+        P.pic_sync(grid.h)
+        torch.cuda.synchronize()
+        out.append((E1, B1, [[t.cpu().numpy() for t in v] for v in lam], grid.particles(0)))
+        if batched:
+            # a corrupt header in the middle of the list: refused, nothing restored
+            bad = [s.clone() for s in states]
+            bad[3][0] = ord("X")
+            before = grid.particles(0)
+            with pytest.raises(P.PicError) as e:
+                P.pic_adjoint_steps(grid.h, bad, *lam)
+            assert e.value.code == P.PIC_ERR_INVALID_ARG
+            after = grid.particles(0)
+            for a, b in zip(before, after):
+                np.testing.assert_array_equal(np.asarray(a), np.asarray(b))
+        grid.close()
+    (Ea, Ba, la, pa), (Eb, Bb, lb, pb) = out
+    for a in range(3):
+        close(Ea[a], Eb[a], 1e-13, f"E[{a}] after the segment")
+        close(Ba[a], Bb[a], 1e-13, f"B[{a}] after the segment")
+    for name, va, vb in zip(("lamE", "lamB", "lamx", "lamw"), la, lb):
+        for a in range(3):
+            if name == "lamx" and a == 2:
+                continue
+            close(va[a], vb[a], 1e-11, f"{name}[{a}]")
+    np.testing.assert_array_equal(pa[0], pb[0])     # the grid holds the first snapshot's state
