@@ -292,12 +292,13 @@ int pic_profile(pic_grid *g, int enable);
 int pic_profile_read(pic_grid *g, double ms[PIC_PROF_N], long long count[PIC_PROF_N]);
 
 /* ---- State snapshots ------------------------------------------------------------
- * A snapshot is one contiguous blob: a 56-byte header ("PICS", version 2,
- * dims, precision, group count, sort phase, particle, cell and tile counts, and
- * a checksum of the header) followed by the particle arrays (cell, id, offsets,
- * momenta, in storage order), the fields E^n, B^{n-1/2}, the tile starts of
- * the particle order (from the last tile sort) and the antenna clock of every
- * run (pic_set_antenna).  pic_state_bytes gives its
+ * A snapshot is one contiguous blob: a 64-byte header ("PICS", version 3,
+ * dims, precision, group count, sort phase, particle, cell, tile and run
+ * counts, and a checksum of the header) followed by the particle arrays (cell,
+ * id, offsets, momenta, in storage order), the fields E^n, B^{n-1/2}, the tile
+ * starts of the particle order (from the last tile sort) and the antenna clock
+ * of every run (pic_set_antenna), each array starting at the next multiple of
+ * 16 bytes.  A device snapshot is copied by one kernel.  pic_state_bytes gives its
  * size.  pic_state_save writes it to dst (device memory if on_device, else host
  * memory); pic_state_restore reads one taken from a grid with the same layout
  * (same runs, species, particle counts and tiles), rebuilds the work items from
@@ -333,8 +334,8 @@ int pic_step_saving(pic_grid *g, int nsteps, void *const *states);
  * scattered into lamE and lamB by atomics.  The particle part runs over the
  * last tile sort's work items with each item's E, B and lamJ staged in shared
  * memory (particles that drifted past their tile's halo read the global
- * arrays); pic_set_adjoint_tiled(g, 0) selects the untiled form instead (one
- * thread per particle, all reads global; the same arithmetic).
+ * arrays), or untiled (one thread per particle, all reads global; the same
+ * arithmetic); see pic_set_adjoint_tiled.
  * pic_adjoint_yee_half_B adds (-(1/2) C_B)^T lamB to lamE (the transpose of one
  * B half step), e.g. to seed a loss that uses B^n = B^{n-1/2} - (1/2) c curl E^n. */
 int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], void *lamw[3]);
@@ -350,7 +351,10 @@ int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], v
 int pic_adjoint_steps(pic_grid *g, void *const *states, int nstates, void *lamE[3], void *lamB[3], void *lamx[3],
                       void *lamw[3]);
 
-/* tiled != 0 (the default): the tiled particle adjoint; 0: the untiled one.
+/* tiled != 0: the tiled particle adjoint (the default in FP32); 0: the
+ * untiled one (the default in FP64, where the FP64 pipe bounds the kernel and
+ * the per-block staging of the tiles costs more than it saves, and the form
+ * used whenever the tiled one's shared tiles would not fit the device).
  * Errors: PIC_ERR_INVALID_ARG for a null grid. */
 int pic_set_adjoint_tiled(pic_grid *g, int tiled);
 int pic_adjoint_yee_half_B(pic_grid *g, void *const lamB[3], void *lamE[3]);

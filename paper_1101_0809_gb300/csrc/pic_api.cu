@@ -41,15 +41,97 @@ int cuda_fail(cudaError_t e, const char *what)
 
 constexpr int kDiagBlocks = 1024;
 
-// A snapshot header written into device memory by a kernel, so that a device
-// snapshot is taken in stream order without a host copy or synchronization.
-struct HeaderBytes {
-    unsigned char b[64];
+// Device-to-device copy of up to kCopySegs segments in one launch (blockIdx.y
+// = segment), plus optionally a small block of bytes passed by value (a
+// snapshot header, written in stream order without a host copy).  Segments
+// whose source and destination agree modulo 16 bytes move as 16-byte words
+// between byte-wise heads and tails; others move byte-wise.
+constexpr int kCopySegs = 16;
+struct CopyList {
+    const unsigned char *src[kCopySegs];
+    unsigned char *dst[kCopySegs];
+    long long bytes[kCopySegs];
+    int n;
+    int inl_bytes;                 // 0..64 bytes of `inl` to write to inl_dst
+    unsigned char *inl_dst;
+    unsigned char inl[64];
 };
-__global__ void k_put_bytes(const HeaderBytes h, unsigned char *dst, int n)
+
+__global__ void k_copy_segments(const CopyList L)
 {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = h.b[i];
+    const int sg = blockIdx.y;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (sg == L.n) {
+        if (t0 < L.inl_bytes) L.inl_dst[t0] = L.inl[t0];
+        return;
+    }
+    const unsigned char *src = L.src[sg];
+    unsigned char *dst = L.dst[sg];
+    const long long nb = L.bytes[sg];
+    const unsigned long long sa = (unsigned long long)src, da = (unsigned long long)dst;
+    if (((sa ^ da) & 15ull) == 0) {
+        long long head = (long long)((16ull - (sa & 15ull)) & 15ull);
+        if (head > nb) head = nb;
+        const long long n16 = (nb - head) >> 4;
+        if (t0 < head) dst[t0] = src[t0];
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + head);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + head);
+        for (long long i = t0; i < n16; i += stride) d4[i] = s4[i];
+        for (long long i = head + (n16 << 4) + t0; i < nb; i += stride) dst[i] = src[i];
+    } else {
+        for (long long i = t0; i < nb; i += stride) dst[i] = src[i];
+    }
 }
+
+// Collects copies and issues them: device-to-device ones as k_copy_segments
+// launches, the others (host memory on one side) as cudaMemcpyAsync.
+struct Copier {
+    cudaStream_t st;
+    cudaMemcpyKind kind;
+    CopyList L;
+    long long maxb = 0;
+    int launches = 0;
+    Copier(cudaStream_t s, cudaMemcpyKind k) : st(s), kind(k)
+    {
+        memset(&L, 0, sizeof(L));
+    }
+    cudaError_t flush()
+    {
+        if (L.n == 0 && L.inl_bytes == 0) return cudaSuccess;
+        const long long per = 256LL * 16 * 4;   // bytes per thread block and pass
+        long long bx = (maxb + per - 1) / per;
+        if (bx < 1) bx = 1;
+        if (bx > 2048) bx = 2048;
+        k_copy_segments<<<dim3((unsigned)bx, (unsigned)(L.n + (L.inl_bytes ? 1 : 0))), 256, 0, st>>>(L);
+        ++launches;
+        const cudaError_t e = cudaGetLastError();
+        memset(&L, 0, sizeof(L));
+        maxb = 0;
+        return e;
+    }
+    cudaError_t add(void *dst, const void *src, size_t bytes)
+    {
+        if (bytes == 0) return cudaSuccess;
+        if (kind != cudaMemcpyDeviceToDevice) return cudaMemcpyAsync(dst, src, bytes, kind, st);
+        if (L.n == kCopySegs) {
+            const cudaError_t e = flush();
+            if (e != cudaSuccess) return e;
+        }
+        L.src[L.n] = (const unsigned char *)src;
+        L.dst[L.n] = (unsigned char *)dst;
+        L.bytes[L.n] = (long long)bytes;
+        ++L.n;
+        if ((long long)bytes > maxb) maxb = (long long)bytes;
+        return cudaSuccess;
+    }
+    void inline_bytes(void *dst, const void *src, int bytes)
+    {
+        L.inl_bytes = bytes;
+        L.inl_dst = (unsigned char *)dst;
+        memcpy(L.inl, src, (size_t)bytes);
+    }
+};
 
 size_t elem(const pic_grid *g) { return g->prec == PIC_FP64 ? sizeof(double) : sizeof(float); }
 
@@ -380,6 +462,9 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
     if (first) {
         g->dims = d->dims;
         g->prec = d->precision;
+        // the FP64 particle adjoint is bound by the FP64 pipe; per-block tile
+        // staging costs it more than the global reads it saves
+        g->adj_tiled = g->prec == PIC_FP32 ? 1 : 0;
         g->halo = d->halo < 0 ? 1 : d->halo;
         if (g->halo > 2) return fail(PIC_ERR_INVALID_ARG, "halo must be 0..2");
         g->sort_interval = d->sort_interval > 0 ? d->sort_interval : 10;
@@ -463,7 +548,6 @@ void destroy_grid(pic_grid *g)
     for (int c = 0; c < 3; ++c) {
         dfree(g->adj_B1[c]);
         dfree(g->adj_lamJ[c]);
-        dfree(g->adj_lamB1[c]);
     }
     graph_drop(g);
     prof_clear(g);
@@ -558,9 +642,13 @@ int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out)
         }
         if ((e = particles_set_smem_limit(g->dims, g->prec, mode, b)) != cudaSuccess) return bail(e, "smem limit");
     }
-    if ((e = adjoint_set_smem_limit(g->dims, g->prec, adjoint_smem_bytes(g->dims, g->prec, g->tile, g->halo,
-                                                                          g->pitch))) != cudaSuccess)
-        return bail(e, "smem limit");
+    {
+        // the tiled particle adjoint where its tiles fit in shared memory
+        const size_t ab = adjoint_smem_bytes(g->dims, g->prec, g->tile, g->halo, g->pitch);
+        g->adj_fits = (long long)ab <= optin ? 1 : 0;
+        if (g->adj_fits && (e = adjoint_set_smem_limit(g->dims, g->prec, ab)) != cudaSuccess)
+            return bail(e, "smem limit");
+    }
     if (g->prec == PIC_FP32 && (e = diag_set_smem_limit(g->dims, diag_items_smem_bytes(g->dims, g->tile, g->halo,
                                                                                       g->pitch))) != cudaSuccess)
         return bail(e, "smem limit");
@@ -1233,13 +1321,18 @@ int pic_diagnostics(pic_grid *g, pic_diag *out) { return pic_diagnostics_run(g, 
 // ---- state snapshots -----------------------------------------------------------
 struct StateHeader {
     char magic[4];            // "PICS"
-    int version;              // 2
+    int version;              // 3
     int dims, prec, ngroups, steps_since_sort;
     long long total, total_cells;
     long long total_tiles;    // tile starts of the particle order follow the fields
+    long long nruns;          // one antenna clock per run at the end
     unsigned checksum;        // FNV-1a of the bytes before this field
     int pad;
 };
+static_assert(sizeof(StateHeader) == 64, "snapshot header");
+
+// Snapshot layout: the header, then each array at the next multiple of 16 bytes.
+static long long seg16(long long b) { return (b + 15) & ~15LL; }
 
 static unsigned fnv1a(const void *p, size_t n)
 {
@@ -1256,7 +1349,7 @@ static void fill_header(const pic_grid *g, StateHeader &h)
 {
     memset(&h, 0, sizeof(h));
     memcpy(h.magic, "PICS", 4);
-    h.version = 2;
+    h.version = 3;
     h.dims = g->dims;
     h.prec = g->prec;
     h.ngroups = (int)g->groups.size();
@@ -1264,6 +1357,7 @@ static void fill_header(const pic_grid *g, StateHeader &h)
     h.total = g->total;
     h.total_cells = g->total_cells;
     h.total_tiles = g->total_tiles;
+    h.nruns = (long long)g->runs.size();
     h.checksum = fnv1a(&h, offsetof(StateHeader, checksum));
 }
 
@@ -1271,52 +1365,56 @@ long long pic_state_bytes(pic_grid *g)
 {
     if (!g) return 0;
     const long long es = (long long)elem(g);
-    return (long long)sizeof(StateHeader) + g->total * (8 + es * (g->dims + 3)) + g->total_cells * es * 6 +
-           (long long)sizeof(long long) * (g->total_tiles + 1 + (long long)g->runs.size());
+    return (long long)sizeof(StateHeader) + 2 * seg16(4 * g->total) + (g->dims + 3) * seg16(es * g->total) +
+           6 * seg16(es * g->total_cells) + seg16(8 * (g->total_tiles + 1)) + seg16(8 * (long long)g->runs.size());
 }
 
-// Enqueues a snapshot of the grid's state into dst on the grid's stream.
+// The (device array, bytes) list of a snapshot, in its order after the header.
+static int state_segments(pic_grid *g, void *arr[kCopySegs], size_t bytes[kCopySegs])
+{
+    const size_t es = elem(g);
+    int n = 0;
+    auto seg = [&](void *p, size_t b) { arr[n] = p; bytes[n] = b; ++n; };
+    seg(g->pool.cell, sizeof(int) * g->total);
+    seg(g->pool.id, sizeof(int) * g->total);
+    for (int a = 0; a < g->dims; ++a) seg(g->pool.off[a], es * g->total);
+    for (int a = 0; a < 3; ++a) seg(g->pool.w[a], es * g->total);
+    for (int a = 0; a < 3; ++a) seg(g->E[a], es * g->total_cells);
+    for (int a = 0; a < 3; ++a) seg(g->B[a], es * g->total_cells);
+    seg(g->tile_start, sizeof(long long) * (g->total_tiles + 1));
+    seg(g->d_ant_n, sizeof(long long) * g->runs.size());
+    return n;
+}
+
+// Enqueues a snapshot of the grid's state into dst on the grid's stream: one
+// copy kernel for a device snapshot, one copy per array for a host one.
 static int save_body(pic_grid *g, void *dst, int on_device)
 {
     StateHeader h;
     fill_header(g, h);
-    const cudaMemcpyKind k = kind_out(on_device);
-    const size_t es = elem(g);
     char *o = (char *)dst;
-    if (on_device) {
-        static_assert(sizeof(StateHeader) <= sizeof(HeaderBytes), "header size");
-        HeaderBytes hb;
-        memset(&hb, 0, sizeof(hb));
-        memcpy(hb.b, &h, sizeof(h));
-        k_put_bytes<<<1, 64, 0, g->stream>>>(hb, (unsigned char *)o, (int)sizeof(h));
-        CK(cudaGetLastError(), "state header");
-        launch_count_add(g, 1);
-    } else {
-        memcpy(o, &h, sizeof(h));
-    }
+    Copier cp(g->stream, kind_out(on_device));
+    if (on_device) cp.inline_bytes(o, &h, (int)sizeof(h));
+    else memcpy(o, &h, sizeof(h));
     o += sizeof(h);
-    auto put = [&](const void *src, size_t bytes) -> cudaError_t {
-        cudaError_t e = bytes ? cudaMemcpyAsync(o, src, bytes, k, g->stream) : cudaSuccess;
-        o += bytes;
-        return e;
-    };
-    CK(put(g->pool.cell, sizeof(int) * g->total), "state cells");
-    CK(put(g->pool.id, sizeof(int) * g->total), "state ids");
-    for (int a = 0; a < g->dims; ++a) CK(put(g->pool.off[a], es * g->total), "state offsets");
-    for (int a = 0; a < 3; ++a) CK(put(g->pool.w[a], es * g->total), "state momenta");
-    for (int a = 0; a < 3; ++a) CK(put(g->E[a], es * g->total_cells), "state E");
-    for (int a = 0; a < 3; ++a) CK(put(g->B[a], es * g->total_cells), "state B");
-    CK(put(g->tile_start, sizeof(long long) * (g->total_tiles + 1)), "state tile starts");
-    CK(put(g->d_ant_n, sizeof(long long) * g->runs.size()), "state antenna clocks");
+    void *arr[kCopySegs];
+    size_t bytes[kCopySegs];
+    const int n = state_segments(g, arr, bytes);
+    for (int q = 0; q < n; ++q) {
+        CK(cp.add(o, arr[q], bytes[q]), "state save");
+        o += seg16((long long)bytes[q]);
+    }
+    CK(cp.flush(), "state save");
+    launch_count_add(g, cp.launches);
     return PIC_OK;
 }
 
 static int check_header(const pic_grid *g, const StateHeader &h)
 {
-    if (memcmp(h.magic, "PICS", 4) != 0 || h.version != 2 || h.checksum != fnv1a(&h, offsetof(StateHeader, checksum)))
+    if (memcmp(h.magic, "PICS", 4) != 0 || h.version != 3 || h.checksum != fnv1a(&h, offsetof(StateHeader, checksum)))
         return fail(PIC_ERR_INVALID_ARG, "not a libpic state snapshot (bad magic, version or header checksum)");
     if (h.dims != g->dims || h.prec != g->prec || h.total != g->total || h.total_cells != g->total_cells ||
-        h.ngroups != (int)g->groups.size() || h.total_tiles != g->total_tiles)
+        h.ngroups != (int)g->groups.size() || h.total_tiles != g->total_tiles || h.nruns != (long long)g->runs.size())
         return fail(PIC_ERR_INVALID_ARG, "state snapshot does not match this grid's layout");
     return PIC_OK;
 }
@@ -1324,24 +1422,19 @@ static int check_header(const pic_grid *g, const StateHeader &h)
 // Enqueues the restore of a snapshot whose header h has been checked.
 static int restore_body(pic_grid *g, const void *src, int on_device, const StateHeader &h)
 {
-    const cudaMemcpyKind k = kind_in(on_device);
-    const size_t es = elem(g);
     const char *o = (const char *)src + sizeof(h);
-    auto get = [&](void *dstp, size_t bytes) -> cudaError_t {
-        cudaError_t e = bytes ? cudaMemcpyAsync(dstp, o, bytes, k, g->stream) : cudaSuccess;
-        o += bytes;
-        return e;
-    };
-    CK(get(g->pool.cell, sizeof(int) * g->total), "state cells");
-    CK(get(g->pool.id, sizeof(int) * g->total), "state ids");
-    for (int a = 0; a < g->dims; ++a) CK(get(g->pool.off[a], es * g->total), "state offsets");
-    for (int a = 0; a < 3; ++a) CK(get(g->pool.w[a], es * g->total), "state momenta");
-    for (int a = 0; a < 3; ++a) CK(get(g->E[a], es * g->total_cells), "state E");
-    for (int a = 0; a < 3; ++a) CK(get(g->B[a], es * g->total_cells), "state B");
+    Copier cp(g->stream, kind_in(on_device));
+    void *arr[kCopySegs];
+    size_t bytes[kCopySegs];
+    const int n = state_segments(g, arr, bytes);
+    for (int q = 0; q < n; ++q) {
+        CK(cp.add(arr[q], o, bytes[q]), "state restore");
+        o += seg16((long long)bytes[q]);
+    }
+    CK(cp.flush(), "state restore");
+    launch_count_add(g, cp.launches);
     // the particles are in the order of the sort before the save: its tile
     // starts give the work items back, and the sort schedule continues
-    CK(get(g->tile_start, sizeof(long long) * (g->total_tiles + 1)), "state tile starts");
-    CK(get(g->d_ant_n, sizeof(long long) * g->runs.size()), "state antenna clocks");
     if (g->total > 0 && !g->groups.empty()) {
         int nl = 0;
         cudaError_t e = build_items(g->stream, g->tile_start, g->total_tiles, g->ppi, g->d_groups,
@@ -1399,7 +1492,6 @@ static int adj_scratch(pic_grid *g)
     for (int c = 0; c < 3; ++c) {
         CK(dalloc_bytes(&g->adj_B1[c], g->total_cells * elem(g)), "adjoint scratch");
         CK(dalloc_bytes(&g->adj_lamJ[c], g->total_cells * elem(g)), "adjoint scratch");
-        CK(dalloc_bytes(&g->adj_lamB1[c], g->total_cells * elem(g)), "adjoint scratch");
     }
     return PIC_OK;
 }
@@ -1440,36 +1532,35 @@ int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], v
     const long long mc = max_run_cells(g);
     const int nr = (int)g->runs.size();
     // B^n = B^{n-1/2} - (1/2) C_B E^n into scratch (the state is not modified)
-    for (int c = 0; c < 3; ++c) CK(cudaMemcpyAsync(g->adj_B1[c], g->B[c], fb, cudaMemcpyDeviceToDevice, g->stream), "B1");
+    Copier cp(g->stream, cudaMemcpyDeviceToDevice);
+    for (int c = 0; c < 3; ++c) CK(cp.add(g->adj_B1[c], g->B[c], fb), "B1");
+    CK(cp.flush(), "B1");
     CK(launch_yee(g->prec, PIC_B_HALF, 0, g->stream, g->d_runs, nr, mc, g->E, g->adj_B1, g->J, g->dims, g->d_ant_n),
        "B1");
     // (E step)^T, (second B half step)^T
     CK(launch_adj_yee(g->dims, g->prec, 2, g->stream, g->d_runs, nr, mc, lamE, lamB, g->adj_lamJ), "adjoint E step");
     CK(launch_adj_yee(g->dims, g->prec, 1, g->stream, g->d_runs, nr, mc, lamE, lamB, nullptr), "adjoint B half step");
-    for (int c = 0; c < 3; ++c)
-        CK(cudaMemcpyAsync(g->adj_lamB1[c], lamB[c], fb, cudaMemcpyDeviceToDevice, g->stream), "lam B1");
-    // particles^T
+    // particles^T: the transposed gather of B^n adds to lamB, which from here on
+    // is the adjoint of B^n (the first B half step's output)
     AdjLaunch lc;
     lc.runs = g->d_runs;
     lc.groups = g->d_groups;
     lc.group_base = g->d_group_base;
     lc.ngroups = (int)g->groups.size();
     lc.total = g->total;
-    lc.items = g->adj_tiled ? g->items : nullptr;
+    lc.items = g->adj_tiled && g->adj_fits ? g->items : nullptr;
     lc.n_items = g->n_items;
     lc.max_items = g->max_items;
     lc.halo = g->halo;
     for (int a = 0; a < 3; ++a) lc.tile[a] = g->tile[a];
     lc.pitch[0] = g->pitch[0];
     lc.pitch[1] = g->pitch[1];
-    CK(launch_particles_adj(g->dims, g->prec, g->stream, lc, g->pool, g->E, g->adj_B1, g->adj_lamJ, lamE,
-                            g->adj_lamB1, lamx, lamw),
+    CK(launch_particles_adj(g->dims, g->prec, g->stream, lc, g->pool, g->E, g->adj_B1, g->adj_lamJ, lamE, lamB,
+                            lamx, lamw),
        "adjoint particles");
-    // (first B half step)^T
-    CK(launch_adj_yee(g->dims, g->prec, 1, g->stream, g->d_runs, nr, mc, lamE, g->adj_lamB1, nullptr),
+    // (first B half step)^T: lamB becomes the adjoint of B^{n-1/2}, unchanged
+    CK(launch_adj_yee(g->dims, g->prec, 1, g->stream, g->d_runs, nr, mc, lamE, lamB, nullptr),
        "adjoint B half step");
-    for (int c = 0; c < 3; ++c)
-        CK(cudaMemcpyAsync(lamB[c], g->adj_lamB1[c], fb, cudaMemcpyDeviceToDevice, g->stream), "lam B");
     launch_count_add(g, 6);
     return PIC_OK;
 }

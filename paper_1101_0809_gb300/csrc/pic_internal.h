@@ -184,7 +184,8 @@ struct pic_grid {
     unsigned *h_drift = nullptr;    // pinned host copy of the drift count (d_err[1])
     void *h_hdr = nullptr;          // pinned host copies of snapshot headers (pic_adjoint_steps)
     size_t h_hdr_cap = 0;
-    int adj_tiled = 1;              // adjoint particle kernel over work items with shared-memory tiles
+    int adj_fits = 1;               // the tiled adjoint's shared memory fits the device
+    int adj_tiled = 1;              // adjoint particle kernel over work items with shared-memory tiles (FP32 default)
     int adaptive_sort = 0;          // sort when the particle kernel's accumulated slowdown exceeds a sort
     bool sort_due = false;
     cudaEvent_t ad_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // particle kernel, sort
@@ -218,10 +219,9 @@ struct pic_grid {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_marks;
     std::vector<cudaEvent_t> prof_free;
 
-    // adjoint scratch: B^n, lamJ, lam B1 (field-sized, allocated on first use)
+    // adjoint scratch: B^n, lamJ (field-sized, allocated on first use)
     void *adj_B1[3] = {nullptr, nullptr, nullptr};
     void *adj_lamJ[3] = {nullptr, nullptr, nullptr};
-    void *adj_lamB1[3] = {nullptr, nullptr, nullptr};
 
     // staging for host-pointer particle loads (grown, never shrunk)
     double *stage = nullptr;
