@@ -153,6 +153,7 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
     // the particle's adjoints at level n+1, loaded first so that their latency
     // overlaps the recomputation
     R lx1[3], lw1[3];
+    #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         lx1[ax] = ax < DIM ? a.lamx[ax][L] : R(0);
         lw1[ax] = a.lamw[ax][L];
@@ -161,6 +162,7 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
     const R w0[3] = {a.P.w[0][p], a.P.w[1][p], a.P.w[2][p]};
     // ---- recompute the forward quantities ------------------------------------
     R f[3][2], S[3][3], df[3][2], dS[3][3];
+    #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         if (ax == 2 && DIM == 2) {
             f[2][0] = R(1); f[2][1] = R(0); S[2][0] = R(0); S[2][1] = R(1); S[2][2] = R(0);
@@ -184,11 +186,13 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
     const R ig = R(1) / g1;
     R n1[3] = {o[0], o[1], o[2]};
     int sh[3] = {0, 0, 0};
+    #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) sh[ax] = renormalize(o[ax], w1[ax] * ig * cN[ax], n1[ax]);
     const R uz = cl * w1[2] * ig;
     // ---- reverse of the deposit ----------------------------------------------
     AxisWin<R> W[3];
     AxisWinAdj<R> WA[3];
+    #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
         axis_window(o[ax], n1[ax], sh[ax], W[ax]);
         axis_window_adj(o[ax], n1[ax], sh[ax], WA[ax]);
@@ -196,12 +200,16 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
     R lPp[3][4] = {{0}}, lPm[3][4] = {{0}}, lD[3][3] = {{0}};
     R luz = 0;
     if (DIM == 3) {
+        #pragma unroll
         for (int cmp = 0; cmp < 3; ++cmp) {
             const int b = (cmp + 1) % 3, cc = (cmp + 2) % 3;
             const R ka = F32 ? R(gr.kff[cmp]) : R(gr.kf[cmp]);
+            #pragma unroll
             for (int wc = 0; wc < 4; ++wc)
+                #pragma unroll
                 for (int wb = 0; wb < 4; ++wb) {
                     const R T = W[b].Pp[wb] * W[cc].Pp[wc] + W[b].Pm[wb] * W[cc].Pm[wc] * third;
+                    #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         int off[3];
                         off[cmp] = W[cmp].lo + 1 + q;
@@ -220,19 +228,25 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
         const R kx = F32 ? R(gr.kff[0]) : R(gr.kf[0]);
         const R ky = F32 ? R(gr.kff[1]) : R(gr.kf[1]);
         const R kz = F32 ? R(gr.kff[2]) : R(gr.kf[2]);
+        #pragma unroll
         for (int wy = 0; wy < 4; ++wy)
+            #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const R G = rd.lj(0, W[0].lo + 1 + q, W[1].lo + wy, 0) * kx;
                 lD[0][q] += G * W[1].Pp[wy];
                 lPp[1][wy] += G * W[0].D[q];
             }
+        #pragma unroll
         for (int wx = 0; wx < 4; ++wx)
+            #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const R G = rd.lj(1, W[0].lo + wx, W[1].lo + 1 + q, 0) * ky;
                 lD[1][q] += G * W[0].Pp[wx];
                 lPp[0][wx] += G * W[1].D[q];
             }
+        #pragma unroll
         for (int wy = 0; wy < 4; ++wy)
+            #pragma unroll
             for (int wx = 0; wx < 4; ++wx) {
                 const R G = rd.lj(2, W[0].lo + wx, W[1].lo + wy, 0) * kz;
                 luz += G * (W[0].Pp[wx] * W[1].Pp[wy] + W[0].Pm[wx] * W[1].Pm[wy] * third);
@@ -243,12 +257,14 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
             }
     }
     R lx0[3] = {R(0), R(0), R(0)};
+    #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
         // D[q] = sum_{w <= q} Pm[w]
         lPm[ax][0] += lD[ax][0] + lD[ax][1] + lD[ax][2];
         lPm[ax][1] += lD[ax][1] + lD[ax][2];
         lPm[ax][2] += lD[ax][2];
         R ln = 0, lo2 = 0;
+        #pragma unroll
         for (int w4 = 0; w4 < 4; ++w4) {
             ln += (lPp[ax][w4] + lPm[ax][w4]) * WA[ax].dN[w4];
             lo2 += (lPp[ax][w4] - lPm[ax][w4]) * WA[ax].dO[w4];
@@ -258,8 +274,10 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
     }
     // ---- reverse of the move: delta_a = cN_a w1_a / gamma1, u_z = c w1_z / gamma1
     const R ig3 = ig * ig * ig;
+    #pragma unroll
     for (int bb = 0; bb < 3; ++bb) {
         R acc = 0;
+        #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             const R jac = (ax == bb ? ig : R(0)) - w1[ax] * w1[bb] * ig3;
             if (ax < DIM) acc += lx1[ax] * cN[ax] * jac;
@@ -272,12 +290,14 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
     R lEp[3], lBp[3], lw0[3];
     {
         R e[3], t[3], b[3], nn3[3], m[3];
+        #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             e[ax] = hq * Ep[ax];
             t[ax] = w0[ax] + e[ax];
         }
         const R gt = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + c2);
         const R s = hq / gt;
+        #pragma unroll
         for (int ax = 0; ax < 3; ++ax) b[ax] = s * Bp[ax];
         nn3[0] = t[0] + (t[1] * b[2] - t[2] * b[1]);
         nn3[1] = t[1] + (t[2] * b[0] - t[0] * b[2]);
@@ -289,6 +309,7 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
         m[2] = nn3[0] * b[1] - nn3[1] * b[0];
         R lt[3], le[3], lm[3], ln3[3], lb[3];
         R lF = 0;
+        #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             lt[ax] = lw1[ax];
             le[ax] = lw1[ax];
@@ -303,6 +324,7 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
         lb[1] = lm[2] * nn3[0] - lm[0] * nn3[2];
         lb[2] = lm[0] * nn3[1] - lm[1] * nn3[0];
         const R lb2 = lF * (-R(2) / ((R(1) + b2) * (R(1) + b2)));
+        #pragma unroll
         for (int ax = 0; ax < 3; ++ax) lb[ax] += R(2) * b[ax] * lb2;
         // n = t + t x b: lt += ln + b x ln, lb += ln x t
         lt[0] += ln3[0] + (b[1] * ln3[2] - b[2] * ln3[1]);
@@ -312,11 +334,13 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
         lb[1] += ln3[2] * t[0] - ln3[0] * t[2];
         lb[2] += ln3[0] * t[1] - ln3[1] * t[0];
         R ls = 0;
+        #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             ls += lb[ax] * Bp[ax];
             lBp[ax] = s * lb[ax];
         }
         const R lgt = -ls * hq / (gt * gt);
+        #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             lt[ax] += lgt * t[ax] / gt;
             lw0[ax] = lt[ax];
@@ -325,14 +349,19 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
     }
     // ---- reverse of the gather: scatter into lamE, lamB1; derivatives of the
     // weights into lx0
+    #pragma unroll
     for (int fld = 0; fld < 2; ++fld)
+        #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const bool intx = (fld == 0) == (c == 0), inty = (fld == 0) == (c == 1), intz = (fld == 0) == (c == 2);
             const int cx = intx ? 2 : 3, cy = inty ? 2 : 3, cz = DIM == 3 ? (intz ? 2 : 3) : 1;
             const int ox = intx ? 0 : -1, oy = inty ? 0 : -1, oz = DIM == 3 ? (intz ? 0 : -1) : 0;
             const R lam = fld == 0 ? lEp[c] : lBp[c];
+            #pragma unroll
             for (int sz = 0; sz < cz; ++sz)
+                #pragma unroll
                 for (int sy = 0; sy < cy; ++sy)
+                    #pragma unroll
                     for (int sx = 0; sx < cx; ++sx) {
                         const int dx = ox + sx, dy = oy + sy, dz = DIM == 3 ? oz + sz : 0;
                         const R vx = intx ? f[0][sx] : S[0][sx], ddx = intx ? df[0][sx] : dS[0][sx];
@@ -346,6 +375,7 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
                         lx0[2] += vx * vy * ddz * fl;
                     }
         }
+    #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         if (ax < DIM) a.lamx[ax][L] = lx0[ax];
         a.lamw[ax][L] = lw0[ax];
