@@ -21,7 +21,7 @@ _lib = None
 class _Grid(C.Structure):
     _fields_ = [("dims", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
-                ("dt", C.c_double), ("c", C.c_double)]
+                ("dt", C.c_double), ("c", C.c_double), ("order2", C.c_int)]
 
 
 class _Antenna(C.Structure):
@@ -65,11 +65,12 @@ class Grid:
     d: tuple = (1.0, 1.0, 1.0)
     dt: float = 0.5
     c: float = 1.0
+    order2: int = 3   # twice the alternating order l_a: 3 (l_a = 1 1/2) or 5 (l_a = 2 1/2)
 
     def cstruct(self):
         nz = self.n[2] if self.dims == 3 else 1
         return _Grid(self.dims, self.n[0], self.n[1], nz, self.d[0], self.d[1], self.d[2],
-                     self.dt, self.c)
+                     self.dt, self.c, self.order2)
 
     @property
     def shape(self):
@@ -122,12 +123,19 @@ def _species_array(species):
     return arr
 
 
-def form_factor(xp):
-    """Closed-form l_a = 1 1/2 values at one position (Sec. 4.5): (i, f[2], dF[3])."""
+def form_factor(xp, order2=3):
+    """Closed-form alternating-order values at one position (Sec. 4.5):
+    (i, f, dF) with f[2], dF[3] for l_a = 1 1/2 (order2 = 3) and f[3], dF[4]
+    for l_a = 2 1/2 (order2 = 5)."""
     i = C.c_longlong()
-    f = (C.c_double * 2)()
-    dF = (C.c_double * 3)()
-    lib().orc_form_factor(C.c_double(xp), C.byref(i), f, dF)
+    if order2 == 5:
+        f = (C.c_double * 3)()
+        dF = (C.c_double * 4)()
+        lib().orc_form_factor5(C.c_double(xp), C.byref(i), f, dF)
+    else:
+        f = (C.c_double * 2)()
+        dF = (C.c_double * 3)()
+        lib().orc_form_factor(C.c_double(xp), C.byref(i), f, dF)
     return i.value, np.array(f[:]), np.array(dF[:])
 
 
@@ -249,7 +257,10 @@ def yee_half_B_adj(g: Grid, lamB, lamE):
 def step_adj(g: Grid, E, Bh, species, lamE, lamB, lam_x, lam_w):
     """One step of the discrete adjoint at level n (state E^n, B^{n-1/2}, species
     at n).  lamE, lamB (fields) and lam_x, lam_w (one (3, n) float64 array per
-    species) hold dL/d(state n+1) on entry and dL/d(state n) on return."""
+    species) hold dL/d(state n+1) on entry and dL/d(state n) on return.
+    Written for l_a = 1 1/2 only."""
+    if g.order2 == 5:
+        raise NotImplementedError("the oracle's adjoint is written for l_a = 1 1/2")
     arr = _species_array(species)
     LX = (_P * len(species))(*[_ptr(a) for a in lam_x])
     LW = (_P * len(species))(*[_ptr(a) for a in lam_w])

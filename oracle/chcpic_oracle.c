@@ -1,7 +1,7 @@
 /*
  * chcpic_oracle.c -- plain, slow, FP64 CPU oracle for one time step of the
  * charge-conserving particle-in-cell (ChCPIC) scheme with the alternating-order
- * form factor of order l_a = 1 1/2 (I. V. Sokolov, "Alternating-Order
+ * form factor of order l_a = 1 1/2 or 2 1/2 (I. V. Sokolov, "Alternating-Order
  * Interpolation in a Charge-Conserving Scheme for Particle-In-Cell
  * Simulations", arXiv:1101.0809).
  *
@@ -40,6 +40,7 @@ typedef struct {
     int nx, ny, nz;        /* cells per axis (nz == 1 when dims == 2) */
     double dx, dy, dz;     /* cell sizes */
     double dt, c;          /* time step, speed of light */
+    int order2;            /* twice the alternating order: 3 (l_a = 1 1/2; also 0) or 5 (l_a = 2 1/2) */
 } orc_grid;
 
 typedef struct {
@@ -78,13 +79,19 @@ static double cell_volume(const orc_grid *g)
 }
 
 /* ---------------------------------------------------------------------------
- * Alternating-order form factor, l_a = 1 1/2 (Sec. 4.5, closed-form values).
- * With i = int(x_p) and d = x_p - i:
- *   point values of f = f^(1) at the integer points i, i+1:         (1-d, d)
- *   cell integrals dF = f^(2) at the half-integers i-1/2, i+1/2, i+3/2:
- *        ((1-d)^2/2, 3/4 - (1/2-d)^2, d^2/2)
- * "int" is read as floor on the wrapped, non-negative position.
- * The half-integer point i+1/2+b-1 (b = 0,1,2) is the centre of cell i-1+b.
+ * Alternating-order form factor (Sec. 4.5, closed-form values).  The weight of
+ * a grid point is f^(l) at integer points and dF = f^(l+1) at half-integer
+ * points (the cell integrals of f^(l), Eq. intff); l_a = l + 1/2.
+ *
+ * l_a = 1 1/2: with i = int(x_p) and d = x_p - i,
+ *   f at the integer points i, i+1:                      (1-d, d)
+ *   dF at the half-integers i-1/2, i+1/2, i+3/2:         ((1-d)^2/2, 3/4 - (1/2-d)^2, d^2/2)
+ * l_a = 2 1/2: with i = int(x_p + 1/2) and d = x_p + 1/2 - i,
+ *   f at the integer points i-1, i, i+1:                 ((1-d)^2/2, 3/4 - (1/2-d)^2, d^2/2)
+ *   dF at the half-integers i-3/2, ..., i+3/2:
+ *        ((1-d)^3/6, (2-d)^3/6 - 2(1-d)^3/3, (1+d)^3/6 - 2d^3/3, d^3/6)
+ * "int" is read as floor on the wrapped, non-negative position.  The
+ * half-integer point c+1/2 is the centre of cell c.
  * ------------------------------------------------------------------------- */
 void orc_form_factor(double xp, long long *i, double f[2], double dF[3])
 {
@@ -98,26 +105,79 @@ void orc_form_factor(double xp, long long *i, double f[2], double dF[3])
     dF[2] = 0.5 * d * d;
 }
 
+void orc_form_factor5(double xp, long long *i, double f[3], double dF[4])
+{
+    double fl = floor(xp + 0.5);
+    double d = xp + 0.5 - fl;
+    double e = 1.0 - d;
+    *i = (long long)fl;
+    f[0] = 0.5 * e * e;
+    f[1] = 0.75 - (0.5 - d) * (0.5 - d);
+    f[2] = 0.5 * d * d;
+    dF[0] = e * e * e / 6.0;
+    dF[1] = (2.0 - d) * (2.0 - d) * (2.0 - d) / 6.0 - 2.0 * e * e * e / 3.0;
+    dF[2] = (1.0 + d) * (1.0 + d) * (1.0 + d) / 6.0 - 2.0 * d * d * d / 3.0;
+    dF[3] = d * d * d / 6.0;
+}
+
+static int grid_order2(const orc_grid *g) { return g->order2 == 5 ? 5 : 3; }
+
+/* Weights of one axis: nf point values f at the integer points ib+fo+a
+ * (a = 0..nf-1) and nS cell integrals dF over the cells ib+so+b (b = 0..nS-1). */
+typedef struct {
+    long long ib;
+    int nf, fo, nS, so;
+    double f[3];
+    double dF[4];
+} orc_axis_w;
+
+static void axis_weights(int order2, double xp, orc_axis_w *w)
+{
+    if (order2 == 5) {
+        orc_form_factor5(xp, &w->ib, w->f, w->dF);
+        w->nf = 3; w->fo = -1; w->nS = 4; w->so = -2;
+    } else {
+        orc_form_factor(xp, &w->ib, w->f, w->dF);
+        w->nf = 2; w->fo = 0; w->nS = 3; w->so = -1;
+    }
+}
+
 /* Per-axis weights of one particle.  In 2D the z axis is degenerate: one
  * point k = 0 with weight 1 for both kinds of point, which drops the z factor
  * from every product below. */
 typedef struct {
-    long long i0[3];
-    double f[3][2];
-    double dF[3][3];
+    orc_axis_w ax[3];
 } orc_weights;
 
 static void particle_weights(const orc_grid *g, const double xp[3], orc_weights *wt)
 {
     for (int a = 0; a < 3; ++a) {
+        orc_axis_w *w = &wt->ax[a];
         if (a == 2 && g->dims == 2) {
-            wt->i0[2] = 0;
-            wt->f[2][0] = 1.0; wt->f[2][1] = 0.0;
-            wt->dF[2][0] = 0.0; wt->dF[2][1] = 1.0; wt->dF[2][2] = 0.0;
+            w->ib = 0;
+            w->nf = 1; w->fo = 0; w->f[0] = 1.0;
+            w->nS = 1; w->so = 0; w->dF[0] = 1.0;
             continue;
         }
-        orc_form_factor(xp[a], &wt->i0[a], wt->f[a], wt->dF[a]);
+        axis_weights(grid_order2(g), xp[a], w);
     }
+}
+
+/* Interpolation sum of one staggered grid function at the particle: along axis
+ * a over the integer points with f when ipt[a] is set, else over the cells
+ * with dF.  F[i,j,k] sits at i (integer) or i+1/2 (cell centre) per axis. */
+static double interp_point(const orc_grid *g, const orc_weights *wt, const int ipt[3], const double *F)
+{
+    const orc_axis_w *X = &wt->ax[0], *Y = &wt->ax[1], *Z = &wt->ax[2];
+    const int nx = ipt[0] ? X->nf : X->nS, ny = ipt[1] ? Y->nf : Y->nS, nz = ipt[2] ? Z->nf : Z->nS;
+    const int ox = ipt[0] ? X->fo : X->so, oy = ipt[1] ? Y->fo : Y->so, oz = ipt[2] ? Z->fo : Z->so;
+    const double *wx = ipt[0] ? X->f : X->dF, *wy = ipt[1] ? Y->f : Y->dF, *wz = ipt[2] ? Z->f : Z->dF;
+    double acc = 0.0;
+    for (int c = 0; c < nz; ++c)
+        for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a)
+                acc += wx[a] * wy[b] * wz[c] * F[cell_index(g, X->ib + ox + a, Y->ib + oy + b, Z->ib + oz + c)];
+    return acc;
 }
 
 /* ---------------------------------------------------------------------------
@@ -125,56 +185,22 @@ static void particle_weights(const orc_grid *g, const double xp[3], orc_weights 
  * beta of Eq. betax).  Along its own axis an E component takes the lower-order
  * point values f at integer points; along the two other axes it takes the cell
  * integrals dF at half-integer points.  A B component is the other way round.
+ *   E^(x) at (i, j+1/2, k+1/2): alpha^(x) = f_i(x) dF_{j+1/2}(y) dF_{k+1/2}(z), cyclically;
+ *   B^(x) at (i+1/2, j, k):     beta^(x)  = dF_{i+1/2}(x) f_j(y) f_k(z), cyclically.
+ * In 2D the z factor is the single weight 1 for both kinds.
  * ------------------------------------------------------------------------- */
 void orc_gather(const orc_grid *g, const double *const E[3], const double *const B[3],
                 const double xp[3], double Ep[3], double Bp[3])
 {
     orc_weights wt;
     particle_weights(g, xp, &wt);
-    const long long i0 = wt.i0[0], j0 = wt.i0[1], k0 = wt.i0[2];
-    const int nzb = g->dims == 2 ? 1 : 2;   /* integer-point count along z */
-    const int nzc = g->dims == 2 ? 1 : 3;   /* half-integer-point count along z */
-    const int kzc = g->dims == 2 ? 0 : -1;  /* first half-integer cell offset along z */
-    const double *fz = wt.f[2], *dFz = g->dims == 2 ? &wt.dF[2][1] : wt.dF[2];
-
-    for (int a = 0; a < 3; ++a) { Ep[a] = 0.0; Bp[a] = 0.0; }
-
-    /* E^(x) at (i, j+1/2, k+1/2): alpha^(x) = f_i(x) dF_{j+1/2}(y) dF_{k+1/2}(z) */
-    for (int c = 0; c < nzc; ++c)
-        for (int b = 0; b < 3; ++b)
-            for (int a = 0; a < 2; ++a)
-                Ep[0] += wt.f[0][a] * wt.dF[1][b] * dFz[c] *
-                         E[0][cell_index(g, i0 + a, j0 - 1 + b, k0 + kzc + c)];
-    /* E^(y) at (i+1/2, j, k+1/2): alpha^(y) = dF_{i+1/2}(x) f_j(y) dF_{k+1/2}(z) */
-    for (int c = 0; c < nzc; ++c)
-        for (int b = 0; b < 2; ++b)
-            for (int a = 0; a < 3; ++a)
-                Ep[1] += wt.dF[0][a] * wt.f[1][b] * dFz[c] *
-                         E[1][cell_index(g, i0 - 1 + a, j0 + b, k0 + kzc + c)];
-    /* E^(z) at (i+1/2, j+1/2, k): alpha^(z) = dF_{i+1/2}(x) dF_{j+1/2}(y) f_k(z) */
-    for (int c = 0; c < nzb; ++c)
-        for (int b = 0; b < 3; ++b)
-            for (int a = 0; a < 3; ++a)
-                Ep[2] += wt.dF[0][a] * wt.dF[1][b] * fz[c] *
-                         E[2][cell_index(g, i0 - 1 + a, j0 - 1 + b, k0 + c)];
-    /* B^(x) at (i+1/2, j, k): beta^(x) = dF_{i+1/2}(x) f_j(y) f_k(z) */
-    for (int c = 0; c < nzb; ++c)
-        for (int b = 0; b < 2; ++b)
-            for (int a = 0; a < 3; ++a)
-                Bp[0] += wt.dF[0][a] * wt.f[1][b] * fz[c] *
-                         B[0][cell_index(g, i0 - 1 + a, j0 + b, k0 + c)];
-    /* B^(y) at (i, j+1/2, k): beta^(y) = f_i(x) dF_{j+1/2}(y) f_k(z) */
-    for (int c = 0; c < nzb; ++c)
-        for (int b = 0; b < 3; ++b)
-            for (int a = 0; a < 2; ++a)
-                Bp[1] += wt.f[0][a] * wt.dF[1][b] * fz[c] *
-                         B[1][cell_index(g, i0 + a, j0 - 1 + b, k0 + c)];
-    /* B^(z) at (i, j, k+1/2): beta^(z) = f_i(x) f_j(y) dF_{k+1/2}(z) */
-    for (int c = 0; c < nzc; ++c)
-        for (int b = 0; b < 2; ++b)
-            for (int a = 0; a < 2; ++a)
-                Bp[2] += wt.f[0][a] * wt.f[1][b] * dFz[c] *
-                         B[2][cell_index(g, i0 + a, j0 + b, k0 + kzc + c)];
+    for (int a = 0; a < 3; ++a) {
+        int ie[3] = { 0, 0, 0 }, ib[3] = { 1, 1, 1 };
+        ie[a] = 1;   /* E^(a): integer points along a */
+        ib[a] = 0;   /* B^(a): cells along a */
+        Ep[a] = interp_point(g, &wt, ie, E[a]);
+        Bp[a] = interp_point(g, &wt, ib, B[a]);
+    }
 }
 
 /* ---------------------------------------------------------------------------
@@ -257,21 +283,20 @@ typedef struct {
     double closure;        /* sum of dF(-) over the window */
 } orc_axis_current;
 
-static int axis_current(double x0, double x1, orc_axis_current *ac)
+static int axis_current(int order2, double x0, double x1, orc_axis_current *ac)
 {
-    long long i0, i1;
-    double f0[2], f1[2], dF0[3], dF1[3];
-    orc_form_factor(x0, &i0, f0, dF0);
-    orc_form_factor(x1, &i1, f1, dF1);
-    long long lo = (i0 < i1 ? i0 : i1) - 1;
-    long long hi = (i0 > i1 ? i0 : i1) + 1;
+    orc_axis_w w0, w1;
+    axis_weights(order2, x0, &w0);
+    axis_weights(order2, x1, &w1);
+    long long lo = (w0.ib < w1.ib ? w0.ib : w1.ib) + w0.so;
+    long long hi = (w0.ib > w1.ib ? w0.ib : w1.ib) + w0.so + w0.nS - 1;
     int len = (int)(hi - lo + 1);
     if (len > ORC_MAXWIN) return -1;
     double old_w[ORC_MAXWIN], new_w[ORC_MAXWIN];
     for (int s = 0; s < len; ++s) { old_w[s] = 0.0; new_w[s] = 0.0; }
-    for (int b = 0; b < 3; ++b) {
-        old_w[i0 - 1 + b - lo] = dF0[b];
-        new_w[i1 - 1 + b - lo] = dF1[b];
+    for (int b = 0; b < w0.nS; ++b) {
+        old_w[w0.ib + w0.so + b - lo] = w0.dF[b];
+        new_w[w1.ib + w1.so + b - lo] = w1.dF[b];
     }
     ac->lo = lo;
     ac->len = len;
@@ -295,7 +320,7 @@ double orc_deposit(const orc_grid *g, const double x0[3], const double x1[3], co
 {
     orc_axis_current ax[3];
     for (int a = 0; a < g->dims; ++a)
-        if (axis_current(x0[a], x1[a], &ax[a]) != 0) return INFINITY;
+        if (axis_current(grid_order2(g), x0[a], x1[a], &ax[a]) != 0) return INFINITY;
     const double qV = qp / cell_volume(g);
     const double dtn = g->dt;
     double worst = 0.0;
@@ -348,7 +373,8 @@ double orc_deposit(const orc_grid *g, const double x0[3], const double x1[3], co
     return worst;
 }
 
-/* Charge density of one species (Eq. rho): rho_{i+1/2,...} += (q_p/V) dF_x dF_y dF_z. */
+/* Charge density of one species (Eq. rho): rho_{i+1/2,...} += (q_p/V) dF_x dF_y dF_z
+ * over the cells of the particle's dF window (3 or 4 per axis). */
 void orc_rho(const orc_grid *g, long long n, const double *const x[3], double qp, double *rho)
 {
     const double qV = qp / cell_volume(g);
@@ -356,14 +382,12 @@ void orc_rho(const orc_grid *g, long long n, const double *const x[3], double qp
         double xp[3] = { x[0][p], x[1][p], g->dims == 3 ? x[2][p] : 0.0 };
         orc_weights wt;
         particle_weights(g, xp, &wt);
-        const int nzc = g->dims == 2 ? 1 : 3;
-        const int kzc = g->dims == 2 ? 0 : -1;
-        const double *dFz = g->dims == 2 ? &wt.dF[2][1] : wt.dF[2];
-        for (int c = 0; c < nzc; ++c)
-            for (int b = 0; b < 3; ++b)
-                for (int a = 0; a < 3; ++a)
-                    rho[cell_index(g, wt.i0[0] - 1 + a, wt.i0[1] - 1 + b, wt.i0[2] + kzc + c)] +=
-                        qV * wt.dF[0][a] * wt.dF[1][b] * dFz[c];
+        const orc_axis_w *X = &wt.ax[0], *Y = &wt.ax[1], *Z = &wt.ax[2];
+        for (int c = 0; c < Z->nS; ++c)
+            for (int b = 0; b < Y->nS; ++b)
+                for (int a = 0; a < X->nS; ++a)
+                    rho[cell_index(g, X->ib + X->so + a, Y->ib + Y->so + b, Z->ib + Z->so + c)] +=
+                        qV * X->dF[a] * Y->dF[b] * Z->dF[c];
     }
 }
 
@@ -639,7 +663,7 @@ int orc_sort_perm(long long n, const int *key, int nkeys, long long *perm)
 
 /* ===========================================================================
  * Discrete adjoint of one time step (hand-derived reverse mode of the
- * Appendix step above).  State at level n: E^n, B^{n-1/2}, x^n, w^{n-1/2};
+ * Appendix step above), for l_a = 1 1/2.  State at level n: E^n, B^{n-1/2}, x^n, w^{n-1/2};
  * the adjoints lam* hold dL/d(state at n+1) on entry and dL/d(state at n) on
  * return.  The step's intermediate quantities are recomputed from the state at
  * n.  Forward order: B1 = B - (1/2) C_B E; particles (gather from E, B1; push;
@@ -737,7 +761,7 @@ void orc_gather_adj(const orc_grid *g, const double *const E[3], const double *c
         dw[a][0][0] = df[0]; dw[a][0][1] = df[1]; dw[a][0][2] = 0.0;
         dw[a][1][0] = dS[0]; dw[a][1][1] = dS[1]; dw[a][1][2] = dS[2];
     }
-    const long long i0[3] = { wt.i0[0], wt.i0[1], wt.i0[2] };
+    const long long i0[3] = { wt.ax[0].ib, wt.ax[1].ib, wt.ax[2].ib };
     /* per component: which family (0 = f at integer points, 1 = dF at half-integers) per axis */
     const int famE[3][3] = { { 0, 1, 1 }, { 1, 0, 1 }, { 1, 1, 0 } };
     const int famB[3][3] = { { 1, 0, 0 }, { 0, 1, 0 }, { 0, 0, 1 } };
@@ -760,8 +784,8 @@ void orc_gather_adj(const orc_grid *g, const double *const E[3], const double *c
                         double v[3], d[3];
                         for (int a = 0; a < 3; ++a) {
                             if (a == 2 && g->dims == 2) { v[a] = 1.0; d[a] = 0.0; continue; }
-                            if (fam[a] == 0) { v[a] = wt.f[a][sidx[a]]; d[a] = dw[a][0][sidx[a]]; }
-                            else { v[a] = wt.dF[a][sidx[a]]; d[a] = dw[a][1][sidx[a]]; }
+                            if (fam[a] == 0) { v[a] = wt.ax[a].f[sidx[a]]; d[a] = dw[a][0][sidx[a]]; }
+                            else { v[a] = wt.ax[a].dF[sidx[a]]; d[a] = dw[a][1][sidx[a]]; }
                         }
                         long long idx = cell_index(g, i0[0] + off[0] + s0, i0[1] + off[1] + s1,
                                                    i0[2] + off[2] + s2);
@@ -836,7 +860,7 @@ typedef struct {
 
 static int axis_current_adj(double x0, double x1, orc_axis_adj *ad)
 {
-    if (axis_current(x0, x1, &ad->cur) != 0) return -1;
+    if (axis_current(3, x0, x1, &ad->cur) != 0) return -1;
     long long i0, i1;
     double f0[2], f1[2], dF0[3], dF1[3], df[2], dS0[3], dS1[3];
     orc_form_factor(x0, &i0, f0, dF0);
@@ -938,6 +962,7 @@ void orc_step_adj(const orc_grid *g, const double *const E[3], const double *con
                   const orc_species *sp, double *lamE[3], double *lamB[3], double *const *lam_x,
                   double *const *lam_w)
 {
+    if (grid_order2(g) != 3) return;   /* the hand-derived adjoint is written for l_a = 1 1/2 */
     const long long N = (long long)g->nx * g->ny * g->nz;
     double *B1[3], *lamJ[3], *lamB1[3];
     for (int a = 0; a < 3; ++a) {
