@@ -67,7 +67,9 @@ typedef struct {
     double dx, dy, dz;      /* cell sizes (dz ignored when dims == 2) */
     double dt, c;           /* time step; speed of light */
     int precision;          /* PIC_FP64 or PIC_FP32 */
-    int order2;             /* twice the alternating order l_a; only 3 (l_a = 1 1/2, Sec. 4.5) */
+    int order2;             /* twice the alternating order l_a (Sec. 4.5): 3 (or 0) for l_a = 1 1/2,
+                               5 for l_a = 2 1/2 (the fused, split and diagnostics paths; the
+                               persistent batch step and the adjoint are l_a = 1 1/2 only) */
     int tile[3];            /* tile extents in cells for the sort and the shared-memory
                                stages (0 = default: 8x8x8 in 3D, 16x16 in 2D) */
     int halo;               /* drift guard in cells around a tile (0..2; -1 = default 1) */
@@ -81,6 +83,7 @@ typedef struct {
 /* Order of the tile sort.  Both sort by tile key first.  PIC_SORT_STABLE keeps
  * the input order inside a tile.  PIC_SORT_BANKED orders a tile's particles by
  * (r, b): b = base mod 32 with base = (i-ox+h+2) + P0*((j-oy+h+2) + P1*(k-oz+h+2))
+ * (h = the halo, plus one for l_a = 2 1/2, whose current tile is one cell wider)
  * (no k term in 2D) the shared-memory bank of the particle's cell in the
  * current tile of its tile (tile origin (ox, oy, oz), halo h, tile pitches
  * P0, P1 as reported by pic_tile_layout), and r the number of earlier
@@ -265,7 +268,9 @@ int pic_diagnostics_run(pic_grid *g, int run, pic_diag *out);
  * persistent kernel runs the B half step (with the J clear), the fused particle
  * work of every run, the second B half step and the E step, separated by
  * grid-wide barriers (its grid is the number of blocks that can be resident at
- * once).  The tile sort adds its own launches every sort_interval steps. */
+ * once).  The tile sort adds its own launches every sort_interval steps.
+ * Built for l_a = 1 1/2: PIC_ERR_INVALID_ARG on a grid with order2 = 5 (as
+ * for pic_step_graph). */
 int pic_step_persistent(pic_grid *g, int nsteps);
 
 /* pic_step_persistent replayed from a CUDA graph of 2*sort_interval steps
@@ -336,6 +341,8 @@ int pic_step_saving(pic_grid *g, int nsteps, void *const *states);
  * memory (particles that drifted past their tile's halo read the global
  * arrays), or untiled (one thread per particle, all reads global; the same
  * arithmetic); see pic_set_adjoint_tiled.
+ * The adjoint is derived for l_a = 1 1/2: PIC_ERR_INVALID_ARG on a grid with
+ * order2 = 5 (also for pic_adjoint_steps).
  * pic_adjoint_yee_half_B adds (-(1/2) C_B)^T lamB to lamE (the transpose of one
  * B half step), e.g. to seed a loss that uses B^n = B^{n-1/2} - (1/2) c curl E^n. */
 int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], void *lamw[3]);

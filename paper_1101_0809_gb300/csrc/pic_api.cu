@@ -358,7 +358,8 @@ int do_sort(pic_grid *g)
     int nl = 0;
     cudaError_t e = sort_and_build_items(g->prec, g->dims, g->stream, g->total, g->pool, g->pool_alt, g->d_groups,
                                          g->d_group_base, (int)g->groups.size(), g->d_runs, g->total_tiles, g->sort,
-                                         g->tile_start, g->item_scan, g->items, g->n_items, g->ppi, g->halo,
+                                         g->tile_start, g->item_scan, g->items, g->n_items, g->ppi,
+                                         g->halo + (g->order2 == 5 ? 1 : 0),   // the current tile's bank base
                                          g->sort_order == PIC_SORT_BANKED ? 1 : 0, &nl);
     launch_count_add(g, nl);
     if (e != cudaSuccess) return cuda_fail(e, "tile sort");
@@ -374,7 +375,8 @@ int launch_part(pic_grid *g, int mode)
     ProfScope ps(g, PIC_PROF_PARTICLES);
     cudaError_t e = launch_particles(g->dims, g->prec, mode, g->stream, g->items, g->n_items, g->max_items, g->d_runs,
                                      g->d_groups, g->pool, g->E, g->B, g->J, g->old_cell, g->old_off, g->halo,
-                                     g->tile[0], g->tile[1], g->tile[2], g->d_err, g->pitch[0], g->pitch[1]);
+                                     g->tile[0], g->tile[1], g->tile[2], g->d_err, g->pitch[0], g->pitch[1],
+                                     g->order2);
     launch_count_add(g, g->max_items > 0 ? 1 : 0);
     if (e != cudaSuccess) return cuda_fail(e, "particle kernel");
     return PIC_OK;
@@ -404,7 +406,9 @@ int launch_fields(pic_grid *g, int which, int zero_j)
 // SM.  In 2D only the x pitch matters.
 static void choose_pitch(pic_grid *g)
 {
-    const int h = g->halo, T0 = g->tile[0], T1 = g->tile[1], T2 = g->dims == 3 ? g->tile[2] : 1;
+    // h: the current tile's halo beyond the first two cells (one more for l_a = 2 1/2)
+    const int h = g->halo + (g->order2 == 5 ? 1 : 0), T0 = g->tile[0], T1 = g->tile[1],
+              T2 = g->dims == 3 ? g->tile[2] : 1;
     const int je0 = T0 + 2 * h + 4, je1 = T1 + 2 * h + 4;
     long long best_key = -1;
     for (int p0 = je0; p0 <= std::max(je0, 32); ++p0) {
@@ -421,7 +425,8 @@ static void choose_pitch(pic_grid *g)
                 mn = std::min(mn, cnt[b]);
                 mx = std::max(mx, cnt[b]);
             }
-            const long long smem = (long long)particles_smem_bytes(g->dims, g->prec, 0, T0, T1, T2, h, p0, p1);
+            const long long smem =
+                (long long)particles_smem_bytes(g->dims, g->prec, 0, T0, T1, T2, g->halo, p0, p1, g->order2);
             const long long two = smem <= 113 * 1024 ? 0 : 1;
             const long long key = ((long long)(mx - mn) << 40) | (two << 39) | smem;
             if (best_key < 0 || key < best_key) {
@@ -443,10 +448,11 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
     if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return fail(PIC_ERR_INVALID_ARG, "cell counts must be positive");
     if (d->dims == 2 && d->nz != 1) return fail(PIC_ERR_INVALID_ARG, "nz must be 1 for a 2D grid");
     if (d->precision != PIC_FP64 && d->precision != PIC_FP32) return fail(PIC_ERR_INVALID_ARG, "bad precision");
-    if (d->order2 != 3 && d->order2 != 0)
-        return fail(PIC_ERR_INVALID_ARG, "only the alternating order l_a = 1 1/2 (order2 = 3) is built");
-    if (!first && (d->dims != g->dims || d->precision != g->prec))
-        return fail(PIC_ERR_INVALID_ARG, "all runs of a batch need the same dims and precision");
+    if (d->order2 != 3 && d->order2 != 5 && d->order2 != 0)
+        return fail(PIC_ERR_INVALID_ARG, "order2 must be 3 (l_a = 1 1/2) or 5 (l_a = 2 1/2)");
+    const int order2 = d->order2 == 5 ? 5 : 3;
+    if (!first && (d->dims != g->dims || d->precision != g->prec || order2 != g->order2))
+        return fail(PIC_ERR_INVALID_ARG, "all runs of a batch need the same dims, precision and order");
     const double dd[3] = {d->dx, d->dy, d->dims == 3 ? d->dz : 1.0};
     for (int a = 0; a < 3; ++a)
         if (!(dd[a] > 0.0) || !std::isfinite(dd[a])) return fail(PIC_ERR_INVALID_ARG, "cell sizes must be positive");
@@ -462,6 +468,7 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
     if (first) {
         g->dims = d->dims;
         g->prec = d->precision;
+        g->order2 = order2;
         // the FP64 particle adjoint is bound by the FP64 pipe; per-block tile
         // staging costs it more than the global reads it saves
         g->adj_tiled = g->prec == PIC_FP32 ? 1 : 0;
@@ -482,11 +489,12 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
     for (int a = 0; a < 3; ++a) t[a] = std::min(g->tile[a], n[a]);
     if (first)
         for (int a = 0; a < 3; ++a) g->tile[a] = t[a];
+    const int staged = 2 * (g->halo + (g->order2 == 5 ? 3 : 2));   // the current tile's halo, both sides
     for (int a = 0; a < d->dims; ++a) {
-        if (n[a] < t[a] + 2 * g->halo + 4)
+        if (n[a] < t[a] + staged)
             return fail(PIC_ERR_INVALID_ARG,
                         "axis %d has %d cells; the tile (%d) plus its staged halo (%d) must fit in the grid", a, n[a],
-                        t[a], 2 * g->halo + 4);
+                        t[a], staged);
     }
     if (first) choose_pitch(g);
     memset(&rd, 0, sizeof(rd));
@@ -634,23 +642,25 @@ int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out)
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     for (int mode = 0; mode < 3; ++mode) {
         const size_t b = particles_smem_bytes(g->dims, g->prec, mode, g->tile[0], g->tile[1], g->tile[2], g->halo,
-                                              g->pitch[0], g->pitch[1]);
+                                              g->pitch[0], g->pitch[1], g->order2);
         if ((long long)b > optin) {
             destroy_grid(g);
             return fail(PIC_ERR_INVALID_ARG, "tile %dx%dx%d with halo %d needs %zu B of shared memory (> %d)",
                         descs[0].tile[0], descs[0].tile[1], descs[0].tile[2], descs[0].halo, b, optin);
         }
-        if ((e = particles_set_smem_limit(g->dims, g->prec, mode, b)) != cudaSuccess) return bail(e, "smem limit");
+        if ((e = particles_set_smem_limit(g->dims, g->prec, mode, b, g->order2)) != cudaSuccess)
+            return bail(e, "smem limit");
     }
     {
         // the tiled particle adjoint where its tiles fit in shared memory
         const size_t ab = adjoint_smem_bytes(g->dims, g->prec, g->tile, g->halo, g->pitch);
-        g->adj_fits = (long long)ab <= optin ? 1 : 0;
+        g->adj_fits = (long long)ab <= optin && g->order2 == 3 ? 1 : 0;
         if (g->adj_fits && (e = adjoint_set_smem_limit(g->dims, g->prec, ab)) != cudaSuccess)
             return bail(e, "smem limit");
     }
-    if (g->prec == PIC_FP32 && (e = diag_set_smem_limit(g->dims, diag_items_smem_bytes(g->dims, g->tile, g->halo,
-                                                                                      g->pitch))) != cudaSuccess)
+    if (g->prec == PIC_FP32 &&
+        (e = diag_set_smem_limit(g->dims, diag_items_smem_bytes(g->dims, g->tile, g->halo, g->pitch, g->order2),
+                                 g->order2)) != cudaSuccess)
         return bail(e, "smem limit");
     if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return bail(e, "create");
     *out = g;
@@ -1166,6 +1176,7 @@ int pic_step_persistent(pic_grid *g, int nsteps)
 {
     if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
     if (nsteps < 0) return fail(PIC_ERR_INVALID_ARG, "negative step count");
+    if (g->order2 != 3) return fail(PIC_ERR_INVALID_ARG, "the persistent batch step is built for l_a = 1 1/2");
     if (g->total == 0) return pic_step(g, nsteps);
     for (int s = 0; s < nsteps; ++s) {
         int rc = persistent_step(g);
@@ -1219,6 +1230,7 @@ int pic_step_graph(pic_grid *g, int nsteps)
 {
     if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
     if (nsteps < 0) return fail(PIC_ERR_INVALID_ARG, "negative step count");
+    if (g->order2 != 3) return fail(PIC_ERR_INVALID_ARG, "the persistent batch step is built for l_a = 1 1/2");
     if (!g->stream) return fail(PIC_ERR_INVALID_ARG, "graph replay needs a non-default stream");
     if (g->total == 0) return pic_step(g, nsteps);
     const int span = 2 * g->sort_interval;
@@ -1290,7 +1302,7 @@ int pic_diagnostics_run(pic_grid *g, int run, pic_diag *out)
                                            (long long)rn.n[0] * rn.n[1] * rn.n[2], rn.cell_base, g->d_groups,
                                            g->d_group_base, (int)g->groups.size(), g->total, g->pool, g->E, g->B,
                                            g->diag, g->have_ref[run] ? 0 : 1, kDiagBlocks, kDiagBlocks, &nl,
-                                           g->items, g->n_items, g->halo, g->tile, g->pitch);
+                                           g->items, g->n_items, g->halo, g->tile, g->pitch, g->order2);
     launch_count_add(g, nl);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
     double r[kDiagResults];
@@ -1523,6 +1535,7 @@ int pic_adjoint_yee_half_B(pic_grid *g, void *const lamB[3], void *lamE[3])
 int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], void *lamw[3])
 {
     if (!g || !lamE || !lamB || !lamx || !lamw) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    if (g->order2 != 3) return fail(PIC_ERR_INVALID_ARG, "the discrete adjoint is built for l_a = 1 1/2");
     for (int c = 0; c < 3; ++c)
         if (!lamE[c] || !lamB[c] || !lamw[c] || (c < g->dims && !lamx[c]))
             return fail(PIC_ERR_INVALID_ARG, "null adjoint component");
@@ -1570,6 +1583,7 @@ int pic_adjoint_steps(pic_grid *g, void *const *states, int nstates, void *lamE[
 {
     if (!g || (nstates > 0 && !states)) return fail(PIC_ERR_INVALID_ARG, "null argument");
     if (nstates < 0) return fail(PIC_ERR_INVALID_ARG, "negative state count");
+    if (g->order2 != 3) return fail(PIC_ERR_INVALID_ARG, "the discrete adjoint is built for l_a = 1 1/2");
     if (nstates == 0) return PIC_OK;
     for (int s = 0; s < nstates; ++s)
         if (!states[s]) return fail(PIC_ERR_INVALID_ARG, "null state buffer %d", s);

@@ -523,6 +523,222 @@ __device__ __forceinline__ void deposit(const Acc &acc, const AxisWin<R> &X, con
 }
 
 // ---------------------------------------------------------------------------
+// Alternating-order form factor l_a = 2 1/2 (Sec. 4.5).  The base index is
+// ib = int(x_p + 1/2) with d = x_p + 1/2 - ib; the point values f = f^(2) at
+// the integer points ib-1, ib, ib+1 are ((1-d)^2/2, 3/4 - (1/2-d)^2, d^2/2) and
+// the cell integrals S = f^(3) over the cells ib-2 .. ib+1 (centres
+// ib-3/2 .. ib+3/2) are the cubic B-spline values
+//   ((1-d)^3/6, (4 - 6d^2 + 3d^3)/6, (1 + 3d + 3d^2 - 3d^3)/6, d^3/6),
+// the second and third being the paper's (2-d)^3/6 - 2(1-d)^3/3 and
+// (1+d)^3/6 - 2d^3/3 multiplied out.  From the stored (cell, offset o):
+// ib = cell + (o >= 1/2), d = o + 1/2 - (o >= 1/2).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int split5(R o, R &d)
+{
+    const int up = o >= R(0.5) ? 1 : 0;
+    d = up ? o - R(0.5) : o + R(0.5);
+    return up;
+}
+
+template <typename R>
+__device__ __forceinline__ void form_factor5(R d, R f[3], R S[4])
+{
+    const R h = R(0.5), s6 = R(1) / R(6);
+    const R e = R(1) - d, m = h - d, d2 = d * d;
+    f[0] = h * e * e;
+    f[1] = R(0.75) - m * m;
+    f[2] = h * d2;
+    S[0] = s6 * e * e * e;
+    S[1] = s6 * (R(4) + d2 * (R(3) * d - R(6)));
+    S[2] = s6 * (R(1) + R(3) * d * (R(1) + d - d2));
+    S[3] = s6 * d2 * d;
+}
+
+// Gather with l_a = 2 1/2 (Eqs. alphax, betax with f^(2) and f^(3)); reader
+// offsets are relative to the base index ib: f index a sits at a - 1, S index
+// b at b - 2.  2D drops every z factor.
+template <int DIM, typename R, class Rd>
+__device__ __forceinline__ void gather5(const Rd &rd, const R fx[3], const R Sx[4], const R fy[3], const R Sy[4],
+                                        const R fz[3], const R Sz[4], R Ep[3], R Bp[3])
+{
+    constexpr int NZS = DIM == 3 ? 4 : 1, NZF = DIM == 3 ? 3 : 1;
+    R ex = 0, ey = 0, ez = 0, bx = 0, by = 0, bz = 0;
+#pragma unroll
+    for (int c = 0; c < NZS; ++c) {   // S along z: E^x, E^y, B^z
+        const R wz = DIM == 3 ? Sz[c] : R(1);
+        const int oz = DIM == 3 ? c - 2 : 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const R t = fx[0] * rd.e(0, -1, b - 2, oz) + fx[1] * rd.e(0, 0, b - 2, oz) + fx[2] * rd.e(0, 1, b - 2, oz);
+            ex += Sy[b] * wz * t;
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const R t = Sx[0] * rd.e(1, -2, b - 1, oz) + Sx[1] * rd.e(1, -1, b - 1, oz) +
+                        Sx[2] * rd.e(1, 0, b - 1, oz) + Sx[3] * rd.e(1, 1, b - 1, oz);
+            ey += fy[b] * wz * t;
+            const R u = fx[0] * rd.b(2, -1, b - 1, oz) + fx[1] * rd.b(2, 0, b - 1, oz) + fx[2] * rd.b(2, 1, b - 1, oz);
+            bz += fy[b] * wz * u;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NZF; ++c) {   // f along z: E^z, B^x, B^y
+        const R wz = DIM == 3 ? fz[c] : R(1);
+        const int oz = DIM == 3 ? c - 1 : 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const R t = Sx[0] * rd.e(2, -2, b - 2, oz) + Sx[1] * rd.e(2, -1, b - 2, oz) +
+                        Sx[2] * rd.e(2, 0, b - 2, oz) + Sx[3] * rd.e(2, 1, b - 2, oz);
+            ez += Sy[b] * wz * t;
+            const R u = fx[0] * rd.b(1, -1, b - 2, oz) + fx[1] * rd.b(1, 0, b - 2, oz) + fx[2] * rd.b(1, 1, b - 2, oz);
+            by += Sy[b] * wz * u;
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const R t = Sx[0] * rd.b(0, -2, b - 1, oz) + Sx[1] * rd.b(0, -1, b - 1, oz) +
+                        Sx[2] * rd.b(0, 0, b - 1, oz) + Sx[3] * rd.b(0, 1, b - 1, oz);
+            bx += fy[b] * wz * t;
+        }
+    }
+    Ep[0] = ex; Ep[1] = ey; Ep[2] = ez;
+    Bp[0] = bx; Bp[1] = by; Bp[2] = bz;
+}
+
+template <typename R>
+struct GlobalReader5 {       // periodic global arrays, offsets -2..2 from the base index
+    const R *E[3];
+    const R *B[3];
+    long long xi[5], yj[5], zk[5];
+    __device__ __forceinline__ long long at(int dx, int dy, int dz) const { return xi[dx + 2] + yj[dy + 2] + zk[dz + 2]; }
+    __device__ __forceinline__ R e(int a, int dx, int dy, int dz) const { return E[a][at(dx, dy, dz)]; }
+    __device__ __forceinline__ R b(int a, int dx, int dy, int dz) const { return B[a][at(dx, dy, dz)]; }
+};
+
+// Deposit window of one axis with l_a = 2 1/2: the cells lo .. lo+4 relative to
+// the old base index (lo = -2, or -3 when the base index moved down), the old
+// and new cell integrals laid on it, Pp/Pm = new +- old, and the partial sums
+// D[q] = sum_{w <= q} Pm[w] at the faces lo+q+1 (q = 0..3; the face after the
+// last cell carries the closure sum only).
+template <typename R>
+struct AxisWin5 {
+    R Pp[5], Pm[5], D[4];
+    int lo;
+};
+
+template <typename R>
+__device__ __forceinline__ void axis_window5(R d0, R d1, int s, AxisWin5<R> &a)
+{
+    R f0[3], S0[4], f1[3], S1[4];
+    form_factor5(d0, f0, S0);
+    form_factor5(d1, f1, S1);
+    const bool neg = s < 0, pos = s > 0;
+    R o[5], n[5];
+#pragma unroll
+    for (int w = 0; w < 5; ++w) {
+        o[w] = neg ? (w == 0 ? R(0) : S0[w - 1]) : (w == 4 ? R(0) : S0[w]);
+        n[w] = pos ? (w == 0 ? R(0) : S1[w - 1]) : (w == 4 ? R(0) : S1[w]);
+    }
+#pragma unroll
+    for (int w = 0; w < 5; ++w) {
+        a.Pp[w] = n[w] + o[w];
+        a.Pm[w] = n[w] - o[w];
+    }
+    a.D[0] = a.Pm[0];
+#pragma unroll
+    for (int q = 1; q < 4; ++q) a.D[q] = a.D[q - 1] + a.Pm[q];
+    a.lo = neg ? -3 : -2;
+}
+
+// Deposit of one particle with l_a = 2 1/2 (Eq. current on the 5-cell windows;
+// the prefactors kf as for deposit()).  Bit a of `full` clear: no particle of
+// the warp moved its base index along a, so the fifth window cell and the
+// fourth face (the closure) are skipped.
+template <int DIM, typename R, class Acc>
+__device__ __forceinline__ void deposit5(const Acc &acc, const AxisWin5<R> &X, const AxisWin5<R> &Y,
+                                         const AxisWin5<R> &Z, const R kf[3], R uz, int full)
+{
+    const R third = R(1) / R(3);
+    const bool fx = full & 1, fy = full & 2, fz = full & 4;
+    if (DIM == 3) {
+#pragma unroll
+        for (int wz = 0; wz < 5; ++wz) {
+            if (wz == 4 && !fz) continue;
+#pragma unroll
+            for (int wy = 0; wy < 5; ++wy) {
+                if (wy == 4 && !fy) continue;
+                const R T = Y.Pp[wy] * Z.Pp[wz] + third * Y.Pm[wy] * Z.Pm[wz];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q == 3 && !fx) continue;
+                    acc.add(0, X.lo + 1 + q, Y.lo + wy, Z.lo + wz, kf[0] * X.D[q], T);
+                }
+            }
+        }
+#pragma unroll
+        for (int wz = 0; wz < 5; ++wz) {
+            if (wz == 4 && !fz) continue;
+#pragma unroll
+            for (int wx = 0; wx < 5; ++wx) {
+                if (wx == 4 && !fx) continue;
+                const R T = X.Pp[wx] * Z.Pp[wz] + third * X.Pm[wx] * Z.Pm[wz];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q == 3 && !fy) continue;
+                    acc.add(1, X.lo + wx, Y.lo + 1 + q, Z.lo + wz, kf[1] * Y.D[q], T);
+                }
+            }
+        }
+#pragma unroll
+        for (int wy = 0; wy < 5; ++wy) {
+            if (wy == 4 && !fy) continue;
+#pragma unroll
+            for (int wx = 0; wx < 5; ++wx) {
+                if (wx == 4 && !fx) continue;
+                const R T = X.Pp[wx] * Y.Pp[wy] + third * X.Pm[wx] * Y.Pm[wy];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q == 3 && !fz) continue;
+                    acc.add(2, X.lo + wx, Y.lo + wy, Z.lo + 1 + q, kf[2] * Z.D[q], T);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int wy = 0; wy < 5; ++wy) {
+            if (wy == 4 && !fy) continue;
+            const R t = kf[0] * Y.Pp[wy];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q == 3 && !fx) continue;
+                acc.add(0, X.lo + 1 + q, Y.lo + wy, 0, t, X.D[q]);
+            }
+        }
+#pragma unroll
+        for (int wx = 0; wx < 5; ++wx) {
+            if (wx == 4 && !fx) continue;
+            const R t = kf[1] * X.Pp[wx];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q == 3 && !fy) continue;
+                acc.add(1, X.lo + wx, Y.lo + 1 + q, 0, t, Y.D[q]);
+            }
+        }
+        const R kz = kf[2] * uz;
+#pragma unroll
+        for (int wy = 0; wy < 5; ++wy) {
+            if (wy == 4 && !fy) continue;
+#pragma unroll
+            for (int wx = 0; wx < 5; ++wx) {
+                if (wx == 4 && !fx) continue;
+                const R T = X.Pp[wx] * Y.Pp[wy] + third * X.Pm[wx] * Y.Pm[wy];
+                acc.add(2, X.lo + wx, Y.lo + wy, 0, kz, T);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Yee updates of one cell l of run rn (Appendix, Eqs. updateB and escheme,
 // completed cyclically; in 2D every z difference vanishes).
 //   B half step:  Bx[i,j,k] -= (c_y/2)(Ez[i,j,k]-Ez[i,j-1,k]) - (c_z/2)(Ey[i,j,k]-Ey[i,j,k-1])

@@ -24,6 +24,16 @@ struct ConvReader {   // reads the state's precision, returns double, periodic i
     __device__ __forceinline__ double b(int a, int dx, int dy, int dz) const { return (double)B[a][at(dx, dy, dz)]; }
 };
 
+template <typename R>
+struct ConvReader5 {   // the same with offsets -2..2 (l_a = 2 1/2, relative to the base index)
+    const R *E[3];
+    const R *B[3];
+    long long xi[5], yj[5], zk[5];
+    __device__ __forceinline__ long long at(int dx, int dy, int dz) const { return xi[dx + 2] + yj[dy + 2] + zk[dz + 2]; }
+    __device__ __forceinline__ double e(int a, int dx, int dy, int dz) const { return (double)E[a][at(dx, dy, dz)]; }
+    __device__ __forceinline__ double b(int a, int dx, int dy, int dz) const { return (double)B[a][at(dx, dy, dz)]; }
+};
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -59,7 +69,9 @@ __device__ void block_reduce_store(double v[kPartVals], int max_slot, double *ou
 
 // Particles: rho deposit (atomics) and kinetic / momentum / half-step sums.
 // Partial slots: 0 kinetic, 1-3 momentum, 4 half-step correction, 5 count.
-template <int DIM, typename R>
+// ORD = 3: l_a = 1 1/2 (rho over the 3 cells per axis around the cell);
+// ORD = 5: l_a = 2 1/2 (rho over the 4 cells ib-2 .. ib+1 of the base index).
+template <int DIM, typename R, int ORD = 3>
 __global__ void __launch_bounds__(kDiagThreads) k_diag_particles(int run, long long total, const long long *group_base,
                                                                  int ngroups, const GroupDev *groups, const RunDev *runs,
                                                                  Pool<R> P, Fields<R> F, double *rho, double *partials)
@@ -78,38 +90,65 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_particles(int run, long l
         const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
         const int c = P.cell[p];
         const int i = c % nx, rest = c / nx, j = rest % ny, k = DIM == 3 ? rest / ny : 0;
-        double fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
-        form_factor((double)P.off[0][p], fx, Sx);
-        form_factor((double)P.off[1][p], fy, Sy);
-        if (DIM == 3) {
-            form_factor((double)P.off[2][p], fz, Sz);
-        } else {
-            fz[0] = 1; fz[1] = 0; Sz[0] = 0; Sz[1] = 1; Sz[2] = 0;
-        }
         const double qV = g.qp / rn.V;
-        const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
-        for (int dz = kz0; dz <= kz1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const long long idx = rn.cell_base + wrapi(i + dx, nx) +
-                                          (long long)nx * (wrapi(j + dy, ny) + (long long)ny * (DIM == 3 ? wrapi(k + dz, nz) : 0));
-                    atomicAdd(&rho[idx], qV * Sx[dx + 1] * Sy[dy + 1] * Sz[dz + 1]);
-                }
+        double Ep[3], Bp[3];
+        if constexpr (ORD == 5) {
+            double e3[3] = {0.5, 0.5, 0.5}, w[21];
+            int u3[3] = {0, 0, 0};
+            for (int ax = 0; ax < DIM; ++ax) u3[ax] = split5((double)P.off[ax][p], e3[ax]);
+            form_factor5(e3[0], w, w + 3);
+            form_factor5(e3[1], w + 7, w + 10);
+            form_factor5(e3[2], w + 14, w + 17);
+            const int ib = i + u3[0], jb = j + u3[1], kb = k + u3[2];
+            const int nzw = DIM == 3 ? 4 : 1;
+            for (int dz = 0; dz < nzw; ++dz)
+                for (int dy = 0; dy < 4; ++dy)
+                    for (int dx = 0; dx < 4; ++dx) {
+                        const long long idx =
+                            rn.cell_base + wrapi(ib + dx - 2, nx) +
+                            (long long)nx * (wrapi(jb + dy - 2, ny) + (long long)ny * (DIM == 3 ? wrapi(kb + dz - 2, nz) : 0));
+                        atomicAdd(&rho[idx], qV * w[3 + dx] * w[10 + dy] * (DIM == 3 ? w[17 + dz] : 1.0));
+                    }
+            ConvReader5<R> rd;
+            for (int q = 0; q < 3; ++q) { rd.E[q] = F.E[q]; rd.B[q] = F.B[q]; }
+            for (int q = 0; q < 5; ++q) {
+                rd.xi[q] = rn.cell_base + wrapi(ib - 2 + q, nx);
+                rd.yj[q] = (long long)nx * wrapi(jb - 2 + q, ny);
+                rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(kb - 2 + q, nz) : 0;
+            }
+            gather5<DIM>(rd, w, w + 3, w + 7, w + 10, w + 14, w + 17, Ep, Bp);
+        } else {
+            double fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
+            form_factor((double)P.off[0][p], fx, Sx);
+            form_factor((double)P.off[1][p], fy, Sy);
+            if (DIM == 3) {
+                form_factor((double)P.off[2][p], fz, Sz);
+            } else {
+                fz[0] = 1; fz[1] = 0; Sz[0] = 0; Sz[1] = 1; Sz[2] = 0;
+            }
+            const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
+            for (int dz = kz0; dz <= kz1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const long long idx = rn.cell_base + wrapi(i + dx, nx) +
+                                              (long long)nx * (wrapi(j + dy, ny) + (long long)ny * (DIM == 3 ? wrapi(k + dz, nz) : 0));
+                        atomicAdd(&rho[idx], qV * Sx[dx + 1] * Sy[dy + 1] * Sz[dz + 1]);
+                    }
+            ConvReader<R> rd;
+            for (int q = 0; q < 3; ++q) { rd.E[q] = F.E[q]; rd.B[q] = F.B[q]; }
+            for (int q = 0; q < 4; ++q) {
+                rd.xi[q] = rn.cell_base + wrapi(i - 1 + q, nx);
+                rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
+                rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
+            }
+            gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+        }
         const double w0 = (double)P.w[0][p], w1 = (double)P.w[1][p], w2 = (double)P.w[2][p];
         const double gam = sqrt(w0 * w0 + w1 * w1 + w2 * w2 + rn.c * rn.c);
         v[0] += g.mp * rn.c * (gam - rn.c);
         v[1] += g.mp * w0;
         v[2] += g.mp * w1;
         v[3] += g.mp * w2;
-        ConvReader<R> rd;
-        for (int q = 0; q < 3; ++q) { rd.E[q] = F.E[q]; rd.B[q] = F.B[q]; }
-        for (int q = 0; q < 4; ++q) {
-            rd.xi[q] = rn.cell_base + wrapi(i - 1 + q, nx);
-            rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
-            rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
-        }
-        double Ep[3], Bp[3];
-        gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
         v[4] += 0.5 * g.qp * rn.dt * rn.c * (w0 * Ep[0] + w1 * Ep[1] + w2 * Ep[2]) / gam;
         v[5] += 1.0;
     }
@@ -136,8 +175,16 @@ struct GlobalZeroB {
     __device__ __forceinline__ float e(int a, int dx, int dy, int dz) const { return E[a][xi[dx + 1] + yj[dy + 1] + zk[dz + 1]]; }
     __device__ __forceinline__ float b(int, int, int, int) const { return 0.0f; }
 };
+struct GlobalZeroB5 {   // offsets -2..2 from the l_a = 2 1/2 base index
+    const float *E[3];
+    long long xi[5], yj[5], zk[5];
+    __device__ __forceinline__ float e(int a, int dx, int dy, int dz) const { return E[a][xi[dx + 2] + yj[dy + 2] + zk[dz + 2]]; }
+    __device__ __forceinline__ float b(int, int, int, int) const { return 0.0f; }
+};
 
-template <int DIM>
+// ORD = 5 (l_a = 2 1/2): E and rho tiles with a halo of (halo + 2) cells, the
+// 4-cell cubic weights around the base index.
+template <int DIM, int ORD = 3>
 __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const WorkItem *items, const int *n_items,
                                                              const GroupDev *groups, const RunDev *runs, Pool<float> P,
                                                              Fields<float> F, int halo, double *rho, double *partials)
@@ -150,7 +197,8 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const W
     const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
     const int T0 = rn.tile[0], T1 = rn.tile[1], T2 = DIM == 3 ? rn.tile[2] : 1;
     const int P0 = rn.pitch[0], P1 = rn.pitch[1];
-    const int fe0 = T0 + 2 * G + 2, fe1 = T1 + 2 * G + 2, fe2 = DIM == 3 ? T2 + 2 * G + 2 : 1;
+    constexpr int FH = ORD == 5 ? 2 : 1;   // tile halo beyond G
+    const int fe0 = T0 + 2 * (G + FH), fe1 = T1 + 2 * (G + FH), fe2 = DIM == 3 ? T2 + 2 * (G + FH) : 1;
     const int nf = P0 * P1 * fe2;
     float *sE[3];
     for (int c = 0; c < 3; ++c) sE[c] = reinterpret_cast<float *>(dsm) + c * nf;
@@ -171,9 +219,9 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const W
             rh[l] = 0;
             rl[l] = 0;
             if (lx >= fe0 || ly >= fe1) continue;   // pitch padding
-            const int gx = wrapi(ox - G - 1 + lx, nx);
-            const int gy = wrapi(oy - G - 1 + ly, ny);
-            const int gz = DIM == 3 ? wrapi(oz - G - 1 + lz, nz) : 0;
+            const int gx = wrapi(ox - G - FH + lx, nx);
+            const int gy = wrapi(oy - G - FH + ly, ny);
+            const int gz = DIM == 3 ? wrapi(oz - G - FH + lz, nz) : 0;
             const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
             for (int c = 0; c < 3; ++c) sE[c][l] = F.E[c][gi];
         }
@@ -208,47 +256,93 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const W
             if (lj >= T1 + G) lj -= ny; if (lj < -G) lj += ny;
             if (DIM == 3) { if (lk >= T2 + G) lk -= nz; if (lk < -G) lk += nz; }
             const bool inr = li >= -G && li < T0 + G && lj >= -G && lj < T1 + G && (DIM == 2 || (lk >= -G && lk < T2 + G));
-            float fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
-            form_factor(P.off[0][p], fx, Sx);
-            form_factor(P.off[1][p], fy, Sy);
-            if (DIM == 3) {
-                form_factor(P.off[2][p], fz, Sz);
-            } else {
-                fz[0] = 1.0f; fz[1] = 0.0f; Sz[0] = 0.0f; Sz[1] = 1.0f; Sz[2] = 0.0f;
-            }
             float Ep[3], Bp[3];
-            if (inr) {
-                ZeroB rd;
-                for (int c = 0; c < 3; ++c) rd.E[c] = sE[c];
-                rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
-                rd.s1 = P0;
-                rd.s2 = P0 * P1;
-                gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
-                acc.base = rd.base;
-                const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
+            if constexpr (ORD == 5) {
+                float e3[3] = {0.5f, 0.5f, 0.5f}, w[21];
+                int u3[3] = {0, 0, 0};
+                u3[0] = split5(P.off[0][p], e3[0]);
+                u3[1] = split5(P.off[1][p], e3[1]);
+                if (DIM == 3) u3[2] = split5(P.off[2][p], e3[2]);
+                form_factor5(e3[0], w, w + 3);
+                form_factor5(e3[1], w + 7, w + 10);
+                form_factor5(e3[2], w + 14, w + 17);
+                const int nzw = DIM == 3 ? 4 : 1;
+                if (inr) {
+                    ZeroB rd;
+                    for (int c = 0; c < 3; ++c) rd.E[c] = sE[c];
+                    rd.base = (li + u3[0] + G + FH) +
+                              P0 * ((lj + u3[1] + G + FH) + (DIM == 3 ? P1 * (lk + u3[2] + G + FH) : 0));
+                    rd.s1 = P0;
+                    rd.s2 = P0 * P1;
+                    gather5<DIM>(rd, w, w + 3, w + 7, w + 10, w + 14, w + 17, Ep, Bp);
+                    acc.base = rd.base;
 #pragma unroll
-                for (int dz = kz0; dz <= kz1; ++dz)
+                    for (int dz = 0; dz < nzw; ++dz)
 #pragma unroll
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        const float t = Sy[dy + 1] * Sz[dz + 1];
+                        for (int dy = 0; dy < 4; ++dy) {
+                            const float t = w[10 + dy] * (DIM == 3 ? w[17 + dz] : 1.0f);
 #pragma unroll
-                        for (int dx = -1; dx <= 1; ++dx) acc.add(0, dx, dy, dz, kq * Sx[dx + 1], t);
+                            for (int dx = 0; dx < 4; ++dx)
+                                acc.add(0, dx - 2, dy - 2, DIM == 3 ? dz - 2 : 0, kq * w[3 + dx], t);
+                        }
+                } else {
+                    const int ib = i + u3[0], jb = j + u3[1], kb = k + u3[2];
+                    GlobalZeroB5 rd;
+                    for (int c = 0; c < 3; ++c) rd.E[c] = F.E[c];
+                    for (int q = 0; q < 5; ++q) {
+                        rd.xi[q] = cb + wrapi(ib - 2 + q, nx);
+                        rd.yj[q] = (long long)nx * wrapi(jb - 2 + q, ny);
+                        rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(kb - 2 + q, nz) : 0;
                     }
-            } else {
-                GlobalZeroB rd;
-                for (int c = 0; c < 3; ++c) rd.E[c] = F.E[c];
-                for (int q = 0; q < 4; ++q) {
-                    rd.xi[q] = cb + wrapi(i - 1 + q, nx);
-                    rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
-                    rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
+                    gather5<DIM>(rd, w, w + 3, w + 7, w + 10, w + 14, w + 17, Ep, Bp);
+                    for (int dz = 0; dz < nzw; ++dz)
+                        for (int dy = 0; dy < 4; ++dy)
+                            for (int dx = 0; dx < 4; ++dx)
+                                atomicAdd(&rho[rd.xi[dx] + rd.yj[dy] + rd.zk[DIM == 3 ? dz : 2]],
+                                          (double)qV * w[3 + dx] * w[10 + dy] * (DIM == 3 ? w[17 + dz] : 1.0f));
                 }
-                gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
-                const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
-                for (int dz = kz0; dz <= kz1; ++dz)
-                    for (int dy = -1; dy <= 1; ++dy)
-                        for (int dx = -1; dx <= 1; ++dx)
-                            atomicAdd(&rho[rd.xi[dx + 1] + rd.yj[dy + 1] + rd.zk[dz + 1]],
-                                      (double)qV * Sx[dx + 1] * Sy[dy + 1] * Sz[dz + 1]);
+            } else {
+                float fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
+                form_factor(P.off[0][p], fx, Sx);
+                form_factor(P.off[1][p], fy, Sy);
+                if (DIM == 3) {
+                    form_factor(P.off[2][p], fz, Sz);
+                } else {
+                    fz[0] = 1.0f; fz[1] = 0.0f; Sz[0] = 0.0f; Sz[1] = 1.0f; Sz[2] = 0.0f;
+                }
+                if (inr) {
+                    ZeroB rd;
+                    for (int c = 0; c < 3; ++c) rd.E[c] = sE[c];
+                    rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
+                    rd.s1 = P0;
+                    rd.s2 = P0 * P1;
+                    gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                    acc.base = rd.base;
+                    const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
+#pragma unroll
+                    for (int dz = kz0; dz <= kz1; ++dz)
+#pragma unroll
+                        for (int dy = -1; dy <= 1; ++dy) {
+                            const float t = Sy[dy + 1] * Sz[dz + 1];
+#pragma unroll
+                            for (int dx = -1; dx <= 1; ++dx) acc.add(0, dx, dy, dz, kq * Sx[dx + 1], t);
+                        }
+                } else {
+                    GlobalZeroB rd;
+                    for (int c = 0; c < 3; ++c) rd.E[c] = F.E[c];
+                    for (int q = 0; q < 4; ++q) {
+                        rd.xi[q] = cb + wrapi(i - 1 + q, nx);
+                        rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
+                        rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
+                    }
+                    gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                    const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
+                    for (int dz = kz0; dz <= kz1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx)
+                                atomicAdd(&rho[rd.xi[dx + 1] + rd.yj[dy + 1] + rd.zk[dz + 1]],
+                                          (double)qV * Sx[dx + 1] * Sy[dy + 1] * Sz[dz + 1]);
+                }
             }
             const float w0 = P.w[0][p], w1 = P.w[1][p], w2 = P.w[2][p];
             const float ww = w0 * w0 + w1 * w1 + w2 * w2;
@@ -268,9 +362,9 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const W
             const int h = rh[l], lo = rl[l];
             if ((h | lo) == 0) continue;
             const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
-            const int gx = wrapi(ox - G - 1 + lx, nx);
-            const int gy = wrapi(oy - G - 1 + ly, ny);
-            const int gz = DIM == 3 ? wrapi(oz - G - 1 + lz, nz) : 0;
+            const int gx = wrapi(ox - G - FH + lx, nx);
+            const int gy = wrapi(oy - G - FH + ly, ny);
+            const int gz = DIM == 3 ? wrapi(oz - G - FH + lz, nz) : 0;
             atomicAdd(&rho[cb + gx + (long long)nx * (gy + (long long)ny * gz)], ((double)h * 65536.0 + (double)lo) * rinv);
         }
         __syncthreads();
@@ -358,7 +452,7 @@ __global__ void k_diag_final(const double *pp, int np, const double *pc, int nc,
     }
 }
 
-template <int DIM, typename R>
+template <int DIM, typename R, int ORD>
 static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run, long long run_cells,
                           const GroupDev *groups, const long long *group_base, int ngroups, long long total,
                           const PoolBuf &P, void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
@@ -388,10 +482,10 @@ static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run, long lon
             ff.B[c] = (float *)B[c];
             ff.J[c] = nullptr;
         }
-        k_diag_items<DIM><<<np_blocks, kDiagThreads, items_smem, st>>>(run, items, n_items, groups, runs, pf, ff, halo,
+        k_diag_items<DIM, ORD><<<np_blocks, kDiagThreads, items_smem, st>>>(run, items, n_items, groups, runs, pf, ff, halo,
                                                                        scr.rho, scr.partials);
     } else {
-        k_diag_particles<DIM, R><<<np_blocks, kDiagThreads, 0, st>>>(run, total, group_base, ngroups, groups, runs,
+        k_diag_particles<DIM, R, ORD><<<np_blocks, kDiagThreads, 0, st>>>(run, total, group_base, ngroups, groups, runs,
                                                                      pool, F, scr.rho, scr.partials);
     }
     k_diag_cells<DIM, R><<<nc_blocks, kDiagThreads, 0, st>>>(runs, run, F, scr.rho, scr.resid_ref, set_ref,
@@ -402,38 +496,59 @@ static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run, long lon
     return cudaGetLastError();
 }
 
+template <int ORD>
+static cudaError_t diag_run_o(int dims, int prec, cudaStream_t st, const RunDev *runs, int run, long long run_cells,
+                              const GroupDev *groups, const long long *group_base, int ngroups, long long total,
+                              const PoolBuf &P, void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
+                              int np_blocks, int nc_blocks, int *launches, const WorkItem *items, const int *n_items,
+                              int halo, size_t items_smem)
+{
+    if (dims == 3)
+        return prec == 0 ? diag_t<3, double, ORD>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E,
+                                                  B, scr, set_ref, np_blocks, nc_blocks, launches, nullptr, nullptr,
+                                                  halo, 0)
+                         : diag_t<3, float, ORD>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E,
+                                                 B, scr, set_ref, np_blocks, nc_blocks, launches, items, n_items,
+                                                 halo, items_smem);
+    return prec == 0 ? diag_t<2, double, ORD>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
+                                              scr, set_ref, np_blocks, nc_blocks, launches, nullptr, nullptr, halo, 0)
+                     : diag_t<2, float, ORD>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
+                                             scr, set_ref, np_blocks, nc_blocks, launches, items, n_items, halo,
+                                             items_smem);
+}
+
 cudaError_t launch_diagnostics_run(int dims, int prec, cudaStream_t st, const RunDev *runs, int run,
                                    long long run_cells, long long cell_base, const GroupDev *groups,
                                    const long long *group_base, int ngroups, long long total, const PoolBuf &P,
                                    void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
                                    int np_blocks, int nc_blocks, int *launches, const WorkItem *items,
-                                   const int *n_items, int halo, const int tile[3], const int pitch[2])
+                                   const int *n_items, int halo, const int tile[3], const int pitch[2], int order2)
 {
     cudaError_t e = cudaMemsetAsync(scr.rho + cell_base, 0, sizeof(double) * run_cells, st);
     if (e != cudaSuccess) return e;
-    const size_t items_smem = diag_items_smem_bytes(dims, tile, halo, pitch);
-    if (dims == 3)
-        return prec == 0 ? diag_t<3, double>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
-                                             scr, set_ref, np_blocks, nc_blocks, launches, nullptr, nullptr, halo, 0)
-                         : diag_t<3, float>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
-                                            scr, set_ref, np_blocks, nc_blocks, launches, items, n_items, halo,
-                                            items_smem);
-    return prec == 0 ? diag_t<2, double>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
-                                         set_ref, np_blocks, nc_blocks, launches, nullptr, nullptr, halo, 0)
-                     : diag_t<2, float>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
-                                        set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
+    const size_t items_smem = diag_items_smem_bytes(dims, tile, halo, pitch, order2);
+    if (order2 == 5)
+        return diag_run_o<5>(dims, prec, st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
+                             set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
+    return diag_run_o<3>(dims, prec, st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
+                         set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
 }
 
-size_t diag_items_smem_bytes(int dims, const int tile[3], int halo, const int pitch[2])
+size_t diag_items_smem_bytes(int dims, const int tile[3], int halo, const int pitch[2], int order2)
 {
-    const long long fe2 = dims == 3 ? tile[2] + 2 * halo + 2 : 1;
+    const int fh = order2 == 5 ? 2 : 1;
+    const long long fe2 = dims == 3 ? tile[2] + 2 * (halo + fh) : 1;
     return (size_t)5 * pitch[0] * pitch[1] * fe2 * sizeof(float);
 }
 
-cudaError_t diag_set_smem_limit(int dims, size_t bytes)
+cudaError_t diag_set_smem_limit(int dims, size_t bytes, int order2)
 {
-    return dims == 3 ? cudaFuncSetAttribute(k_diag_items<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
-                     : cudaFuncSetAttribute(k_diag_items<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const int b = (int)bytes;
+    if (order2 == 5)
+        return dims == 3 ? cudaFuncSetAttribute(k_diag_items<3, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)
+                         : cudaFuncSetAttribute(k_diag_items<2, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return dims == 3 ? cudaFuncSetAttribute(k_diag_items<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)
+                     : cudaFuncSetAttribute(k_diag_items<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
 }  // namespace pic

@@ -42,8 +42,10 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
                              const int *n_items, int max_items, const RunDev *runs, const GroupDev *groups,
                              const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
                              int *old_cell, void *const old_off[3], int halo, int max_tile_x,
-                             int max_tile_y, int max_tile_z, int *err, int p0, int p1);
-size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo, int p0, int p1);
+                             int max_tile_y, int max_tile_z, int *err, int p0, int p1, int order2 = 3);
+// order2 = 3: l_a = 1 1/2; 5: l_a = 2 1/2 (tiles one cell wider on every side).
+size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo, int p0, int p1,
+                            int order2 = 3);
 // One cooperative launch per step over every run (see k_step_persistent);
 // *grid_blocks = 0 asks for the occupancy-derived grid and returns it; launch = 0
 // only prepares (attributes and grid size), which must happen outside a capture.
@@ -52,7 +54,7 @@ cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const Wo
                                    void *const B[3], void *const J[3], int halo, int tx, int ty, int tz, int *err,
                                    int nruns, const long long *run_cell_base, int *grid_blocks, int launch, int p0,
                                    int p1, long long *ant_n, int antennas);
-cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes);
+cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes, int order2 = 3);
 
 cudaError_t launch_load(int prec, cudaStream_t st, long long n, const double *x0, const double *x1,
                         const double *x2, const double *w0, const double *w1, const double *w2,
@@ -108,9 +110,10 @@ cudaError_t launch_diagnostics_run(int dims, int prec, cudaStream_t st, const Ru
                                    const long long *group_base, int ngroups, long long total, const PoolBuf &P,
                                    void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
                                    int np_blocks, int nc_blocks, int *launches, const WorkItem *items,
-                                   const int *n_items, int halo, const int tile[3], const int pitch[2]);
-size_t diag_items_smem_bytes(int dims, const int tile[3], int halo, const int pitch[2]);
-cudaError_t diag_set_smem_limit(int dims, size_t bytes);
+                                   const int *n_items, int halo, const int tile[3], const int pitch[2],
+                                   int order2 = 3);
+size_t diag_items_smem_bytes(int dims, const int tile[3], int halo, const int pitch[2], int order2 = 3);
+cudaError_t diag_set_smem_limit(int dims, size_t bytes, int order2 = 3);
 constexpr int kDiagResults = 12;
 
 void set_last_error(const char *msg);
@@ -184,6 +187,7 @@ struct pic_grid {
     unsigned *h_drift = nullptr;    // pinned host copy of the drift count (d_err[1])
     void *h_hdr = nullptr;          // pinned host copies of snapshot headers (pic_adjoint_steps)
     size_t h_hdr_cap = 0;
+    int order2 = 3;                 // twice the alternating order: 3 (l_a = 1 1/2) or 5 (l_a = 2 1/2)
     int adj_fits = 1;               // the tiled adjoint's shared memory fits the device
     int adj_tiled = 1;              // adjoint particle kernel over work items with shared-memory tiles (FP32 default)
     int adaptive_sort = 0;          // sort when the particle kernel's accumulated slowdown exceeds a sort

@@ -15,11 +15,13 @@ static cudaError_t launch_mode(int mode, cudaStream_t st, int max_items, size_t 
     }
 }
 
-size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo, int p0, int p1)
+size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo, int p0, int p1,
+                            int order2)
 {
     const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
-    const long long fe = (long long)p0 * p1 * (dims == 3 ? tz + 2 * halo + 2 : 1);
-    const long long je = (long long)p0 * p1 * (dims == 3 ? tz + 2 * halo + 4 : 1);
+    const int ext = order2 == 5 ? 1 : 0;   // l_a = 2 1/2 reaches one cell further
+    const long long fe = (long long)p0 * p1 * (dims == 3 ? tz + 2 * (halo + 1 + ext) : 1);
+    const long long je = (long long)p0 * p1 * (dims == 3 ? tz + 2 * (halo + 2 + ext) : 1);
     size_t b = 0;
     if (mode != 2) b += 6 * fe * es;
     if (mode != 1) b += (prec == 0 ? 24 : 28) * je + (size_t)(kThreads / 32) * kQueueCap * (kQueueVals * es + sizeof(int));
@@ -37,8 +39,9 @@ static cudaError_t set_limit_t(int mode, size_t bytes)
     }
 }
 
-cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes)
+cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes, int order2)
 {
+    if (order2 == 5) return particles_o5_set_smem_limit(dims, prec, mode, bytes);
     if (prec != 0 && mode == 0) {
         const cudaError_t e = fixed_set_smem_limit(dims, bytes);
         if (e != cudaSuccess) return e;
@@ -47,39 +50,18 @@ cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes)
     return prec == 0 ? set_limit_t<2, double>(mode, bytes) : set_limit_t<2, float>(mode, bytes);
 }
 
-template <typename R>
-static PartArgs<R> make_args(const WorkItem *items, const int *n_items, const RunDev *runs, const GroupDev *groups,
-                             const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3], int *old_cell,
-                             void *const old_off[3], int halo, int *err)
-{
-    PartArgs<R> a;
-    a.items = items;
-    a.n_items = n_items;
-    a.runs = runs;
-    a.groups = groups;
-    a.P.cell = P.cell;
-    a.P.id = P.id;
-    for (int c = 0; c < 3; ++c) {
-        a.P.off[c] = static_cast<R *>(P.off[c]);
-        a.P.w[c] = static_cast<R *>(P.w[c]);
-        a.F.E[c] = static_cast<R *>(E[c]);
-        a.F.B[c] = static_cast<R *>(B[c]);
-        a.F.J[c] = static_cast<R *>(J[c]);
-        a.old_off[c] = static_cast<R *>(old_off[c]);
-    }
-    a.old_cell = old_cell;
-    a.halo = halo;
-    a.err = err;
-    return a;
-}
 
 cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, const WorkItem *items,
                              const int *n_items, int max_items, const RunDev *runs, const GroupDev *groups,
                              const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
                              int *old_cell, void *const old_off[3], int halo, int max_tile_x, int max_tile_y,
-                             int max_tile_z, int *err, int p0, int p1)
+                             int max_tile_z, int *err, int p0, int p1, int order2)
 {
-    const size_t smem = particles_smem_bytes(dims, prec, mode, max_tile_x, max_tile_y, max_tile_z, halo, p0, p1);
+    const size_t smem =
+        particles_smem_bytes(dims, prec, mode, max_tile_x, max_tile_y, max_tile_z, halo, p0, p1, order2);
+    if (order2 == 5)
+        return launch_particles_o5(dims, prec, mode, st, max_items, smem, items, n_items, runs, groups, P, E, B, J,
+                                   old_cell, old_off, halo, err);
     if (prec == 0) {
         auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
         return dims == 3 ? launch_mode<3, double>(mode, st, max_items, smem, a)

@@ -105,13 +105,46 @@ __device__ __noinline__ void deposit_global(const Fields<R> &F, long long cb, in
     deposit<DIM>(acc, win[0], win[1], win[2], kf, uz, 7);
 }
 
+// The same for l_a = 2 1/2; (i, j, k) is the particle's base index.
+template <int DIM, typename R>
+__device__ __noinline__ void gather_global5(const Fields<R> &F, long long cb, int i, int j, int k, int nx, int ny,
+                                            int nz, const R *w, R *Ep, R *Bp)
+{
+    GlobalReader5<R> rd;
+    for (int c = 0; c < 3; ++c) { rd.E[c] = F.E[c]; rd.B[c] = F.B[c]; }
+    for (int q = 0; q < 5; ++q) {
+        rd.xi[q] = cb + wrapi(i - 2 + q, nx);
+        rd.yj[q] = (long long)nx * wrapi(j - 2 + q, ny);
+        rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 2 + q, nz) : 0;
+    }
+    // w: f (3) and S (4) per axis
+    gather5<DIM>(rd, w, w + 3, w + 7, w + 10, w + 14, w + 17, Ep, Bp);
+}
+
+template <int DIM, typename R>
+__device__ __noinline__ void deposit_global5(const Fields<R> &F, long long cb, int i, int j, int k, int nx, int ny,
+                                             int nz, const AxisWin5<R> *win, const R *kf, R uz)
+{
+    GlobalAcc<R> acc;
+    for (int c = 0; c < 3; ++c) acc.J[c] = F.J[c];
+    acc.cell_base = cb;
+    acc.i = i; acc.j = j; acc.k = k;
+    acc.nx = nx; acc.ny = ny; acc.nz = nz;
+    deposit5<DIM>(acc, win[0], win[1], win[2], kf, uz, 7);
+}
+
 // MODE 0: fused gather + push + move + deposit (pic_step).
 // MODE 1: gather + push + move, keeping x^n (pic_gather_push).
 // MODE 2: deposit from the kept x^n and the current x^{n+1} (pic_deposit_current).
 // Shared memory: E and B tiles (6 * nf values of R) for MODES 0, 1; the current
 // tile for MODES 0, 2: in FP32 two int32 fixed-point words per value, in FP64
 // one double -- 24 * nj bytes either way.
-template <int DIM, typename R, int MODE, class GEO>
+// ORD = 3 is l_a = 1 1/2, ORD = 5 is l_a = 2 1/2 (Sec. 4.5): its stencil
+// reaches one cell further, so the field tile has a halo of (halo + 2) cells
+// and the current tile one of (halo + 3), and every particle deposits through
+// the bias-removing accumulator (the per-cell counts serve the l_a = 1 1/2
+// stencil only).
+template <int DIM, typename R, int MODE, class GEO, int ORD = 3>
 __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
 {
     constexpr bool FIX = sizeof(R) == 4;
@@ -126,8 +159,9 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     const int ty = (it.tile / rn.ntile[0]) % rn.ntile[1];
     const int tz = DIM == 3 ? it.tile / (rn.ntile[0] * rn.ntile[1]) : 0;
     const int ox = tx * T0, oy = ty * T1, oz = tz * T2;
-    const int fe0 = T0 + 2 * G + 2, fe1 = T1 + 2 * G + 2, fe2 = DIM == 3 ? T2 + 2 * G + 2 : 1;
-    const int je0 = T0 + 2 * G + 4, je1 = T1 + 2 * G + 4, je2 = DIM == 3 ? T2 + 2 * G + 4 : 1;
+    constexpr int FH = ORD == 5 ? 2 : 1, JH = ORD == 5 ? 3 : 2;   // field and current halo beyond G
+    const int fe0 = T0 + 2 * (G + FH), fe1 = T1 + 2 * (G + FH), fe2 = DIM == 3 ? T2 + 2 * (G + FH) : 1;
+    const int je0 = T0 + 2 * (G + JH), je1 = T1 + 2 * (G + JH), je2 = DIM == 3 ? T2 + 2 * (G + JH) : 1;
     // the field tile is stored with the current tile's x and y pitches, so that
     // a particle's field and current bases differ by a constant and one bank
     // order of the particles (set by the tile sort) serves both
@@ -163,9 +197,9 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         for (int l = threadIdx.x; l < nf; l += blockDim.x) {
             const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
             if (lx >= fe0 || ly >= fe1) continue;   // pitch padding
-            const int gx = wrapi(ox - G - 1 + lx, nx);
-            const int gy = wrapi(oy - G - 1 + ly, ny);
-            const int gz = DIM == 3 ? wrapi(oz - G - 1 + lz, nz) : 0;
+            const int gx = wrapi(ox - G - FH + lx, nx);
+            const int gy = wrapi(oy - G - FH + ly, ny);
+            const int gz = DIM == 3 ? wrapi(oz - G - FH + lz, nz) : 0;
             const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -235,6 +269,24 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             deposit<DIM>(acc, X, Y, Z, kf, uz, full);
         }
     };
+    auto deposit_local5 = [&](int base, const AxisWin5<R> &X, const AxisWin5<R> &Y, const AxisWin5<R> &Z, R uz,
+                              int full) {
+        if constexpr (FIX) {
+            FixedAcc acc;
+            for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
+            acc.base = base;
+            acc.s1 = P0;
+            acc.s2 = P0 * P1;
+            deposit5<DIM>(acc, X, Y, Z, kfs, uz, full);
+        } else {
+            SmemAcc<R> acc;
+            for (int c = 0; c < 3; ++c) acc.J[c] = sJ[c];
+            acc.base = base;
+            acc.s1 = P0;
+            acc.s2 = P0 * P1;
+            deposit5<DIM>(acc, X, Y, Z, kf, uz, full);
+        }
+    };
     // deposits the queue entries [first, first + 32) whose lanes have `on`
     auto drain = [&](int first, bool on) {
         const int slot = first + lane;
@@ -257,11 +309,19 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         const int full = (__any_sync(0xffffffffu, q0 != 0) ? 1 : 0) | (__any_sync(0xffffffffu, q1 != 0) ? 2 : 0) |
                          (DIM == 3 && __any_sync(0xffffffffu, q2 != 0) ? 4 : 0);
         if (on) {
-            AxisWin<R> X, Y, Z;
-            axis_window(d0, e0, q0, X);
-            axis_window(d1, e1, q1, Y);
-            if (DIM == 3) axis_window(d2, e2, q2, Z); else Z = X;
-            deposit_local(code >> 8, X, Y, Z, u, full);
+            if constexpr (ORD == 5) {   // the entries hold the l_a = 2 1/2 d values
+                AxisWin5<R> X, Y, Z;
+                axis_window5(d0, e0, q0, X);
+                axis_window5(d1, e1, q1, Y);
+                if (DIM == 3) axis_window5(d2, e2, q2, Z); else Z = X;
+                deposit_local5(code >> 8, X, Y, Z, u, full);
+            } else {
+                AxisWin<R> X, Y, Z;
+                axis_window(d0, e0, q0, X);
+                axis_window(d1, e1, q1, Y);
+                if (DIM == 3) axis_window(d2, e2, q2, Z); else Z = X;
+                deposit_local(code >> 8, X, Y, Z, u, full);
+            }
         }
     };
 
@@ -302,27 +362,47 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             n0 = o0; n1 = o1; n2 = o2;
             live = true;
             if (MODE != 2) {
-                R fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
-                form_factor(o0, fx, Sx);
-                form_factor(o1, fy, Sy);
-                if (DIM == 3) {
-                    form_factor(o2, fz, Sz);
-                } else {
-                    fz[0] = R(1); fz[1] = R(0);
-                    Sz[0] = R(0); Sz[1] = R(1); Sz[2] = R(0);
-                }
                 R Ep[3], Bp[3];
-                if (inr) {
-                    SmemReader<R> rd;
-                    for (int c = 0; c < 3; ++c) { rd.E[c] = sE[c]; rd.B[c] = sB[c]; }
-                    rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
-                    rd.s1 = P0;
-                    rd.s2 = P0 * P1;
-                    gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                if constexpr (ORD == 5) {
+                    R e0, e1, e2 = R(0.5);
+                    const int u0 = split5(o0, e0), u1 = split5(o1, e1), u2 = DIM == 3 ? split5(o2, e2) : 0;
+                    R w[21];   // f (3) and S (4) along x, y, z
+                    form_factor5(e0, w, w + 3);
+                    form_factor5(e1, w + 7, w + 10);
+                    form_factor5(e2, w + 14, w + 17);
+                    if (inr) {
+                        SmemReader<R> rd;
+                        for (int c = 0; c < 3; ++c) { rd.E[c] = sE[c]; rd.B[c] = sB[c]; }
+                        rd.base = (li + u0 + G + FH) +
+                                  P0 * ((lj + u1 + G + FH) + (DIM == 3 ? P1 * (lk + u2 + G + FH) : 0));
+                        rd.s1 = P0;
+                        rd.s2 = P0 * P1;
+                        gather5<DIM>(rd, w, w + 3, w + 7, w + 10, w + 14, w + 17, Ep, Bp);
+                    } else {
+                        gather_global5<DIM, R>(a.F, cb, i + u0, j + u1, k + u2, nx, ny, nz, w, Ep, Bp);
+                    }
                 } else {
-                    R w6[15] = {fx[0], fx[1], Sx[0], Sx[1], Sx[2], fy[0], fy[1], Sy[0], Sy[1], Sy[2],
-                                fz[0], fz[1], Sz[0], Sz[1], Sz[2]};
-                    gather_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, w6, Ep, Bp);
+                    R fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
+                    form_factor(o0, fx, Sx);
+                    form_factor(o1, fy, Sy);
+                    if (DIM == 3) {
+                        form_factor(o2, fz, Sz);
+                    } else {
+                        fz[0] = R(1); fz[1] = R(0);
+                        Sz[0] = R(0); Sz[1] = R(1); Sz[2] = R(0);
+                    }
+                    if (inr) {
+                        SmemReader<R> rd;
+                        for (int c = 0; c < 3; ++c) { rd.E[c] = sE[c]; rd.B[c] = sB[c]; }
+                        rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
+                        rd.s1 = P0;
+                        rd.s2 = P0 * P1;
+                        gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                    } else {
+                        R w6[15] = {fx[0], fx[1], Sx[0], Sx[1], Sx[2], fy[0], fy[1], Sy[0], Sy[1], Sy[2],
+                                    fz[0], fz[1], Sz[0], Sz[1], Sz[2]};
+                        gather_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, w6, Ep, Bp);
+                    }
                 }
                 boris(w, Ep, Bp, hq, c2);
                 if (!finite3(w[0], w[1], w[2])) {
@@ -376,47 +456,82 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         if (MODE == 1) continue;
 
         // ---- virtual-path current (Eq. current) -------------------------------
-        const bool moved = (s0 | s1 | s2) != 0;
-        const int base = (li + G + 2) + P0 * ((lj + G + 2) + (DIM == 3 ? P1 * (lk + G + 2) : 0));
+        // The windows take the d values and shifts of the base index: for
+        // l_a = 1 1/2 the offsets and cell shifts themselves; for l_a = 2 1/2 the
+        // base index is cell + (offset >= 1/2), so it moves with the cell shift
+        // and the half-offset flags.
+        int q0 = s0, q1 = s1, q2 = s2;
+        R a0 = o0, a1 = o1, a2 = o2, b0 = n0, b1 = n1, b2 = n2;
+        int ub0 = 0, ub1 = 0, ub2 = 0;   // old base index - old cell
+        if constexpr (ORD == 5) {
+            ub0 = split5(o0, a0);
+            ub1 = split5(o1, a1);
+            const int v0 = split5(n0, b0), v1 = split5(n1, b1);
+            q0 = s0 + v0 - ub0;
+            q1 = s1 + v1 - ub1;
+            if (DIM == 3) {
+                ub2 = split5(o2, a2);
+                q2 = s2 + split5(n2, b2) - ub2;
+            }
+        }
+        const bool moved = (q0 | q1 | q2) != 0;
+        const int base = (li + ub0 + G + JH) +
+                         P0 * ((lj + ub1 + G + JH) + (DIM == 3 ? P1 * (lk + ub2 + G + JH) : 0));
         if (live && inr && !moved) {
-            AxisWin<R> X, Y, Z;
-            axis_window_still(o0, n0, X);
-            axis_window_still(o1, n1, Y);
-            if (DIM == 3) axis_window_still(o2, n2, Z); else Z = X;
-            if constexpr (FIX) {
-                // fixed stencil: the bias comes off once per word at the flush
-                FixedAccT<false> acc;
-                for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
-                acc.base = base;
-                acc.s1 = P0;
-                acc.s2 = P0 * P1;
-                deposit<DIM>(acc, X, Y, Z, kfs, uz, 0);
-                atomicAdd(&scnt[base], 1);
+            if constexpr (ORD == 5) {
+                AxisWin5<R> X, Y, Z;
+                axis_window5(a0, b0, 0, X);
+                axis_window5(a1, b1, 0, Y);
+                if (DIM == 3) axis_window5(a2, b2, 0, Z); else Z = X;
+                deposit_local5(base, X, Y, Z, uz, 0);
             } else {
-                deposit_local(base, X, Y, Z, uz, 0);
+                AxisWin<R> X, Y, Z;
+                axis_window_still(o0, n0, X);
+                axis_window_still(o1, n1, Y);
+                if (DIM == 3) axis_window_still(o2, n2, Z); else Z = X;
+                if constexpr (FIX) {
+                    // fixed stencil: the bias comes off once per word at the flush
+                    FixedAccT<false> acc;
+                    for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
+                    acc.base = base;
+                    acc.s1 = P0;
+                    acc.s2 = P0 * P1;
+                    deposit<DIM>(acc, X, Y, Z, kfs, uz, 0);
+                    atomicAdd(&scnt[base], 1);
+                } else {
+                    deposit_local(base, X, Y, Z, uz, 0);
+                }
             }
         } else if (live && !inr) {
-            AxisWin<R> win[3];
-            axis_window(o0, n0, s0, win[0]);
-            axis_window(o1, n1, s1, win[1]);
-            if (DIM == 3) axis_window(o2, n2, s2, win[2]); else win[2] = win[0];
-            deposit_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, win, kf, uz);
+            if constexpr (ORD == 5) {
+                AxisWin5<R> win[3];
+                axis_window5(a0, b0, q0, win[0]);
+                axis_window5(a1, b1, q1, win[1]);
+                if (DIM == 3) axis_window5(a2, b2, q2, win[2]); else win[2] = win[0];
+                deposit_global5<DIM, R>(a.F, cb, i + ub0, j + ub1, k + ub2, nx, ny, nz, win, kf, uz);
+            } else {
+                AxisWin<R> win[3];
+                axis_window(o0, n0, s0, win[0]);
+                axis_window(o1, n1, s1, win[1]);
+                if (DIM == 3) axis_window(o2, n2, s2, win[2]); else win[2] = win[0];
+                deposit_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, win, kf, uz);
+            }
         }
         const bool enq = live && inr && moved;
         const unsigned qm = __ballot_sync(0xffffffffu, enq);
         if (enq) {
             const int slot = qn + __popc(qm & ((1u << lane) - 1u));
-            qv[0 * kQueueCap + slot] = o0;
-            qv[1 * kQueueCap + slot] = o1;
-            qv[3 * kQueueCap + slot] = n0;
-            qv[4 * kQueueCap + slot] = n1;
+            qv[0 * kQueueCap + slot] = a0;
+            qv[1 * kQueueCap + slot] = a1;
+            qv[3 * kQueueCap + slot] = b0;
+            qv[4 * kQueueCap + slot] = b1;
             if (DIM == 3) {
-                qv[2 * kQueueCap + slot] = o2;
-                qv[5 * kQueueCap + slot] = n2;
+                qv[2 * kQueueCap + slot] = a2;
+                qv[5 * kQueueCap + slot] = b2;
             } else {
                 qv[6 * kQueueCap + slot] = uz;
             }
-            qs[slot] = (base << 8) | (s0 + 1) | ((s1 + 1) << 2) | ((s2 + 1) << 4);
+            qs[slot] = (base << 8) | (q0 + 1) | ((q1 + 1) << 2) | ((q2 + 1) << 4);
         }
         qn += __popc(qm);
         if (qn >= 32) {   // warp-uniform
@@ -437,9 +552,9 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         for (int l = threadIdx.x; l < nj; l += blockDim.x) {
             const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
             if (lx >= je0 || ly >= je1) continue;   // pitch padding
-            const int gx = wrapi(ox - G - 2 + lx, nx);
-            const int gy = wrapi(oy - G - 2 + ly, ny);
-            const int gz = DIM == 3 ? wrapi(oz - G - 2 + lz, nz) : 0;
+            const int gx = wrapi(ox - G - JH + lx, nx);
+            const int gy = wrapi(oy - G - JH + ly, ny);
+            const int gz = DIM == 3 ? wrapi(oz - G - JH + lz, nz) : 0;
             const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
             // FP32: contributions of particles that stayed in their cell, per
             // component: the stencil of such a particle with base b covers the
@@ -447,7 +562,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             // for J^x (faces 0, 1; cells -1..1), likewise for J^y and J^z, so a
             // cell l received sum_{b in l - stencil} cnt[b] of them
             unsigned nst[3] = {0u, 0u, 0u};
-            if constexpr (FIX) {
+            if constexpr (FIX && ORD == 3) {
                 if (lx >= 1 && lx < je0 - 1 && ly >= 1 && ly < je1 - 1 && (DIM == 2 || (lz >= 1 && lz < je2 - 1))) {
                     if (DIM == 3) {
                         unsigned tot = 0, px = 0, py = 0, pz = 0;   // all 27, and the +1 planes
@@ -500,11 +615,11 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     __syncthreads();   // the shared tiles are free for the block's next item
 }
 
-template <int DIM, typename R, int MODE, class GEO = GeoDyn>
+template <int DIM, typename R, int MODE, class GEO = GeoDyn, int ORD = 3>
 __global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
 {
     if ((int)blockIdx.x >= *a.n_items) return;
-    process_item<DIM, R, MODE, GEO>(a, blockIdx.x);
+    process_item<DIM, R, MODE, GEO, ORD>(a, blockIdx.x);
 }
 
 // Run of a batch that owns concatenated cell l (run_cell_base has nruns + 1 entries).
@@ -555,11 +670,11 @@ __global__ void __launch_bounds__(kThreads) k_step_persistent(const PartArgs<R> 
     }
 }
 
-template <int DIM, typename R, int MODE, class GEO = GeoDyn>
+template <int DIM, typename R, int MODE, class GEO = GeoDyn, int ORD = 3>
 static cudaError_t launch_t(cudaStream_t st, int max_items, size_t smem, const PartArgs<R> &a)
 {
     if (max_items <= 0) return cudaSuccess;
-    k_particles<DIM, R, MODE, GEO><<<max_items, kThreads, smem, st>>>(a);
+    k_particles<DIM, R, MODE, GEO, ORD><<<max_items, kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -586,6 +701,33 @@ static cudaError_t persistent_t(cudaStream_t st, size_t smem, int nruns, const l
     return cudaLaunchCooperativeKernel((const void *)fn, dim3(*grid_blocks), dim3(kThreads), args, smem, st);
 }
 
+// Kernel arguments from the host-side buffers.
+template <typename R>
+inline PartArgs<R> make_args(const WorkItem *items, const int *n_items, const RunDev *runs, const GroupDev *groups,
+                             const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3], int *old_cell,
+                             void *const old_off[3], int halo, int *err)
+{
+    PartArgs<R> a;
+    a.items = items;
+    a.n_items = n_items;
+    a.runs = runs;
+    a.groups = groups;
+    a.P.cell = P.cell;
+    a.P.id = P.id;
+    for (int c = 0; c < 3; ++c) {
+        a.P.off[c] = static_cast<R *>(P.off[c]);
+        a.P.w[c] = static_cast<R *>(P.w[c]);
+        a.F.E[c] = static_cast<R *>(E[c]);
+        a.F.B[c] = static_cast<R *>(B[c]);
+        a.F.J[c] = static_cast<R *>(J[c]);
+        a.old_off[c] = static_cast<R *>(old_off[c]);
+    }
+    a.old_cell = old_cell;
+    a.halo = halo;
+    a.err = err;
+    return a;
+}
+
 // Kernels with a fixed tile geometry (pic_particles_fixed.cu), FP32 fused step
 // and persistent batch step.  Each returns false, without launching, when no
 // fixed kernel has the grid's geometry.
@@ -595,5 +737,12 @@ bool launch_persistent_fixed(int dims, cudaStream_t st, size_t smem, int nruns, 
                              const PartArgs<float> &a, int *grid_blocks, int launch, const int tile[3], int halo,
                              int p0, int p1, long long *ant_n, int antennas, cudaError_t *err);
 cudaError_t fixed_set_smem_limit(int dims, size_t bytes);
+
+// The l_a = 2 1/2 particle kernels (pic_particles_o5.cu), any tile geometry.
+cudaError_t launch_particles_o5(int dims, int prec, int mode, cudaStream_t st, int max_items, size_t smem,
+                                const WorkItem *items, const int *n_items, const RunDev *runs, const GroupDev *groups,
+                                const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
+                                int *old_cell, void *const old_off[3], int halo, int *err);
+cudaError_t particles_o5_set_smem_limit(int dims, int prec, int mode, size_t bytes);
 
 }  // namespace pic

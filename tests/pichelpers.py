@@ -46,8 +46,8 @@ def fp64_field_tol(wl, species, tol=FP64_TOL):
     return max(tol, 4 * float(np.spacing(n_max)) / max(delta, 1e-300))
 
 
-def oracle_grid(wl):
-    return O.Grid(wl.dims, wl.n, wl.d, wl.dt, wl.c)
+def oracle_grid(wl, order2=3):
+    return O.Grid(wl.dims, wl.n, wl.d, wl.dt, wl.c, order2)
 
 
 def oracle_species(wl):
@@ -93,11 +93,13 @@ def compare_particles(wl, sp_index, grid, osp, tol, check_cells=True):
         close(w[a][order], ref.w[a], tol, f"species {sp_index} w[{a}]")
 
 
-def make_grid(P, wl, precision, stream=None, tile=None, halo=-1, sort_interval=None, ppb=0, sort_order=0):
+def make_grid(P, wl, precision, stream=None, tile=None, halo=-1, sort_interval=None, ppb=0, sort_order=0,
+              order2=3):
     desc = P.make_desc(wl.dims, wl.n, wl.d, wl.dt, wl.c, precision,
                        tile=tile if tile is not None else wl.tile, halo=halo,
                        sort_interval=sort_interval if sort_interval is not None else wl.sort_interval,
-                       particles_per_block=ppb, rho_bg=wl.rho_bg, stream=stream, sort_order=sort_order)
+                       particles_per_block=ppb, rho_bg=wl.rho_bg, stream=stream, sort_order=sort_order,
+                       order2=order2)
     grid = P.Grid(desc)
     for s, sp in enumerate(wl.species):
         grid.load(s, sp.q, sp.m, sp.weight, sp.x, sp.w)
