@@ -65,7 +65,7 @@ class Grid:
     d: tuple = (1.0, 1.0, 1.0)
     dt: float = 0.5
     c: float = 1.0
-    order2: int = 3   # twice the alternating order l_a: 3 (l_a = 1 1/2) or 5 (l_a = 2 1/2)
+    order2: int = 3   # 3: l_a = 1 1/2; 5: l_a = 2 1/2; 4: the uniform l = 2 comparison scheme (Eq. wrong1)
 
     def cstruct(self):
         nz = self.n[2] if self.dims == 3 else 1
@@ -259,7 +259,7 @@ def step_adj(g: Grid, E, Bh, species, lamE, lamB, lam_x, lam_w):
     at n).  lamE, lamB (fields) and lam_x, lam_w (one (3, n) float64 array per
     species) hold dL/d(state n+1) on entry and dL/d(state n) on return.
     Written for l_a = 1 1/2 only."""
-    if g.order2 == 5:
+    if g.order2 in (4, 5):
         raise NotImplementedError("the oracle's adjoint is written for l_a = 1 1/2")
     arr = _species_array(species)
     LX = (_P * len(species))(*[_ptr(a) for a in lam_x])

@@ -40,7 +40,8 @@ typedef struct {
     int nx, ny, nz;        /* cells per axis (nz == 1 when dims == 2) */
     double dx, dy, dz;     /* cell sizes */
     double dt, c;          /* time step, speed of light */
-    int order2;            /* twice the alternating order: 3 (l_a = 1 1/2; also 0) or 5 (l_a = 2 1/2) */
+    int order2;            /* 3 (l_a = 1 1/2; also 0), 5 (l_a = 2 1/2), or 4: the uniform-order l = 2
+                              comparison scheme of Eq. wrong1 */
 } orc_grid;
 
 typedef struct {
@@ -92,6 +93,14 @@ static double cell_volume(const orc_grid *g)
  *        ((1-d)^3/6, (2-d)^3/6 - 2(1-d)^3/3, (1+d)^3/6 - 2d^3/3, d^3/6)
  * "int" is read as floor on the wrapped, non-negative position.  The
  * half-integer point c+1/2 is the centre of cell c.
+ *
+ * The comparison scheme of Eq. wrong1 (Sec. 5, the "conventional" l = 2
+ * interpolation) keeps the l_a = 1 1/2 cell integrals dF at half-integer points
+ * and replaces the point values at an integer point i by the mean of the two
+ * neighbouring cell integrals, (dF_{i-1/2} + dF_{i+1/2})/2: the cell-centred
+ * weight applied to the field averaged over the two faces of the cell.  With
+ * dF nonzero on the cells i0-1 .. i0+1 this gives four integer points
+ * i0-1 .. i0+2.  The deposit and rho are those of l_a = 1 1/2.
  * ------------------------------------------------------------------------- */
 void orc_form_factor(double xp, long long *i, double f[2], double dF[3])
 {
@@ -120,14 +129,14 @@ void orc_form_factor5(double xp, long long *i, double f[3], double dF[4])
     dF[3] = d * d * d / 6.0;
 }
 
-static int grid_order2(const orc_grid *g) { return g->order2 == 5 ? 5 : 3; }
+static int grid_order2(const orc_grid *g) { return g->order2 == 5 || g->order2 == 4 ? g->order2 : 3; }
 
 /* Weights of one axis: nf point values f at the integer points ib+fo+a
  * (a = 0..nf-1) and nS cell integrals dF over the cells ib+so+b (b = 0..nS-1). */
 typedef struct {
     long long ib;
     int nf, fo, nS, so;
-    double f[3];
+    double f[4];
     double dF[4];
 } orc_axis_w;
 
@@ -136,6 +145,15 @@ static void axis_weights(int order2, double xp, orc_axis_w *w)
     if (order2 == 5) {
         orc_form_factor5(xp, &w->ib, w->f, w->dF);
         w->nf = 3; w->fo = -1; w->nS = 4; w->so = -2;
+    } else if (order2 == 4) {   /* Eq. wrong1 */
+        double f1[2];
+        orc_form_factor(xp, &w->ib, f1, w->dF);
+        w->nS = 3; w->so = -1;
+        w->nf = 4; w->fo = -1;
+        w->f[0] = 0.5 * w->dF[0];
+        w->f[1] = 0.5 * (w->dF[0] + w->dF[1]);
+        w->f[2] = 0.5 * (w->dF[1] + w->dF[2]);
+        w->f[3] = 0.5 * w->dF[2];
     } else {
         orc_form_factor(xp, &w->ib, w->f, w->dF);
         w->nf = 2; w->fo = 0; w->nS = 3; w->so = -1;
