@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch-runs", type=int, default=256)
     ap.add_argument("--no-laser", action="store_true")
     ap.add_argument("--no-order5", action="store_true", help="skip the l_a = 2 1/2 leg")
+    ap.add_argument("--no-energy", action="store_true", help="skip the Sec. 5 energy (X1) leg")
+    ap.add_argument("--energy-x4", action="store_true", help="add the 8000-step two-stream run to the energy leg")
     ap.add_argument("--laser-warmup", type=int, default=480)
     return ap.parse_args()
 
@@ -434,6 +436,39 @@ def order5_arm(P, torch, wl, stream, hbm_peak, value_l15, steps):
                          "alg_bytes_per_launch": alg}}
 
 
+def energy_arm(P, args):
+    """The energy test of Sec. 5 (X1: 3D 64^3, 2 electrons per cell, v_th = 0.05c,
+    immovable ions at the electron positions, 503 steps, FP64) with the
+    alternating orders l_a = 1 1/2 and 2 1/2 and the uniform-order l = 2
+    interpolation of Eq. wrong1; the largest relative defect of the energy
+    integral (sampled every 10 steps) and the stepping rates (FP64 and FP32).
+    With --energy-x4 also the two-stream test (B_x with omega_Be = omega_pe,
+    streams +-0.1c, 8000 steps)."""
+    from paper_1101_0809_gb300 import workloads as W
+    from paper_1101_0809_gb300.energy import energy_run
+    wl = W.x1_energy()
+    out = {"workload": wl.name + ", 503 steps, FP64", "particles": wl.n_particles, "x1": {}}
+    for order2, name in ((3, "l_a_1_5"), (4, "wrong1_l_2"), (5, "l_a_2_5")):
+        r64 = energy_run(wl, order2, P.PIC_FP64)
+        r32 = energy_run(wl, order2, P.PIC_FP32)
+        out["x1"][name] = {"max_rel_defect": r64["max_rel_defect"], "final_rel_defect": r64["final_rel_defect"],
+                           "fp64_particle_steps_per_s": r64["particle_steps_per_s"],
+                           "fp32_particle_steps_per_s": r32["particle_steps_per_s"],
+                           "fp32_max_rel_defect": r32["max_rel_defect"]}
+    x1 = out["x1"]
+    out["defect_ratio_wrong1_to_l_a_1_5"] = x1["wrong1_l_2"]["max_rel_defect"] / x1["l_a_1_5"]["max_rel_defect"]
+    out["speed_ratio_l_a_1_5_to_wrong1_fp32"] = (x1["l_a_1_5"]["fp32_particle_steps_per_s"] /
+                                                 x1["wrong1_l_2"]["fp32_particle_steps_per_s"])
+    if args.energy_x4:
+        wl4, bx = W.x4_two_stream()
+        out["x4"] = {"workload": wl4.name + ", 8000 steps, FP64, initial B_x field energy excluded"}
+        for order2, name in ((3, "l_a_1_5"), (4, "wrong1_l_2")):
+            r = energy_run(wl4, order2, P.PIC_FP64, every=100, bx=bx)
+            out["x4"][name] = {"max_rel_defect": r["max_rel_defect"], "final_rel_defect": r["final_rel_defect"],
+                               "fp64_particle_steps_per_s": r["particle_steps_per_s"]}
+    return out
+
+
 def our_arm(args):
     import torch
     rank, local, world = dist_env()
@@ -594,6 +629,9 @@ def our_arm(args):
     laser = None
     if not args.no_laser:
         laser = laser_arm(P, W, torch, args)
+    energy = None
+    if not args.no_energy and rank == 0:
+        energy = energy_arm(P, args)
     order5 = None
     if not args.no_order5:
         order5 = order5_arm(P, torch, wl, stream, hbm_peak, value / world, min(args.steps, 10))
@@ -608,7 +646,8 @@ def our_arm(args):
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                           "l2": "inputs larger than L2 (3.76 GB of particle SoA per replica); no flush"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-               "fp64": fp64, "batched": batched, "adjoint": adjoint, "laser": laser, "l_a_2_5": order5}
+               "fp64": fp64, "batched": batched, "adjoint": adjoint, "laser": laser, "l_a_2_5": order5,
+               "energy": energy}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

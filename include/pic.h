@@ -68,8 +68,12 @@ typedef struct {
     double dt, c;           /* time step; speed of light */
     int precision;          /* PIC_FP64 or PIC_FP32 */
     int order2;             /* twice the alternating order l_a (Sec. 4.5): 3 (or 0) for l_a = 1 1/2,
-                               5 for l_a = 2 1/2 (the fused, split and diagnostics paths; the
-                               persistent batch step and the adjoint are l_a = 1 1/2 only) */
+                               5 for l_a = 2 1/2; 4 selects the uniform-order l = 2 comparison
+                               scheme of Eq. wrong1 (Sec. 5: fields interpolated with the
+                               cell-centred weights averaged over the faces, l_a = 1 1/2 charge
+                               and current).  Orders 4 and 5 run the fused, split and
+                               diagnostics paths; the persistent batch step and the adjoint
+                               are l_a = 1 1/2 only */
     int tile[3];            /* tile extents in cells for the sort and the shared-memory
                                stages (0 = default: 8x8x8 in 3D, 16x16 in 2D) */
     int halo;               /* drift guard in cells around a tile (0..2; -1 = default 1) */

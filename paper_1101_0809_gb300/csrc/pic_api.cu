@@ -448,9 +448,9 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
     if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return fail(PIC_ERR_INVALID_ARG, "cell counts must be positive");
     if (d->dims == 2 && d->nz != 1) return fail(PIC_ERR_INVALID_ARG, "nz must be 1 for a 2D grid");
     if (d->precision != PIC_FP64 && d->precision != PIC_FP32) return fail(PIC_ERR_INVALID_ARG, "bad precision");
-    if (d->order2 != 3 && d->order2 != 5 && d->order2 != 0)
-        return fail(PIC_ERR_INVALID_ARG, "order2 must be 3 (l_a = 1 1/2) or 5 (l_a = 2 1/2)");
-    const int order2 = d->order2 == 5 ? 5 : 3;
+    if (d->order2 != 3 && d->order2 != 4 && d->order2 != 5 && d->order2 != 0)
+        return fail(PIC_ERR_INVALID_ARG, "order2 must be 3 (l_a = 1 1/2), 5 (l_a = 2 1/2) or 4 (Eq. wrong1)");
+    const int order2 = d->order2 == 0 ? 3 : d->order2;
     if (!first && (d->dims != g->dims || d->precision != g->prec || order2 != g->order2))
         return fail(PIC_ERR_INVALID_ARG, "all runs of a batch need the same dims, precision and order");
     const double dd[3] = {d->dx, d->dy, d->dims == 3 ? d->dz : 1.0};

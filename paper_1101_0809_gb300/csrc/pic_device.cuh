@@ -605,6 +605,72 @@ __device__ __forceinline__ void gather5(const Rd &rd, const R fx[3], const R Sx[
     Bp[0] = bx; Bp[1] = by; Bp[2] = bz;
 }
 
+// Gather of the comparison scheme of Eq. wrong1 (Sec. 5, the "conventional"
+// uniform-order l = 2 interpolation): the l_a = 1 1/2 cell integrals S at the
+// cells -1..1 of the particle's cell, and at the integer points -1..2 the mean
+// of the two neighbouring cell integrals, g = (S0/2, (S0+S1)/2, (S1+S2)/2, S2/2).
+// Reader offsets are relative to the cell.  2D drops every z factor.
+template <typename R>
+__device__ __forceinline__ void wrong1_points(const R S[3], R g[4])
+{
+    const R h = R(0.5);
+    g[0] = h * S[0];
+    g[1] = h * (S[0] + S[1]);
+    g[2] = h * (S[1] + S[2]);
+    g[3] = h * S[2];
+}
+
+template <int DIM, typename R, class Rd>
+__device__ __forceinline__ void gather_w1(const Rd &rd, const R Sx[3], const R Sy[3], const R Sz[3], R Ep[3],
+                                          R Bp[3])
+{
+    R gx[4], gy[4], gz[4];
+    wrong1_points(Sx, gx);
+    wrong1_points(Sy, gy);
+    wrong1_points(Sz, gz);
+    constexpr int NZS = DIM == 3 ? 3 : 1, NZG = DIM == 3 ? 4 : 1;
+    R ex = 0, ey = 0, ez = 0, bx = 0, by = 0, bz = 0;
+#pragma unroll
+    for (int c = 0; c < NZS; ++c) {   // S along z: E^x, E^y, B^z
+        const R wz = DIM == 3 ? Sz[c] : R(1);
+        const int oz = DIM == 3 ? c - 1 : 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const R t = gx[0] * rd.e(0, -1, b - 1, oz) + gx[1] * rd.e(0, 0, b - 1, oz) +
+                        gx[2] * rd.e(0, 1, b - 1, oz) + gx[3] * rd.e(0, 2, b - 1, oz);
+            ex += Sy[b] * wz * t;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const R t = Sx[0] * rd.e(1, -1, b - 1, oz) + Sx[1] * rd.e(1, 0, b - 1, oz) + Sx[2] * rd.e(1, 1, b - 1, oz);
+            ey += gy[b] * wz * t;
+            const R u = gx[0] * rd.b(2, -1, b - 1, oz) + gx[1] * rd.b(2, 0, b - 1, oz) +
+                        gx[2] * rd.b(2, 1, b - 1, oz) + gx[3] * rd.b(2, 2, b - 1, oz);
+            bz += gy[b] * wz * u;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NZG; ++c) {   // g along z: E^z, B^x, B^y
+        const R wz = DIM == 3 ? gz[c] : R(1);
+        const int oz = DIM == 3 ? c - 1 : 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const R t = Sx[0] * rd.e(2, -1, b - 1, oz) + Sx[1] * rd.e(2, 0, b - 1, oz) + Sx[2] * rd.e(2, 1, b - 1, oz);
+            ez += Sy[b] * wz * t;
+            const R u = gx[0] * rd.b(1, -1, b - 1, oz) + gx[1] * rd.b(1, 0, b - 1, oz) +
+                        gx[2] * rd.b(1, 1, b - 1, oz) + gx[3] * rd.b(1, 2, b - 1, oz);
+            by += Sy[b] * wz * u;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const R t = Sx[0] * rd.b(0, -1, b - 1, oz) + Sx[1] * rd.b(0, 0, b - 1, oz) + Sx[2] * rd.b(0, 1, b - 1, oz);
+            bx += gy[b] * wz * t;
+        }
+    }
+    Ep[0] = ex; Ep[1] = ey; Ep[2] = ez;
+    Bp[0] = bx; Bp[1] = by; Bp[2] = bz;
+}
+
 template <typename R>
 struct GlobalReader5 {       // periodic global arrays, offsets -2..2 from the base index
     const R *E[3];

@@ -70,7 +70,8 @@ __device__ void block_reduce_store(double v[kPartVals], int max_slot, double *ou
 // Particles: rho deposit (atomics) and kinetic / momentum / half-step sums.
 // Partial slots: 0 kinetic, 1-3 momentum, 4 half-step correction, 5 count.
 // ORD = 3: l_a = 1 1/2 (rho over the 3 cells per axis around the cell);
-// ORD = 5: l_a = 2 1/2 (rho over the 4 cells ib-2 .. ib+1 of the base index).
+// ORD = 5: l_a = 2 1/2 (rho over the 4 cells ib-2 .. ib+1 of the base index);
+// ORD = 4: the comparison scheme of Eq. wrong1 (rho of l_a = 1 1/2, its own gather).
 template <int DIM, typename R, int ORD = 3>
 __global__ void __launch_bounds__(kDiagThreads) k_diag_particles(int run, long long total, const long long *group_base,
                                                                  int ngroups, const GroupDev *groups, const RunDev *runs,
@@ -141,7 +142,10 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_particles(int run, long l
                 rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
                 rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
             }
-            gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+            if constexpr (ORD == 4)
+                gather_w1<DIM>(rd, Sx, Sy, Sz, Ep, Bp);
+            else
+                gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
         }
         const double w0 = (double)P.w[0][p], w1 = (double)P.w[1][p], w2 = (double)P.w[2][p];
         const double gam = sqrt(w0 * w0 + w1 * w1 + w2 * w2 + rn.c * rn.c);
@@ -183,7 +187,8 @@ struct GlobalZeroB5 {   // offsets -2..2 from the l_a = 2 1/2 base index
 };
 
 // ORD = 5 (l_a = 2 1/2): E and rho tiles with a halo of (halo + 2) cells, the
-// 4-cell cubic weights around the base index.
+// 4-cell cubic weights around the base index.  ORD = 4 (Eq. wrong1): the same
+// halo for its gather, the l_a = 1 1/2 charge.
 template <int DIM, int ORD = 3>
 __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const WorkItem *items, const int *n_items,
                                                              const GroupDev *groups, const RunDev *runs, Pool<float> P,
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const W
     const int nx = rn.n[0], ny = rn.n[1], nz = rn.n[2];
     const int T0 = rn.tile[0], T1 = rn.tile[1], T2 = DIM == 3 ? rn.tile[2] : 1;
     const int P0 = rn.pitch[0], P1 = rn.pitch[1];
-    constexpr int FH = ORD == 5 ? 2 : 1;   // tile halo beyond G
+    constexpr int FH = ORD == 3 ? 1 : 2;   // tile halo beyond G
     const int fe0 = T0 + 2 * (G + FH), fe1 = T1 + 2 * (G + FH), fe2 = DIM == 3 ? T2 + 2 * (G + FH) : 1;
     const int nf = P0 * P1 * fe2;
     float *sE[3];
@@ -313,10 +318,13 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const W
                 if (inr) {
                     ZeroB rd;
                     for (int c = 0; c < 3; ++c) rd.E[c] = sE[c];
-                    rd.base = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
+                    rd.base = (li + G + FH) + P0 * ((lj + G + FH) + (DIM == 3 ? P1 * (lk + G + FH) : 0));
                     rd.s1 = P0;
                     rd.s2 = P0 * P1;
-                    gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                    if constexpr (ORD == 4)
+                        gather_w1<DIM>(rd, Sx, Sy, Sz, Ep, Bp);
+                    else
+                        gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
                     acc.base = rd.base;
                     const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
 #pragma unroll
@@ -335,7 +343,10 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_items(int run, const W
                         rd.yj[q] = (long long)nx * wrapi(j - 1 + q, ny);
                         rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 1 + q, nz) : 0;
                     }
-                    gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
+                    if constexpr (ORD == 4)
+                        gather_w1<DIM>(rd, Sx, Sy, Sz, Ep, Bp);
+                    else
+                        gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
                     const int kz0 = DIM == 3 ? -1 : 0, kz1 = DIM == 3 ? 1 : 0;
                     for (int dz = kz0; dz <= kz1; ++dz)
                         for (int dy = -1; dy <= 1; ++dy)
@@ -530,13 +541,16 @@ cudaError_t launch_diagnostics_run(int dims, int prec, cudaStream_t st, const Ru
     if (order2 == 5)
         return diag_run_o<5>(dims, prec, st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
                              set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
+    if (order2 == 4)
+        return diag_run_o<4>(dims, prec, st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
+                             set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
     return diag_run_o<3>(dims, prec, st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
                          set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
 }
 
 size_t diag_items_smem_bytes(int dims, const int tile[3], int halo, const int pitch[2], int order2)
 {
-    const int fh = order2 == 5 ? 2 : 1;
+    const int fh = order2 == 3 ? 1 : 2;
     const long long fe2 = dims == 3 ? tile[2] + 2 * (halo + fh) : 1;
     return (size_t)5 * pitch[0] * pitch[1] * fe2 * sizeof(float);
 }
@@ -547,6 +561,9 @@ cudaError_t diag_set_smem_limit(int dims, size_t bytes, int order2)
     if (order2 == 5)
         return dims == 3 ? cudaFuncSetAttribute(k_diag_items<3, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)
                          : cudaFuncSetAttribute(k_diag_items<2, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (order2 == 4)
+        return dims == 3 ? cudaFuncSetAttribute(k_diag_items<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)
+                         : cudaFuncSetAttribute(k_diag_items<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     return dims == 3 ? cudaFuncSetAttribute(k_diag_items<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)
                      : cudaFuncSetAttribute(k_diag_items<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }

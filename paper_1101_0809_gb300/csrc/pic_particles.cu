@@ -19,9 +19,11 @@ size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz
                             int order2)
 {
     const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
-    const int ext = order2 == 5 ? 1 : 0;   // l_a = 2 1/2 reaches one cell further
-    const long long fe = (long long)p0 * p1 * (dims == 3 ? tz + 2 * (halo + 1 + ext) : 1);
-    const long long je = (long long)p0 * p1 * (dims == 3 ? tz + 2 * (halo + 2 + ext) : 1);
+    // l_a = 2 1/2 reaches one cell further in both tiles; the gather of
+    // Eq. wrong1 (order2 = 4) in the field tile only
+    const int fext = order2 == 3 ? 0 : 1, jext = order2 == 5 ? 1 : 0;
+    const long long fe = (long long)p0 * p1 * (dims == 3 ? tz + 2 * (halo + 1 + fext) : 1);
+    const long long je = (long long)p0 * p1 * (dims == 3 ? tz + 2 * (halo + 2 + jext) : 1);
     size_t b = 0;
     if (mode != 2) b += 6 * fe * es;
     if (mode != 1) b += (prec == 0 ? 24 : 28) * je + (size_t)(kThreads / 32) * kQueueCap * (kQueueVals * es + sizeof(int));
@@ -42,6 +44,7 @@ static cudaError_t set_limit_t(int mode, size_t bytes)
 cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes, int order2)
 {
     if (order2 == 5) return particles_o5_set_smem_limit(dims, prec, mode, bytes);
+    if (order2 == 4) return particles_w1_set_smem_limit(dims, prec, mode, bytes);
     if (prec != 0 && mode == 0) {
         const cudaError_t e = fixed_set_smem_limit(dims, bytes);
         if (e != cudaSuccess) return e;
@@ -61,6 +64,9 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
         particles_smem_bytes(dims, prec, mode, max_tile_x, max_tile_y, max_tile_z, halo, p0, p1, order2);
     if (order2 == 5)
         return launch_particles_o5(dims, prec, mode, st, max_items, smem, items, n_items, runs, groups, P, E, B, J,
+                                   old_cell, old_off, halo, err);
+    if (order2 == 4)
+        return launch_particles_w1(dims, prec, mode, st, max_items, smem, items, n_items, runs, groups, P, E, B, J,
                                    old_cell, old_off, halo, err);
     if (prec == 0) {
         auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);

@@ -133,6 +133,21 @@ __device__ __noinline__ void deposit_global5(const Fields<R> &F, long long cb, i
     deposit5<DIM>(acc, win[0], win[1], win[2], kf, uz, 7);
 }
 
+// The comparison scheme of Eq. wrong1 on the global arrays; (i, j, k) is the cell.
+template <int DIM, typename R>
+__device__ __noinline__ void gather_global_w1(const Fields<R> &F, long long cb, int i, int j, int k, int nx, int ny,
+                                              int nz, const R *S, R *Ep, R *Bp)
+{
+    GlobalReader5<R> rd;
+    for (int c = 0; c < 3; ++c) { rd.E[c] = F.E[c]; rd.B[c] = F.B[c]; }
+    for (int q = 0; q < 5; ++q) {
+        rd.xi[q] = cb + wrapi(i - 2 + q, nx);
+        rd.yj[q] = (long long)nx * wrapi(j - 2 + q, ny);
+        rd.zk[q] = DIM == 3 ? (long long)nx * ny * wrapi(k - 2 + q, nz) : 0;
+    }
+    gather_w1<DIM>(rd, S, S + 3, S + 6, Ep, Bp);
+}
+
 // MODE 0: fused gather + push + move + deposit (pic_step).
 // MODE 1: gather + push + move, keeping x^n (pic_gather_push).
 // MODE 2: deposit from the kept x^n and the current x^{n+1} (pic_deposit_current).
@@ -143,7 +158,9 @@ __device__ __noinline__ void deposit_global5(const Fields<R> &F, long long cb, i
 // reaches one cell further, so the field tile has a halo of (halo + 2) cells
 // and the current tile one of (halo + 3), and every particle deposits through
 // the bias-removing accumulator (the per-cell counts serve the l_a = 1 1/2
-// stencil only).
+// stencil only).  ORD = 4 is the comparison scheme of Eq. wrong1: its gather
+// reaches the integer points -1..2 (field tile halo (halo + 2)); its charge and
+// current are those of l_a = 1 1/2.
 template <int DIM, typename R, int MODE, class GEO, int ORD = 3>
 __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
 {
@@ -159,7 +176,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     const int ty = (it.tile / rn.ntile[0]) % rn.ntile[1];
     const int tz = DIM == 3 ? it.tile / (rn.ntile[0] * rn.ntile[1]) : 0;
     const int ox = tx * T0, oy = ty * T1, oz = tz * T2;
-    constexpr int FH = ORD == 5 ? 2 : 1, JH = ORD == 5 ? 3 : 2;   // field and current halo beyond G
+    constexpr int FH = ORD == 3 ? 1 : 2, JH = ORD == 5 ? 3 : 2;   // field and current halo beyond G
     const int fe0 = T0 + 2 * (G + FH), fe1 = T1 + 2 * (G + FH), fe2 = DIM == 3 ? T2 + 2 * (G + FH) : 1;
     const int je0 = T0 + 2 * (G + JH), je1 = T1 + 2 * (G + JH), je2 = DIM == 3 ? T2 + 2 * (G + JH) : 1;
     // the field tile is stored with the current tile's x and y pitches, so that
@@ -381,6 +398,21 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                     } else {
                         gather_global5<DIM, R>(a.F, cb, i + u0, j + u1, k + u2, nx, ny, nz, w, Ep, Bp);
                     }
+                } else if constexpr (ORD == 4) {
+                    R f[2], S[9] = {R(0), R(1), R(0), R(0), R(1), R(0), R(0), R(1), R(0)};   // S along x, y, z
+                    form_factor(o0, f, S);
+                    form_factor(o1, f, S + 3);
+                    if (DIM == 3) form_factor(o2, f, S + 6);
+                    if (inr) {
+                        SmemReader<R> rd;
+                        for (int c = 0; c < 3; ++c) { rd.E[c] = sE[c]; rd.B[c] = sB[c]; }
+                        rd.base = (li + G + FH) + P0 * ((lj + G + FH) + (DIM == 3 ? P1 * (lk + G + FH) : 0));
+                        rd.s1 = P0;
+                        rd.s2 = P0 * P1;
+                        gather_w1<DIM>(rd, S, S + 3, S + 6, Ep, Bp);
+                    } else {
+                        gather_global_w1<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, S, Ep, Bp);
+                    }
                 } else {
                     R fx[2], Sx[3], fy[2], Sy[3], fz[2], Sz[3];
                     form_factor(o0, fx, Sx);
@@ -562,7 +594,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             // for J^x (faces 0, 1; cells -1..1), likewise for J^y and J^z, so a
             // cell l received sum_{b in l - stencil} cnt[b] of them
             unsigned nst[3] = {0u, 0u, 0u};
-            if constexpr (FIX && ORD == 3) {
+            if constexpr (FIX && ORD != 5) {
                 if (lx >= 1 && lx < je0 - 1 && ly >= 1 && ly < je1 - 1 && (DIM == 2 || (lz >= 1 && lz < je2 - 1))) {
                     if (DIM == 3) {
                         unsigned tot = 0, px = 0, py = 0, pz = 0;   // all 27, and the +1 planes
@@ -738,11 +770,64 @@ bool launch_persistent_fixed(int dims, cudaStream_t st, size_t smem, int nruns, 
                              int p0, int p1, long long *ant_n, int antennas, cudaError_t *err);
 cudaError_t fixed_set_smem_limit(int dims, size_t bytes);
 
-// The l_a = 2 1/2 particle kernels (pic_particles_o5.cu), any tile geometry.
+// Launch and shared-memory limit of the kernels of another stencil (ORD = 5:
+// l_a = 2 1/2 in pic_particles_o5.cu; ORD = 4: Eq. wrong1 in pic_particles_w1.cu),
+// any tile geometry, both precisions, all three modes.
+template <int DIM, typename R, int ORD>
+static cudaError_t launch_mode_ord(int mode, cudaStream_t st, int max_items, size_t smem, const PartArgs<R> &a)
+{
+    switch (mode) {
+    case 0: return launch_t<DIM, R, 0, GeoDyn, ORD>(st, max_items, smem, a);
+    case 1: return launch_t<DIM, R, 1, GeoDyn, ORD>(st, max_items, smem, a);
+    default: return launch_t<DIM, R, 2, GeoDyn, ORD>(st, max_items, smem, a);
+    }
+}
+
+template <int ORD>
+static cudaError_t launch_particles_ord_t(int dims, int prec, int mode, cudaStream_t st, int max_items, size_t smem,
+                                          const WorkItem *items, const int *n_items, const RunDev *runs,
+                                          const GroupDev *groups, const PoolBuf &P, void *const E[3],
+                                          void *const B[3], void *const J[3], int *old_cell, void *const old_off[3],
+                                          int halo, int *err)
+{
+    if (prec == 0) {
+        auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
+        return dims == 3 ? launch_mode_ord<3, double, ORD>(mode, st, max_items, smem, a)
+                         : launch_mode_ord<2, double, ORD>(mode, st, max_items, smem, a);
+    }
+    auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
+    return dims == 3 ? launch_mode_ord<3, float, ORD>(mode, st, max_items, smem, a)
+                     : launch_mode_ord<2, float, ORD>(mode, st, max_items, smem, a);
+}
+
+template <int DIM, typename R, int ORD>
+static cudaError_t set_limit_ord(int mode, size_t bytes)
+{
+    const int b = (int)bytes;
+    switch (mode) {
+    case 0: return cudaFuncSetAttribute(k_particles<DIM, R, 0, GeoDyn, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 1: return cudaFuncSetAttribute(k_particles<DIM, R, 1, GeoDyn, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    default: return cudaFuncSetAttribute(k_particles<DIM, R, 2, GeoDyn, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    }
+}
+
+template <int ORD>
+static cudaError_t particles_ord_set_smem_limit_t(int dims, int prec, int mode, size_t bytes)
+{
+    if (dims == 3)
+        return prec == 0 ? set_limit_ord<3, double, ORD>(mode, bytes) : set_limit_ord<3, float, ORD>(mode, bytes);
+    return prec == 0 ? set_limit_ord<2, double, ORD>(mode, bytes) : set_limit_ord<2, float, ORD>(mode, bytes);
+}
+
 cudaError_t launch_particles_o5(int dims, int prec, int mode, cudaStream_t st, int max_items, size_t smem,
                                 const WorkItem *items, const int *n_items, const RunDev *runs, const GroupDev *groups,
                                 const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
                                 int *old_cell, void *const old_off[3], int halo, int *err);
 cudaError_t particles_o5_set_smem_limit(int dims, int prec, int mode, size_t bytes);
+cudaError_t launch_particles_w1(int dims, int prec, int mode, cudaStream_t st, int max_items, size_t smem,
+                                const WorkItem *items, const int *n_items, const RunDev *runs, const GroupDev *groups,
+                                const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
+                                int *old_cell, void *const old_off[3], int halo, int *err);
+cudaError_t particles_w1_set_smem_limit(int dims, int prec, int mode, size_t bytes);
 
 }  // namespace pic

@@ -437,7 +437,7 @@ def pic_tile_sort_perm_noalloc(cell, n, dims, ncell, tile, perm, tile_start=None
 def make_desc(dims, n, d, dt, c, precision=PIC_FP64, tile=(0, 0, 0), halo=-1, sort_interval=0,
               particles_per_block=0, rho_bg=0.0, stream=None, sort_order=PIC_SORT_BANKED, order2=3):
     """Fill a pic_grid_desc; ``stream`` is a raw cudaStream_t handle (int) or None;
-    order2 = 3 for l_a = 1 1/2, 5 for l_a = 2 1/2."""
+    order2 = 3 for l_a = 1 1/2, 5 for l_a = 2 1/2, 4 for the comparison scheme of Eq. wrong1."""
     return pic_grid_desc(dims, n[0], n[1], n[2] if dims == 3 else 1, d[0], d[1], d[2], dt, c,
                          precision, order2, (C.c_int * 3)(*tile), halo, sort_interval,
                          particles_per_block, rho_bg, stream, sort_order)

@@ -203,3 +203,37 @@ def c3_run(params):
     sp = SpeciesInit("electrons", -1.0, 1.0, W, x, w)
     return Workload(f"2D3V {N}x{N} {ppc}ppc vth={vth:.3f}c", 2, (N, N, 1), (1.0, 1.0, 1.0), dt, c,
                     [sp], W * ppc / V, 500, (16, 16, 1), 10)
+
+
+# Ions that do not move: a species of charge +e whose mass makes q dt/(2m) about
+# 1e-32 of the electrons', so that over any run here they stay put to about
+# 1e-30 cells and carry no kinetic energy (the paper's immovable ions).
+IMMOVABLE_MASS = 1.0e30
+
+
+def x1_energy(n=64, ppc=2, steps=503, seed_offset=6, tile=(8, 4, 4)):
+    """The energy test of Sec. 5: 3D n^3 periodic, ppc electrons per cell,
+    v_th = 0.05c, dx = lambda_De (omega_pe = 1), omega_pe dt = 0.025, 503 steps
+    (about two plasma periods); the same number of immovable ions at the
+    electrons' initial positions, so that the field is zero at t = 0."""
+    wl = thermal_plasma(f"X1 {n}^3 {ppc}ppc vth=0.05c, immovable ions at the electron positions", 3,
+                        (n, n, n), ppc, 0.05, steps, SEED_BASE + seed_offset, tile=tile)
+    e = wl.species[0]
+    wl.species.append(SpeciesInit("immovable ions", 1.0, IMMOVABLE_MASS, e.weight, e.x.copy(), np.zeros_like(e.w)))
+    wl.rho_bg = 0.0
+    return wl
+
+
+def x4_two_stream(n=64, ppc=2, steps=8000, seed_offset=7, tile=(8, 4, 4)):
+    """The two-stream test of Sec. 5: X1's plasma with a uniform B_x such that
+    the electron cyclotron frequency equals omega_pe (B_x = m c / |q| = c), and
+    a directed momentum +2 v_th (= 0.1c in w = gamma v) along x added to half of
+    the electrons and -2 v_th to the other half.  Returns the workload and B_x;
+    the energy integral excludes the field energy of the initial B_x."""
+    wl = x1_energy(n, ppc, steps, seed_offset, tile)
+    wl.name = f"X4 two-stream {n}^3 {ppc}ppc, B_x with omega_Be = omega_pe, streams +-0.1c"
+    e = wl.species[0]
+    half = e.n // 2
+    e.w[0][:half] += 2.0
+    e.w[0][half:] -= 2.0
+    return wl, wl.c
