@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-order5", action="store_true", help="skip the l_a = 2 1/2 leg")
     ap.add_argument("--no-energy", action="store_true", help="skip the Sec. 5 energy (X1) leg")
     ap.add_argument("--energy-x4", action="store_true", help="add the 8000-step two-stream run to the energy leg")
+    ap.add_argument("--energy-x5-steps", type=int, default=4000, help="steps of the Langmuir run (X5)")
     ap.add_argument("--laser-warmup", type=int, default=480)
     return ap.parse_args()
 
@@ -442,8 +443,13 @@ def energy_arm(P, args):
     alternating orders l_a = 1 1/2 and 2 1/2 and the uniform-order l = 2
     interpolation of Eq. wrong1; the largest relative defect of the energy
     integral (sampled every 10 steps) and the stepping rates (FP64 and FP32).
-    With --energy-x4 also the two-stream test (B_x with omega_Be = omega_pe,
-    streams +-0.1c, 8000 steps)."""
+    Also the Langmuir test X5 (1 electron per cell of twice the charge, B_x
+    with omega_Be = omega_pe, all electrons streaming at 0.1c: the largest
+    defect of the total energy and the period of the field energy) and the
+    gyration test X6 (an electron and a positron at w = +-0.5c in B_z with
+    omega_Be = 10, 1600 steps: kinetic energy ratio and Larmor radii).  With
+    --energy-x4 also the two-stream test (B_x with omega_Be = omega_pe, streams
+    +-0.1c, 8000 steps)."""
     from paper_1101_0809_gb300 import workloads as W
     from paper_1101_0809_gb300.energy import energy_run
     wl = W.x1_energy()
@@ -459,6 +465,19 @@ def energy_arm(P, args):
     out["defect_ratio_wrong1_to_l_a_1_5"] = x1["wrong1_l_2"]["max_rel_defect"] / x1["l_a_1_5"]["max_rel_defect"]
     out["speed_ratio_l_a_1_5_to_wrong1_fp32"] = (x1["l_a_1_5"]["fp32_particle_steps_per_s"] /
                                                  x1["wrong1_l_2"]["fp32_particle_steps_per_s"])
+    from paper_1101_0809_gb300.energy import gyration_run, oscillation_period
+    wl5, bx5 = W.x5_langmuir(steps=args.energy_x5_steps)
+    r5 = energy_run(wl5, 3, P.PIC_FP64, every=5, bx=bx5)
+    steps5 = [q[0] for q in r5["series"]]
+    out["x5"] = {"workload": wl5.name + f", {wl5.steps} steps, FP64, l_a = 1 1/2",
+                 "max_rel_defect": r5["max_rel_defect"],
+                 "field_energy_period_steps": oscillation_period(steps5, [q[3] for q in r5["series"]]),
+                 "expected_period_steps": math.pi * (1.0 + (2.0 / wl5.c) ** 2) ** 0.75 / wl5.dt,
+                 "kinetic_range": [min(q[2] for q in r5["series"]), max(q[2] for q in r5["series"])],
+                 "field_E_range": [min(q[3] for q in r5["series"]), max(q[3] for q in r5["series"])]}
+    wl6, bz6 = W.x6_gyration()
+    out["x6"] = {"workload": wl6.name + f", {wl6.steps} steps, FP64, l_a = 1 1/2",
+                 **gyration_run(wl6, 3, P.PIC_FP64, bz6)}
     if args.energy_x4:
         wl4, bx = W.x4_two_stream()
         out["x4"] = {"workload": wl4.name + ", 8000 steps, FP64, initial B_x field energy excluded"}

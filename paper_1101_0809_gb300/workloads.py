@@ -237,3 +237,34 @@ def x4_two_stream(n=64, ppc=2, steps=8000, seed_offset=7, tile=(8, 4, 4)):
     e.w[0][:half] += 2.0
     e.w[0][half:] -= 2.0
     return wl, wl.c
+
+
+def x5_langmuir(n=64, steps=4000, seed_offset=8, tile=(8, 4, 4)):
+    """The Langmuir test of Sec. 5 (Fig. 3, left): X4's setup with one electron
+    per cell of twice the charge (still omega_pe = 1), B_x with
+    omega_Be = omega_pe, and the directed momentum +2 v_th (0.1c) added to every
+    electron, so that the electrons oscillate as a whole against the immovable
+    ions.  Returns the workload and B_x."""
+    wl = x1_energy(n, 1, steps, seed_offset, tile)
+    wl.name = f"X5 Langmuir {n}^3 1ppc (charge x2), B_x with omega_Be = omega_pe, stream +0.1c"
+    wl.species[0].w[0] += 2.0
+    return wl, wl.c
+
+
+def x6_gyration(n=64, steps=1600, tile=(8, 4, 4)):
+    """The gyration test of Sec. 5 (Fig. 3, right): an electron and a positron at
+    the centre of an n^3 box with opposite momenta w = +-0.5c along x, in a
+    uniform B_z with omega_Be = 10 (B_z = 10 m c / |q|), so that
+    omega_Be dt = 0.25; the charge is that of X5's particles.  Returns the
+    workload and B_z."""
+    vth = 1.0
+    c = vth / 0.05
+    dt = 0.5 / c
+    V = 1.0
+    W = V / (4.0 * math.pi)        # X5's macro charge: one particle per cell gives omega_pe = 1
+    x = np.full((3, 1), n / 2.0 + 0.25)
+    e = SpeciesInit("electron", -1.0, 1.0, W, x.copy(), np.array([[0.5 * c], [0.0], [0.0]]))
+    p = SpeciesInit("positron", 1.0, 1.0, W, x.copy(), np.array([[-0.5 * c], [0.0], [0.0]]))
+    wl = Workload(f"X6 gyration in B_z with omega_Be = 10, w = +-0.5c, {n}^3 box", 3, (n, n, n), (1.0, 1.0, 1.0),
+                  dt, c, [e, p], 0.0, steps, tuple(tile), 10)
+    return wl, 10.0 * c

@@ -223,7 +223,7 @@ def test_calls_built_for_l_a_1_5_refuse_l_a_2_5(P):
     with pytest.raises(P.PicError) as e:
         P.pic_adjoint_step(grid.h, f, [t.clone() for t in f], p, [t.clone() for t in p])
     assert e.value.code == P.PIC_ERR_INVALID_ARG
-    for bad in (dict(order2=4), dict(order2=5, tile=(8, 8, 8), dims3=True)):
+    for bad in (dict(order2=6), dict(order2=5, tile=(8, 8, 8), dims3=True)):
         if bad.pop("dims3", False):
             w3 = small3d()
             desc = P.make_desc(3, w3.n, w3.d, w3.dt, w3.c, P.PIC_FP64, **bad)   # shared memory of the tiles
