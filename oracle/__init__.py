@@ -249,6 +249,26 @@ def sort_perm(key, nkeys):
     return perm
 
 
+def update_A(g: Grid, E, A):
+    """A^{n+1/2} = A^{n-1/2} - c dt E^n (Eq. dadt), in place; call with E^n before step()."""
+    lib().orc_update_A(C.byref(g.cstruct()), _fields(E), _fields(A))
+
+
+def curl_A(g: Grid, A):
+    """B = curl_h A on the staggered grid (Eq. viaA)."""
+    B = g.zeros()
+    lib().orc_curl_A(C.byref(g.cstruct()), _fields(A), _fields(B))
+    return B
+
+
+def generalized_momentum(g: Grid, A, species):
+    """sum_p m_p w_p + (q_p/c) A(x_p - (dt/2) u_p), A at the E points (Sec. 4.2)."""
+    arr = _species_array(species)
+    P = (C.c_double * 3)()
+    lib().orc_generalized_momentum(C.byref(g.cstruct()), _fields(A), C.c_int(len(species)), arr, P)
+    return np.array(P[:])
+
+
 def yee_half_B_adj(g: Grid, lamB, lamE):
     """lamE += (-(1/2) C_B)^T lamB (transpose of the B half step)."""
     lib().orc_yee_half_B_adj(C.byref(g.cstruct()), _fields(lamB), _fields(lamE))

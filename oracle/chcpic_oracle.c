@@ -460,6 +460,70 @@ void orc_yee_E(const orc_grid *g, const double *const B[3], const double *const 
 }
 
 /* ---------------------------------------------------------------------------
+ * Vector-potential formulation (Sec. 4.2).  A sits on the E points; one step
+ * advances it by Eq. dadt, A^{n+1/2} = A^{n-1/2} - c dt E^n, with the E^n of the
+ * step (call before orc_step).  B = curl_h A on the staggered grid (Eq. viaA,
+ * grid form):
+ *   Bx[i,j,k] = (Az[i,j,k] - Az[i,j-1,k])/dy - (Ay[i,j,k] - Ay[i,j,k-1])/dz, cyclically;
+ * in 2D the z differences vanish.
+ * ------------------------------------------------------------------------- */
+void orc_update_A(const orc_grid *g, const double *const E[3], double *A[3])
+{
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    for (int a = 0; a < 3; ++a)
+        for (long long p = 0; p < N; ++p) A[a][p] -= g->c * g->dt * E[a][p];
+}
+
+void orc_curl_A(const orc_grid *g, const double *const A[3], double *B[3])
+{
+    const double idz = g->dims == 2 ? 0.0 : 1.0 / g->dz;
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                long long p = cell_index(g, i, j, k);
+                B[0][p] = (A[2][p] - A[2][cell_index(g, i, j - 1, k)]) / g->dy -
+                          (A[1][p] - A[1][cell_index(g, i, j, k - 1)]) * idz;
+                B[1][p] = (A[0][p] - A[0][cell_index(g, i, j, k - 1)]) * idz -
+                          (A[2][p] - A[2][cell_index(g, i - 1, j, k)]) / g->dx;
+                B[2][p] = (A[1][p] - A[1][cell_index(g, i - 1, j, k)]) / g->dx -
+                          (A[0][p] - A[0][cell_index(g, i, j - 1, k)]) / g->dy;
+            }
+}
+
+/* Generalized momentum of the particles (Sec. 4.2): sum over p of
+ * m_p w_p^{n-1/2} + (q_p/c) A^{n-1/2}(x_p^n - (dt/2) u_p^{n-1/2}), with A
+ * interpolated by the weights alpha of E (Eq. A) at the time-centred position
+ * (in cell units the shift is c_a u_a / (2c) per axis). */
+void orc_generalized_momentum(const orc_grid *g, const double *const A[3], int nsp, const orc_species *sp,
+                              double P[3])
+{
+    const double cN[3] = { g->c * g->dt / g->dx, g->c * g->dt / g->dy, g->dims == 2 ? 0.0 : g->c * g->dt / g->dz };
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    double *zero[3];
+    for (int a = 0; a < 3; ++a) zero[a] = (double *)calloc((size_t)N, sizeof(double));
+    P[0] = P[1] = P[2] = 0.0;
+    for (int s = 0; s < nsp; ++s) {
+        const double mp = sp[s].m * sp[s].weight, qp = sp[s].q * sp[s].weight;
+        for (long long p = 0; p < sp[s].n; ++p) {
+            double w[3] = { sp[s].w[0][p], sp[s].w[1][p], sp[s].w[2][p] };
+            double gam = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + g->c * g->c);
+            double xh[3] = { 0.0, 0.0, 0.0 };
+            for (int a = 0; a < g->dims; ++a) {
+                double x = sp[s].x[a][p] - 0.5 * cN[a] * w[a] / gam;
+                double n = a == 0 ? g->nx : a == 1 ? g->ny : g->nz;
+                x = fmod(x, n);
+                if (x < 0.0) x += n;
+                xh[a] = x;
+            }
+            double Ap[3], Bp[3];
+            orc_gather(g, A, (const double *const *)zero, xh, Ap, Bp);
+            for (int a = 0; a < 3; ++a) P[a] += mp * w[a] + qp / g->c * Ap[a];
+        }
+    }
+    for (int a = 0; a < 3; ++a) free(zero[a]);
+}
+
+/* ---------------------------------------------------------------------------
  * Particle part of the step for one species (Appendix, step 2): per particle,
  * in storage order, form factor at x^n, gather E and B (B at time n), push,
  * move, deposit, wrap.  Returns the worst deposit closure |sum dF(-)|.
