@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-energy", action="store_true", help="skip the Sec. 5 energy (X1) leg")
     ap.add_argument("--energy-x4", action="store_true", help="add the 8000-step two-stream run to the energy leg")
     ap.add_argument("--energy-x5-steps", type=int, default=4000, help="steps of the Langmuir run (X5)")
+    ap.add_argument("--no-vecpot", action="store_true", help="skip the vector-potential (generalized momentum) leg")
     ap.add_argument("--laser-warmup", type=int, default=480)
     return ap.parse_args()
 
@@ -488,6 +489,43 @@ def energy_arm(P, args):
     return out
 
 
+def vecpot_arm(P):
+    """Generalized-momentum conservation (Sec. 4.2) with the vector-potential
+    formulation: 262,144 test particles (w ~ N(0, 0.3c), negligible charge) in
+    the static field A_z = 3 (sin(2 pi 8 x/256) + cos(2 pi 8 y/256)) of a 2D
+    256^2 grid, FP64, over 120 time units of 0.4 / nsub steps; the largest
+    change of the summed P_z per particle, for dt and dt/2, with l_a = 1 1/2
+    and with the interpolation of Eq. wrong1."""
+    import numpy as np
+    n, count, wt = 256, 262144, 1e-12
+    X, Y = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5)
+    Az = (3.0 * (np.sin(2 * math.pi * 8 * X / n) + np.cos(2 * math.pi * 8 * Y / n))).reshape(1, n, n)
+    rng = np.random.default_rng(9)
+    x = np.zeros((3, count))
+    x[0] = rng.uniform(0, n, count)
+    x[1] = rng.uniform(0, n, count)
+    w = rng.normal(0, 0.3, (3, count))
+    out = {"workload": "262,144 test particles in a static A_z(x, y) on a 2D 256^2 grid, FP64, 120 time units",
+           "unit": "largest |P_z(t) - P_z(0)| per particle and unit weight"}
+    for order2, name in ((3, "l_a_1_5"), (4, "wrong1_l_2")):
+        drifts = []
+        for nsub in (1, 2):
+            desc = P.make_desc(2, (n, n, 1), (1.0, 1.0, 1.0), 0.4 / nsub, 1.0, P.PIC_FP64, tile=(16, 16, 1),
+                               order2=order2)
+            g = P.Grid(desc)
+            P.pic_set_vector_potential(g.h, [np.zeros((1, n, n)), np.zeros((1, n, n)), Az], set_B=True)
+            g.load(0, -1.0, 1.0, wt, x, w)
+            p0 = P.pic_generalized_momentum(g.h)[2] / wt
+            worst = 0.0
+            for _ in range(120):
+                P.pic_step(g.h, nsub)
+                worst = max(worst, abs(P.pic_generalized_momentum(g.h)[2] / wt - p0))
+            g.close()
+            drifts.append(worst / count)
+        out[name] = {"drift_dt": drifts[0], "drift_dt_half": drifts[1], "ratio": drifts[0] / drifts[1]}
+    return out
+
+
 def our_arm(args):
     import torch
     rank, local, world = dist_env()
@@ -651,6 +689,9 @@ def our_arm(args):
     energy = None
     if not args.no_energy and rank == 0:
         energy = energy_arm(P, args)
+    vecpot = None
+    if not args.no_vecpot and rank == 0:
+        vecpot = vecpot_arm(P)
     order5 = None
     if not args.no_order5:
         order5 = order5_arm(P, torch, wl, stream, hbm_peak, value / world, min(args.steps, 10))
@@ -666,7 +707,7 @@ def our_arm(args):
                           "l2": "inputs larger than L2 (3.76 GB of particle SoA per replica); no flush"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                "fp64": fp64, "batched": batched, "adjoint": adjoint, "laser": laser, "l_a_2_5": order5,
-               "energy": energy}
+               "energy": energy, "vector_potential": vecpot}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

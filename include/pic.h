@@ -300,6 +300,29 @@ enum {
 int pic_profile(pic_grid *g, int enable);
 int pic_profile_read(pic_grid *g, double ms[PIC_PROF_N], long long count[PIC_PROF_N]);
 
+/* ---- Vector-potential formulation (Sec. 4.2) -----------------------------------------
+ * pic_set_vector_potential starts tracking the vector potential A^{n-1/2} on the
+ * E points (three arrays of the grid's precision, runs concatenated like the
+ * fields; host or device memory, copied).  From then on every E step (pic_step,
+ * pic_yee_update(PIC_E_FULL)) first advances it by Eq. dadt,
+ * A^{n+1/2} = A^{n-1/2} - c dt E^n.  With set_B != 0 the call also sets
+ * B^{n-1/2} = curl_h A^{n-1/2} (Eq. viaA, grid form:
+ * Bx[i,j,k] = (Az[i,j,k] - Az[i,j-1,k])/dy - (Ay[i,j,k] - Ay[i,j,k-1])/dz,
+ * cyclically), so that B stays the curl of A.  A = NULL stops tracking.  The
+ * vector potential is not part of a state snapshot, and pic_step_persistent and
+ * pic_step_graph refuse a grid that tracks it (PIC_ERR_INVALID_ARG).
+ * pic_generalized_momentum_run returns P = sum_p m_p w_p^{n-1/2} +
+ * (q_p/c) A^{n-1/2}(x_p^n - (dt/2) u_p^{n-1/2}) over the run's particles, A
+ * interpolated with the E weights alpha of the grid's interpolation (Eq. A),
+ * summed in FP64; it is conserved along an axis the fields do not depend on
+ * (Sec. 4.2, up to the time discretization).  Errors: PIC_ERR_INVALID_ARG for
+ * null arguments or a bad run; PIC_ERR_STATE when no vector potential is
+ * tracked. */
+int pic_set_vector_potential(pic_grid *g, const void *const A[3], int on_device, int set_B);
+int pic_get_vector_potential(pic_grid *g, void *A[3], int on_device);
+int pic_generalized_momentum(pic_grid *g, double P[3]);
+int pic_generalized_momentum_run(pic_grid *g, int run, double P[3]);
+
 /* ---- State snapshots ------------------------------------------------------------
  * A snapshot is one contiguous blob: a 64-byte header ("PICS", version 3,
  * dims, precision, group count, sort phase, particle, cell, tile and run

@@ -387,8 +387,14 @@ int launch_fields(pic_grid *g, int which, int zero_j)
     long long maxc = 0;
     for (auto &r : g->runs) maxc = std::max(maxc, (long long)r.dev.n[0] * r.dev.n[1] * r.dev.n[2]);
     ProfScope ps(g, which == PIC_B_HALF ? PIC_PROF_YEE_B : PIC_PROF_YEE_E);
-    cudaError_t e = launch_yee(g->prec, which, zero_j, g->stream, g->d_runs, (int)g->runs.size(), maxc, g->E, g->B,
-                               g->J, g->dims, g->d_ant_n);
+    cudaError_t e;
+    if (which == PIC_E_FULL && g->vecpot) {   // Eq. dadt with E^n, before the E step changes it
+        e = launch_update_A(g->prec, g->stream, g->d_runs, (int)g->runs.size(), maxc, g->d_A, g->E);
+        launch_count_add(g, 1);
+        if (e != cudaSuccess) return cuda_fail(e, "vector potential");
+    }
+    e = launch_yee(g->prec, which, zero_j, g->stream, g->d_runs, (int)g->runs.size(), maxc, g->E, g->B, g->J,
+                   g->dims, g->d_ant_n);
     launch_count_add(g, 1);
     if (e != cudaSuccess) return cuda_fail(e, "Yee kernel");
     if (which == PIC_E_FULL && g->antennas > 0) {   // the E step ends a step of the antenna clock
@@ -555,6 +561,8 @@ void destroy_grid(pic_grid *g)
         if (ev) cudaEventDestroy(ev);
     for (int c = 0; c < 3; ++c) {
         dfree(g->adj_B1[c]);
+        dfree(g->d_A[c]);
+        if (c == 0) dfree(g->d_gm);
         dfree(g->adj_lamJ[c]);
     }
     graph_drop(g);
@@ -1177,6 +1185,7 @@ int pic_step_persistent(pic_grid *g, int nsteps)
     if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
     if (nsteps < 0) return fail(PIC_ERR_INVALID_ARG, "negative step count");
     if (g->order2 != 3) return fail(PIC_ERR_INVALID_ARG, "the persistent batch step is built for l_a = 1 1/2");
+    if (g->vecpot) return fail(PIC_ERR_INVALID_ARG, "the vector potential is advanced by pic_step and pic_yee_update");
     if (g->total == 0) return pic_step(g, nsteps);
     for (int s = 0; s < nsteps; ++s) {
         int rc = persistent_step(g);
@@ -1231,6 +1240,7 @@ int pic_step_graph(pic_grid *g, int nsteps)
     if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
     if (nsteps < 0) return fail(PIC_ERR_INVALID_ARG, "negative step count");
     if (g->order2 != 3) return fail(PIC_ERR_INVALID_ARG, "the persistent batch step is built for l_a = 1 1/2");
+    if (g->vecpot) return fail(PIC_ERR_INVALID_ARG, "the vector potential is advanced by pic_step and pic_yee_update");
     if (!g->stream) return fail(PIC_ERR_INVALID_ARG, "graph replay needs a non-default stream");
     if (g->total == 0) return pic_step(g, nsteps);
     const int span = 2 * g->sort_interval;
@@ -1329,6 +1339,61 @@ int pic_diagnostics_run(pic_grid *g, int run, pic_diag *out)
 }
 
 int pic_diagnostics(pic_grid *g, pic_diag *out) { return pic_diagnostics_run(g, 0, out); }
+
+// ---- vector potential ------------------------------------------------------------
+int pic_set_vector_potential(pic_grid *g, const void *const A[3], int on_device, int set_B)
+{
+    if (!g) return fail(PIC_ERR_INVALID_ARG, "null grid");
+    if (!A) {   // stop tracking
+        for (int c = 0; c < 3; ++c) { dfree(g->d_A[c]); g->d_A[c] = nullptr; }
+        g->vecpot = 0;
+        return PIC_OK;
+    }
+    for (int c = 0; c < 3; ++c)
+        if (!A[c]) return fail(PIC_ERR_INVALID_ARG, "null vector potential component");
+    const size_t bytes = g->total_cells * elem(g);
+    for (int c = 0; c < 3; ++c)
+        if (!g->d_A[c]) CK(dalloc_bytes(&g->d_A[c], bytes), "vector potential");
+    if (!g->d_gm) CK(dalloc(&g->d_gm, 3), "generalized momentum");
+    for (int c = 0; c < 3; ++c) CK(cudaMemcpyAsync(g->d_A[c], A[c], bytes, kind_in(on_device), g->stream), "set A");
+    g->vecpot = 1;
+    if (set_B) {
+        long long maxc = 0;
+        for (auto &r : g->runs) maxc = std::max(maxc, (long long)r.dev.n[0] * r.dev.n[1] * r.dev.n[2]);
+        CK(launch_curl_A(g->dims, g->prec, g->stream, g->d_runs, (int)g->runs.size(), maxc, g->d_A, g->B), "curl A");
+        launch_count_add(g, 1);
+    }
+    if (!on_device) CK(cudaStreamSynchronize(g->stream), "set A");
+    return PIC_OK;
+}
+
+int pic_get_vector_potential(pic_grid *g, void *A[3], int on_device)
+{
+    if (!g || !A) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    if (!g->vecpot) return fail(PIC_ERR_STATE, "no vector potential is tracked (pic_set_vector_potential)");
+    const size_t bytes = g->total_cells * elem(g);
+    for (int c = 0; c < 3; ++c)
+        if (A[c]) CK(cudaMemcpyAsync(A[c], g->d_A[c], bytes, kind_out(on_device), g->stream), "get A");
+    if (!on_device) CK(cudaStreamSynchronize(g->stream), "get A");
+    return PIC_OK;
+}
+
+int pic_generalized_momentum_run(pic_grid *g, int run, double P[3])
+{
+    int rc = check_run_index(g, run);
+    if (rc != PIC_OK) return rc;
+    if (!P) return fail(PIC_ERR_INVALID_ARG, "null argument");
+    if (!g->vecpot) return fail(PIC_ERR_STATE, "no vector potential is tracked (pic_set_vector_potential)");
+    CK(launch_gen_momentum(g->dims, g->prec, g->order2, g->stream, run, g->total, g->d_group_base,
+                           (int)g->groups.size(), g->d_groups, g->d_runs, g->pool, g->d_A, g->d_gm),
+       "generalized momentum");
+    launch_count_add(g, 1);
+    CK(cudaMemcpyAsync(P, g->d_gm, 3 * sizeof(double), cudaMemcpyDeviceToHost, g->stream), "generalized momentum");
+    CK(cudaStreamSynchronize(g->stream), "generalized momentum");
+    return PIC_OK;
+}
+
+int pic_generalized_momentum(pic_grid *g, double P[3]) { return pic_generalized_momentum_run(g, 0, P); }
 
 // ---- state snapshots -----------------------------------------------------------
 struct StateHeader {

@@ -143,6 +143,16 @@ cudaError_t launch_particles_adj(int dims, int prec, cudaStream_t st, const AdjL
                                  void *const E[3], void *const B1[3], void *const lamJ[3], void *const lamE[3],
                                  void *const lamB1[3], void *const lamx[3], void *const lamw[3]);
 size_t adjoint_smem_bytes(int dims, int prec, const int tile[3], int halo, const int pitch[2]);
+
+// Vector-potential formulation (pic_vecpot.cu): A -= c dt E (Eq. dadt), B = curl_h A
+// (Eq. viaA), and the generalized momentum of one run's particles into out[3].
+cudaError_t launch_update_A(int prec, cudaStream_t st, const RunDev *runs, int nruns, long long max_cells,
+                            void *const A[3], void *const E[3]);
+cudaError_t launch_curl_A(int dims, int prec, cudaStream_t st, const RunDev *runs, int nruns, long long max_cells,
+                          void *const A[3], void *const B[3]);
+cudaError_t launch_gen_momentum(int dims, int prec, int order2, cudaStream_t st, int run, long long total,
+                                const long long *gbase, int ngroups, const GroupDev *groups, const RunDev *runs,
+                                const PoolBuf &P, void *const A[3], double *out);
 cudaError_t adjoint_set_smem_limit(int dims, int prec, size_t bytes);
 
 }  // namespace pic
@@ -223,6 +233,10 @@ struct pic_grid {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_marks;
     std::vector<cudaEvent_t> prof_free;
 
+    // vector potential A at the E points (pic_set_vector_potential), advanced with the E step
+    void *d_A[3] = {nullptr, nullptr, nullptr};
+    int vecpot = 0;
+    double *d_gm = nullptr;          // generalized momentum result (3 doubles)
     // adjoint scratch: B^n, lamJ (field-sized, allocated on first use)
     void *adj_B1[3] = {nullptr, nullptr, nullptr};
     void *adj_lamJ[3] = {nullptr, nullptr, nullptr};

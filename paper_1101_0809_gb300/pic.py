@@ -412,6 +412,33 @@ def pic_adjoint_steps(g, states, lamE, lamB, lamx, lamw):
                                   _triple(lamx)[0], _triple(lamw)[0]))
 
 
+_lib.pic_set_vector_potential.argtypes = [_VP, C.POINTER(_VP), C.c_int, C.c_int]
+_lib.pic_get_vector_potential.argtypes = [_VP, _VP3, C.c_int]
+_lib.pic_generalized_momentum_run.argtypes = [_VP, C.c_int, C.POINTER(C.c_double)]
+_lib.pic_generalized_momentum.argtypes = [_VP, C.POINTER(C.c_double)]
+
+
+def pic_set_vector_potential(g, A, set_B=True):
+    """Track the vector potential A (3 arrays or tensors; None stops tracking);
+    with set_B also B = curl_h A."""
+    if A is None:
+        _check(_lib.pic_set_vector_potential(g, None, 0, 0))
+        return
+    a, d = _triple(A)
+    _check(_lib.pic_set_vector_potential(g, a, d, 1 if set_B else 0))
+
+
+def pic_get_vector_potential(g, A):
+    a, d = _triple(A)
+    _check(_lib.pic_get_vector_potential(g, a, d))
+
+
+def pic_generalized_momentum(g, run=0):
+    out = (C.c_double * 3)()
+    _check(_lib.pic_generalized_momentum_run(g, run, out))
+    return np.array(out[:])
+
+
 def pic_set_adjoint_tiled(g, tiled):
     _check(_lib.pic_set_adjoint_tiled(g, 1 if tiled else 0))
 

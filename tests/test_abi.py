@@ -117,5 +117,9 @@ def test_null_arguments_return_errors(P):
     assert lib.pic_set_adjoint_tiled(None, 1) == P.PIC_ERR_INVALID_ARG
     assert lib.pic_step_saving(None, 1, None) == P.PIC_ERR_INVALID_ARG
     z = P._VP3()
+    assert lib.pic_get_vector_potential(None, z, 0) == P.PIC_ERR_INVALID_ARG
+    out = (C.c_double * 3)()
+    assert lib.pic_generalized_momentum_run(None, 0, out) == P.PIC_ERR_INVALID_ARG
+    z = P._VP3()
     assert lib.pic_adjoint_steps(None, None, 1, z, z, z, z) == P.PIC_ERR_INVALID_ARG
     assert lib.pic_set_antenna(None, 0, None) == P.PIC_ERR_INVALID_ARG
