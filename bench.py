@@ -493,7 +493,7 @@ def vecpot_arm(P):
     """Generalized-momentum conservation (Sec. 4.2) with the vector-potential
     formulation: 262,144 test particles (w ~ N(0, 0.3c), negligible charge) in
     the static field A_z = 3 (sin(2 pi 8 x/256) + cos(2 pi 8 y/256)) of a 2D
-    256^2 grid, FP64, over 120 time units of 0.4 / nsub steps; the largest
+    256^2 grid, FP64, over 48 time units (120 x nsub steps of 0.4 / nsub); the largest
     change of the summed P_z per particle, for dt and dt/2, with l_a = 1 1/2
     and with the interpolation of Eq. wrong1."""
     import numpy as np
@@ -505,7 +505,7 @@ def vecpot_arm(P):
     x[0] = rng.uniform(0, n, count)
     x[1] = rng.uniform(0, n, count)
     w = rng.normal(0, 0.3, (3, count))
-    out = {"workload": "262,144 test particles in a static A_z(x, y) on a 2D 256^2 grid, FP64, 120 time units",
+    out = {"workload": "262,144 test particles in a static A_z(x, y) on a 2D 256^2 grid, FP64, 48 time units",
            "unit": "largest |P_z(t) - P_z(0)| per particle and unit weight"}
     for order2, name in ((3, "l_a_1_5"), (4, "wrong1_l_2")):
         drifts = []
