@@ -62,9 +62,11 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
 {
     const size_t smem =
         particles_smem_bytes(dims, prec, mode, max_tile_x, max_tile_y, max_tile_z, halo, p0, p1, order2);
-    if (order2 == 5)
+    if (order2 == 5) {
+        const int tile[3] = {max_tile_x, max_tile_y, max_tile_z};
         return launch_particles_o5(dims, prec, mode, st, max_items, smem, items, n_items, runs, groups, P, E, B, J,
-                                   old_cell, old_off, halo, err);
+                                   old_cell, old_off, halo, err, tile, p0, p1);
+    }
     if (order2 == 4)
         return launch_particles_w1(dims, prec, mode, st, max_items, smem, items, n_items, runs, groups, P, E, B, J,
                                    old_cell, old_off, halo, err);

@@ -822,7 +822,8 @@ static cudaError_t particles_ord_set_smem_limit_t(int dims, int prec, int mode, 
 cudaError_t launch_particles_o5(int dims, int prec, int mode, cudaStream_t st, int max_items, size_t smem,
                                 const WorkItem *items, const int *n_items, const RunDev *runs, const GroupDev *groups,
                                 const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
-                                int *old_cell, void *const old_off[3], int halo, int *err);
+                                int *old_cell, void *const old_off[3], int halo, int *err, const int tile[3], int p0,
+                                int p1);
 cudaError_t particles_o5_set_smem_limit(int dims, int prec, int mode, size_t bytes);
 cudaError_t launch_particles_w1(int dims, int prec, int mode, cudaStream_t st, int max_items, size_t smem,
                                 const WorkItem *items, const int *n_items, const RunDev *runs, const GroupDev *groups,

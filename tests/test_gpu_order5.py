@@ -117,12 +117,14 @@ def test_split_calls_equal_the_step(P, which):
     grid.close()
 
 
-@pytest.mark.parametrize("which", ["2d", "3d", "3d-8x8x4"])
+@pytest.mark.parametrize("which", ["2d", "3d", "3d-8x8x4", "3d-4x4x4"])
 def test_fp32_one_step_from_the_rounded_oracle_state(P, which):
     wl = W.c0_small2d() if which == "2d" else small3d()
-    tile = (8, 8, 4) if which == "3d-8x8x4" else None
+    tile = {"3d-8x8x4": (8, 8, 4), "3d-4x4x4": (4, 4, 4)}.get(which)
     g, osp, E, B, J = run_oracle(wl, 5)
     grid = grid5(P, wl, P.PIC_FP32, tile=tile)
+    if which == "3d-4x4x4":
+        assert tuple(P.pic_tile_layout(grid.h)[2]) == (12, 12)    # the fixed-geometry kernel
     grid.set_fields([a.astype(np.float32) for a in E], [a.astype(np.float32) for a in B])
     for s, sp in enumerate(osp):
         grid.load(s, sp.q, sp.m, sp.weight, sp.x, sp.w.astype(np.float32).astype(np.float64))
