@@ -60,6 +60,9 @@ def parse():
     return ap.parse_args()
 
 
+from paper_1101_0809_gb300.replicas import max_over_ranks  # noqa: E402  (host arithmetic only)
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -232,9 +235,7 @@ def timed_steps(P, torch, grid, steps, dist=None, sampler=None):
     P.pic_profile(grid.h, False)
     launches = P.pic_kernel_launches(grid.h) - l0
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(dist, ms, "cuda")
         dist.barrier()
     return ms, prof, launches, clocks
 
@@ -294,9 +295,7 @@ def batched_arm(P, W, torch, args, dist):
     launches = P.pic_kernel_launches(b.h) - l0
     P.pic_sync(b.h)
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(dist, ms, "cuda")
     npart = sum(wl.n_particles for wl in runs)
     ncell = sum(wl.n_cells for wl in runs)
     b.close()
@@ -611,9 +610,7 @@ def our_arm(args):
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
             if dist is not None:
-                t = torch.tensor([el], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                el = float(t.item())
+                el = max_over_ranks(dist, el, "cuda")
             return el
 
         nbytes = P.pic_state_bytes(grid.h)
