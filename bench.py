@@ -37,7 +37,7 @@ WORKLOAD = ("3D3V periodic 128^3 Yee grid, electrons + ions (mass ratio 1836), 3
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=24, help="timed steps (24: three whole sort intervals)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
