@@ -342,6 +342,16 @@ long long pic_state_bytes(pic_grid *g);
 int pic_state_save(pic_grid *g, void *dst, int on_device);
 int pic_state_restore(pic_grid *g, const void *src, int on_device);
 
+/* pic_state_restore without the final wait: the header is read and checked
+ * at once (a device snapshot's header after a synchronization of the grid's
+ * stream), and the copies are only enqueued on the grid's stream, so that a
+ * host-to-device restore of one grid can run under the kernels of another
+ * grid on another stream.  The caller keeps src allocated and unchanged until
+ * the grid's stream has passed the copies (pic_sync, or a call that returns
+ * results, such as pic_diagnostics).  Errors: those of pic_state_restore; a
+ * CUDA error of a copy may be reported by a later call. */
+int pic_state_restore_async(pic_grid *g, const void *src, int on_device);
+
 /* The recompute pass of a checkpointed adjoint: nsteps steps as
  * pic_step(g, 1) each, with a device snapshot of the state before step s
  * written to states[s] (nsteps device buffers of pic_state_bytes(g) bytes,

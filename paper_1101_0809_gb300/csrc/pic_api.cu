@@ -1535,17 +1535,34 @@ int pic_state_save(pic_grid *g, void *dst, int on_device)
     return PIC_OK;
 }
 
-int pic_state_restore(pic_grid *g, const void *src, int on_device)
+// Reads and checks a snapshot's header, then enqueues the restore; waits for
+// the copies only if wait is set.
+static int state_restore(pic_grid *g, const void *src, int on_device, bool wait)
 {
     if (!g || !src) return fail(PIC_ERR_INVALID_ARG, "null argument");
     StateHeader h;
-    CK(cudaStreamSynchronize(g->stream), "state header");   // a device snapshot may still be in flight
-    CK(cudaMemcpy(&h, src, sizeof(h), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost), "state header");
+    if (on_device) {
+        // a device snapshot may still be in flight on the grid's stream
+        CK(cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDeviceToHost, g->stream), "state header");
+        CK(cudaStreamSynchronize(g->stream), "state header");
+    } else {
+        memcpy(&h, src, sizeof(h));
+    }
     int rc = check_header(g, h);
     if (rc == PIC_OK) rc = restore_body(g, src, on_device, h);
     if (rc != PIC_OK) return rc;
-    CK(cudaStreamSynchronize(g->stream), "state restore");
+    if (wait) CK(cudaStreamSynchronize(g->stream), "state restore");
     return PIC_OK;
+}
+
+int pic_state_restore(pic_grid *g, const void *src, int on_device)
+{
+    return state_restore(g, src, on_device, true);
+}
+
+int pic_state_restore_async(pic_grid *g, const void *src, int on_device)
+{
+    return state_restore(g, src, on_device, false);
 }
 
 int pic_step_saving(pic_grid *g, int nsteps, void *const *states)

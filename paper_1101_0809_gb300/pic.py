@@ -363,6 +363,7 @@ _lib.pic_state_bytes.argtypes = [_VP]
 _lib.pic_state_bytes.restype = C.c_longlong
 _lib.pic_state_save.argtypes = [_VP, _VP, C.c_int]
 _lib.pic_state_restore.argtypes = [_VP, _VP, C.c_int]
+_lib.pic_state_restore_async.argtypes = [_VP, _VP, C.c_int]
 _lib.pic_adjoint_step.argtypes = [_VP, _VP3, _VP3, _VP3, _VP3]
 _lib.pic_adjoint_yee_half_B.argtypes = [_VP, _VP3, _VP3]
 _lib.pic_step_saving.argtypes = [_VP, C.c_int, C.POINTER(_VP)]
@@ -392,6 +393,13 @@ def pic_state_save(g, dst):
 def pic_state_restore(g, src):
     p, d = _addr(src)
     _check(_lib.pic_state_restore(g, p, d))
+
+
+def pic_state_restore_async(g, src):
+    """Enqueues the restore on the grid's stream and returns; src must stay
+    unchanged until the stream has passed it (pic_sync, pic_diagnostics)."""
+    p, d = _addr(src)
+    _check(_lib.pic_state_restore_async(g, p, d))
 
 
 def pic_adjoint_step(g, lamE, lamB, lamx, lamw):

@@ -255,6 +255,76 @@ def test_state_snapshot_restarts_the_same_run(env):
     grid.close()
 
 
+def test_async_restore_on_two_streams_matches_the_waiting_restore(env):
+    """pic_state_restore_async from a pinned host snapshot, two FP32 3D grids on
+    two streams taking steps in turn (each upload under the other grid's
+    kernels), and from a device snapshot: every step gives the state and
+    diagnostics of pic_state_restore + pic_step on one grid."""
+    P, torch = env
+    wl = W.thermal_plasma("3D", 3, (24, 16, 20), 3, 0.1, 2, W.SEED_BASE + 51, ions=1836.0, tile=(8, 4, 4),
+                          dt_courant=0.45)
+
+    def grid_on(stream):
+        desc = P.make_desc(3, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP32, tile=wl.tile, rho_bg=wl.rho_bg,
+                           stream=stream.cuda_stream)
+        g = P.Grid(desc)
+        for s, sp in enumerate(wl.species):
+            g.load(s, sp.q, sp.m, sp.weight, sp.x, sp.w)
+        return g
+
+    s0, s1 = torch.cuda.Stream(), torch.cuda.Stream()
+    ga, gb = grid_on(s0), grid_on(s1)
+    P.pic_step(ga.h, 3)
+    host = torch.empty(P.pic_state_bytes(ga.h), dtype=torch.uint8).pin_memory()
+    P.pic_state_save(ga.h, host)
+    P.pic_state_restore(ga.h, host)
+    P.pic_step(ga.h, 1)
+    want_d = P.pic_diagnostics(ga.h)
+    E0, B0, J0 = ga.get_fields()
+    parts0 = [ga.particles(s) for s in range(len(wl.species))]
+
+    def check(g, d):
+        # the particle state is bit-exact; J (global float atomics at the tile
+        # borders) and E after it may differ in the last bit
+        assert d.total == pytest.approx(want_d.total, rel=1e-9)
+        E, B, J = g.get_fields()
+        for a in range(3):
+            close(E[a], E0[a], 1e-6, f"E[{a}]")
+            close(B[a], B0[a], 1e-6, f"B[{a}]")
+            close(J[a], J0[a], 1e-6, f"J[{a}]")
+        for s in range(len(wl.species)):
+            cell, off, w, ident = g.particles(s)
+            assert np.array_equal(ident, parts0[s][3]) and np.array_equal(cell, parts0[s][0])
+            for a in range(3):
+                assert np.array_equal(off[a], parts0[s][1][a]) and np.array_equal(w[a], parts0[s][2][a])
+
+    pair = (ga, gb)
+    P.pic_state_restore_async(ga.h, host)
+    P.pic_step(ga.h, 1)
+    for k in range(4):
+        if k + 1 < 4:
+            P.pic_state_restore_async(pair[(k + 1) % 2].h, host)
+            P.pic_step(pair[(k + 1) % 2].h, 1)
+        d = P.pic_diagnostics(pair[k % 2].h)
+        assert d.total == pytest.approx(want_d.total, rel=1e-9)
+    P.pic_sync(ga.h)
+    P.pic_sync(gb.h)
+    check(gb, P.pic_diagnostics(gb.h))
+
+    dev = host.to("cuda")
+    P.pic_step(ga.h, 2)
+    P.pic_state_restore_async(ga.h, dev)
+    P.pic_step(ga.h, 1)
+    check(ga, P.pic_diagnostics(ga.h))
+    bad = host.clone()
+    bad[0] = ord("X")
+    with pytest.raises(P.PicError) as e:
+        P.pic_state_restore_async(gb.h, bad)
+    assert e.value.code == P.PIC_ERR_INVALID_ARG
+    ga.close()
+    gb.close()
+
+
 def test_batched_segment_calls_match_step_by_step(env):
     """pic_step_saving + pic_adjoint_steps (one host synchronization per
     segment) against pic_state_save / pic_step / pic_state_restore /
