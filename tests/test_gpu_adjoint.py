@@ -286,7 +286,7 @@ def test_async_restore_on_two_streams_matches_the_waiting_restore(env):
     def check(g, d):
         # the particle state is bit-exact; J (global float atomics at the tile
         # borders) and E after it may differ in the last bit
-        assert d.total == pytest.approx(want_d.total, rel=1e-9)
+        assert d["total"] == pytest.approx(want_d["total"], rel=1e-9)
         E, B, J = g.get_fields()
         for a in range(3):
             close(E[a], E0[a], 1e-6, f"E[{a}]")
@@ -306,7 +306,7 @@ def test_async_restore_on_two_streams_matches_the_waiting_restore(env):
             P.pic_state_restore_async(pair[(k + 1) % 2].h, host)
             P.pic_step(pair[(k + 1) % 2].h, 1)
         d = P.pic_diagnostics(pair[k % 2].h)
-        assert d.total == pytest.approx(want_d.total, rel=1e-9)
+        assert d["total"] == pytest.approx(want_d["total"], rel=1e-9)
     P.pic_sync(ga.h)
     P.pic_sync(gb.h)
     check(gb, P.pic_diagnostics(gb.h))
