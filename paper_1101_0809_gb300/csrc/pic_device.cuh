@@ -564,9 +564,11 @@ __device__ __forceinline__ void gather5(const Rd &rd, const R fx[3], const R Sx[
 {
     constexpr int NZS = DIM == 3 ? 4 : 1, NZF = DIM == 3 ? 3 : 1;
     R ex = 0, ey = 0, ez = 0, bx = 0, by = 0, bz = 0;
-#pragma unroll
+    // The z planes are a loop, not unrolled: unrolled, the 252 taps of the
+    // 3D gather need more than the 128 registers of two blocks per SM and spill.
+#pragma unroll 1
     for (int c = 0; c < NZS; ++c) {   // S along z: E^x, E^y, B^z
-        const R wz = DIM == 3 ? Sz[c] : R(1);
+        const R wz = DIM == 3 ? (c == 0 ? Sz[0] : c == 1 ? Sz[1] : c == 2 ? Sz[2] : Sz[3]) : R(1);
         const int oz = DIM == 3 ? c - 2 : 0;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -582,9 +584,9 @@ __device__ __forceinline__ void gather5(const Rd &rd, const R fx[3], const R Sx[
             bz += fy[b] * wz * u;
         }
     }
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < NZF; ++c) {   // f along z: E^z, B^x, B^y
-        const R wz = DIM == 3 ? fz[c] : R(1);
+        const R wz = DIM == 3 ? (c == 0 ? fz[0] : c == 1 ? fz[1] : fz[2]) : R(1);
         const int oz = DIM == 3 ? c - 1 : 0;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -630,9 +632,11 @@ __device__ __forceinline__ void gather_w1(const Rd &rd, const R Sx[3], const R S
     wrong1_points(Sz, gz);
     constexpr int NZS = DIM == 3 ? 3 : 1, NZG = DIM == 3 ? 4 : 1;
     R ex = 0, ey = 0, ez = 0, bx = 0, by = 0, bz = 0;
-#pragma unroll
+    // The z planes are a loop, not unrolled: unrolled, the 252 taps of the
+    // 3D gather need more than the 128 registers of two blocks per SM and spill.
+#pragma unroll 1
     for (int c = 0; c < NZS; ++c) {   // S along z: E^x, E^y, B^z
-        const R wz = DIM == 3 ? Sz[c] : R(1);
+        const R wz = DIM == 3 ? (c == 0 ? Sz[0] : c == 1 ? Sz[1] : c == 2 ? Sz[2] : Sz[3]) : R(1);
         const int oz = DIM == 3 ? c - 1 : 0;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {

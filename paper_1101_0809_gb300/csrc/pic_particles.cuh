@@ -515,7 +515,18 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                 axis_window5(a0, b0, 0, X);
                 axis_window5(a1, b1, 0, Y);
                 if (DIM == 3) axis_window5(a2, b2, 0, Z); else Z = X;
-                deposit_local5(base, X, Y, Z, uz, 0);
+                if constexpr (FIX) {
+                    // fixed stencil: the bias comes off once per word at the flush
+                    FixedAccT<false> acc;
+                    for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
+                    acc.base = base;
+                    acc.s1 = P0;
+                    acc.s2 = P0 * P1;
+                    deposit5<DIM>(acc, X, Y, Z, kfs, uz, 0);
+                    atomicAdd(&scnt[base], 1);
+                } else {
+                    deposit_local5(base, X, Y, Z, uz, 0);
+                }
             } else {
                 AxisWin<R> X, Y, Z;
                 axis_window_still(o0, n0, X);
@@ -594,6 +605,41 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             // for J^x (faces 0, 1; cells -1..1), likewise for J^y and J^z, so a
             // cell l received sum_{b in l - stencil} cnt[b] of them
             unsigned nst[3] = {0u, 0u, 0u};
+            if constexpr (FIX && ORD == 5) {
+                // l_a = 2 1/2: the stencil of base b covers b + (dx, dy, dz) with
+                // dx in {-1, 0, 1} (faces) and dy, dz in {-2, ..., 1} (cells) for
+                // J^x, likewise for J^y and J^z; so the bases of word l are
+                // l + o, o in {-1, ..., 2} per axis, without the o_a = 2 plane for
+                // J^a.  A base is the local cell (in [-G, T + G)) plus the
+                // half-offset flag (0 or 1) plus G + JH, so bases lie in
+                // [JH, T + 2G + JH] = [JH, je - JH] along each axis: only those
+                // indices are read, which keeps every read in the tile.
+                bool vx[4], vy[4], vz[4];
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    vx[o] = lx + o - 1 >= JH && lx + o - 1 <= je0 - JH;
+                    vy[o] = ly + o - 1 >= JH && ly + o - 1 <= je1 - JH;
+                    vz[o] = DIM == 3 ? (lz + o - 1 >= JH && lz + o - 1 <= je2 - JH) : o == 1;
+                }
+                unsigned tot = 0, px = 0, py = 0, pz = 0;   // all, and the o = 2 planes
+#pragma unroll
+                for (int oz = -1; oz <= (DIM == 3 ? 2 : -1); ++oz)
+#pragma unroll
+                    for (int oy = -1; oy <= 2; ++oy)
+#pragma unroll
+                        for (int ox = -1; ox <= 2; ++ox) {
+                            const int dz = DIM == 3 ? oz : 0;
+                            if (!(vx[ox + 1] && vy[oy + 1] && vz[dz + 1])) continue;
+                            const unsigned v = (unsigned)scnt[l + ox + P0 * (oy + P1 * dz)];
+                            tot += v;
+                            if (ox == 2) px += v;
+                            if (oy == 2) py += v;
+                            if (DIM == 3 && oz == 2) pz += v;
+                        }
+                nst[0] = tot - px;
+                nst[1] = tot - py;
+                nst[2] = tot - pz;
+            }
             if constexpr (FIX && ORD != 5) {
                 if (lx >= 1 && lx < je0 - 1 && ly >= 1 && ly < je1 - 1 && (DIM == 2 || (lz >= 1 && lz < je2 - 1))) {
                     if (DIM == 3) {

@@ -143,6 +143,45 @@ def test_fp32_one_step_from_the_rounded_oracle_state(P, which):
     grid.close()
 
 
+@pytest.mark.parametrize("which", ["2d", "3d-4x4x4"])
+def test_fp32_one_step_with_particles_drifted_into_the_halo(P, which):
+    """Six unsorted steps carry particles into the one-cell halo of their tile,
+    some past its upper edge with offset >= 1/2, where the base index reaches its
+    largest value in the current tile; then one step against the oracle from the
+    GPU's own state."""
+    wl = ragged2d(vth=0.3) if which == "2d" else small3d(vth=0.3)
+    tile = (8, 8, 1) if which == "2d" else (4, 4, 4)
+    grid = grid5(P, wl, P.PIC_FP32, tile=tile, halo=1, sort_interval=1000)
+    P.pic_step(grid.h, 6)
+    g = oracle_grid(wl, ORDER2)
+    osp = oracle_species(wl)
+    E, B, _ = grid.get_fields()
+    E = [a.astype(np.float64) for a in E]
+    B = [a.astype(np.float64) for a in B]
+    J = g.zeros()
+    edge = 0
+    for s, sp in enumerate(wl.species):
+        cell, off, w, ident = grid.particles(s)
+        order = np.argsort(ident)
+        osp[s].x[:] = positions_from_gpu(wl, cell[order], [o[order] for o in off])
+        for a in range(3):
+            osp[s].w[a][:] = w[a][order]
+        # local coordinate in the tile the particle was sorted into at the load
+        for a in range(wl.dims):
+            n = wl.n[a]
+            t0 = (np.floor(sp.x[a]).astype(np.int64) % n) // tile[a] * tile[a]
+            li = (np.floor(osp[s].x[a]).astype(np.int64) - t0) % n
+            li[li > n // 2] -= n
+            fr = osp[s].x[a] - np.floor(osp[s].x[a])
+            edge += int(np.count_nonzero((li == tile[a]) & (fr >= 0.5)))
+    assert edge > 0
+    P.pic_step(grid.h, 1)
+    P.pic_sync(grid.h)
+    O.step(g, E, B, J, osp)
+    check_state(wl, grid, osp, E, B, J, FP32_TOL, check_cells=False)
+    grid.close()
+
+
 def test_fp32_gauss_residual_over_many_steps(P):
     wl = W.c0_small2d(steps=200)
     grid = grid5(P, wl, P.PIC_FP32)
