@@ -92,7 +92,9 @@ typedef struct {
  * current tile of its tile (tile origin (ox, oy, oz), halo h, tile pitches
  * P0, P1 as reported by pic_tile_layout), and r the number of earlier
  * particles (input order) of the same tile with the same b; so that 32
- * consecutive particles fall on 32 different banks. */
+ * consecutive particles fall on 32 different banks.  For l_a = 2 1/2 the
+ * interpolation is anchored at the base index, the cell plus (offset >= 1/2)
+ * per axis, so i, j, k in base are those of the base index. */
 enum { PIC_SORT_BANKED = 0, PIC_SORT_STABLE = 1 };
 
 /* One species.  The macro-particle charge is q_p = weight*q, its mass m_p = weight*m;

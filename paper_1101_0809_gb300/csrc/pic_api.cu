@@ -360,7 +360,7 @@ int do_sort(pic_grid *g)
                                          g->d_group_base, (int)g->groups.size(), g->d_runs, g->total_tiles, g->sort,
                                          g->tile_start, g->item_scan, g->items, g->n_items, g->ppi,
                                          g->halo + (g->order2 == 5 ? 1 : 0),   // the current tile's bank base
-                                         g->sort_order == PIC_SORT_BANKED ? 1 : 0, &nl);
+                                         g->sort_order == PIC_SORT_BANKED ? 1 : 0, g->order2 == 5 ? 1 : 0, &nl);
     launch_count_add(g, nl);
     if (e != cudaSuccess) return cuda_fail(e, "tile sort");
     if (g->total > 0 && !g->groups.empty()) std::swap(g->pool, g->pool_alt);

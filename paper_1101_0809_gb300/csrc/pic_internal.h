@@ -85,7 +85,7 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  const PoolBuf &dst, const GroupDev *groups, const long long *group_base_dev,
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
-                                 int particles_per_item, int halo, int banked, int *launches);
+                                 int particles_per_item, int halo, int banked, int half, int *launches);
 // Work items (ranges of at most particles_per_item particles of one tile) from
 // the tile starts of the current particle order.
 cudaError_t build_items(cudaStream_t st, const long long *tile_start, int total_tiles, int particles_per_item,

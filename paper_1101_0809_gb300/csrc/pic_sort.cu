@@ -219,9 +219,14 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(const unsigned *keys
 // the r-th particle (r = its rank among the tile's particles of bank b) goes to
 // slot S(r) + #{b' < b : cnt[b'] > r}, with S(r) = sum_b' min(cnt[b'], r).  The
 // key order (by tile) is unchanged; only the order inside a tile changes.
+// With half != 0 (l_a = 2 1/2) the accesses are relative to the base index
+// cell + (offset >= 1/2) per axis, so that index takes the cell's place; the
+// offsets are FP64 (prec 0) or FP32.
 __global__ void __launch_bounds__(kSortThreads) k_bank_order(const long long *tile_start, const unsigned *vals_in,
                                                              unsigned *vals_out, const int *cell, const GroupDev *groups,
-                                                             int ngroups, const RunDev *runs, int halo, int dims)
+                                                             int ngroups, const RunDev *runs, int halo, int dims,
+                                                             int half, int prec, const void *off0, const void *off1,
+                                                             const void *off2)
 {
     constexpr int kRankTab = 1024;   // ranks with a precomputed slot table
     __shared__ unsigned cnt[32];
@@ -255,7 +260,18 @@ __global__ void __launch_bounds__(kSortThreads) k_bank_order(const long long *ti
         const int i = c - r * nx;
         const int k = dims == 3 ? divu31(r, rn.div_ny) : 0;
         const int j = r - k * ny;
-        const int base = (i - ox + halo + 2) + P0 * ((j - oy + halo + 2) + (dims == 3 ? P1 * (k - oz + halo + 2) : 0));
+        int u0 = 0, u1 = 0, u2 = 0;
+        if (half) {
+            auto up = [&](const void *o) -> int {
+                return prec == 0 ? (static_cast<const double *>(o)[v] >= 0.5 ? 1 : 0)
+                                 : (static_cast<const float *>(o)[v] >= 0.5f ? 1 : 0);
+            };
+            u0 = up(off0);
+            u1 = up(off1);
+            if (dims == 3) u2 = up(off2);
+        }
+        const int base = (i + u0 - ox + halo + 2) +
+                         P0 * ((j + u1 - oy + halo + 2) + (dims == 3 ? P1 * (k + u2 - oz + halo + 2) : 0));
         return (unsigned)base & 31u;
     };
     if (tid < 32) {
@@ -401,7 +417,7 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  const PoolBuf &dst, const GroupDev *groups, const long long *group_base_dev,
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
-                                 int particles_per_item, int halo, int banked, int *launches)
+                                 int particles_per_item, int halo, int banked, int half, int *launches)
 {
     cudaError_t e;
     if (total <= 0 || ngroups <= 0) {
@@ -438,7 +454,8 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (banked) {
         k_bank_order<<<(unsigned)total_tiles, kSortThreads, 0, st>>>(tile_start, scr.vals[cur], scr.vals[1 - cur],
-                                                                   src.cell, groups, ngroups, runs, halo, dims);
+                                                                   src.cell, groups, ngroups, runs, halo, dims, half,
+                                                                   prec, src.off[0], src.off[1], src.off[2]);
         *launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         cur = 1 - cur;

@@ -106,13 +106,15 @@ def make_grid(P, wl, precision, stream=None, tile=None, halo=-1, sort_interval=N
     return grid
 
 
-def tile_sort_perm(wl, cells, tile, halo=1, banked=True, pitch=None):
+def tile_sort_perm(wl, cells, tile, halo=1, banked=True, pitch=None, up=None):
     """The tile sort's permutation written out from its definition (integer work,
     compared bit-exactly): sort by tile key; with ``banked``, inside a tile by
     (r, b) where b is the shared-memory bank of the cell's base address in the
     tile's current stage, base = (i-ox+h+2) + P0*((j-oy+h+2) + P1*(k-oz+h+2)) with
     the grid's tile pitches (pic_tile_layout), and r the particle's rank among
-    the tile's particles of bank b in input order.  Returns perm[o] = input
+    the tile's particles of bank b in input order.  ``up`` (l_a = 2 1/2): per
+    axis the 0/1 flags offset >= 1/2, added to i, j, k in the base (the base
+    index of the interpolation), not in the tile key.  Returns perm[o] = input
     index at slot o."""
     nx, ny = wl.n[0], wl.n[1]
     cells = np.asarray(cells, dtype=np.int64)
@@ -123,10 +125,11 @@ def tile_sort_perm(wl, cells, tile, halo=1, banked=True, pitch=None):
     key = (tk * nty + tj) * ntx + ti
     if not banked:
         return np.argsort(key, kind="stable")
+    u = [np.zeros_like(i)] * 3 if up is None else [np.asarray(a, dtype=np.int64) for a in up]
     je0, je1 = pitch if pitch is not None else (T[0] + 2 * halo + 4, T[1] + 2 * halo + 4)
-    base = (i - ti * T[0] + halo + 2) + je0 * (j - tj * T[1] + halo + 2)
+    base = (i + u[0] - ti * T[0] + halo + 2) + je0 * (j + u[1] - tj * T[1] + halo + 2)
     if wl.dims == 3:
-        base = base + je0 * je1 * (k - tk * T[2] + halo + 2)
+        base = base + je0 * je1 * (k + u[2] - tk * T[2] + halo + 2)
     b = base % 32
     kb = key * 32 + b
     idx = np.argsort(kb, kind="stable")          # groups (tile, bank), input order inside

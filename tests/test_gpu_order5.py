@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 from paper_1101_0809_gb300 import workloads as W
 from pichelpers import (FP32_TOL, FP64_TOL, close, compare_particles, fp64_field_tol, make_grid, oracle_grid,
-                        oracle_species, positions_from_gpu)
+                        oracle_species, positions_from_gpu, tile_sort_perm)
 
 pytestmark = pytest.mark.gpu
 ORDER2 = 5
@@ -179,6 +179,34 @@ def test_fp32_one_step_with_particles_drifted_into_the_halo(P, which):
     P.pic_sync(grid.h)
     O.step(g, E, B, J, osp)
     check_state(wl, grid, osp, E, B, J, FP32_TOL, check_cells=False)
+    grid.close()
+
+
+@pytest.mark.parametrize("which", ["2d-fp64", "2d-fp32", "3d-fp32"])
+def test_banked_sort_is_by_the_bank_of_the_base_index(P, which):
+    """After six unsorted steps, pic_sort gives the defined permutation with the
+    bank taken at the base index (the cell plus offset >= 1/2 per axis) and the
+    current tile one cell wider (h = halo + 1); bit-exact."""
+    wl = ragged2d(vth=0.3) if which.startswith("2d") else small3d(vth=0.3)
+    tile = (8, 8, 1) if which.startswith("2d") else (4, 4, 4)
+    prec = P.PIC_FP64 if which.endswith("fp64") else P.PIC_FP32
+    grid = grid5(P, wl, prec, tile=tile, halo=1, sort_interval=1000)
+    P.pic_step(grid.h, 6)
+    before = [grid.particles(s) for s in range(len(wl.species))]
+    P.pic_sort(grid.h)
+    pitch = P.pic_tile_layout(grid.h)[2]
+    moved = 0
+    for s in range(len(wl.species)):
+        cell_b, off_b, w_b, id_b = before[s]
+        cell_a, off_a, w_a, id_a = grid.particles(s)
+        up = [(off_b[a] >= 0.5).astype(np.int64) for a in range(3)]
+        perm = tile_sort_perm(wl, cell_b, tile, 2, True, pitch, up)
+        np.testing.assert_array_equal(id_a, id_b[perm])
+        np.testing.assert_array_equal(cell_a, cell_b[perm])
+        for a in range(3):
+            np.testing.assert_array_equal(off_a[a], off_b[a][perm])
+        moved += int(np.count_nonzero(perm != tile_sort_perm(wl, cell_b, tile, 2, True, pitch)))
+    assert moved > 0     # the half-offset flags change the order
     grid.close()
 
 
