@@ -299,12 +299,96 @@ def batched_arm(P, W, torch, args, dist):
     npart = sum(wl.n_particles for wl in runs)
     ncell = sum(wl.n_cells for wl in runs)
     b.close()
+    accuracy = batched_accuracy(P, runs[::8], best, build, 20)
     world = dist.get_world_size() if dist is not None else 1
     return {"workload": f"{len(runs)} independent 2D3V periodic runs, N ~ U{{32..256}}^2, 4-64 e-/cell, "
                         "v_th ~ U[0.01c, 0.3c], FP32, one cooperative launch per step, CUDA graphs",
             "value": world * npart * nsteps / (ms * 1e-3), "unit": UNIT, "steps": nsteps, "ms_per_step": ms / nsteps,
             "particles": npart, "cells": ncell, "autotuned": best, "autotune_cached": cached,
-            "autotune_table": [[c, t] for c, t, _ in table], "gpu_launches": launches}
+            "autotune_table": [[c, t] for c, t, _ in table], "gpu_launches": launches,
+            "accuracy_vs_fp64": accuracy}
+
+
+def main_accuracy(P, wl, stream, g64, steps):
+    """The FP32 form against the plain FP64 method on the main workload: a fresh
+    FP32 grid takes the `steps` steps that g64 took from the same initial state;
+    the largest relative differences of E and J, the rms relative difference of
+    the momenta and the largest position difference (cells), particle by
+    particle, and both Gauss residuals relative to 4 pi times one species'
+    density."""
+    g32 = build_grid(P, wl, P.PIC_FP32, stream)
+    d0 = P.pic_diagnostics(g32.h)
+    P.pic_step(g32.h, steps)
+    E32, _, J32 = g32.get_fields()
+    E64, _, J64 = g64.get_fields()
+    out = {"steps": steps, "E_max_rel": rel_max(E32, E64), "J_max_rel": rel_max(J32, J64)}
+    num = den = 0.0
+    xmax = 0.0
+    for s in range(len(wl.species)):
+        c32, o32, w32, i32 = g32.particles(s)
+        c64, o64, w64, i64 = g64.particles(s)
+        at = np.empty(i64.shape[0], dtype=np.int64)
+        at[i64] = np.arange(i64.shape[0])
+        k = at[i32]                         # row of each FP32 particle in the FP64 arrays
+        for a in range(3):
+            d = w32[a].astype(np.float64) - w64[a][k]
+            num += float(np.dot(d, d))
+            den += float(np.dot(w64[a], w64[a]))
+        n3 = wl.n
+        for a, (div, mod) in enumerate(((1, n3[0]), (n3[0], n3[1]), (n3[0] * n3[1], n3[2]))):
+            x32 = (c32 // div) % mod + o32[a].astype(np.float64)
+            x64 = (c64[k] // div) % mod + o64[a][k]
+            d = x32 - x64
+            d -= mod * np.round(d / mod)
+            xmax = max(xmax, float(np.abs(d).max()))
+        del c32, o32, w32, i32, c64, o64, w64, i64, at, k
+    out["w_rms_rel"] = math.sqrt(num / den) if den > 0 else 0.0
+    out["x_max_abs_cells"] = xmax
+    rho = abs(wl.species[0].q * wl.species[0].weight) * wl.species[0].x.shape[1] / wl.n_cells
+    d32 = P.pic_diagnostics(g32.h)
+    out["gauss_rel_fp32"] = d32["gauss_resid_max"] / (4 * math.pi * rho)
+    out["energy_rel"] = abs(d32["total"] - P.pic_diagnostics(g64.h)["total"]) / abs(d0["total"])
+    g32.close()
+    return out
+
+
+def rel_max(a, b):
+    """max |a - b| / max |b| over the arrays of two lists."""
+    num = max(float(np.abs(x.astype(np.float64) - y.astype(np.float64)).max()) for x, y in zip(a, b))
+    den = max(float(np.abs(y).max()) for y in b)
+    return num / den if den > 0 else num
+
+
+def batched_accuracy(P, sub, cand, build, steps):
+    """The batched FP32 form (the persistent kernel) against the plain FP64 method
+    (pic_step) on the same runs from the same initial state, after `steps` steps:
+    per run the largest relative difference of E and of the total energy, and the
+    FP32 Gauss residual; the worst run of each."""
+    b32 = build(sub, cand)
+    d64 = [P.make_desc(2, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP64, tile=(cand["tile"], cand["tile"], 1), halo=1,
+                       sort_interval=cand["K"], rho_bg=wl.rho_bg, stream=b32.desc.cuda_stream) for wl in sub]
+    b64 = P.Batch(d64)
+    P.pic_load_particles_runs(b64.h, list(range(len(sub))), 0,
+                              [(wl.species[0].q, wl.species[0].m, wl.species[0].weight) for wl in sub],
+                              [list(wl.species[0].x) for wl in sub], [list(wl.species[0].w) for wl in sub])
+    for r in range(len(sub)):       # the residual references are taken at the initial state
+        P.pic_diagnostics_run(b32.h, r)
+        P.pic_diagnostics_run(b64.h, r)
+    P.pic_step_persistent(b32.h, steps)
+    P.pic_step(b64.h, steps)
+    e_rel, w_rel, gauss = 0.0, 0.0, 0.0
+    for r, wl in enumerate(sub):
+        E32 = b32.get_fields_run(r)[0]
+        E64 = b64.get_fields_run(r)[0]
+        e_rel = max(e_rel, rel_max(E32, E64))
+        a, c = P.pic_diagnostics_run(b32.h, r), P.pic_diagnostics_run(b64.h, r)
+        w_rel = max(w_rel, abs(a["total"] - c["total"]) / abs(c["total"]))
+        rho = abs(wl.species[0].q * wl.species[0].weight) * wl.n_particles / wl.n_cells
+        gauss = max(gauss, a["gauss_resid_max"] / (4 * math.pi * rho))
+    b32.close()
+    b64.close()
+    return {"runs": len(sub), "steps": steps, "fp32": "pic_step_persistent", "fp64": "pic_step",
+            "E_max_rel_worst_run": e_rel, "energy_rel_worst_run": w_rel, "gauss_rel_fp32_worst_run": gauss}
 
 
 def adjoint_arm(P, W, torch, args):
@@ -712,6 +796,8 @@ def our_arm(args):
                 "ms_per_step": ms64 / k64, "dtype": "f64",
                 "roofline_hbm": {"achieved": ach64, "peak": hbm_peak, "unit": "GB/s", "frac": ach64 / hbm_peak},
                 "fp32_speedup": (npart * args.steps / (ms * 1e-3)) / (npart * k64 / (ms64 * 1e-3))}
+        if rank == 0:
+            fp64["fp32_vs_fp64"] = main_accuracy(P, wl, stream, g64, min(args.warmup, 2) + k64)
         g64.close()
 
     batched = None
