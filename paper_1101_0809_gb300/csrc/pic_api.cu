@@ -532,7 +532,7 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
 void destroy_grid(pic_grid *g)
 {
     if (!g) return;
-    if (g->stream || true) cudaStreamSynchronize(g->stream);
+    cudaStreamSynchronize(g->stream);   // work still in flight may use the buffers freed below
     for (int c = 0; c < 3; ++c) {
         dfree(g->E[c]);
         dfree(g->B[c]);

@@ -632,11 +632,11 @@ __device__ __forceinline__ void gather_w1(const Rd &rd, const R Sx[3], const R S
     wrong1_points(Sz, gz);
     constexpr int NZS = DIM == 3 ? 3 : 1, NZG = DIM == 3 ? 4 : 1;
     R ex = 0, ey = 0, ez = 0, bx = 0, by = 0, bz = 0;
-    // The z planes are a loop, not unrolled: unrolled, the 252 taps of the
+    // The z planes are a loop, not unrolled: unrolled, the 132 taps of the
     // 3D gather need more than the 128 registers of two blocks per SM and spill.
 #pragma unroll 1
     for (int c = 0; c < NZS; ++c) {   // S along z: E^x, E^y, B^z
-        const R wz = DIM == 3 ? (c == 0 ? Sz[0] : c == 1 ? Sz[1] : c == 2 ? Sz[2] : Sz[3]) : R(1);
+        const R wz = DIM == 3 ? (c == 0 ? Sz[0] : c == 1 ? Sz[1] : Sz[2]) : R(1);
         const int oz = DIM == 3 ? c - 1 : 0;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
@@ -653,9 +653,9 @@ __device__ __forceinline__ void gather_w1(const Rd &rd, const R Sx[3], const R S
             bz += gy[b] * wz * u;
         }
     }
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < NZG; ++c) {   // g along z: E^z, B^x, B^y
-        const R wz = DIM == 3 ? gz[c] : R(1);
+        const R wz = DIM == 3 ? (c == 0 ? gz[0] : c == 1 ? gz[1] : c == 2 ? gz[2] : gz[3]) : R(1);
         const int oz = DIM == 3 ? c - 1 : 0;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {

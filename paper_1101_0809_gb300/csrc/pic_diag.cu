@@ -464,7 +464,7 @@ __global__ void k_diag_final(const double *pp, int np, const double *pc, int nc,
 }
 
 template <int DIM, typename R, int ORD>
-static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run, long long run_cells,
+static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run,
                           const GroupDev *groups, const long long *group_base, int ngroups, long long total,
                           const PoolBuf &P, void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
                           int np_blocks, int nc_blocks, int *launches, const WorkItem *items, const int *n_items,
@@ -508,22 +508,22 @@ static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run, long lon
 }
 
 template <int ORD>
-static cudaError_t diag_run_o(int dims, int prec, cudaStream_t st, const RunDev *runs, int run, long long run_cells,
+static cudaError_t diag_run_o(int dims, int prec, cudaStream_t st, const RunDev *runs, int run,
                               const GroupDev *groups, const long long *group_base, int ngroups, long long total,
                               const PoolBuf &P, void *const E[3], void *const B[3], DiagScratch &scr, int set_ref,
                               int np_blocks, int nc_blocks, int *launches, const WorkItem *items, const int *n_items,
                               int halo, size_t items_smem)
 {
     if (dims == 3)
-        return prec == 0 ? diag_t<3, double, ORD>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E,
+        return prec == 0 ? diag_t<3, double, ORD>(st, runs, run, groups, group_base, ngroups, total, P, E,
                                                   B, scr, set_ref, np_blocks, nc_blocks, launches, nullptr, nullptr,
                                                   halo, 0)
-                         : diag_t<3, float, ORD>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E,
+                         : diag_t<3, float, ORD>(st, runs, run, groups, group_base, ngroups, total, P, E,
                                                  B, scr, set_ref, np_blocks, nc_blocks, launches, items, n_items,
                                                  halo, items_smem);
-    return prec == 0 ? diag_t<2, double, ORD>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
+    return prec == 0 ? diag_t<2, double, ORD>(st, runs, run, groups, group_base, ngroups, total, P, E, B,
                                               scr, set_ref, np_blocks, nc_blocks, launches, nullptr, nullptr, halo, 0)
-                     : diag_t<2, float, ORD>(st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B,
+                     : diag_t<2, float, ORD>(st, runs, run, groups, group_base, ngroups, total, P, E, B,
                                              scr, set_ref, np_blocks, nc_blocks, launches, items, n_items, halo,
                                              items_smem);
 }
@@ -539,12 +539,12 @@ cudaError_t launch_diagnostics_run(int dims, int prec, cudaStream_t st, const Ru
     if (e != cudaSuccess) return e;
     const size_t items_smem = diag_items_smem_bytes(dims, tile, halo, pitch, order2);
     if (order2 == 5)
-        return diag_run_o<5>(dims, prec, st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
+        return diag_run_o<5>(dims, prec, st, runs, run, groups, group_base, ngroups, total, P, E, B, scr,
                              set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
     if (order2 == 4)
-        return diag_run_o<4>(dims, prec, st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
+        return diag_run_o<4>(dims, prec, st, runs, run, groups, group_base, ngroups, total, P, E, B, scr,
                              set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
-    return diag_run_o<3>(dims, prec, st, runs, run, run_cells, groups, group_base, ngroups, total, P, E, B, scr,
+    return diag_run_o<3>(dims, prec, st, runs, run, groups, group_base, ngroups, total, P, E, B, scr,
                          set_ref, np_blocks, nc_blocks, launches, items, n_items, halo, items_smem);
 }
 

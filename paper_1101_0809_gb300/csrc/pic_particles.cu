@@ -18,6 +18,8 @@ static cudaError_t launch_mode(int mode, cudaStream_t st, int max_items, size_t 
 size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo, int p0, int p1,
                             int order2)
 {
+    (void)tx;   // the x and y extents enter through the pitches (p0, p1 cover the widest tile)
+    (void)ty;
     const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
     // l_a = 2 1/2 reaches one cell further in both tiles; the gather of
     // Eq. wrong1 (order2 = 4) in the field tile only

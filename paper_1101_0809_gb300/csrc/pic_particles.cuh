@@ -185,6 +185,13 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     const int P0 = GEO::dyn ? rn.pitch[0] : GEO::P0;   // >= je0 (see the tile layout choice)
     const int P1 = GEO::dyn ? rn.pitch[1] : GEO::P1;   // >= je1
     const int nf = P0 * P1 * fe2, nj = P0 * P1 * je2;
+    // l_a = 2 1/2, FP32: particles whose base index stayed add raw words and the
+    // bias comes off at the flush, which sums 64 counts per word of the current
+    // tile.  That pays when the item has at least about 2/3 of a particle per
+    // word (each such particle saves two integer subtractions on each of its
+    // 144 contributions); sparser items take the bias off per contribution.
+    // The choice is uniform over the block.
+    const bool fix5 = FIX && ORD == 5 && (it.end - it.begin) * 3 >= 2LL * nj;
     constexpr bool NEED_F = MODE != 2;
     constexpr bool NEED_J = MODE != 1;
     const long long cb = rn.cell_base;
@@ -515,7 +522,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                 axis_window5(a0, b0, 0, X);
                 axis_window5(a1, b1, 0, Y);
                 if (DIM == 3) axis_window5(a2, b2, 0, Z); else Z = X;
-                if constexpr (FIX) {
+                if (fix5) {
                     // fixed stencil: the bias comes off once per word at the flush
                     FixedAccT<false> acc;
                     for (int c = 0; c < 3; ++c) { acc.hi[c] = sJh[c]; acc.lo[c] = sJl[c]; }
@@ -605,7 +612,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             // for J^x (faces 0, 1; cells -1..1), likewise for J^y and J^z, so a
             // cell l received sum_{b in l - stencil} cnt[b] of them
             unsigned nst[3] = {0u, 0u, 0u};
-            if constexpr (FIX && ORD == 5) {
+            if (fix5) {
                 // l_a = 2 1/2: the stencil of base b covers b + (dx, dy, dz) with
                 // dx in {-1, 0, 1} (faces) and dy, dz in {-2, ..., 1} (cells) for
                 // J^x, likewise for J^y and J^z; so the bases of word l are

@@ -29,10 +29,13 @@ def P():
     return pic
 
 
-def small3d(steps=3, vth=0.1, ions=True):
+def small3d(steps=3, vth=0.1, ions=True, ppc=4):
     """Tiles of 8x4x4: with l_a = 2 1/2 an FP64 8^3 tile would need more shared
-    memory than a block can have (the grid refuses it at creation)."""
-    return W.thermal_plasma("3D small", 3, (20, 18, 22), 4, vth, steps, W.SEED_BASE + 11,
+    memory than a block can have (the grid refuses it at creation).  With
+    ppc = 16 per species a 4x4x4 tile holds 2048 particles, enough for the FP32
+    kernel to take the bias of particles whose base index stayed off at the
+    flush (at 4 it takes it off per contribution)."""
+    return W.thermal_plasma("3D small", 3, (20, 18, 22), ppc, vth, steps, W.SEED_BASE + 11,
                             ions=1836.0 if ions else None, tile=(8, 4, 4), dt_courant=0.45)
 
 
@@ -117,13 +120,13 @@ def test_split_calls_equal_the_step(P, which):
     grid.close()
 
 
-@pytest.mark.parametrize("which", ["2d", "3d", "3d-8x8x4", "3d-4x4x4"])
+@pytest.mark.parametrize("which", ["2d", "3d", "3d-8x8x4", "3d-4x4x4", "3d-4x4x4-dense"])
 def test_fp32_one_step_from_the_rounded_oracle_state(P, which):
-    wl = W.c0_small2d() if which == "2d" else small3d()
-    tile = {"3d-8x8x4": (8, 8, 4), "3d-4x4x4": (4, 4, 4)}.get(which)
+    wl = W.c0_small2d() if which == "2d" else small3d(ppc=16 if which.endswith("dense") else 4)
+    tile = {"3d-8x8x4": (8, 8, 4), "3d-4x4x4": (4, 4, 4), "3d-4x4x4-dense": (4, 4, 4)}.get(which)
     g, osp, E, B, J = run_oracle(wl, 5)
     grid = grid5(P, wl, P.PIC_FP32, tile=tile)
-    if which == "3d-4x4x4":
+    if which.startswith("3d-4x4x4"):
         assert tuple(P.pic_tile_layout(grid.h)[2]) == (12, 12)    # the fixed-geometry kernel
     grid.set_fields([a.astype(np.float32) for a in E], [a.astype(np.float32) for a in B])
     for s, sp in enumerate(osp):
@@ -143,13 +146,13 @@ def test_fp32_one_step_from_the_rounded_oracle_state(P, which):
     grid.close()
 
 
-@pytest.mark.parametrize("which", ["2d", "3d-4x4x4"])
+@pytest.mark.parametrize("which", ["2d", "3d-4x4x4", "3d-4x4x4-dense"])
 def test_fp32_one_step_with_particles_drifted_into_the_halo(P, which):
     """Six unsorted steps carry particles into the one-cell halo of their tile,
     some past its upper edge with offset >= 1/2, where the base index reaches its
     largest value in the current tile; then one step against the oracle from the
     GPU's own state."""
-    wl = ragged2d(vth=0.3) if which == "2d" else small3d(vth=0.3)
+    wl = ragged2d(vth=0.3) if which == "2d" else small3d(vth=0.3, ppc=16 if which.endswith("dense") else 4)
     tile = (8, 8, 1) if which == "2d" else (4, 4, 4)
     grid = grid5(P, wl, P.PIC_FP32, tile=tile, halo=1, sort_interval=1000)
     P.pic_step(grid.h, 6)
