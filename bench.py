@@ -837,6 +837,18 @@ def our_arm(args):
                 "ms_per_step": ms64 / k64, "dtype": "f64",
                 "roofline_hbm": {"achieved": ach64, "peak": hbm_peak, "unit": "GB/s", "frac": ach64 / hbm_peak},
                 "fp32_speedup": (npart * args.steps / (ms * 1e-3)) / (npart * k64 / (ms64 * 1e-3))}
+        # the unit that binds the FP64 kernel: the FP64 pipe, 2 instructions (DADD,
+        # DMUL or DFMA) per SM per clock; FP64 instructions per particle from the
+        # committed ncu summary of the same kernel source
+        f64pp = ncu_per_particle("fp64", "fp64_instr_per_particle")
+        if f64pp:
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            alu_peak = 2.0 * sms * sm_mhz * 1e6
+            alu_ach = f64pp * npart / (pk64_ms / pk64_n * 1e-3)
+            fp64["roofline_fp64"] = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
+                                     "unit": "FP64 instructions/s", "frac": alu_ach / alu_peak,
+                                     "fp64_instructions_per_particle": f64pp,
+                                     "peak_source": f"2 per SM per clock x {sms} SMs x {sm_mhz:.0f} MHz (sampled)"}
         if rank == 0:
             fp64["fp32_vs_fp64"] = main_accuracy(P, wl, stream, g64, min(args.warmup, 2) + k64)
         g64.close()
