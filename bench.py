@@ -430,7 +430,22 @@ def batched_accuracy(P, sub, cand, build, steps):
             "E_max_rel_worst_run": e_rel, "energy_rel_worst_run": w_rel, "gauss_rel_fp32_worst_run": gauss}
 
 
-def adjoint_arm(P, W, torch, args):
+def adjoint_bytes(es):
+    """Algorithmic HBM bytes per particle-step of the 2D differentiable run with
+    elements of es bytes: the forward step reads and writes the state (cell,
+    two offsets, three momenta); the backward pass recomputes each step with a
+    snapshot of the state and ids written, restores the snapshot (read, write),
+    and the particle adjoint reads the state and reads and writes the adjoints
+    of the offsets (two) and the momenta (three).  The grid's share (65,536
+    cells against 1,048,576 particles) is left out."""
+    state = 4 + 2 * es + 3 * es
+    snap = state + 4
+    fwd = 2 * state
+    bwd = (2 * state + snap) + 2 * snap + (state + 2 * 5 * es)
+    return fwd, fwd + bwd
+
+
+def adjoint_arm(P, W, torch, args, hbm_peak):
     """Differentiable 2D3V run: 256^2 periodic grid, 16 e-/cell, v_th = 0.05c,
     density perturbation A = 0.05 in mode k = 2; loss = field energy in a 32x32
     probe window after `adj_steps` steps; gradient with respect to A and the
@@ -479,6 +494,14 @@ def adjoint_arm(P, W, torch, args):
         npart = wl0.n_particles
         out[name] = {"fwd": npart * steps / (t1 - t0), "fwd_adj": npart * steps / (t2 - t0), "unit": UNIT,
                      "fwd_s": t1 - t0, "adj_s": t2 - t1, "loss": float(L.detach()), "dL_dA": float(A.grad.item())}
+        bf, bfa = adjoint_bytes(4 if name == "fp32" else 8)
+        out[name]["roofline_hbm"] = {
+            "scope": "whole pass through the autograd API, host loads included",
+            "bytes_per_particle_step": {"fwd": bf, "fwd_adj": bfa},
+            "fwd": {"achieved": bf * out[name]["fwd"] / 1e9, "frac": bf * out[name]["fwd"] / 1e9 / hbm_peak},
+            "fwd_adj": {"achieved": bfa * out[name]["fwd_adj"] / 1e9,
+                        "frac": bfa * out[name]["fwd_adj"] / 1e9 / hbm_peak},
+            "unit": "GB/s", "peak": hbm_peak}
         if name == "fp64":
             h = 1e-7 * amp
             lp = run.forward(torch.from_numpy(x_of(amp + h)), torch.from_numpy(w0))
@@ -858,7 +881,7 @@ def our_arm(args):
         batched = batched_arm(P, W, torch, args, dist)
     adjoint = None
     if not args.no_adjoint and rank == 0:
-        adjoint = adjoint_arm(P, W, torch, args)
+        adjoint = adjoint_arm(P, W, torch, args, hbm_peak)
     laser = None
     if not args.no_laser:
         laser = laser_arm(P, W, torch, args)
