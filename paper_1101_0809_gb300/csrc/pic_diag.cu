@@ -430,35 +430,56 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_cells(const RunDev *runs,
 
 // One block: fixed-order reduction of the partial slots into result[0..11]:
 // kinetic, field_E, field_B, half_step_corr, total, px, py, pz, charge,
-// resid_max, resid_rms, n_particles.
-__global__ void k_diag_final(const double *pp, int np, const double *pc, int nc, const RunDev *runs, int run,
-                             double *result)
+// resid_max, resid_rms, n_particles.  Thread t sums the slots of blocks t,
+// t + kFinalThreads, ... in order, then a pairwise tree in shared memory
+// combines the threads' sums: the order is fixed, so the result is the same
+// on every call.
+constexpr int kFinalThreads = 256;
+__global__ void __launch_bounds__(kFinalThreads) k_diag_final(const double *pp, int np, const double *pc, int nc,
+                                                             const RunDev *runs, int run, double *result)
 {
-    __shared__ double acc[12];
-    if (threadIdx.x == 0) {
-        const RunDev rn = runs[run];
-        double s[kPartVals] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int b = 0; b < np; ++b)
-            for (int q = 0; q < kPartVals; ++q) s[q] += pp[b * kPartVals + q];
-        double c[kPartVals] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int b = 0; b < nc; ++b) {
-            c[0] = fmax(c[0], pc[b * kPartVals + 0]);
-            for (int q = 1; q < kPartVals; ++q) c[q] += pc[b * kPartVals + q];
+    __shared__ double sp[kPartVals][kFinalThreads];
+    __shared__ double sc[kPartVals][kFinalThreads];
+    const int t = threadIdx.x;
+    double s[kPartVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double c[kPartVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = t; b < np; b += kFinalThreads)
+        for (int q = 0; q < kPartVals; ++q) s[q] += pp[(long long)b * kPartVals + q];
+    for (int b = t; b < nc; b += kFinalThreads) {
+        c[0] = fmax(c[0], pc[(long long)b * kPartVals + 0]);
+        for (int q = 1; q < kPartVals; ++q) c[q] += pc[(long long)b * kPartVals + q];
+    }
+    for (int q = 0; q < kPartVals; ++q) {
+        sp[q][t] = s[q];
+        sc[q][t] = c[q];
+    }
+    __syncthreads();
+    for (int h = kFinalThreads / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            for (int q = 0; q < kPartVals; ++q) {
+                sp[q][t] += sp[q][t + h];
+                sc[q][t] = q == 0 ? fmax(sc[q][t], sc[q][t + h]) : sc[q][t] + sc[q][t + h];
+            }
         }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const RunDev rn = runs[run];
         const double ncell = (double)rn.n[0] * rn.n[1] * rn.n[2];
         const double fe = rn.V / (8.0 * kPi);
-        acc[0] = s[0];
-        acc[1] = fe * c[3];
-        acc[2] = fe * c[4];
-        acc[3] = s[4];
+        double acc[12];
+        acc[0] = sp[0][0];
+        acc[1] = fe * sc[3][0];
+        acc[2] = fe * sc[4][0];
+        acc[3] = sp[4][0];
         acc[4] = acc[0] + acc[1] + acc[2] + acc[3];
-        acc[5] = s[1];
-        acc[6] = s[2];
-        acc[7] = s[3];
-        acc[8] = c[2];
-        acc[9] = c[0];
-        acc[10] = sqrt(c[1] / ncell);
-        acc[11] = s[5];
+        acc[5] = sp[1][0];
+        acc[6] = sp[2][0];
+        acc[7] = sp[3][0];
+        acc[8] = sc[2][0];
+        acc[9] = sc[0][0];
+        acc[10] = sqrt(sc[1][0] / ncell);
+        acc[11] = sp[5][0];
         for (int q = 0; q < 12; ++q) result[q] = acc[q];
     }
 }
@@ -501,7 +522,7 @@ static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run,
     }
     k_diag_cells<DIM, R><<<nc_blocks, kDiagThreads, 0, st>>>(runs, run, F, scr.rho, scr.resid_ref, set_ref,
                                                              scr.partials + (long long)np_blocks * kPartVals);
-    k_diag_final<<<1, 32, 0, st>>>(scr.partials, np_blocks, scr.partials + (long long)np_blocks * kPartVals,
+    k_diag_final<<<1, kFinalThreads, 0, st>>>(scr.partials, np_blocks, scr.partials + (long long)np_blocks * kPartVals,
                                    nc_blocks, runs, run, scr.result);
     *launches += 3;
     return cudaGetLastError();
