@@ -502,6 +502,7 @@ static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run,
         F.B[c] = (R *)B[c];
         F.J[c] = nullptr;
     }
+    int np_items = np_blocks;   // blocks of the particle pass (partial slots filled)
     if (sizeof(R) == 4 && items) {
         Pool<float> pf;
         Fields<float> ff;
@@ -514,16 +515,25 @@ static cudaError_t diag_t(cudaStream_t st, const RunDev *runs, int run,
             ff.B[c] = (float *)B[c];
             ff.J[c] = nullptr;
         }
-        k_diag_items<DIM, ORD><<<np_blocks, kDiagThreads, items_smem, st>>>(run, items, n_items, groups, runs, pf, ff, halo,
-                                                                       scr.rho, scr.partials);
+        // one wave of resident blocks, each looping over the items: no partial last wave
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_diag_items<DIM, ORD>, kDiagThreads,
+                                                               items_smem)) != cudaSuccess)
+            return e;
+        if (per_sm > 0 && sms * per_sm < np_blocks) np_items = sms * per_sm;
+        k_diag_items<DIM, ORD><<<np_items, kDiagThreads, items_smem, st>>>(run, items, n_items, groups, runs, pf, ff,
+                                                                          halo, scr.rho, scr.partials);
     } else {
         k_diag_particles<DIM, R, ORD><<<np_blocks, kDiagThreads, 0, st>>>(run, total, group_base, ngroups, groups, runs,
                                                                      pool, F, scr.rho, scr.partials);
     }
     k_diag_cells<DIM, R><<<nc_blocks, kDiagThreads, 0, st>>>(runs, run, F, scr.rho, scr.resid_ref, set_ref,
                                                              scr.partials + (long long)np_blocks * kPartVals);
-    k_diag_final<<<1, kFinalThreads, 0, st>>>(scr.partials, np_blocks, scr.partials + (long long)np_blocks * kPartVals,
-                                   nc_blocks, runs, run, scr.result);
+    k_diag_final<<<1, kFinalThreads, 0, st>>>(scr.partials, np_items, scr.partials + (long long)np_blocks * kPartVals,
+                                              nc_blocks, runs, run, scr.result);
     *launches += 3;
     return cudaGetLastError();
 }
