@@ -22,7 +22,8 @@ def P():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    with open(HEADER) as f:
+        text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(pic_[a-z_0-9]+)\s*\(", text)))
 
@@ -57,7 +58,8 @@ int main(void) {
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         exe = os.path.join(d, "t")
-        open(c, "w").write(src)
+        with open(c, "w") as f:
+            f.write(src)
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         vals = [int(v) for v in subprocess.check_output([exe]).split()]
     assert vals[0] == C.sizeof(P.pic_grid_desc)
