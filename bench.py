@@ -214,7 +214,8 @@ class ClockSampler:
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("pic_device.cuh", "pic_particles.cuh", "pic_particles.cu", "pic_particles_fixed.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1101_0809_gb300", "csrc", f), "rb").read())
+        with open(os.path.join(ROOT, "paper_1101_0809_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -682,8 +683,11 @@ def our_arm(args):
         dist = D
     else:
         torch.cuda.set_device(0)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peaks = None
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            peaks = json.load(f)
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     peak_note = "measured" if peaks else "fallback"
 
