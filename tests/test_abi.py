@@ -118,6 +118,8 @@ def test_null_arguments_return_errors(P):
     assert lib.pic_set_sort_policy(None, 1) == P.PIC_ERR_INVALID_ARG
     assert lib.pic_set_adjoint_tiled(None, 1) == P.PIC_ERR_INVALID_ARG
     assert lib.pic_step_saving(None, 1, None) == P.PIC_ERR_INVALID_ARG
+    assert lib.pic_state_restore(None, None, 0) == P.PIC_ERR_INVALID_ARG
+    assert lib.pic_state_restore_async(None, None, 0) == P.PIC_ERR_INVALID_ARG
     z = P._VP3()
     assert lib.pic_get_vector_potential(None, z, 0) == P.PIC_ERR_INVALID_ARG
     out = (C.c_double * 3)()
