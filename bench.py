@@ -98,6 +98,26 @@ def time_oracle(n, ppc, target_s=15.0, steps=None, fraction=None):
     return rate, sample, fraction, steps
 
 
+def time_oracle_small():
+    """The oracle single-threaded on the two 2D configurations in full: the 32x32
+    correctness run (8,192 electrons, 50 steps) and two steps of the 256x256
+    differentiable run (1,048,576 electrons)."""
+    import oracle as O
+    from paper_1101_0809_gb300 import workloads as W
+    out = {}
+    for name, wl, nsteps in (("2D 32x32 8 e-/cell, 50 steps", W.c0_small2d(steps=50), 50),
+                             ("2D 256x256 16 e-/cell perturbed, 2 steps", W.c4_perturbed2d(steps=2), 2)):
+        g = O.Grid(wl.dims, wl.n, wl.d, wl.dt, wl.c)
+        sp = [O.Species(s.q, s.m, s.weight, s.x, s.w) for s in wl.species]
+        E, B, J = g.zeros(), g.zeros(), g.zeros()
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            O.step(g, E, B, J, sp)
+        dt = time.perf_counter() - t0
+        out[name] = {"value": wl.n_particles * nsteps / dt, "unit": UNIT, "cores": 1, "seconds": dt}
+    return out
+
+
 def _oracle_proc(n, ppc, steps, fraction, barrier, q):
     """One of the concurrent oracle processes of time_oracle_cores."""
     sys.path.insert(0, ROOT)
@@ -697,7 +717,7 @@ def our_arm(args):
         rate1, sample1, frac, nst = time_oracle(args.n, args.ppc)
         rate, sample, cores = time_oracle_cores(args.n, args.ppc, nst, frac)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "single_core": {"value": rate1, "sample": sample1}}
+               "single_core": {"value": rate1, "sample": sample1}, "other_configs": time_oracle_small()}
 
     from paper_1101_0809_gb300 import build as B
     B.build()
