@@ -441,6 +441,75 @@ def test_p11_uniform_B_gyration_closed_form():
     assert R == pytest.approx(rL * math.sqrt(1 + bmag ** 2), rel=1e-12)
 
 
+def test_boris_rotation_angle_takes_gamma_at_the_half_kicked_momentum():
+    """With E and B both non-zero, the Appendix's step 2 is a half kick by e, a
+    rotation of w~ = w^{n-1/2} + e about B, and a second half kick.  A rotation
+    by the vector b (w_n = w~ + w~ x b; w' = w~ + 2 (w_n x b)/(1 + b^2)) is a
+    rotation about b by the angle 2 arctan|b| (the Cayley form of a rotation),
+    and the Appendix defines |b| with sqrt(w~^2 + c^2), the Lorentz factor of
+    the half-kicked momentum.  So the component of w^{n+1/2} - e along B equals
+    that of w~, and the angle between their components across B is
+    2 arctan(|q dt B / 2m| / sqrt(w~^2 + c^2)), in the sense of -q B.  The
+    fields are strong enough that the Lorentz factor of w^{n-1/2} would give an
+    angle off by far more than the tolerance."""
+    rng = np.random.default_rng(7)
+    worst_alt = 0.0
+    for _ in range(200):
+        c = rng.choice([1.0, 2.0, 20.0])
+        qm = rng.choice([-1.0, 1.0 / 1836, 2.0])
+        dt = rng.uniform(0.05, 0.5)
+        w = rng.normal(size=3) * c
+        Ep = rng.normal(size=3) * c / (abs(qm) * dt)      # |e| comparable to |w|
+        Bp = rng.normal(size=3) * 3 * c / (abs(qm) * dt)
+        w1 = O.boris(w, Ep, Bp, qm, dt, c)
+        e = 0.5 * qm * dt * Ep
+        wm, wp = w + e, w1 - e
+        bh = Bp / np.linalg.norm(Bp)
+        scale = np.linalg.norm(wm)
+        assert np.dot(wp, bh) == pytest.approx(np.dot(wm, bh), abs=1e-13 * scale)
+        pm, pp = wm - np.dot(wm, bh) * bh, wp - np.dot(wp, bh) * bh
+        cosang = np.dot(pm, pp)
+        sinang = np.dot(np.cross(pm, pp), -np.sign(qm) * bh)
+        angle = math.atan2(sinang, cosang)
+        half = 0.5 * abs(qm) * dt * np.linalg.norm(Bp)
+        want = 2 * math.atan(half / math.sqrt(np.dot(wm, wm) + c * c))
+        alt = 2 * math.atan(half / math.sqrt(np.dot(w, w) + c * c))
+        assert angle == pytest.approx(want, rel=1e-11, abs=1e-12)
+        worst_alt = max(worst_alt, abs(alt - want) / want)
+    assert worst_alt > 1e-2      # the test would see the other Lorentz factor
+
+
+def test_boris_gyration_phase_in_parallel_E_and_B_converges_at_second_order():
+    """Uniform E and B both along z: w_z(t) = w_z(0) + (q/m) E t, |w_perp| is
+    constant, and w_perp turns at the rate |q| B / (m sqrt(w_perp^2 + w_z(t)^2 + c^2)),
+    so the phase turned between t0 and t1 is
+    (|q| B / (q E / m)) [asinh(w_z(t1)/s) - asinh(w_z(t0)/s)] with
+    s = sqrt(w_perp^2 + c^2) (closed form of the relativistic motion in
+    parallel fields).  The push evaluates the rate at the half-kicked momentum
+    w~, whose w_z is that of t^n, the centre of the step, so the phase error
+    falls as dt^2; a Lorentz factor taken at w^{n-1/2} (time t^{n-1/2}) would
+    make it first order."""
+    c, qm, B0, E0 = 1.0, -1.0, 2.0, 0.5
+    a = qm * E0
+    wperp, T = 0.5, 4.0
+    s = math.sqrt(wperp ** 2 + c * c)
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        nsteps = int(round(T / dt))
+        w = np.array([wperp, 0.0, -0.5 * a * dt])          # w^{-1/2}: w_z(t) = a t
+        phase = 0.0
+        for n in range(nsteps):
+            w1 = O.boris(w, [0, 0, E0], [0, 0, B0], qm, dt, c)
+            assert w1[2] == pytest.approx(a * (n + 0.5) * dt, rel=1e-13, abs=1e-15)
+            assert math.hypot(w1[0], w1[1]) == pytest.approx(wperp, rel=1e-13)
+            phase += math.atan2(w[0] * w1[1] - w[1] * w1[0], w[0] * w1[0] + w[1] * w1[1])
+            w = w1
+        t0, t1 = -0.5 * dt, (nsteps - 0.5) * dt
+        turned = (abs(qm) * B0 / a) * (math.asinh(a * t1 / s) - math.asinh(a * t0 / s))
+        errs.append(abs(phase - (-np.sign(qm)) * turned))     # charge q < 0 turns counter-clockwise about +B
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
 def test_boris_magnetic_part_preserves_energy_p2():
     for _ in range(100):
         w = RNG.normal(size=3) * 3
