@@ -51,6 +51,7 @@ def test_fp32_3d_fixed_tile_one_step_matches_oracle(env):
     osp = oracle_from_gpu(wl, grid.particles)
     g = O.Grid(wl.dims, wl.n, wl.d, wl.dt, wl.c)
     E, B, J = g.zeros(), g.zeros(), g.zeros()
+    x_prev = [sp.x.copy() for sp in osp]
     P.pic_step(grid.h, 1)
     P.pic_sync(grid.h)
     O.step(g, E, B, J, osp)
@@ -60,7 +61,7 @@ def test_fp32_3d_fixed_tile_one_step_matches_oracle(env):
         close(gB[a], B[a], FP32_TOL, f"B[{a}]")
         close(gJ[a], J[a], FP32_TOL, f"J[{a}]")
     for s in range(len(wl.species)):
-        compare_particles(wl, s, grid, osp, FP32_TOL, check_cells=False)
+        compare_particles(wl, s, grid, osp, FP32_TOL, x_prev=x_prev[s])
     grid.close()
 
 

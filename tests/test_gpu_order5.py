@@ -57,14 +57,14 @@ def run_oracle(wl, steps):
     return g, sp, E, B, J
 
 
-def check_state(wl, grid, osp, E, B, J, tol, check_cells=True):
+def check_state(wl, grid, osp, E, B, J, tol, x_prev=None):
     gE, gB, gJ = grid.get_fields()
     for a in range(3):
         close(gE[a], E[a], tol, f"E[{a}]")
         close(gB[a], B[a], tol, f"B[{a}]")
         close(gJ[a], J[a], tol, f"J[{a}]")
     for s in range(len(wl.species)):
-        compare_particles(wl, s, grid, osp, tol, check_cells=check_cells)
+        compare_particles(wl, s, grid, osp, tol, x_prev=None if x_prev is None else x_prev[s])
 
 
 @pytest.mark.parametrize("which", ["2d", "3d"])
@@ -139,10 +139,11 @@ def test_fp32_one_step_from_the_rounded_oracle_state(P, which):
             osp[s].w[a][:] = w[a][order]
     E = [a.astype(np.float32).astype(np.float64) for a in E]
     B = [a.astype(np.float32).astype(np.float64) for a in B]
+    x_prev = [sp.x.copy() for sp in osp]
     P.pic_step(grid.h, 1)
     P.pic_sync(grid.h)
     O.step(g, E, B, J, osp)
-    check_state(wl, grid, osp, E, B, J, FP32_TOL, check_cells=False)
+    check_state(wl, grid, osp, E, B, J, FP32_TOL, x_prev=x_prev)
     grid.close()
 
 
@@ -178,10 +179,11 @@ def test_fp32_one_step_with_particles_drifted_into_the_halo(P, which):
             fr = osp[s].x[a] - np.floor(osp[s].x[a])
             edge += int(np.count_nonzero((li == tile[a]) & (fr >= 0.5)))
     assert edge > 0
+    x_prev = [sp.x.copy() for sp in osp]
     P.pic_step(grid.h, 1)
     P.pic_sync(grid.h)
     O.step(g, E, B, J, osp)
-    check_state(wl, grid, osp, E, B, J, FP32_TOL, check_cells=False)
+    check_state(wl, grid, osp, E, B, J, FP32_TOL, x_prev=x_prev)
     grid.close()
 
 
