@@ -405,6 +405,23 @@ int pic_adjoint_steps(pic_grid *g, void *const *states, int nstates, void *lamE[
 int pic_set_adjoint_tiled(pic_grid *g, int tiled);
 int pic_adjoint_yee_half_B(pic_grid *g, void *const lamB[3], void *lamE[3]);
 
+/* ---- The FP32 form's renormalization -----------------------------------------
+ * After the move of Eq. coordscheme (Appendix, step 2c) the FP32 form stores a
+ * position as an int32 cell and a float offset in [0, 1).  Moving offset o by a
+ * displacement d (|d| < 1 cell, the Courant limit) gives the cell shift
+ * k = floor(o + d) and the new offset, the float nearest to the exact o + d - k
+ * (round to nearest even), as a double-precision renormalization rounded once
+ * would give; an offset that rounds to 1 becomes offset 0 of the next cell
+ * (k + 1).  pic_renormalize_f32 applies the device function the FP32 particle
+ * kernels use to n pairs: offset[p], delta[p] (device memory, float) give
+ * shift[p] (int) and offset_out[p] (float), device memory owned by the caller.
+ * Enqueued on cuda_stream (NULL = legacy default stream); returns without
+ * waiting.  Errors: PIC_ERR_INVALID_ARG for null arrays or n < 0; PIC_ERR_CUDA
+ * for a failed launch.  Inputs with |delta| >= 1 or offsets outside [0, 1)
+ * are outside the contract (the result is then unspecified, never a fault). */
+int pic_renormalize_f32(const float *offset, const float *delta, long long n, int *shift, float *offset_out,
+                        void *cuda_stream);
+
 /* ---- Tile sort without device allocation -----------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot
  * allocate device memory: code running inside a memory budget that another

@@ -455,6 +455,21 @@ def pic_adjoint_yee_half_B(g, lamB, lamE):
     _check(_lib.pic_adjoint_yee_half_B(g, _triple(lamB)[0], _triple(lamE)[0]))
 
 
+_lib.pic_renormalize_f32.argtypes = [_VP, _VP, C.c_longlong, _VP, _VP, _VP]
+
+
+def pic_renormalize_f32(offset, delta, shift, offset_out, stream=None):
+    """The FP32 form's offset-to-cell renormalization on device tensors (float32
+    offset and delta in, int32 shift and float32 offset_out out)."""
+    n = int(offset.numel())
+    assert delta.numel() == n and shift.numel() == n and offset_out.numel() == n
+    po, _ = _addr(offset)
+    pd, _ = _addr(delta)
+    ps, _ = _addr(shift)
+    pr, _ = _addr(offset_out)
+    _check(_lib.pic_renormalize_f32(po, pd, n, ps, pr, stream))
+
+
 PIC_NOALLOC_MAX_PARTICLES = 1048576
 _lib.pic_tile_sort_perm_noalloc.argtypes = [_VP, C.c_longlong, C.c_int, C.c_int * 3, C.c_int * 3, _VP, _VP, _VP]
 

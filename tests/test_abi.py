@@ -127,3 +127,5 @@ def test_null_arguments_return_errors(P):
     z = P._VP3()
     assert lib.pic_adjoint_steps(None, None, 1, z, z, z, z) == P.PIC_ERR_INVALID_ARG
     assert lib.pic_set_antenna(None, 0, None) == P.PIC_ERR_INVALID_ARG
+    assert lib.pic_renormalize_f32(None, None, C.c_longlong(5), None, None, None) == P.PIC_ERR_INVALID_ARG
+    assert lib.pic_renormalize_f32(None, None, C.c_longlong(-1), None, None, None) == P.PIC_ERR_INVALID_ARG
