@@ -57,7 +57,7 @@ cudaError_t scratch_address(unsigned **out)
 }
 
 __global__ void k_tile_keys(long long n, const int *cell, int nx, int ny, int tx, int ty, int tz, int ntx, int nty,
-                            unsigned *keys, unsigned *vals, int *bad)
+                            unsigned *keys, unsigned *vals)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -126,7 +126,7 @@ extern "C" int pic_tile_sort_perm_noalloc(const int *cell, long long n, int dims
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail(PIC_ERR_CUDA, "cell check failed");
     if (hbad) return fail(PIC_ERR_INVALID_ARG, "a cell index is outside the grid");
-    k_tile_keys<<<nb, nthr, 0, st>>>(n, cell, nn[0], nn[1], tt[0], tt[1], tt[2], nt[0], nt[1], keys[0], vals[0], bad);
+    k_tile_keys<<<nb, nthr, 0, st>>>(n, cell, nn[0], nn[1], tt[0], tt[1], tt[2], nt[0], nt[1], keys[0], vals[0]);
     if (cudaGetLastError() != cudaSuccess) return fail(PIC_ERR_CUDA, "key kernel launch failed");
     int nbits = 1;
     while ((1LL << nbits) < ntiles) ++nbits;
