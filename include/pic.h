@@ -81,12 +81,16 @@ typedef struct {
     int particles_per_block;/* particles per thread block work item (0 = default 8192) */
     double rho_bg;          /* uniform immobile background charge density (enters rho only) */
     void *cuda_stream;      /* cudaStream_t to enqueue on; NULL = the legacy default stream */
-    int sort_order;         /* PIC_SORT_BANKED (0, default) or PIC_SORT_STABLE (1), see pic_sort */
+    int sort_order;         /* PIC_SORT_AUTO (0, default), PIC_SORT_STABLE, PIC_SORT_BANKED or
+                               PIC_SORT_CELL_LANES; see the enum below */
 } pic_grid_desc;
 
-/* Order of the tile sort.  Both sort by tile key first.  PIC_SORT_STABLE keeps
- * the input order inside a tile.  PIC_SORT_BANKED orders a tile's particles by
- * (r, b): b = base mod 32 with base = (i-ox+h+2) + P0*((j-oy+h+2) + P1*(k-oz+h+2))
+/* Order of the tile sort.  Every order sorts by tile key first (the tile of
+ * the particle's cell, tiles numbered (tk*nty + tj)*ntx + ti per run and
+ * species); they differ inside a tile.
+ * PIC_SORT_STABLE keeps the input order inside a tile.
+ * PIC_SORT_BANKED orders a tile's particles by (r, b): b = base mod 32 with
+ * base = (i-ox+h+2) + P0*((j-oy+h+2) + P1*(k-oz+h+2))
  * (h = the halo, plus one for l_a = 2 1/2, whose current tile is one cell wider)
  * (no k term in 2D) the shared-memory bank of the particle's cell in the
  * current tile of its tile (tile origin (ox, oy, oz), halo h, tile pitches
@@ -94,8 +98,19 @@ typedef struct {
  * particles (input order) of the same tile with the same b; so that 32
  * consecutive particles fall on 32 different banks.  For l_a = 2 1/2 the
  * interpolation is anchored at the base index, the cell plus (offset >= 1/2)
- * per axis, so i, j, k in base are those of the base index. */
-enum { PIC_SORT_BANKED = 0, PIC_SORT_STABLE = 1 };
+ * per axis, so i, j, k in base are those of the base index.
+ * PIC_SORT_CELL_LANES (tiles of at most 128 cells) gives each cell of a tile,
+ * c = (i-ox) + Tx*((j-oy) + Ty*(k-oz)), a lane L(c): the cells ranked by
+ * descending particle count, ties by c.  The particle of rank r among its
+ * cell's particles (input order) takes slot P(r) + L(c) of the tile, with
+ * P(r) = sum over the tile's cells of min(count, r).  A thread per lane then
+ * walks the particles of one cell while the threads of a warp read
+ * consecutive slots; the FP32 fused step of 3D grids with 8x4x4 tiles, halo 1
+ * and l_a = 1 1/2 runs that way when this order is requested (the particles
+ * that have left their cell since the sort take a general path, so the order
+ * pays off for slow species and short sort intervals).
+ * PIC_SORT_AUTO (0, the default) is PIC_SORT_BANKED. */
+enum { PIC_SORT_AUTO = 0, PIC_SORT_STABLE = 1, PIC_SORT_BANKED = 2, PIC_SORT_CELL_LANES = 3 };
 
 /* One species.  The macro-particle charge is q_p = weight*q, its mass m_p = weight*m;
  * the push uses q/m (Eq. 1), the deposit q_p/V (Eq. xi). */
@@ -230,7 +245,7 @@ int pic_set_sort_policy(pic_grid *g, int adaptive);
  * tile-sorted particles, B half step, E full step. */
 int pic_step(pic_grid *g, int nsteps);
 
-/* Sort all particles by tile (order inside a tile: see PIC_SORT_BANKED). */
+/* Sort all particles by tile (order inside a tile: see PIC_SORT_AUTO). */
 int pic_sort(pic_grid *g);
 
 /* FP64 diagnostics (see pic_diag).  Synchronizes the grid's stream. */
@@ -326,12 +341,14 @@ int pic_generalized_momentum(pic_grid *g, double P[3]);
 int pic_generalized_momentum_run(pic_grid *g, int run, double P[3]);
 
 /* ---- State snapshots ------------------------------------------------------------
- * A snapshot is one contiguous blob: a 64-byte header ("PICS", version 3,
+ * A snapshot is one contiguous blob: a 64-byte header ("PICS", version 4,
  * dims, precision, group count, sort phase, particle, cell, tile and run
- * counts, and a checksum of the header) followed by the particle arrays (cell,
- * id, offsets, momenta, in storage order), the fields E^n, B^{n-1/2}, the tile
- * starts of the particle order (from the last tile sort) and the antenna clock
- * of every run (pic_set_antenna), each array starting at the next multiple of
+ * counts, whether cell-lane tables follow, and a checksum of the header)
+ * followed by the particle arrays (cell, id, offsets, momenta, in storage
+ * order), the fields E^n, B^{n-1/2}, the tile starts of the particle order
+ * (from the last tile sort), the antenna clock of every run (pic_set_antenna)
+ * and, for a grid in the cell-lane order, every tile's lane cells (128 bytes)
+ * and lane counts (128 int32), each array starting at the next multiple of
  * 16 bytes.  A device snapshot is copied by one kernel.  pic_state_bytes gives its
  * size.  pic_state_save writes it to dst (device memory if on_device, else host
  * memory); pic_state_restore reads one taken from a grid with the same layout

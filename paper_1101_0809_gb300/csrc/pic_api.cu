@@ -191,9 +191,15 @@ void free_sort(pic_grid *g)
     dfree(g->tile_start);
     dfree(g->item_scan);
     dfree(g->items);
+    dfree(g->lane_cell);
+    dfree(g->lane_count);
+    dfree(g->drift);
     g->tile_start = nullptr;
     g->item_scan = nullptr;
     g->items = nullptr;
+    g->lane_cell = nullptr;
+    g->lane_count = nullptr;
+    g->drift = nullptr;
 }
 
 int launch_count_add(pic_grid *g, int n)
@@ -276,6 +282,11 @@ int size_particle_buffers(pic_grid *g, long long total)
     CK(dalloc(&g->item_scan, (size_t)g->total_tiles + 1), "item scan");
     g->max_items = g->total_tiles + (int)((total + g->ppi - 1) / g->ppi) + 1;
     CK(dalloc(&g->items, (size_t)g->max_items), "work items");
+    if (g->sort_order == PIC_SORT_CELL_LANES) {
+        CK(dalloc(&g->lane_cell, (size_t)std::max(1, g->total_tiles) * 128), "lane cells");
+        CK(dalloc(&g->lane_count, (size_t)std::max(1, g->total_tiles) * 128), "lane counts");
+        CK(dalloc(&g->drift, std::max(1LL, total)), "drift lists");
+    }
     CK(dalloc(&g->old_cell, std::max(1LL, total)), "saved cells");
     for (int c = 0; c < g->dims; ++c) CK(dalloc_bytes(&g->old_off[c], std::max(1LL, total) * elem(g)), "saved offsets");
     return PIC_OK;
@@ -360,7 +371,9 @@ int do_sort(pic_grid *g)
                                          g->d_group_base, (int)g->groups.size(), g->d_runs, g->total_tiles, g->sort,
                                          g->tile_start, g->item_scan, g->items, g->n_items, g->ppi,
                                          g->halo + (g->order2 == 5 ? 1 : 0),   // the current tile's bank base
-                                         g->sort_order == PIC_SORT_BANKED ? 1 : 0, g->order2 == 5 ? 1 : 0, &nl);
+                                         g->sort_order == PIC_SORT_BANKED ? 1 : 0, g->order2 == 5 ? 1 : 0, &nl,
+                                         g->sort_order == PIC_SORT_CELL_LANES ? g->lane_cell : nullptr,
+                                         g->sort_order == PIC_SORT_CELL_LANES ? g->lane_count : nullptr);
     launch_count_add(g, nl);
     if (e != cudaSuccess) return cuda_fail(e, "tile sort");
     if (g->total > 0 && !g->groups.empty()) std::swap(g->pool, g->pool_alt);
@@ -370,9 +383,25 @@ int do_sort(pic_grid *g)
     return PIC_OK;
 }
 
+// The fused step of a grid in the cell-lane order whose geometry the cell-lane
+// kernel is built for.
+static bool uses_cell_lanes(const pic_grid *g)
+{
+    return g->sort_order == PIC_SORT_CELL_LANES &&
+           particles_cl_applies(g->dims, g->prec, g->order2, g->tile, g->halo);
+}
+
 int launch_part(pic_grid *g, int mode)
 {
     ProfScope ps(g, PIC_PROF_PARTICLES);
+    if (mode == 0 && uses_cell_lanes(g)) {
+        cudaError_t e = launch_particles_cl(g->stream, g->total_tiles, g->tile_start, g->lane_cell, g->lane_count,
+                                            g->drift, g->d_groups, (int)g->groups.size(), g->d_runs, g->pool, g->E,
+                                            g->B, g->J, g->ppi, g->d_err);
+        launch_count_add(g, g->total_tiles > 0 ? 1 : 0);
+        if (e != cudaSuccess) return cuda_fail(e, "particle kernel");
+        return PIC_OK;
+    }
     cudaError_t e = launch_particles(g->dims, g->prec, mode, g->stream, g->items, g->n_items, g->max_items, g->d_runs,
                                      g->d_groups, g->pool, g->E, g->B, g->J, g->old_cell, g->old_off, g->halo,
                                      g->tile[0], g->tile[1], g->tile[2], g->d_err, g->pitch[0], g->pitch[1],
@@ -484,8 +513,10 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
         g->ppi = d->particles_per_block > 0 ? d->particles_per_block : 8192;
         if (g->ppi > 8192) return fail(PIC_ERR_INVALID_ARG, "particles_per_block must be <= 8192");
         if (g->ppi % 32 != 0) return fail(PIC_ERR_INVALID_ARG, "particles_per_block must be a multiple of 32");
-        if (d->sort_order != PIC_SORT_BANKED && d->sort_order != PIC_SORT_STABLE)
-            return fail(PIC_ERR_INVALID_ARG, "sort_order must be PIC_SORT_BANKED or PIC_SORT_STABLE");
+        if (d->sort_order != PIC_SORT_AUTO && d->sort_order != PIC_SORT_BANKED && d->sort_order != PIC_SORT_STABLE &&
+            d->sort_order != PIC_SORT_CELL_LANES)
+            return fail(PIC_ERR_INVALID_ARG,
+                        "sort_order must be PIC_SORT_AUTO, PIC_SORT_STABLE, PIC_SORT_BANKED or PIC_SORT_CELL_LANES");
         g->sort_order = d->sort_order;
         for (int a = 0; a < 3; ++a) g->tile[a] = d->tile[a] > 0 ? d->tile[a] : (d->dims == 3 ? 8 : 16);
         if (d->dims == 2) g->tile[2] = 1;
@@ -502,7 +533,13 @@ int check_run(const pic_grid_desc *d, pic_grid *g, RunDev &rd, bool first)
                         "axis %d has %d cells; the tile (%d) plus its staged halo (%d) must fit in the grid", a, n[a],
                         t[a], staged);
     }
-    if (first) choose_pitch(g);
+    if (first) {
+        choose_pitch(g);
+        if (g->sort_order == PIC_SORT_AUTO) g->sort_order = PIC_SORT_BANKED;
+        if (g->sort_order == PIC_SORT_CELL_LANES && g->tile[0] * g->tile[1] * g->tile[2] > 128)
+            return fail(PIC_ERR_INVALID_ARG, "the cell-lane order needs tiles of at most 128 cells (tile %dx%dx%d)",
+                        g->tile[0], g->tile[1], g->tile[2]);
+    }
     memset(&rd, 0, sizeof(rd));
     rd.pitch[0] = g->pitch[0];
     rd.pitch[1] = g->pitch[1];
@@ -659,6 +696,7 @@ int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out)
         if ((e = particles_set_smem_limit(g->dims, g->prec, mode, b, g->order2)) != cudaSuccess)
             return bail(e, "smem limit");
     }
+    if (uses_cell_lanes(g) && (e = particles_cl_set_smem_limit()) != cudaSuccess) return bail(e, "smem limit");
     {
         // the tiled particle adjoint where its tiles fit in shared memory
         const size_t ab = adjoint_smem_bytes(g->dims, g->prec, g->tile, g->halo, g->pitch);
@@ -1398,13 +1436,13 @@ int pic_generalized_momentum(pic_grid *g, double P[3]) { return pic_generalized_
 // ---- state snapshots -----------------------------------------------------------
 struct StateHeader {
     char magic[4];            // "PICS"
-    int version;              // 3
+    int version;              // 4
     int dims, prec, ngroups, steps_since_sort;
     long long total, total_cells;
     long long total_tiles;    // tile starts of the particle order follow the fields
     long long nruns;          // one antenna clock per run at the end
+    int lanes;                // 1: the cell-lane tables of the particle order follow the antenna clocks
     unsigned checksum;        // FNV-1a of the bytes before this field
-    int pad;
 };
 static_assert(sizeof(StateHeader) == 64, "snapshot header");
 
@@ -1426,7 +1464,7 @@ static void fill_header(const pic_grid *g, StateHeader &h)
 {
     memset(&h, 0, sizeof(h));
     memcpy(h.magic, "PICS", 4);
-    h.version = 3;
+    h.version = 4;
     h.dims = g->dims;
     h.prec = g->prec;
     h.ngroups = (int)g->groups.size();
@@ -1435,6 +1473,7 @@ static void fill_header(const pic_grid *g, StateHeader &h)
     h.total_cells = g->total_cells;
     h.total_tiles = g->total_tiles;
     h.nruns = (long long)g->runs.size();
+    h.lanes = g->sort_order == PIC_SORT_CELL_LANES ? 1 : 0;
     h.checksum = fnv1a(&h, offsetof(StateHeader, checksum));
 }
 
@@ -1443,11 +1482,13 @@ long long pic_state_bytes(pic_grid *g)
     if (!g) return 0;
     const long long es = (long long)elem(g);
     return (long long)sizeof(StateHeader) + 2 * seg16(4 * g->total) + (g->dims + 3) * seg16(es * g->total) +
-           6 * seg16(es * g->total_cells) + seg16(8 * (g->total_tiles + 1)) + seg16(8 * (long long)g->runs.size());
+           6 * seg16(es * g->total_cells) + seg16(8 * (g->total_tiles + 1)) + seg16(8 * (long long)g->runs.size()) +
+           (g->sort_order == PIC_SORT_CELL_LANES ? seg16(128LL * g->total_tiles) + seg16(512LL * g->total_tiles) : 0);
 }
 
 // The (device array, bytes) list of a snapshot, in its order after the header.
-static int state_segments(pic_grid *g, void *arr[kCopySegs], size_t bytes[kCopySegs])
+constexpr int kStateSegs = 18;
+static int state_segments(pic_grid *g, void *arr[kStateSegs], size_t bytes[kStateSegs])
 {
     const size_t es = elem(g);
     int n = 0;
@@ -1460,6 +1501,10 @@ static int state_segments(pic_grid *g, void *arr[kCopySegs], size_t bytes[kCopyS
     for (int a = 0; a < 3; ++a) seg(g->B[a], es * g->total_cells);
     seg(g->tile_start, sizeof(long long) * (g->total_tiles + 1));
     seg(g->d_ant_n, sizeof(long long) * g->runs.size());
+    if (g->sort_order == PIC_SORT_CELL_LANES) {
+        seg(g->lane_cell, 128 * (size_t)g->total_tiles);
+        seg(g->lane_count, 512 * (size_t)g->total_tiles);
+    }
     return n;
 }
 
@@ -1474,8 +1519,8 @@ static int save_body(pic_grid *g, void *dst, int on_device)
     if (on_device) cp.inline_bytes(o, &h, (int)sizeof(h));
     else memcpy(o, &h, sizeof(h));
     o += sizeof(h);
-    void *arr[kCopySegs];
-    size_t bytes[kCopySegs];
+    void *arr[kStateSegs];
+    size_t bytes[kStateSegs];
     const int n = state_segments(g, arr, bytes);
     for (int q = 0; q < n; ++q) {
         CK(cp.add(o, arr[q], bytes[q]), "state save");
@@ -1488,10 +1533,11 @@ static int save_body(pic_grid *g, void *dst, int on_device)
 
 static int check_header(const pic_grid *g, const StateHeader &h)
 {
-    if (memcmp(h.magic, "PICS", 4) != 0 || h.version != 3 || h.checksum != fnv1a(&h, offsetof(StateHeader, checksum)))
+    if (memcmp(h.magic, "PICS", 4) != 0 || h.version != 4 || h.checksum != fnv1a(&h, offsetof(StateHeader, checksum)))
         return fail(PIC_ERR_INVALID_ARG, "not a libpic state snapshot (bad magic, version or header checksum)");
     if (h.dims != g->dims || h.prec != g->prec || h.total != g->total || h.total_cells != g->total_cells ||
-        h.ngroups != (int)g->groups.size() || h.total_tiles != g->total_tiles || h.nruns != (long long)g->runs.size())
+        h.ngroups != (int)g->groups.size() || h.total_tiles != g->total_tiles || h.nruns != (long long)g->runs.size() ||
+        h.lanes != (g->sort_order == PIC_SORT_CELL_LANES ? 1 : 0))
         return fail(PIC_ERR_INVALID_ARG, "state snapshot does not match this grid's layout");
     return PIC_OK;
 }
@@ -1501,8 +1547,8 @@ static int restore_body(pic_grid *g, const void *src, int on_device, const State
 {
     const char *o = (const char *)src + sizeof(h);
     Copier cp(g->stream, kind_in(on_device));
-    void *arr[kCopySegs];
-    size_t bytes[kCopySegs];
+    void *arr[kStateSegs];
+    size_t bytes[kStateSegs];
     const int n = state_segments(g, arr, bytes);
     for (int q = 0; q < n; ++q) {
         CK(cp.add(arr[q], o, bytes[q]), "state restore");

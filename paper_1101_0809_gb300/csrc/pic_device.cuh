@@ -219,17 +219,28 @@ __device__ __forceinline__ void gather(const Rd &rd, const R fx[2], const R Sx[3
 // b = (q dt/2m) B / sqrt(w~^2 + c^2); w_n = w~ + w~ x b;
 // w' = w~ + e + 2 (w_n x b)/(1 + b^2).   hq = q dt/(2m).
 // ---------------------------------------------------------------------------
+// The reciprocal of sqrt(x) and the quotient 2/(1 + b^2): correctly rounded in
+// FP64; in FP32 the hardware reciprocal square root and a fast reciprocal, whose
+// few-ulp errors lie far below the FP32 form's tolerance and replace the
+// longer IEEE division and square-root sequences.
+__device__ __forceinline__ double rsqrt_r(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double div_sqrt(double a, double x) { return a / sqrt(x); }
+__device__ __forceinline__ float div_sqrt(float a, float x) { return a * rsqrtf(x); }
+__device__ __forceinline__ double two_over(double x) { return 2.0 / x; }
+__device__ __forceinline__ float two_over(float x) { return __fdividef(2.0f, x); }
+
 template <typename R>
 __device__ __forceinline__ void boris(R w[3], const R Ep[3], const R Bp[3], R hq, R c2)
 {
     const R e0 = hq * Ep[0], e1 = hq * Ep[1], e2 = hq * Ep[2];
     const R t0 = w[0] + e0, t1 = w[1] + e1, t2 = w[2] + e2;
-    const R s = hq / sqrt(t0 * t0 + t1 * t1 + t2 * t2 + c2);
+    const R s = div_sqrt(hq, t0 * t0 + t1 * t1 + t2 * t2 + c2);
     const R b0 = s * Bp[0], b1 = s * Bp[1], b2 = s * Bp[2];
     const R n0 = t0 + (t1 * b2 - t2 * b1);
     const R n1 = t1 + (t2 * b0 - t0 * b2);
     const R n2 = t2 + (t0 * b1 - t1 * b0);
-    const R f = R(2) / (R(1) + b0 * b0 + b1 * b1 + b2 * b2);
+    const R f = two_over(R(1) + b0 * b0 + b1 * b1 + b2 * b2);
     w[0] = t0 + e0 + f * (n1 * b2 - n2 * b1);
     w[1] = t1 + e1 + f * (n2 * b0 - n0 * b2);
     w[2] = t2 + e2 + f * (n0 * b1 - n1 * b0);
@@ -352,20 +363,22 @@ __device__ __forceinline__ void axis_window(R d0, R d1, int s, AxisWin<R> &a)
 template <typename R>
 __device__ __forceinline__ void axis_window_still(R d0, R d1, AxisWin<R> &a)
 {
-    R f0[2], S0[3], f1[2], S1[3];
-    form_factor(d0, f0, S0);
-    form_factor(d1, f1, S1);
-    R pm[3];
-    still_pm(d0, d1, pm);
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        a.Pp[t] = S1[t] + S0[t];
-        a.Pm[t] = pm[t];
-    }
+    // Pp = S(d1) + S(d0): Pp0 = ((1-d0)^2 + (1-d1)^2)/2, Pp2 = (d0^2 + d1^2)/2 and
+    // Pp1 = 2 - Pp0 - Pp2 (the cell integrals sum to one); Pm in the factored
+    // form of still_pm with h = (d1 - d0)/2 and s = d0 + d1: Pm0 = h (s - 2),
+    // Pm2 = h s, Pm1 = -(Pm0 + Pm2); the face sums D0 = Pm0, D1 = -Pm2.
+    const R e0 = R(1) - d0, e1 = R(1) - d1;
+    a.Pp[0] = R(0.5) * (e0 * e0 + e1 * e1);
+    a.Pp[2] = R(0.5) * (d0 * d0 + d1 * d1);
+    a.Pp[1] = (R(2) - a.Pp[0]) - a.Pp[2];
     a.Pp[3] = R(0);
+    const R h = R(0.5) * (d1 - d0), sm = d0 + d1;
+    a.Pm[0] = h * (sm - R(2));
+    a.Pm[2] = h * sm;
+    a.Pm[1] = -(a.Pm[0] + a.Pm[2]);
     a.Pm[3] = R(0);
     a.D[0] = a.Pm[0];
-    a.D[1] = a.D[0] + a.Pm[1];
+    a.D[1] = -a.Pm[2];
     a.D[2] = R(0);
     a.lo = -1;
 }

@@ -85,7 +85,24 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  const PoolBuf &dst, const GroupDev *groups, const long long *group_base_dev,
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
-                                 int particles_per_item, int halo, int banked, int half, int *launches);
+                                 int particles_per_item, int halo, int banked, int half, int *launches,
+                                 unsigned char *lane_cell = nullptr, int *lane_count = nullptr);
+// With lane_cell and lane_count (total_tiles * 128 entries each) the order
+// inside a tile is the cell-lane order (PIC_SORT_CELL_LANES) instead of the
+// banked or stable one, and the two tables receive every tile's lane cells
+// and counts.
+
+// The FP32 fused step over the cell-lane order (pic_particles_cl.cu): 3D,
+// l_a = 1 1/2, 8x4x4 tiles with halo 1; one block of 128
+// threads per tile.  drift is pool-sized scratch.  ppb: the particles per block
+// the groups' fixed-point scales were set for.
+bool particles_cl_applies(int dims, int prec, int order2, const int tile[3], int halo);
+size_t particles_cl_smem_bytes();
+cudaError_t particles_cl_set_smem_limit();
+cudaError_t launch_particles_cl(cudaStream_t st, int total_tiles, const long long *tile_start,
+                                const unsigned char *lane_cell, const int *lane_count, int *drift,
+                                const GroupDev *groups, int ngroups, const RunDev *runs, const PoolBuf &P,
+                                void *const E[3], void *const B[3], void *const J[3], int ppb, int *err);
 // Work items (ranges of at most particles_per_item particles of one tile) from
 // the tile starts of the current particle order.
 cudaError_t build_items(cudaStream_t st, const long long *tile_start, int total_tiles, int particles_per_item,
@@ -159,7 +176,7 @@ cudaError_t adjoint_set_smem_limit(int dims, int prec, size_t bytes);
 
 struct pic_grid {
     int dims = 3, prec = 0;
-    int halo = 1, sort_interval = 10, ppi = 8192, sort_order = 0;
+    int halo = 1, sort_interval = 10, ppi = 8192, sort_order = 0;   // sort_order: the resolved PIC_SORT_*
     int tile[3] = {8, 8, 8};
     int pitch[2] = {0, 0};   // x, y pitch of the shared tiles (chosen at create)
     cudaStream_t stream = nullptr;
@@ -190,6 +207,9 @@ struct pic_grid {
 
     // sort products
     pic::SortScratch sort;
+    unsigned char *lane_cell = nullptr;   // cell-lane order: per tile and lane, the lane's cell ...
+    int *lane_count = nullptr;            // ... and its particle count (total_tiles * 128 each)
+    int *drift = nullptr;                 // cell-lane kernel: drift lists, pool-sized
     long long *tile_start = nullptr;
     unsigned *item_scan = nullptr;
     pic::WorkItem *items = nullptr;

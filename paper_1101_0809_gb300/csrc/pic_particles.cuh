@@ -448,7 +448,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                     atomicOr(a.err, ERR_NONFINITE);
                     live = false;   // the particle keeps x^n and contributes no current
                 } else {
-                    const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
+                    const R ig = rsqrt_r(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
                     s0 = renormalize(o0, w[0] * ig * cN0, n0);
                     s1 = renormalize(o1, w[1] * ig * cN1, n1);
                     if (DIM == 3) s2 = renormalize(o2, w[2] * ig * cN2, n2);
@@ -483,7 +483,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                 s1 = j1 - j; if (s1 > 1) s1 -= ny; if (s1 < -1) s1 += ny;
                 if (DIM == 3) { s2 = k1 - k; if (s2 > 1) s2 -= nz; if (s2 < -1) s2 += nz; }
                 if (DIM == 2) {
-                    const R ig = R(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
+                    const R ig = rsqrt_r(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
                     uz = cl * w[2] * ig;
                 }
             }

@@ -352,6 +352,117 @@ __global__ void __launch_bounds__(kSortThreads) k_bank_order(const long long *ti
     }
 }
 
+// ---------------------------------------------------------------------------
+// Cell-lane order inside a tile (PIC_SORT_CELL_LANES; tiles of at most 128
+// cells).  The tile's cells are ranked by descending particle count, ties by
+// their index c = lx + Tx (ly + Ty lz) in the tile: cell c gets lane L(c).  The
+// particle of rank r among its cell's particles (input order) goes to slot
+// P(r) + L(c) of the tile, P(r) = sum over the tile's cells of min(count, r):
+// the slots of rank r follow those of all lower ranks, and within a rank the
+// cells that still have particles come in lane order.  Per tile the kernel also
+// writes, for every lane, its cell (lane_cell) and count (lane_count).
+// ---------------------------------------------------------------------------
+constexpr int kLaneCells = 128;
+__global__ void __launch_bounds__(kSortThreads) k_cell_lane_order(const long long *tile_start, const unsigned *vals_in,
+                                                                  unsigned *vals_out, const int *cell,
+                                                                  const GroupDev *groups, int ngroups,
+                                                                  const RunDev *runs, unsigned char *lane_cell,
+                                                                  int *lane_count)
+{
+    constexpr int kRankTab = 1024;   // ranks with a precomputed P(r)
+    constexpr int kW = kSortThreads / 32;
+    __shared__ unsigned cnt[kLaneCells];
+    __shared__ unsigned lane_of[kLaneCells];
+    __shared__ unsigned scnt[kLaneCells];   // counts by lane (descending)
+    __shared__ unsigned run[kLaneCells];    // particles of each cell in earlier chunks
+    __shared__ unsigned wh[kW][kLaneCells];
+    __shared__ unsigned pre[kW][kLaneCells];
+    __shared__ unsigned ptab[kRankTab];
+    const int t = blockIdx.x;
+    const long long b0 = tile_start[t], e0 = tile_start[t + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int lo = 0, hi = ngroups;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (groups[mid].tile_base <= t) lo = mid; else hi = mid;
+    }
+    const RunDev &rn = runs[groups[lo].run];
+    const int lt = t - groups[lo].tile_base;
+    const int T0 = rn.tile[0], T1 = rn.tile[1];
+    const int ox = (lt % rn.ntile[0]) * T0, oy = ((lt / rn.ntile[0]) % rn.ntile[1]) * T1;
+    const int oz = (lt / (rn.ntile[0] * rn.ntile[1])) * rn.tile[2];
+    const int nx = rn.n[0], ny = rn.n[1];
+    auto local_cell = [&](unsigned v) -> unsigned {
+        const int c = cell[v];
+        const int r = divu31(c, rn.div_nx);
+        const int i = c - r * nx;
+        const int k = divu31(r, rn.div_ny);
+        const int j = r - k * ny;
+        return (unsigned)((i - ox) + T0 * ((j - oy) + T1 * (k - oz)));
+    };
+    for (int c = tid; c < kLaneCells; c += kSortThreads) {
+        cnt[c] = 0;
+        run[c] = 0;
+    }
+    for (int q = tid; q < kW * kLaneCells; q += kSortThreads) (&wh[0][0])[q] = 0;
+    __syncthreads();
+    for (long long o = b0 + tid; o < e0; o += kSortThreads) atomicAdd(&cnt[local_cell(vals_in[o])], 1u);
+    __syncthreads();
+    for (int c = tid; c < kLaneCells; c += kSortThreads) {
+        const unsigned mc = cnt[c];
+        unsigned r = 0;
+        for (int d = 0; d < kLaneCells; ++d) {
+            const unsigned md = cnt[d];
+            r += (md > mc || (md == mc && d < c)) ? 1u : 0u;
+        }
+        lane_of[c] = r;
+        scnt[r] = mc;
+        lane_cell[(long long)t * kLaneCells + r] = (unsigned char)c;
+        lane_count[(long long)t * kLaneCells + r] = (int)mc;
+    }
+    __syncthreads();
+    const unsigned maxc = scnt[0];
+    const unsigned nt = maxc < (unsigned)kRankTab ? maxc : (unsigned)kRankTab;
+    for (unsigned r = tid; r < nt; r += kSortThreads) {
+        unsigned s = 0;
+        for (int l = 0; l < kLaneCells; ++l) s += min(scnt[l], r);
+        ptab[r] = s;
+    }
+    __syncthreads();
+    const unsigned ltm = (1u << lane) - 1u;
+    for (long long r0 = b0; r0 < e0; r0 += kSortThreads) {
+        const long long o = r0 + tid;
+        const bool valid = o < e0;
+        const unsigned v = valid ? vals_in[o] : 0u;
+        const unsigned lc = valid ? local_cell(v) : (unsigned)kLaneCells;
+        const unsigned peers = __match_any_sync(0xffffffffu, lc);
+        const unsigned rk = __popc(peers & ltm);
+        if (valid && (__ffs(peers) - 1) == lane) wh[warp][lc] = __popc(peers);
+        __syncthreads();
+        for (int c = tid; c < kLaneCells; c += kSortThreads) {
+            unsigned acc = run[c];
+            for (int w = 0; w < kW; ++w) {
+                const unsigned x = wh[w][c];
+                pre[w][c] = acc;
+                acc += x;
+                wh[w][c] = 0;
+            }
+            run[c] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            const unsigned rank = pre[warp][lc] + rk;   // rank among the cell's particles
+            unsigned P = 0;
+            if (rank < nt) {
+                P = ptab[rank];
+            } else {
+                for (int l = 0; l < kLaneCells; ++l) P += min(scnt[l], rank);
+            }
+            vals_out[b0 + P + lane_of[lc]] = v;
+        }
+    }
+}
+
 // Permute every particle array: dst[o] = src[perm[o]].
 template <typename R, int DIM>
 __global__ void k_permute(long long n, const unsigned *perm, Pool<R> src, Pool<R> dst)
@@ -417,7 +528,8 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  const PoolBuf &dst, const GroupDev *groups, const long long *group_base_dev,
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
-                                 int particles_per_item, int halo, int banked, int half, int *launches)
+                                 int particles_per_item, int halo, int banked, int half, int *launches,
+                                 unsigned char *lane_cell, int *lane_count)
 {
     cudaError_t e;
     if (total <= 0 || ngroups <= 0) {
@@ -452,7 +564,14 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
     k_tile_start<<<nbp, nt, 0, st>>>(scr.keys[cur], total, total_tiles, tile_start);
     *launches += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (banked) {
+    if (lane_cell && lane_count) {
+        k_cell_lane_order<<<(unsigned)total_tiles, kSortThreads, 0, st>>>(tile_start, scr.vals[cur], scr.vals[1 - cur],
+                                                                        src.cell, groups, ngroups, runs, lane_cell,
+                                                                        lane_count);
+        *launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cur = 1 - cur;
+    } else if (banked) {
         k_bank_order<<<(unsigned)total_tiles, kSortThreads, 0, st>>>(tile_start, scr.vals[cur], scr.vals[1 - cur],
                                                                    src.cell, groups, ngroups, runs, halo, dims, half,
                                                                    prec, src.off[0], src.off[1], src.off[2]);

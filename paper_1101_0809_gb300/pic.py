@@ -18,7 +18,7 @@ PIC_OK, PIC_ERR_INVALID_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_CUDA = 0, 1, 2, 3
 PIC_ERR_NONFINITE, PIC_ERR_OUT_OF_TILE, PIC_ERR_TIMEOUT, PIC_ERR_STATE = 5, 6, 7, 8
 PIC_FP64, PIC_FP32 = 0, 1
 PIC_B_HALF, PIC_E_FULL = 1, 2
-PIC_SORT_BANKED, PIC_SORT_STABLE = 0, 1
+PIC_SORT_AUTO, PIC_SORT_STABLE, PIC_SORT_BANKED, PIC_SORT_CELL_LANES = 0, 1, 2, 3
 
 
 class PicError(RuntimeError):
@@ -485,7 +485,7 @@ def pic_tile_sort_perm_noalloc(cell, n, dims, ncell, tile, perm, tile_start=None
 
 
 def make_desc(dims, n, d, dt, c, precision=PIC_FP64, tile=(0, 0, 0), halo=-1, sort_interval=0,
-              particles_per_block=0, rho_bg=0.0, stream=None, sort_order=PIC_SORT_BANKED, order2=3):
+              particles_per_block=0, rho_bg=0.0, stream=None, sort_order=PIC_SORT_AUTO, order2=3):
     """Fill a pic_grid_desc; ``stream`` is a raw cudaStream_t handle (int) or None;
     order2 = 3 for l_a = 1 1/2, 5 for l_a = 2 1/2, 4 for the comparison scheme of Eq. wrong1."""
     return pic_grid_desc(dims, n[0], n[1], n[2] if dims == 3 else 1, d[0], d[1], d[2], dt, c,

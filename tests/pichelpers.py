@@ -157,7 +157,7 @@ def make_grid(P, wl, precision, stream=None, tile=None, halo=-1, sort_interval=N
     return grid
 
 
-def tile_sort_perm(wl, cells, tile, halo=1, banked=True, pitch=None, up=None):
+def tile_sort_perm(wl, cells, tile, halo=1, banked=True, pitch=None, up=None, cell_lanes=False):
     """The tile sort's permutation written out from its definition (integer work,
     compared bit-exactly): sort by tile key; with ``banked``, inside a tile by
     (r, b) where b is the shared-memory bank of the cell's base address in the
@@ -165,8 +165,12 @@ def tile_sort_perm(wl, cells, tile, halo=1, banked=True, pitch=None, up=None):
     the grid's tile pitches (pic_tile_layout), and r the particle's rank among
     the tile's particles of bank b in input order.  ``up`` (l_a = 2 1/2): per
     axis the 0/1 flags offset >= 1/2, added to i, j, k in the base (the base
-    index of the interpolation), not in the tile key.  Returns perm[o] = input
-    index at slot o."""
+    index of the interpolation), not in the tile key.  With ``cell_lanes``: the
+    tile's cells c = (i-ox) + Tx ((j-oy) + Ty (k-oz)) get lanes L(c) by
+    descending particle count, ties by c; the particle of rank r among its
+    cell's particles (input order) takes slot P(r) + L(c) of the tile, with
+    P(r) = sum over the tile's Tx Ty Tz cells of min(count, r).  Returns
+    perm[o] = input index at slot o."""
     nx, ny = wl.n[0], wl.n[1]
     cells = np.asarray(cells, dtype=np.int64)
     i, j, k = cells % nx, (cells // nx) % ny, cells // (nx * ny)
@@ -174,6 +178,29 @@ def tile_sort_perm(wl, cells, tile, halo=1, banked=True, pitch=None, up=None):
     ntx, nty = -(-nx // T[0]), -(-ny // T[1])
     ti, tj, tk = i // T[0], j // T[1], (k // T[2] if wl.dims == 3 else 0 * k)
     key = (tk * nty + tj) * ntx + ti
+    if cell_lanes:
+        ncell = T[0] * T[1] * (T[2] if wl.dims == 3 else 1)
+        c = (i - ti * T[0]) + T[0] * ((j - tj * T[1]) + T[1] * ((k - tk * T[2]) if wl.dims == 3 else 0))
+        order = np.argsort(key, kind="stable")
+        out = np.empty(cells.size, dtype=np.int64)
+        keys_sorted = key[order]
+        starts = np.r_[0, np.flatnonzero(np.diff(keys_sorted)) + 1]
+        ends = np.r_[starts[1:], keys_sorted.size]
+        for s0, e0 in zip(starts, ends):
+            members = order[s0:e0]                     # this tile's particles, input order
+            cc = c[members]
+            count = np.bincount(cc, minlength=ncell)
+            lanes = np.lexsort((np.arange(ncell), -count))   # lane -> cell
+            lane_of = np.empty(ncell, dtype=np.int64)
+            lane_of[lanes] = np.arange(ncell)
+            rank = np.empty(cc.size, dtype=np.int64)
+            seen = np.zeros(ncell, dtype=np.int64)
+            for q, cq in enumerate(cc):
+                rank[q] = seen[cq]
+                seen[cq] += 1
+            P = np.array([np.minimum(count, r).sum() for r in range(int(count.max()) + 1)])
+            out[s0 + P[rank] + lane_of[cc]] = members
+        return out
     if not banked:
         return np.argsort(key, kind="stable")
     u = [np.zeros_like(i)] * 3 if up is None else [np.asarray(a, dtype=np.int64) for a in up]
@@ -190,4 +217,3 @@ def tile_sort_perm(wl, cells, tile, halo=1, banked=True, pitch=None, up=None):
     r = np.empty(cells.size, dtype=np.int64)
     r[idx] = np.arange(skb.size) - grp
     return np.lexsort((b, r, key))
-
