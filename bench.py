@@ -29,9 +29,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s and % HBM roofline (fwd, fwd+adjoint) FP32 vs FP64 at 1 GB300"
 UNIT = "particle-steps/s"
-WORKLOAD = ("3D3V periodic 128^3 Yee grid, electrons + ions (mass ratio 1836), 32 per cell each "
-            "(134,217,728 particles), v_th,e = 0.1c, dt = 0.45 dx/c, l_a = 1 1/2 gather, "
-            "virtual-path deposit")
+WORKLOAD = ("3D3V 128^3 periodic, e- and ions (m_i/m_e = 1836), 32+32 per cell, v_th,e = 0.1c, "
+            "dt = 0.45 dx/c, FP32 form")
 
 
 def parse():
@@ -57,6 +56,7 @@ def parse():
     ap.add_argument("--energy-x5-steps", type=int, default=4000, help="steps of the Langmuir run (X5)")
     ap.add_argument("--no-vecpot", action="store_true", help="skip the vector-potential (generalized momentum) leg")
     ap.add_argument("--laser-warmup", type=int, default=480)
+    ap.add_argument("--no-gauss", action="store_true", help="skip the 200-step full-size Gauss residual")
     return ap.parse_args()
 
 
@@ -300,7 +300,7 @@ def timed_steps(P, torch, grid, steps, dist=None, sampler=None):
     return ms, prof, launches, clocks
 
 
-def batched_arm(P, W, torch, args, dist):
+def batched_arm(P, W, torch, args, dist, hbm_peak):
     """The batched ensemble: independent 2D3V periodic runs with N ~ U{32..256}
     per axis, 4-64 electrons per cell and v_th ~ U[0.01c, 0.3c], FP32, advanced
     together by one cooperative launch per step replayed from CUDA graphs, with
@@ -340,7 +340,7 @@ def batched_arm(P, W, torch, args, dist):
         finally:
             b.close()
 
-    cands = [dict(tile=t, ppb=p, K=k) for t in (8, 16) for p in (8192,) for k in (2, 3, 5, 8)]
+    cands = [dict(tile=t, ppb=p, K=k) for t in (8, 16) for p in (2048, 4096, 8192) for k in (2, 3, 5, 8)]
     key = AT.workload_key("ensemble2d", [(r["n"], r["ppc"], round(r["vth"], 6)) for r in params[::8]])
     best, table, cached = AT.tune(key, torch.cuda.get_device_name(), cands, time_candidate)
     b = build(runs, best)
@@ -361,11 +361,19 @@ def batched_arm(P, W, torch, args, dist):
     b.close()
     accuracy = batched_accuracy(P, runs[::8], best, build, 20)
     world = dist.get_world_size() if dist is not None else 1
+    # the whole step's algorithmic bytes: the 2D FP32 particle state read and
+    # written (24 B each way) and per cell E, B, J through the particle pass and
+    # the three field passes (120 B); the sort's share is left out
+    alg = npart * 48 + ncell * 120
+    ach = alg / (ms / nsteps * 1e-3) / 1e9
     return {"workload": f"{len(runs)} independent 2D3V periodic runs, N ~ U{{32..256}}^2, 4-64 e-/cell, "
                         "v_th ~ U[0.01c, 0.3c], FP32, one cooperative launch per step, CUDA graphs",
             "value": world * npart * nsteps / (ms * 1e-3), "unit": UNIT, "steps": nsteps, "ms_per_step": ms / nsteps,
             "particles": npart, "cells": ncell, "autotuned": best, "autotune_cached": cached,
-            "autotune_table": [[c, t] for c, t, _ in table], "gpu_launches": launches,
+            "autotune_candidates": len(table), "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                         "scope": "whole step (persistent kernel, sorts included in the time)",
+                         "alg_bytes_per_step": alg},
             "accuracy_vs_fp64": accuracy}
 
 
@@ -529,13 +537,70 @@ def adjoint_arm(P, W, torch, args, hbm_peak):
             lm = run.forward(torch.from_numpy(x_of(amp - h)), torch.from_numpy(w0))
             out["fp64_central_fd_dL_dA"] = (lp - lm) / (2 * h)
         run.grid.close()
+    out["fp32_device"] = adjoint_device(P, torch, W, wl0, x_of(amp), w0, hbm_peak)
     fd = out["fp64_central_fd_dL_dA"]
     out["fp32_grad_rel_err_vs_fp64_fd"] = abs(out["fp32"]["dL_dA"] - fd) / abs(fd)
     out["fp64_grad_rel_err_vs_fp64_fd"] = abs(out["fp64"]["dL_dA"] - fd) / abs(fd)
     return out
 
 
-def laser_arm(P, W, torch, args):
+def adjoint_device(P, torch, W, wl0, x0, w0, hbm_peak, nsteps=20):
+    """Device-only rates of the FP32 differentiable run's two passes, with CUDA
+    events on the grid's stream: the forward step (pic_step) and the adjoint
+    step (pic_adjoint_step, with device-resident adjoint arrays), each over
+    `nsteps` steps after warm-up.  HBM fractions from the algorithmic bytes of
+    the particle kernels (forward: state read and written, 48 B per particle,
+    and E, B, J, 36 B per cell; adjoint: state read 24 B, the adjoints of the
+    offsets and momenta read and written 40 B, and E, B^n, lamJ, lamE, lamB,
+    96 B per cell) over each pass's measured time."""
+    st = torch.cuda.Stream()
+    desc = P.make_desc(2, wl0.n, wl0.d, wl0.dt, wl0.c, P.PIC_FP32, tile=(16, 16, 1), rho_bg=wl0.rho_bg,
+                       stream=st.cuda_stream)
+    g = P.Grid(desc)
+    sp = wl0.species[0]
+    g.load(0, sp.q, sp.m, sp.weight, x0, w0)
+    P.pic_step(g.h, 20)            # fields that are not zero
+    P.pic_sync(g.h)
+    npart, ncell = wl0.n_particles, wl0.n_cells
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    shape = g.shape
+    lamE = [torch.randn(shape, device="cuda", generator=gen) for _ in range(3)]
+    lamB = [torch.randn(shape, device="cuda", generator=gen) for _ in range(3)]
+    lamx = [torch.randn(npart, device="cuda", generator=gen) for _ in range(3)]
+    lamw = [torch.randn(npart, device="cuda", generator=gen) for _ in range(3)]
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            for _ in range(nsteps):
+                fn()
+            e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / nsteps
+
+    snap = torch.empty(P.pic_state_bytes(g.h), dtype=torch.uint8, device="cuda")
+    P.pic_state_save(g.h, snap)
+    fwd_ms = timed(lambda: P.pic_step(g.h, 1))
+    P.pic_state_restore(g.h, snap)
+    adj_ms = timed(lambda: P.pic_adjoint_step(g.h, lamE, lamB, lamx, lamw))
+    P.pic_sync(g.h)
+    g.close()
+    fb, ab = npart * 48 + ncell * 36, npart * 64 + ncell * 96
+    fa, aa = fb / (fwd_ms * 1e-3) / 1e9, ab / (adj_ms * 1e-3) / 1e9
+    return {"scope": "device only: CUDA events around pic_step and pic_adjoint_step, arrays resident",
+            "fwd": npart / (fwd_ms * 1e-3), "adj": npart / (adj_ms * 1e-3),
+            "fwd_adj": npart / ((fwd_ms + adj_ms) * 1e-3), "unit": UNIT, "fwd_ms": fwd_ms, "adj_ms": adj_ms,
+            "roofline_hbm": {"fwd_frac": fa / hbm_peak, "adj_frac": aa / hbm_peak,
+                             "fwd_adj_frac": (fb + ab) / ((fwd_ms + adj_ms) * 1e-3) / 1e9 / hbm_peak,
+                             "bytes": {"fwd": fb, "adj": ab}, "peak": hbm_peak, "unit": "GB/s"}}
+
+
+def laser_arm(P, W, torch, args, hbm_peak):
     """3D relativistic laser-plasma: 512x128x128 periodic box, a0 = 5 plane wave
     of wavelength 20 cells from a one-way antenna plane at x = 8, cold electron
     slab (ramp 128-178, plateau to 384 at 0.01 n_c, 16 per cell), FP32, tile
@@ -554,22 +619,36 @@ def laser_arm(P, W, torch, args):
     P.pic_step(g.h, args.laser_warmup)
     P.pic_sync(g.h)
     nsteps = 20
-    P.pic_profile(g.h, True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    P.pic_step(g.h, nsteps)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / nsteps
-    prof = P.pic_profile_read(g.h)
+
+    def window():
+        P.pic_profile(g.h, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        P.pic_step(g.h, nsteps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nsteps
+        prof = P.pic_profile_read(g.h)
+        P.pic_profile(g.h, False)
+        pk = prof["particles"][0] / max(prof["particles"][1], 1)
+        ach = (wl.n_particles * 56 + wl.n_cells * 36) / (pk * 1e-3) / 1e9
+        return {"value": wl.n_particles / (ms * 1e-3), "ms_per_step": ms, "particles_ms": pk,
+                "sorts": prof["sort"][1], "sort_ms": prof["sort"][0] / max(prof["sort"][1], 1),
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach / hbm_peak, "alg_bytes_per_launch": wl.n_particles * 56 + wl.n_cells * 36}}
+
+    adaptive = window()
+    # the configuration as stated: the fixed sort interval of 10 steps, over the
+    # next 20 steps (two sorts)
+    P.pic_set_sort_policy(g.h, False)
+    fixed = window()
     d = P.pic_diagnostics(g.h)
     out = {"workload": "3D relativistic laser-plasma 512x128x128, a0 = 5, lambda = 20 cells, cold electron slab "
-                       "0.01 n_c (ramp 128-178, plateau to 384), 16 per cell, FP32, adaptive tile sort",
-           "value": wl.n_particles / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "particles": wl.n_particles,
-           "cells": wl.n_cells, "timed_from_step": args.laser_warmup, "steps": nsteps,
-           "particles_ms": prof["particles"][0] / max(prof["particles"][1], 1),
-           "sorts": prof["sort"][1], "sort_ms": prof["sort"][0] / max(prof["sort"][1], 1),
+                       "0.01 n_c (ramp 128-178, plateau to 384), 16 per cell, FP32",
+           "value": fixed["value"], "unit": UNIT, "particles": wl.n_particles, "cells": wl.n_cells,
+           "timed_from_step": args.laser_warmup, "steps": nsteps,
+           "fixed_sort_interval_10": fixed, "adaptive_sort": adaptive,
            "kinetic": d["kinetic"], "field_E": d["field_E"]}
     g.close()
     return out
@@ -692,6 +771,96 @@ def vecpot_arm(P):
     return out
 
 
+def _g(v, digits=4):
+    """A number rounded to a few significant digits for the compact summary."""
+    if v is None:
+        return None
+    if isinstance(v, bool) or isinstance(v, int):
+        return v
+    return float(f"{v:.{digits}g}")
+
+
+def summary_line(value, ms_step, roof, gauss, fp64, batched, adjoint, laser, order5, energy, vecpot, e2e, cpu):
+    """The flat summary that ends the JSON line: every leg's headline figures,
+    rounded, so that the end of the line alone carries them.  Rates in
+    particle-steps/s; *_frac are fractions of the measured HBM (or FP64 FMA)
+    peak; *_rel are relative differences against the FP64 method."""
+    s = {"fp32": _g(value), "fp32_ms_step": _g(ms_step), "fp32_kernel_ms": _g(roof["avg_launch_ms"]),
+         "fp32_hbm_frac": _g(roof["frac"]), "sort_share": _g(roof["step_share"].get("sort"))}
+    if gauss:
+        s["gauss_fp32_200_steps_rel"] = _g(gauss["gauss_resid_max_rel"])
+    if fp64:
+        s["fp64"] = _g(fp64["value"])
+        s["fp64_hbm_frac"] = _g(fp64["roofline_hbm"]["frac"])
+        if "roofline_fp64" in fp64:
+            s["fp64_fma_frac"] = _g(fp64["roofline_fp64"]["frac"])
+        s["fp64_fma_peak_per_s"] = _g(fp64["fp64_fma_peak_measured"]["fma_per_s"])
+        s["fp32_over_fp64"] = _g(fp64["fp32_speedup"])
+        acc = fp64.get("fp32_vs_fp64")
+        if acc:
+            for k in ("E_max_rel", "J_max_rel", "w_rms_rel", "x_max_abs_cells", "gauss_rel_fp32"):
+                s["fp32_vs_fp64_" + k] = _g(acc[k], 3)
+    if batched:
+        s["batched"] = _g(batched["value"])
+        s["batched_hbm_frac"] = _g(batched["roofline"]["frac"])
+        s["batched_tile_ppb_K"] = [batched["autotuned"][k] for k in ("tile", "ppb", "K")]
+        s["batched_E_rel_worst"] = _g(batched["accuracy_vs_fp64"]["E_max_rel_worst_run"], 3)
+    if adjoint:
+        s["adj_fp32_fwd_adj"] = _g(adjoint["fp32"]["fwd_adj"])
+        s["adj_fp32_fwd_adj_hbm_frac"] = _g(adjoint["fp32"]["roofline_hbm"]["fwd_adj"]["frac"], 3)
+        s["adj_fp64_fwd_adj"] = _g(adjoint["fp64"]["fwd_adj"])
+        dev = adjoint.get("fp32_device")
+        if dev:
+            s["adj_dev_fwd_adj"] = _g(dev["fwd_adj"])
+            s["adj_dev_adj_hbm_frac"] = _g(dev["roofline_hbm"]["adj_frac"], 3)
+            s["adj_dev_fwd_adj_hbm_frac"] = _g(dev["roofline_hbm"]["fwd_adj_frac"], 3)
+        s["adj_fp32_grad_rel_vs_fd"] = _g(adjoint["fp32_grad_rel_err_vs_fp64_fd"], 3)
+    if laser:
+        s["laser_k10"] = _g(laser["fixed_sort_interval_10"]["value"])
+        s["laser_k10_hbm_frac"] = _g(laser["fixed_sort_interval_10"]["roofline"]["frac"], 3)
+        s["laser_adaptive"] = _g(laser["adaptive_sort"]["value"])
+    if order5:
+        s["la25"] = _g(order5["value"])
+        s["la25_hbm_frac"] = _g(order5["roofline"]["frac"], 3)
+    if energy:
+        s["x1_defect_la15"] = _g(energy["x1"]["l_a_1_5"]["max_rel_defect"], 3)
+        s["x1_defect_wrong1"] = _g(energy["x1"]["wrong1_l_2"]["max_rel_defect"], 3)
+        s["x5_period_vs_expected"] = [_g(energy["x5"]["field_energy_period_steps"]),
+                                      _g(energy["x5"]["expected_period_steps"])]
+    if vecpot:
+        s["pz_drift_ratio_la15_wrong1"] = [_g(vecpot["l_a_1_5"]["ratio"], 3), _g(vecpot["wrong1_l_2"]["ratio"], 3)]
+    if e2e:
+        s["e2e_serial"] = _g(e2e["serial"]["value"])
+    if cpu:
+        s["cpu_1core"] = _g(cpu["single_core"]["value"])
+    return s
+
+
+def measure_fp64_fma(P, torch):
+    """The device's FP64 FMA rate: the pic_measure_fp64_fma kernel (8 blocks of
+    256 threads per SM, 8 independent chains per thread), timed with CUDA events
+    after a warm-up launch; best of 3."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    iters = 20000
+    P.pic_measure_fp64_fma(1000, 8, sink, st.cuda_stream)
+    best = None
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        n = P.pic_measure_fp64_fma(iters, 8, sink, st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        if best is None or ms < best[0]:
+            best = (ms, n)
+    ms, n = best
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rate = n / (ms * 1e-3)
+    return {"fma_per_s": rate, "flops": 2 * rate, "ms": ms, "fma": n, "sms": sms}
+
+
 def our_arm(args):
     import torch
     rank, local, world = dist_env()
@@ -732,11 +901,24 @@ def our_arm(args):
 
     # ---- FP32 form, device-resident --------------------------------------------------
     grid = build_grid(P, wl, P.PIC_FP32, stream)
+    P.pic_diagnostics(grid.h)          # the residual reference of Gauss's law: the initial state
     for _ in range(args.warmup):
         P.pic_step(grid.h, 1)
     P.pic_sync(grid.h)
     ms, prof, launches, clocks = timed_steps(P, torch, grid, args.steps, dist, sampler)
     P.pic_sync(grid.h)
+    # the FP32 charge-conservation residual after the workload's 200 steps at full size
+    gauss = None
+    if not args.no_gauss:
+        done = args.warmup + args.steps
+        if done < 200:
+            P.pic_step(grid.h, 200 - done)
+        dg = P.pic_diagnostics(grid.h)
+        rho_e = abs(wl.species[0].q * wl.species[0].weight) * wl.species[0].x.shape[1] / (ncell * wl.volume)
+        gauss = {"steps": max(done, 200), "gauss_resid_max_rel": dg["gauss_resid_max"] / (4 * math.pi * rho_e),
+                 "gauss_resid_rms_rel": dg["gauss_resid_rms"] / (4 * math.pi * rho_e),
+                 "scale": "4 pi |q_e| n_e (one species' density)", "n_particles": dg["n_particles"],
+                 "error_word": dg["error_word"]}
     ms_step = ms / args.steps
     value = world * npart * args.steps / (ms * 1e-3)
     pk_ms, pk_n = prof["particles"]
@@ -888,27 +1070,27 @@ def our_arm(args):
         # DMUL or DFMA) per SM per clock; FP64 instructions per particle from the
         # committed ncu summary of the same kernel source
         f64pp = ncu_per_particle("fp64", "fp64_instr_per_particle")
+        fma_rate = measure_fp64_fma(P, torch)
+        fp64["fp64_fma_peak_measured"] = fma_rate
         if f64pp:
-            sms = torch.cuda.get_device_properties(0).multi_processor_count
-            alu_peak = 2.0 * sms * sm_mhz * 1e6
             alu_ach = f64pp * npart / (pk64_ms / pk64_n * 1e-3)
-            fp64["roofline_fp64"] = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
-                                     "unit": "FP64 instructions/s", "frac": alu_ach / alu_peak,
+            fp64["roofline_fp64"] = {"bound": "alu", "achieved": alu_ach, "peak": fma_rate["fma_per_s"],
+                                     "unit": "FP64 instructions/s", "frac": alu_ach / fma_rate["fma_per_s"],
                                      "fp64_instructions_per_particle": f64pp,
-                                     "peak_source": f"2 per SM per clock x {sms} SMs x {sm_mhz:.0f} MHz (sampled)"}
+                                     "peak_source": "measured: the FP64 FMA rate of pic_measure_fp64_fma"}
         if rank == 0:
             fp64["fp32_vs_fp64"] = main_accuracy(P, wl, stream, g64, min(args.warmup, 2) + k64)
         g64.close()
 
     batched = None
     if not args.no_batch:
-        batched = batched_arm(P, W, torch, args, dist)
+        batched = batched_arm(P, W, torch, args, dist, hbm_peak)
     adjoint = None
     if not args.no_adjoint and rank == 0:
         adjoint = adjoint_arm(P, W, torch, args, hbm_peak)
     laser = None
     if not args.no_laser:
-        laser = laser_arm(P, W, torch, args)
+        laser = laser_arm(P, W, torch, args, hbm_peak)
     energy = None
     if not args.no_energy and rank == 0:
         energy = energy_arm(P, args)
@@ -920,17 +1102,28 @@ def our_arm(args):
         order5 = order5_arm(P, torch, wl, stream, hbm_peak, value / world, min(args.steps, 10))
 
     if rank == 0:
+        detail = {"roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gauss_200": gauss, "fp64": fp64,
+                  "batched": batched, "adjoint": adjoint, "laser": laser, "l_a_2_5": order5, "energy": energy,
+                  "vector_potential": vecpot}
+        # every leg in full on stderr; stdout carries the one compact line
+        print(json.dumps({"detail": detail}), file=sys.stderr, flush=True)
+        roof_line = {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
+                                          "peak_source", "alg_bytes_per_launch", "avg_launch_ms")}
+        cpu_line = None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        e2e_line = None if e2e is None else {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step",
+                                                                 "d2h_bytes_per_step", "steps")}
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": WORKLOAD, "model": "ChCPIC step, FP32 form", "global_batch": world * npart,
-                          "particles_per_gpu": npart, "cells": ncell, "tile": list(wl.tile),
-                          "sort_interval": wl.sort_interval, "halo": 1, "particles_per_block": 8192,
+               "config": {"workload": WORKLOAD, "model": "ChCPIC step, FP32 form",
+                          "global_batch": world * npart, "particles_per_gpu": npart, "cells": ncell,
+                          "tile": list(wl.tile), "sort_interval": wl.sort_interval,
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                          "l2": "inputs larger than L2 (3.76 GB of particle SoA per replica); no flush"},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-               "fp64": fp64, "batched": batched, "adjoint": adjoint, "laser": laser, "l_a_2_5": order5,
-               "energy": energy, "vector_potential": vecpot}
+                          "l2": "inputs larger than L2 (3.76 GB of particle SoA); no flush"},
+               "roofline": roof_line, "cpu_baseline": cpu_line, "e2e": e2e_line, "gpu_launches": launches,
+               "clocks": clocks,
+               "summary": summary_line(value, ms_step, roof, gauss, fp64, batched, adjoint, laser, order5, energy,
+                                       vecpot, e2e, cpu)}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -257,6 +257,16 @@ int pic_sync(pic_grid *g);
 /* Message of the last failure on the calling thread ("" if none). */
 const char *pic_last_error(void);
 
+/* Allocation-failure injection, for testing the failure paths (the paper has
+ * no counterpart).  After the call, the library's next `after` device
+ * allocations succeed and the one after them fails as an out-of-memory
+ * condition would; the call that made it returns PIC_ERR_OOM.  One failure per
+ * arming; after < 0 disarms.  Process-wide.  A load that fails this way leaves
+ * the grid usable: a failure while the new particle pool is allocated keeps
+ * the previous particles, a later one leaves the grid with its fields and no
+ * particles. */
+int pic_inject_alloc_failure(long long after);
+
 /* Number of kernels this grid has launched since creation (for accounting). */
 long long pic_kernel_launches(pic_grid *g);
 
@@ -438,6 +448,17 @@ int pic_adjoint_yee_half_B(pic_grid *g, void *const lamB[3], void *lamE[3]);
  * are outside the contract (the result is then unspecified, never a fault). */
 int pic_renormalize_f32(const float *offset, const float *delta, long long n, int *shift, float *offset_out,
                         void *cuda_stream);
+
+/* ---- FP64 FMA rate ---------------------------------------------------------------
+ * The paper has no counterpart: a measurement aid for the roofline of the FP64
+ * path, which is bound by the FP64 pipe.  Enqueues on cuda_stream one launch of
+ * blocks_per_sm blocks of 256 threads per SM, each thread running 8 independent
+ * chains of iters FP64 fused multiply-adds, and returns in *fma_count the FMAs
+ * it executes; the caller times the launch (e.g. with events on the stream).
+ * sink: one device double the kernel may write (never read back).  Errors:
+ * PIC_ERR_INVALID_ARG for non-positive counts or null pointers, PIC_ERR_CUDA
+ * for a failed launch. */
+int pic_measure_fp64_fma(long long iters, int blocks_per_sm, double *sink, long long *fma_count, void *cuda_stream);
 
 /* ---- Tile sort without device allocation -----------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot

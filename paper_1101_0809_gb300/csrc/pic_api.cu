@@ -7,6 +7,8 @@
 #include <cstddef>
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <string>
 #include <new>
 
 #include "../../include/pic.h"
@@ -135,11 +137,25 @@ struct Copier {
 
 size_t elem(const pic_grid *g) { return g->prec == PIC_FP64 ? sizeof(double) : sizeof(float); }
 
+// Allocation-failure injection (pic_inject_alloc_failure): the number of device
+// allocations still to succeed before one fails; -1 when disarmed.
+std::atomic<long long> g_alloc_fail_in{-1};
+
+bool injected_alloc_failure()
+{
+    long long n = g_alloc_fail_in.load();
+    while (n >= 0) {
+        if (g_alloc_fail_in.compare_exchange_weak(n, n - 1)) return n == 0;
+    }
+    return false;
+}
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t count)
 {
     *p = nullptr;
     if (count == 0) return cudaSuccess;
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
     return cudaMalloc((void **)p, count * sizeof(T));
 }
 
@@ -147,6 +163,7 @@ cudaError_t dalloc_bytes(void **p, size_t bytes)
 {
     *p = nullptr;
     if (bytes == 0) return cudaSuccess;
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
     return cudaMalloc(p, bytes);
 }
 
@@ -365,6 +382,11 @@ int upload_groups(pic_grid *g)
 
 int do_sort(pic_grid *g)
 {
+    if (g->total <= 0 || g->groups.empty() || !g->tile_start) {   // nothing to sort
+        g->steps_since_sort = 0;
+        g->have_old = false;
+        return PIC_OK;
+    }
     ProfScope ps(g, PIC_PROF_SORT);
     int nl = 0;
     cudaError_t e = sort_and_build_items(g->prec, g->dims, g->stream, g->total, g->pool, g->pool_alt, g->d_groups,
@@ -619,6 +641,12 @@ extern "C" {
 
 const char *pic_last_error(void) { return t_err; }
 
+int pic_inject_alloc_failure(long long after)
+{
+    g_alloc_fail_in.store(after < 0 ? -1 : after);
+    return PIC_OK;
+}
+
 int pic_create_batch(const pic_grid_desc *descs, int nruns, pic_grid **out)
 {
     if (!out) return fail(PIC_ERR_INVALID_ARG, "null output pointer");
@@ -842,6 +870,29 @@ int pic_get_fields(pic_grid *g, void *E[3], void *B[3], void *J[3], int on_devic
     return pic_get_fields_run(g, 0, E, B, J, on_device);
 }
 
+// Frees every particle buffer and leaves the grid with its fields and no
+// particles (the state of a new grid's particles).
+static void drop_particles(pic_grid *g)
+{
+    cudaStreamSynchronize(g->stream);
+    free_pool(g->pool);
+    free_pool(g->pool_alt);
+    free_sort(g);
+    dfree(g->old_cell);
+    g->old_cell = nullptr;
+    for (int c = 0; c < 3; ++c) {
+        dfree(g->old_off[c]);
+        g->old_off[c] = nullptr;
+    }
+    g->groups.clear();
+    g->total = 0;
+    g->have_old = false;
+    g->max_items = 0;
+    cudaMemsetAsync(g->n_items, 0, sizeof(int), g->stream);
+    upload_groups(g);
+    graph_drop(g);
+}
+
 static bool group_before(int run_a, int sp_a, int run_b, int sp_b)
 {
     return run_a < run_b || (run_a == run_b && sp_a < sp_b);
@@ -1005,9 +1056,15 @@ static int load_many(pic_grid *g, std::vector<LoadReq> &reqs, int on_device)
     g->groups = ng;
     g->total = total;
     int rc = upload_groups(g);
-    if (rc != PIC_OK) return rc;
-    rc = size_particle_buffers(g, total);
-    if (rc != PIC_OK) return rc;
+    if (rc == PIC_OK) rc = size_particle_buffers(g, total);
+    if (rc != PIC_OK) {
+        // the new layout could not get its buffers: the grid keeps its fields
+        // and no particles, and stays usable (a later load starts afresh)
+        const std::string msg = pic_last_error();
+        drop_particles(g);
+        set_last_error((msg + "; the grid's particles were dropped").c_str());
+        return rc;
+    }
     rc = do_sort(g);
     if (rc != PIC_OK) return rc;
     for (auto &q : reqs) g->have_ref[q.run] = 0;

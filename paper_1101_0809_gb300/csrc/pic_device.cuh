@@ -402,7 +402,10 @@ struct SmemAcc {
 // for every possible contribution; the host sets the scale).  It is split into
 // hi = rint(q/2^16) and lo = rint(q - hi*2^16) (|lo| <= 2^15), both taken from
 // the 1.5*2^23 magic-number addition, with the product formed inside the fused
-// multiply-adds.  The two integer sums are exact and stay below 2^31 for up to
+// multiply-adds: magic + hi = fma(kp/2^16, t, magic), then the exact constant
+// magic - hi*2^16 = fma(magic + hi, -2^16, magic*(2^16 + 1)) (at most 18
+// significant bits), and magic + lo = fma(kp, t, magic - hi*2^16), rounded once
+// to an integer because it lies in [2^23, 2^24).  The two integer sums are exact and stay below 2^31 for up to
 // 2^13 particles per block; the block converts hi*2^16 + lo back once.
 // The words added are the bit patterns of magic + hi and magic + lo, i.e.
 // kFixBias + hi and kFixBias + lo.  With SUB the bias is taken off before each
@@ -420,8 +423,8 @@ struct FixedAccT {
     {
         const float magic = 12582912.0f;   // 1.5 * 2^23
         const float th = fmaf(kp * (1.0f / 65536.0f), t, magic);   // magic + hi
-        const float mh = fmaf(th, -65536.0f, magic * 65536.0f);      // -hi * 2^16, exact
-        const float tl = fmaf(kp, t, mh) + magic;                    // magic + lo
+        const float ch = fmaf(th, -65536.0f, magic * 65537.0f);      // magic - hi * 2^16, exact
+        const float tl = fmaf(kp, t, ch);                            // magic + lo, one rounding
         const int idx = base + dx + s1 * dy + s2 * dz;
         atomicAdd(&hi[a][idx], SUB ? __float_as_int(th) - (int)kFixBias : __float_as_int(th));
         atomicAdd(&lo[a][idx], SUB ? __float_as_int(tl) - (int)kFixBias : __float_as_int(tl));

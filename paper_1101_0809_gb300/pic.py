@@ -470,6 +470,25 @@ def pic_renormalize_f32(offset, delta, shift, offset_out, stream=None):
     _check(_lib.pic_renormalize_f32(po, pd, n, ps, pr, stream))
 
 
+_lib.pic_measure_fp64_fma.argtypes = [C.c_longlong, C.c_int, _VP, C.POINTER(C.c_longlong), _VP]
+
+
+def pic_measure_fp64_fma(iters, blocks_per_sm, sink, stream=None):
+    """Enqueue the FP64 FMA-rate kernel; sink is a CUDA float64 tensor; returns
+    the number of FMAs the launch executes (time it on the stream)."""
+    n = C.c_longlong(0)
+    _check(_lib.pic_measure_fp64_fma(iters, blocks_per_sm, _addr(sink)[0], C.byref(n), stream))
+    return n.value
+
+
+_lib.pic_inject_alloc_failure.argtypes = [C.c_longlong]
+
+
+def pic_inject_alloc_failure(after):
+    """Make the library's (after+1)-th device allocation from now fail (after < 0 disarms)."""
+    _check(_lib.pic_inject_alloc_failure(after))
+
+
 PIC_NOALLOC_MAX_PARTICLES = 1048576
 _lib.pic_tile_sort_perm_noalloc.argtypes = [_VP, C.c_longlong, C.c_int, C.c_int * 3, C.c_int * 3, _VP, _VP, _VP]
 

@@ -129,3 +129,4 @@ def test_null_arguments_return_errors(P):
     assert lib.pic_set_antenna(None, 0, None) == P.PIC_ERR_INVALID_ARG
     assert lib.pic_renormalize_f32(None, None, C.c_longlong(5), None, None, None) == P.PIC_ERR_INVALID_ARG
     assert lib.pic_renormalize_f32(None, None, C.c_longlong(-1), None, None, None) == P.PIC_ERR_INVALID_ARG
+    assert lib.pic_measure_fp64_fma(C.c_longlong(0), 1, None, None, None) == P.PIC_ERR_INVALID_ARG
