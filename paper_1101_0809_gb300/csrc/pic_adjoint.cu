@@ -34,6 +34,11 @@ struct AdjArgs {
     R *lamB1[3];
     R *lamx[3];
     R *lamw[3];
+    // FP32 tiled form: largest |lambda| of a gathered field value seen by the
+    // previous launch (bits of a non-negative float; 0: none yet) and the word
+    // this launch records its own into
+    const unsigned *lam_prev;
+    unsigned *lam_cur;
 };
 
 template <typename R>
@@ -104,6 +109,7 @@ __device__ __forceinline__ void adj_wrap(AdjWrap &w, const RunDev &rn, int i, in
 // or from a work item's shared-memory tiles.
 template <typename R>
 struct AdjGlobalRd {
+    static constexpr bool kFixed = false;
     const R *E[3];
     const R *B[3];
     const R *LJ[3];
@@ -122,6 +128,7 @@ struct AdjGlobalRd {
 
 template <typename R>
 struct AdjSmemRd {
+    static constexpr bool kFixed = false;
     const R *E[3];
     const R *B[3];
     const R *LJ[3];
@@ -142,11 +149,86 @@ struct AdjSmemRd {
     }
 };
 
+// Six-component fixed-point accumulator for the adjoint's lambda_E and lambda_B
+// tiles (the FixedAcc split, components 0..5).
+struct FixedAcc6 {
+    int *hi[6];
+    int *lo[6];
+    int base, s1, s2;
+    __device__ __forceinline__ void add(int a, int dx, int dy, int dz, float kp, float t) const
+    {
+        const float magic = 12582912.0f;   // 1.5 * 2^23
+        const float th = fmaf(kp * (1.0f / 65536.0f), t, magic);   // magic + hi
+        const float ch = fmaf(th, -65536.0f, magic * 65537.0f);      // magic - hi * 2^16, exact
+        const float tl = fmaf(kp, t, ch);                            // magic + lo, one rounding
+        const int idx = base + dx + s1 * dy + s2 * dz;
+        atomicAdd(&hi[a][idx], __float_as_int(th) - (int)kFixBias);
+        atomicAdd(&lo[a][idx], __float_as_int(tl) - (int)kFixBias);
+    }
+};
+
+// FP32 tiles with the transposed gather in exact fixed point: the block's
+// lambda_E / lambda_B tiles are pairs of int32 words (FixedAcc), the scale a
+// power of two chosen from the largest |lambda| of the previous launch with a
+// margin, so that every contribution of a particle whose lambdas stay below
+// `bound` keeps within the fixed-point range.  A particle above it (the first
+// launch, or a sudden growth) scatters into the global arrays instead.
+struct AdjSmemRdFixed {
+    static constexpr bool kFixed = true;
+    const float *E[3];
+    const float *B[3];
+    const float *LJ[3];
+    FixedAcc6 acc;       // base set per particle to its field-tile cell
+    float kp;            // the fixed-point scale
+    float bound;         // largest |lambda| kept in the tiles
+    int fb, jb, s1, s2;
+    __device__ __forceinline__ float e(int c, int dx, int dy, int dz) const { return E[c][fb + dx + s1 * dy + s2 * dz]; }
+    __device__ __forceinline__ float b(int c, int dx, int dy, int dz) const { return B[c][fb + dx + s1 * dy + s2 * dz]; }
+    __device__ __forceinline__ float lj(int c, int dx, int dy, int dz) const
+    {
+        return LJ[c][jb + dx + s1 * dy + s2 * dz];
+    }
+    // fld 0: lambda_E (components 0..2 of the accumulator), 1: lambda_B (3..5)
+    __device__ __forceinline__ void scatter(int fld, int c, int dx, int dy, int dz, float v) const
+    {
+        acc.add(fld * 3 + c, dx, dy, dz, kp, v);
+    }
+};
+
+
 // Reverse of one particle's step: from lambda_x, lambda_w at level n+1 (index
 // L) to level n, adding the transposed gather into lambda_E and lambda_B1.
+// The transposed gather of one particle into the global lambda_E and
+// lambda_B1 arrays (the fixed-point tiles' fallback for a particle whose
+// lambdas exceed the tiles' bound): weights f, S per axis, old cell (i, j, k).
+template <int DIM, typename R>
+__device__ __noinline__ void adj_scatter_global(const AdjArgs<R> &a, const RunDev &rn, int i, int j, int k,
+                                                const R *f, const R *S, const R *lEp, const R *lBp)
+{
+    AdjWrap w;
+    adj_wrap<DIM>(w, rn, i, j, k);
+    for (int fld = 0; fld < 2; ++fld)
+        for (int c = 0; c < 3; ++c) {
+            const bool intx = (fld == 0) == (c == 0), inty = (fld == 0) == (c == 1), intz = (fld == 0) == (c == 2);
+            const int cx = intx ? 2 : 3, cy = inty ? 2 : 3, cz = DIM == 3 ? (intz ? 2 : 3) : 1;
+            const int ox = intx ? 0 : -1, oy = inty ? 0 : -1, oz = DIM == 3 ? (intz ? 0 : -1) : 0;
+            const R lam = fld == 0 ? lEp[c] : lBp[c];
+            R *dst = fld == 0 ? a.lamE[c] : a.lamB1[c];
+            for (int sz = 0; sz < cz; ++sz)
+                for (int sy = 0; sy < cy; ++sy)
+                    for (int sx = 0; sx < cx; ++sx) {
+                        const R vx = intx ? f[0 * 2 + sx] : S[0 * 3 + sx];
+                        const R vy = inty ? f[1 * 2 + sy] : S[1 * 3 + sy];
+                        const R vz = DIM == 3 ? (intz ? f[2 * 2 + sz] : S[2 * 3 + sz]) : R(1);
+                        atomicAdd(&dst[w.at(ox + sx, oy + sy, DIM == 3 ? oz + sz : 0)], vx * vy * vz * lam);
+                    }
+        }
+}
+
 template <int DIM, typename R, class Rd>
 __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev &gr, const RunDev &rn, long long p,
-                                             long long L, const Rd &rd)
+                                             long long L, const Rd &rd, int ci = 0, int cj = 0, int ck = 0,
+                                             float *lam_seen = nullptr)
 {
     constexpr bool F32 = sizeof(R) == 4;
     const R third = R(1) / R(3);
@@ -182,8 +264,7 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
                      F32 ? R(rn.cNf[2]) : R(rn.cN[2])};
     R w1[3] = {w0[0], w0[1], w0[2]};
     boris(w1, Ep, Bp, hq, c2);
-    const R g1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2] + c2);
-    const R ig = R(1) / g1;
+    const R ig = rsqrt_r(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2] + c2);   // as the forward kernels
     R n1[3] = {o[0], o[1], o[2]};
     int sh[3] = {0, 0, 0};
     #pragma unroll
@@ -349,6 +430,28 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
     }
     // ---- reverse of the gather: scatter into lamE, lamB1; derivatives of the
     // weights into lx0
+    bool big = false;   // (fixed-point tiles) the particle's lambdas exceed their bound
+    if constexpr (Rd::kFixed) {
+        float mx = 0.f;
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            big = big || !(fabsf(lEp[c]) <= rd.bound) || !(fabsf(lBp[c]) <= rd.bound);
+            mx = fmaxf(mx, fmaxf(fabsf(lEp[c]), fabsf(lBp[c])));
+        }
+        *lam_seen = fmaxf(*lam_seen, mx);
+        if (big) {
+            R fw[6], Sw[9];
+            #pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                fw[2 * ax] = f[ax][0];
+                fw[2 * ax + 1] = f[ax][1];
+                Sw[3 * ax] = S[ax][0];
+                Sw[3 * ax + 1] = S[ax][1];
+                Sw[3 * ax + 2] = S[ax][2];
+            }
+            adj_scatter_global<DIM, R>(a, rn, ci, cj, ck, fw, Sw, lEp, lBp);
+        }
+    }
     #pragma unroll
     for (int fld = 0; fld < 2; ++fld)
         #pragma unroll
@@ -368,7 +471,7 @@ __device__ __forceinline__ void adj_particle(const AdjArgs<R> &a, const GroupDev
                         const R vy = inty ? f[1][sy] : S[1][sy], ddy = inty ? df[1][sy] : dS[1][sy];
                         const R vz = DIM == 3 ? (intz ? f[2][sz] : S[2][sz]) : R(1);
                         const R ddz = DIM == 3 ? (intz ? df[2][sz] : dS[2][sz]) : R(0);
-                        rd.scatter(fld, c, dx, dy, dz, vx * vy * vz * lam);
+                        if (!big) rd.scatter(fld, c, dx, dy, dz, vx * vy * vz * lam);
                         const R fl = (fld == 0 ? rd.e(c, dx, dy, dz) : rd.b(c, dx, dy, dz)) * lam;
                         lx0[0] += ddx * vy * vz * fl;
                         lx0[1] += vx * ddy * vz * fl;
@@ -436,14 +539,16 @@ __global__ void __launch_bounds__(256) k_particles_adj(const AdjArgs<R> a)
 // with a halo of (halo + 2) cells in shared memory, in the particle kernels'
 // tile pitches, then takes every nsplit-th round of 256 particles of the item.
 // Reads come from the tiles; the transposed gather adds into the block's
-// lambda_E / lambda_B tiles (shared-memory float atomics, which run several
-// times faster here than global reductions to scattered addresses), flushed to
-// the global arrays once per block.  A particle that drifted past the tile's
-// halo takes the global-memory form.
+// lambda_E / lambda_B tiles, flushed to the global arrays once per block.  In
+// FP32 those tiles hold exact fixed-point sums (integer atomics, at a scale set
+// from the previous launch's largest lambda; AdjSmemRdFixed); in FP64 they are
+// float tiles.  A particle that drifted past the tile's halo takes the
+// global-memory form.
 template <int DIM, typename R>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_particles_adj_tiled(const AdjArgs<R> a, const WorkItem *items,
                                                                   const int *n_items, int halo, int nsplit)
 {
+    constexpr bool FIX = sizeof(R) == 4;
     const int item = blockIdx.x / nsplit, part = blockIdx.x - item * nsplit;
     if (item >= *n_items) return;
     const WorkItem it = items[item];
@@ -462,21 +567,37 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_particles_
     const int nf = P0 * P1 * fe2, nj = P0 * P1 * je2;
     const long long cb = rn.cell_base;
     R *sE[3], *sB[3], *sL[3], *sLE[3], *sLB[3];
+    int *sH[6], *sLo[6];   // FP32: hi and lo words of lambda_E (0..2) and lambda_B (3..5)
     {
+        // FP64: E, B1, lambda_E, lambda_B1 (12 tiles of nf), lambda_J (3 of nj);
+        // FP32: E, B1 (6 of nf), the int hi/lo words (12 of nf), lambda_J
         R *s = reinterpret_cast<R *>(g_smem);
+        int *q = reinterpret_cast<int *>(s + 6 * nf);
         for (int c = 0; c < 3; ++c) {
             sE[c] = s + c * nf;
             sB[c] = s + (3 + c) * nf;
             sLE[c] = s + (6 + c) * nf;
             sLB[c] = s + (9 + c) * nf;
-            sL[c] = s + 12 * nf + c * nj;
+            sL[c] = s + (FIX ? 18 : 12) * nf + c * nj;
+        }
+        for (int c = 0; c < 6; ++c) {
+            sH[c] = q + c * nf;
+            sLo[c] = q + (6 + c) * nf;
         }
     }
     for (int l = threadIdx.x; l < nf; l += blockDim.x) {
+        if constexpr (FIX) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            sLE[c][l] = R(0);
-            sLB[c][l] = R(0);
+            for (int c = 0; c < 6; ++c) {
+                sH[c][l] = 0;
+                sLo[c][l] = 0;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sLE[c][l] = R(0);
+                sLB[c][l] = R(0);
+            }
         }
         const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
         if (lx >= fe0 || ly >= fe1) continue;   // pitch padding
@@ -500,7 +621,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_particles_
 #pragma unroll
         for (int c = 0; c < 3; ++c) sL[c][l] = a.lamJ[c][gi];
     }
+    // FP32: the fixed-point scale, 2^(33 - ceil(log2 bound)) for lambdas up to
+    // bound = 256 x the previous launch's largest (a work item holds at most
+    // 8192 particles, so every word's sum stays within 2^46); none yet: every
+    // particle scatters into the global arrays
+    float bound = -1.f, kp = 1.f;
+    if (FIX) {
+        const float prev = __uint_as_float(*a.lam_prev);
+        if (prev > 0.f && prev < 1e30f) {
+            bound = 256.f * prev;
+            int e2 = 0;
+            frexpf(bound, &e2);   // bound <= 2^e2
+            kp = ldexpf(1.0f, 33 - e2);
+        }
+    }
     __syncthreads();
+    float lam_seen = 0.f;
     const long long step = (long long)nsplit * blockDim.x;
     for (long long p = it.begin + (long long)part * blockDim.x + threadIdx.x; p < it.end; p += step) {
         const long long L = gr.base + a.P.id[p];
@@ -512,25 +648,56 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_particles_
         const bool inr =
             li >= -G && li < T0 + G && lj >= -G && lj < T1 + G && (DIM == 2 || (lk >= -G && lk < T2 + G));
         if (inr) {
-            AdjSmemRd<R> rd;
-            for (int c = 0; c < 3; ++c) {
-                rd.E[c] = sE[c];
-                rd.B[c] = sB[c];
-                rd.LJ[c] = sL[c];
-                rd.LE[c] = sLE[c];
-                rd.LB[c] = sLB[c];
+            const int fb = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
+            const int jb = (li + G + 2) + P0 * ((lj + G + 2) + (DIM == 3 ? P1 * (lk + G + 2) : 0));
+            if constexpr (FIX) {
+                AdjSmemRdFixed rd;
+                for (int c = 0; c < 3; ++c) {
+                    rd.E[c] = reinterpret_cast<const float *>(sE[c]);
+                    rd.B[c] = reinterpret_cast<const float *>(sB[c]);
+                    rd.LJ[c] = reinterpret_cast<const float *>(sL[c]);
+                }
+                for (int c = 0; c < 6; ++c) {
+                    rd.acc.hi[c] = sH[c];
+                    rd.acc.lo[c] = sLo[c];
+                }
+                rd.acc.base = fb;
+                rd.acc.s1 = P0;
+                rd.acc.s2 = P0 * P1;
+                rd.kp = kp;
+                rd.bound = bound;
+                rd.s1 = P0;
+                rd.s2 = P0 * P1;
+                rd.fb = fb;
+                rd.jb = jb;
+                adj_particle<DIM, R>(a, gr, rn, p, L, rd, i, j, k, &lam_seen);
+            } else {
+                AdjSmemRd<R> rd;
+                for (int c = 0; c < 3; ++c) {
+                    rd.E[c] = sE[c];
+                    rd.B[c] = sB[c];
+                    rd.LJ[c] = sL[c];
+                    rd.LE[c] = sLE[c];
+                    rd.LB[c] = sLB[c];
+                }
+                rd.s1 = P0;
+                rd.s2 = P0 * P1;
+                rd.fb = fb;
+                rd.jb = jb;
+                adj_particle<DIM, R>(a, gr, rn, p, L, rd);
             }
-            rd.s1 = P0;
-            rd.s2 = P0 * P1;
-            rd.fb = (li + G + 1) + P0 * ((lj + G + 1) + (DIM == 3 ? P1 * (lk + G + 1) : 0));
-            rd.jb = (li + G + 2) + P0 * ((lj + G + 2) + (DIM == 3 ? P1 * (lk + G + 2) : 0));
-            adj_particle<DIM, R>(a, gr, rn, p, L, rd);
         } else {
             adj_particle_global_body<DIM, R>(a, gr, rn, p, L, i, j, k);
         }
     }
+    if (FIX) {   // the launch's largest lambda, for the next launch's scale
+        unsigned m = __float_as_uint(lam_seen);
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(a.lam_cur, m);
+    }
     // the block's lambda_E / lambda_B tiles into the global arrays
     __syncthreads();
+    const float inv = 1.0f / kp;
     for (int l = threadIdx.x; l < nf; l += blockDim.x) {
         const int lx = l % P0, r = l / P0, ly = r % P1, lz = r / P1;
         if (lx >= fe0 || ly >= fe1) continue;
@@ -540,9 +707,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_particles_
         const long long gi = cb + gx + (long long)nx * (gy + (long long)ny * gz);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const R ve = sLE[c][l], vb = sLB[c][l];
-            if (ve != R(0)) atomicAdd(&a.lamE[c][gi], ve);
-            if (vb != R(0)) atomicAdd(&a.lamB1[c][gi], vb);
+            if constexpr (FIX) {
+                const int he = sH[c][l], le = sLo[c][l], hb = sH[3 + c][l], lb = sLo[3 + c][l];
+                if ((he | le) != 0) atomicAdd(&a.lamE[c][gi], (R)(fmaf((float)he, 65536.0f, (float)le) * inv));
+                if ((hb | lb) != 0) atomicAdd(&a.lamB1[c][gi], (R)(fmaf((float)hb, 65536.0f, (float)lb) * inv));
+            } else {
+                const R ve = sLE[c][l], vb = sLB[c][l];
+                if (ve != R(0)) atomicAdd(&a.lamE[c][gi], ve);
+                if (vb != R(0)) atomicAdd(&a.lamB1[c][gi], vb);
+            }
         }
     }
 }
@@ -665,6 +838,8 @@ static cudaError_t adj_part_t(cudaStream_t st, const AdjLaunch &lc, const PoolBu
         a.lamx[c] = (R *)lamx[c];
         a.lamw[c] = (R *)lamw[c];
     }
+    a.lam_prev = lc.lam_prev;
+    a.lam_cur = lc.lam_cur;
     if (lc.total <= 0) return cudaSuccess;
     if (lc.items && lc.max_items > 0) {
         // blocks per work item: about 512 particles or more per block on average
@@ -689,7 +864,10 @@ size_t adjoint_smem_bytes(int dims, int prec, const int tile[3], int halo, const
     const size_t fe2 = dims == 3 ? (size_t)tile[2] + 2 * halo + 2 : 1;
     const size_t je2 = dims == 3 ? (size_t)tile[2] + 2 * halo + 4 : 1;
     const size_t plane = (size_t)pitch[0] * pitch[1];
-    return (12 * plane * fe2 + 3 * plane * je2) * (prec == 0 ? sizeof(double) : sizeof(float));
+    // FP64: E, B1, lambda_E, lambda_B1 (12 tiles) and lambda_J; FP32: E, B1,
+    // the hi and lo words of lambda_E and lambda_B1 (12 int tiles) and lambda_J
+    return prec == 0 ? (12 * plane * fe2 + 3 * plane * je2) * sizeof(double)
+                     : (18 * plane * fe2 + 3 * plane * je2) * sizeof(float);
 }
 
 cudaError_t adjoint_set_smem_limit(int dims, int prec, size_t bytes)

@@ -624,6 +624,7 @@ void destroy_grid(pic_grid *g)
         if (c == 0) dfree(g->d_gm);
         dfree(g->adj_lamJ[c]);
     }
+    dfree(g->adj_lam);
     graph_drop(g);
     prof_clear(g);
     for (auto e : g->prof_free) cudaEventDestroy(e);
@@ -1685,10 +1686,15 @@ int pic_step_saving(pic_grid *g, int nsteps, void *const *states)
 // ---- adjoint ---------------------------------------------------------------------
 static int adj_scratch(pic_grid *g)
 {
-    if (g->adj_B1[0]) return PIC_OK;
+    if (g->adj_B1[0] && g->adj_lam) return PIC_OK;
     for (int c = 0; c < 3; ++c) {
-        CK(dalloc_bytes(&g->adj_B1[c], g->total_cells * elem(g)), "adjoint scratch");
-        CK(dalloc_bytes(&g->adj_lamJ[c], g->total_cells * elem(g)), "adjoint scratch");
+        if (!g->adj_B1[c]) CK(dalloc_bytes(&g->adj_B1[c], g->total_cells * elem(g)), "adjoint scratch");
+        if (!g->adj_lamJ[c]) CK(dalloc_bytes(&g->adj_lamJ[c], g->total_cells * elem(g)), "adjoint scratch");
+    }
+    if (!g->adj_lam) {
+        CK(dalloc(&g->adj_lam, 2), "adjoint scratch");
+        CK(cudaMemsetAsync(g->adj_lam, 0, 2 * sizeof(unsigned), g->stream), "adjoint scratch");
+        g->adj_lam_cur = 0;
     }
     return PIC_OK;
 }
@@ -1753,9 +1759,16 @@ int pic_adjoint_step(pic_grid *g, void *lamE[3], void *lamB[3], void *lamx[3], v
     for (int a = 0; a < 3; ++a) lc.tile[a] = g->tile[a];
     lc.pitch[0] = g->pitch[0];
     lc.pitch[1] = g->pitch[1];
+    // the FP32 tiled form's lagged scale: the launch reads the largest lambda
+    // recorded by the previous one and records its own into the other word
+    unsigned *cur = g->adj_lam + g->adj_lam_cur;
+    lc.lam_prev = g->adj_lam + (1 - g->adj_lam_cur);
+    lc.lam_cur = cur;
+    CK(cudaMemsetAsync(cur, 0, sizeof(unsigned), g->stream), "adjoint scale");
     CK(launch_particles_adj(g->dims, g->prec, g->stream, lc, g->pool, g->E, g->adj_B1, g->adj_lamJ, lamE, lamB,
                             lamx, lamw),
        "adjoint particles");
+    if (lc.items) g->adj_lam_cur = 1 - g->adj_lam_cur;
     // (first B half step)^T: lamB becomes the adjoint of B^{n-1/2}, unchanged
     CK(launch_adj_yee(g->dims, g->prec, 1, g->stream, g->d_runs, nr, mc, lamE, lamB, nullptr),
        "adjoint B half step");

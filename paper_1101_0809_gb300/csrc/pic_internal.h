@@ -155,6 +155,8 @@ struct AdjLaunch {
     int halo;
     int tile[3];
     int pitch[2];
+    const unsigned *lam_prev = nullptr;   // FP32 tiled form: previous launch's largest |lambda| (float bits)
+    unsigned *lam_cur = nullptr;          // this launch's
 };
 cudaError_t launch_particles_adj(int dims, int prec, cudaStream_t st, const AdjLaunch &lc, const PoolBuf &P,
                                  void *const E[3], void *const B1[3], void *const lamJ[3], void *const lamE[3],
@@ -260,6 +262,8 @@ struct pic_grid {
     // adjoint scratch: B^n, lamJ (field-sized, allocated on first use)
     void *adj_B1[3] = {nullptr, nullptr, nullptr};
     void *adj_lamJ[3] = {nullptr, nullptr, nullptr};
+    unsigned *adj_lam = nullptr;     // two words: largest |lambda| of the last tiled adjoint launches (FP32)
+    int adj_lam_cur = 0;             // which of them the next launch records into
 
     // staging for host-pointer particle loads (grown, never shrunk)
     double *stage = nullptr;

@@ -80,6 +80,72 @@ def test_adjoint_step_matches_oracle(env, which, tiled):
 
 
 @pytest.mark.parametrize("which", ["2d", "3d"])
+def test_fp32_tiled_adjoint_fixed_point_tiles_match_oracle(env, which):
+    """The FP32 tiled adjoint sums the transposed gather in fixed-point tiles at
+    a scale set from the previous launch's largest lambda; the first launch has
+    no such scale and scatters into the global arrays.  Both launches, on the
+    same FP32 state and adjoint inputs, against the oracle's FP64 adjoint of that
+    state (FP32 tolerance), and against each other."""
+    P, torch = env
+    if which == "2d":
+        wl = W.c4_perturbed2d(n=32, ppc=8, steps=3)
+        tile = (8, 8, 1)
+    else:
+        wl = W.thermal_plasma("3D small", 3, (20, 18, 22), 2, 0.1, 3, W.SEED_BASE + 11, ions=1836.0,
+                              tile=(8, 4, 4), dt_courant=0.45)
+        tile = (8, 4, 4)
+    desc = P.make_desc(wl.dims, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP32, tile=tile, rho_bg=wl.rho_bg)
+    grid = P.Grid(desc)
+    P.pic_set_adjoint_tiled(grid.h, True)
+    for s, o in enumerate(wl.species):
+        grid.load(s, o.q, o.m, o.weight, o.x, o.w)
+    P.pic_step(grid.h, 3)
+    P.pic_sync(grid.h)
+    g = oracle_grid(wl)
+    E, B, _ = grid.get_fields()
+    E = [np.asarray(a, np.float64) for a in E]
+    B = [np.asarray(a, np.float64) for a in B]
+    sp = []
+    for s, o in enumerate(wl.species):
+        cell, off, w, ident = grid.particles(s)
+        order = np.argsort(ident)
+        x = positions_from_gpu(wl, cell[order], [a[order] for a in off])
+        sp.append(O.Species(o.q, o.m, o.weight, x, np.array([a[order] for a in w], dtype=np.float64)))
+    rng = np.random.default_rng(79)
+    lamE = [rng.normal(size=g.shape).astype(np.float32).astype(np.float64) for _ in range(3)]
+    lamB = [rng.normal(size=g.shape).astype(np.float32).astype(np.float64) for _ in range(3)]
+    lx = [rng.normal(size=(3, o.x.shape[1])).astype(np.float32).astype(np.float64) for o in sp]
+    lw = [rng.normal(size=(3, o.x.shape[1])).astype(np.float32).astype(np.float64) for o in sp]
+    if wl.dims == 2:
+        for a in lx:
+            a[2] = 0.0
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.float32)).cuda()
+    got = []
+    for launch in range(2):
+        gE = [dev(a) for a in lamE]
+        gB = [dev(a) for a in lamB]
+        gx = [dev(np.concatenate([a[c] for a in lx])) for c in range(3)]
+        gw = [dev(np.concatenate([a[c] for a in lw])) for c in range(3)]
+        torch.cuda.synchronize()
+        P.pic_adjoint_step(grid.h, gE, gB, gx, gw)
+        torch.cuda.synchronize()
+        got.append([[t.cpu().numpy().astype(np.float64) for t in v] for v in (gE, gB, gx, gw)])
+    O.step_adj(g, E, B, sp, lamE, lamB, lx, lw)
+    want = (lamE, lamB, [np.concatenate([v[a] for v in lx]) for a in range(3)],
+            [np.concatenate([v[a] for v in lw]) for a in range(3)])
+    for launch in range(2):
+        for name, gv, wv in zip(("lamE", "lamB", "lamx", "lamw"), got[launch], want):
+            for a in range(3):
+                if name == "lamx" and a >= wl.dims:
+                    continue
+                close(gv[a], wv[a], 1e-4, f"launch {launch} {name}[{a}]")
+    for name, g0, g1 in zip(("lamE", "lamB", "lamx", "lamw"), got[0], got[1]):
+        for a in range(3):
+            close(g1[a], g0[a], 2e-5, f"fixed-point tiles vs global scatter {name}[{a}]")
+    grid.close()
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
 def test_tiled_adjoint_with_particles_past_their_tiles(env, which):
     """Halo 0 and no sort for 4 steps: every particle that left its tile since
     the load takes the global-memory form inside the tiled kernel.  Both forms
