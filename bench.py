@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-vecpot", action="store_true", help="skip the vector-potential (generalized momentum) leg")
     ap.add_argument("--laser-warmup", type=int, default=480)
     ap.add_argument("--no-gauss", action="store_true", help="skip the 200-step full-size Gauss residual")
+    ap.add_argument("--cell-lanes", action="store_true",
+                    help="run the main grids in the cell-lane particle order (PIC_SORT_CELL_LANES)")
+    ap.add_argument("--sort-interval", type=int, default=0, help="override the main workload's sort interval")
     return ap.parse_args()
 
 
@@ -263,10 +266,13 @@ def ncu_traffic_per_particle(precision):
     return ncu_per_particle(precision, "dram_bytes_per_particle")
 
 
-def build_grid(P, wl, precision, stream):
+SORT_ORDER = 0   # PIC_SORT_AUTO; --cell-lanes selects PIC_SORT_CELL_LANES for the main grids
+
+
+def build_grid(P, wl, precision, stream, sort_interval=None):
     desc = P.make_desc(wl.dims, wl.n, wl.d, wl.dt, wl.c, precision, tile=wl.tile, halo=1,
-                       sort_interval=wl.sort_interval, particles_per_block=8192, rho_bg=wl.rho_bg,
-                       stream=stream)
+                       sort_interval=sort_interval or wl.sort_interval, particles_per_block=8192,
+                       rho_bg=wl.rho_bg, stream=stream, sort_order=SORT_ORDER)
     grid = P.Grid(desc)
     for s, sp in enumerate(wl.species):
         grid.load(s, sp.q, sp.m, sp.weight, sp.x, sp.w)
@@ -893,7 +899,12 @@ def our_arm(args):
     from paper_1101_0809_gb300 import pic as P
     from paper_1101_0809_gb300 import workloads as W
 
+    global SORT_ORDER
+    if args.cell_lanes:
+        SORT_ORDER = P.PIC_SORT_CELL_LANES
     wl = W.c1_thermal3d(n=args.n, ppc=args.ppc, steps=args.steps)
+    if args.sort_interval > 0:
+        wl.sort_interval = args.sort_interval
     npart = wl.n_particles
     ncell = wl.n_cells
     stream = torch.cuda.current_stream().cuda_stream
