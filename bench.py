@@ -36,7 +36,7 @@ WORKLOAD = ("3D3V 128^3 periodic, e- and ions (m_i/m_e = 1836), 32+32 per cell, 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=24, help="timed steps (24: three whole sort intervals)")
+    ap.add_argument("--steps", type=int, default=48, help="timed steps (48: six whole sort intervals)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
@@ -195,7 +195,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -205,6 +205,15 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first(self, timeout=5.0):
+        """Block until nvidia-smi has printed its first sample (it takes a
+        fraction of a second to start); the samples before the timed region
+        begins are then left out."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+        self.first = len(self.lines)
 
     def stop(self):
         if not self.proc:
@@ -217,7 +226,8 @@ class ClockSampler:
         self.th.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        timed = self.lines[getattr(self, "first", 0):]
+        for ln in timed or self.lines[-1:]:
             f = [v.strip() for v in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -288,6 +298,7 @@ def timed_steps(P, torch, grid, steps, dist=None, sampler=None):
     P.pic_profile(grid.h, True)
     if sampler:
         sampler.start()
+        sampler.wait_first()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)

@@ -187,6 +187,7 @@ cudaError_t alloc_pool(pic_grid *g, PoolBuf &P, long long n)
 {
     P = PoolBuf();
     cudaError_t e;
+    n = (n + 3) & ~3LL;   // whole 16-byte groups: the re-sort copies segments rounded out to them
     if ((e = dalloc(&P.cell, n)) != cudaSuccess) return e;
     if ((e = dalloc(&P.id, n)) != cudaSuccess) return e;
     for (int c = 0; c < 3; ++c) {
@@ -204,7 +205,11 @@ void free_sort(pic_grid *g)
     }
     dfree(g->sort.hist);
     dfree(g->sort.block_sums);
+    for (int c = 0; c < 5; ++c) dfree(g->sort.tcnt[c]);
+    dfree(g->sort.m_total);
+    dfree(g->sort.cls);
     g->sort = SortScratch();
+    g->tiles_valid = false;
     dfree(g->tile_start);
     dfree(g->item_scan);
     dfree(g->items);
@@ -292,6 +297,9 @@ int size_particle_buffers(pic_grid *g, long long total)
     }
     CK(dalloc(&g->sort.hist, hist), "sort histogram");
     CK(dalloc(&g->sort.block_sums, sums), "scan sums");
+    for (int c = 0; c < 5; ++c) CK(dalloc(&g->sort.tcnt[c], (size_t)g->total_tiles + 1), "re-sort counts");
+    CK(dalloc(&g->sort.m_total, 2), "re-sort mover count");   // movers, then their histogram length
+    CK(dalloc(&g->sort.cls, (std::max(1LL, total) + 3) & ~3LL), "re-sort classes");   // whole 4-byte words
     g->sort.capacity = total;
     g->sort.hist_capacity = hist;
     g->sort.sums_capacity = sums;
@@ -311,6 +319,7 @@ int size_particle_buffers(pic_grid *g, long long total)
 
 int upload_groups(pic_grid *g)
 {
+    g->tiles_valid = false;   // the next sort starts from the keys alone
     dfree(g->d_groups);
     dfree(g->d_group_base);
     g->d_groups = nullptr;
@@ -395,9 +404,12 @@ int do_sort(pic_grid *g)
                                          g->halo + (g->order2 == 5 ? 1 : 0),   // the current tile's bank base
                                          g->sort_order == PIC_SORT_BANKED ? 1 : 0, g->order2 == 5 ? 1 : 0, &nl,
                                          g->sort_order == PIC_SORT_CELL_LANES ? g->lane_cell : nullptr,
-                                         g->sort_order == PIC_SORT_CELL_LANES ? g->lane_count : nullptr);
+                                         g->sort_order == PIC_SORT_CELL_LANES ? g->lane_count : nullptr,
+                                         g->tiles_valid && g->sort_order != PIC_SORT_CELL_LANES ? 1 : 0);
     launch_count_add(g, nl);
+    g->tiles_valid = false;
     if (e != cudaSuccess) return cuda_fail(e, "tile sort");
+    g->tiles_valid = true;
     if (g->total > 0 && !g->groups.empty()) std::swap(g->pool, g->pool_alt);
     if (!g->capturing) graph_drop(g);   // a captured graph assumes its own buffer parity
     g->steps_since_sort = 0;
@@ -1625,6 +1637,7 @@ static int restore_body(pic_grid *g, const void *src, int on_device, const State
     }
     g->steps_since_sort = h.steps_since_sort;
     g->have_old = false;
+    g->tiles_valid = g->total > 0 && !g->groups.empty();   // the saved segments describe the saved pool
     if (!g->capturing) graph_drop(g);
     for (auto &r : g->have_ref) r = 0;
     return PIC_OK;

@@ -76,6 +76,9 @@ struct SortScratch {
     unsigned *vals[2] = {nullptr, nullptr};
     unsigned *hist = nullptr;      // 256 * max_chunks
     unsigned *block_sums = nullptr;
+    unsigned *tcnt[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // re-sort: per-tile counts (total_tiles + 1 each)
+    unsigned *m_total = nullptr;                       // re-sort: number of movers, histogram length
+    unsigned char *cls = nullptr;                      // re-sort: class of every particle (capacity)
     long long capacity = 0;
     long long hist_capacity = 0;
     long long sums_capacity = 0;
@@ -86,11 +89,14 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
                                  int particles_per_item, int halo, int banked, int half, int *launches,
-                                 unsigned char *lane_cell = nullptr, int *lane_count = nullptr);
+                                 unsigned char *lane_cell = nullptr, int *lane_count = nullptr, int resort = 0);
 // With lane_cell and lane_count (total_tiles * 128 entries each) the order
 // inside a tile is the cell-lane order (PIC_SORT_CELL_LANES) instead of the
 // banked or stable one, and the two tables receive every tile's lane cells
-// and counts.
+// and counts.  With resort (banked or stable order only), tile_start on entry
+// holds the segments of the previous sort of this same pool and group layout,
+// and only the particles whose tile changed are sorted globally; the result is
+// the same.
 
 // The FP32 fused step over the cell-lane order (pic_particles_cl.cu): 3D,
 // l_a = 1 1/2, 8x4x4 tiles with halo 1; one block of 128
@@ -213,6 +219,7 @@ struct pic_grid {
     int *lane_count = nullptr;            // ... and its particle count (total_tiles * 128 each)
     int *drift = nullptr;                 // cell-lane kernel: drift lists, pool-sized
     long long *tile_start = nullptr;
+    bool tiles_valid = false;       // tile_start holds the segments of the last sort of the current pool
     unsigned *item_scan = nullptr;
     pic::WorkItem *items = nullptr;
     long long *d_ant_n = nullptr;   // antenna clock per run (device)
