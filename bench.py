@@ -36,7 +36,7 @@ WORKLOAD = ("3D3V 128^3 periodic, e- and ions (m_i/m_e = 1836), 32+32 per cell, 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=48, help="timed steps (48: six whole sort intervals)")
+    ap.add_argument("--steps", type=int, default=48, help="timed steps (48: eight whole sort intervals of 6 steps)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="cells per axis")

@@ -984,25 +984,9 @@ __global__ void __launch_bounds__(kSortThreads) k_resort_order(const long long *
     }
 }
 
-// Permute every particle array: dst[o] = src[perm[o]].
-template <typename R, int DIM>
-__global__ void k_permute(long long n, const unsigned *perm, Pool<R> src, Pool<R> dst)
-{
-    const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (o >= n) return;
-    const unsigned s = perm[o];
-    dst.cell[o] = src.cell[s];
-    dst.off[0][o] = src.off[0][s];
-    dst.off[1][o] = src.off[1][s];
-    if (DIM == 3) dst.off[2][o] = src.off[2][s];
-    dst.w[0][o] = src.w[0][s];
-    dst.w[1][o] = src.w[1][s];
-    dst.w[2][o] = src.w[2][s];
-    dst.id[o] = src.id[s];
-}
-
-// The same, four slots per thread: one 16-byte read of perm, four gathers per
-// array in flight together, 16-byte writes.
+// Permute every particle array, dst[o] = src[perm[o]], four slots per thread:
+// one 16-byte read of perm, four gathers per array in flight together, 16-byte
+// writes.
 template <typename T>
 __device__ __forceinline__ void gather4(const T *__restrict__ src, T *__restrict__ dst, long long o, uint4 p)
 {
@@ -1267,31 +1251,9 @@ static cudaError_t permute_and_build(int prec, int dims, cudaStream_t st, long l
                                      unsigned *item_scan, WorkItem *items, int *n_items, int particles_per_item,
                                      int *launches)
 {
-    cudaError_t e;
-    const int nt = 256;
-    const unsigned nbp = (unsigned)((total + nt - 1) / nt);
-    if (prec == 0) {
-        Pool<double> s, d;
-        s.cell = src.cell; s.id = src.id; d.cell = dst.cell; d.id = dst.id;
-        for (int c = 0; c < 3; ++c) {
-            s.off[c] = (double *)src.off[c]; s.w[c] = (double *)src.w[c];
-            d.off[c] = (double *)dst.off[c]; d.w[c] = (double *)dst.w[c];
-        }
-        if (dims == 3) k_permute<double, 3><<<nbp, nt, 0, st>>>(total, perm, s, d);
-        else k_permute<double, 2><<<nbp, nt, 0, st>>>(total, perm, s, d);
-    } else {
-        Pool<float> s, d;
-        s.cell = src.cell; s.id = src.id; d.cell = dst.cell; d.id = dst.id;
-        for (int c = 0; c < 3; ++c) {
-            s.off[c] = (float *)src.off[c]; s.w[c] = (float *)src.w[c];
-            d.off[c] = (float *)dst.off[c]; d.w[c] = (float *)dst.w[c];
-        }
-        if (dims == 3) k_permute<float, 3><<<nbp, nt, 0, st>>>(total, perm, s, d);
-        else k_permute<float, 2><<<nbp, nt, 0, st>>>(total, perm, s, d);
-    }
+    cudaError_t e = launch_permute4(prec, dims, st, total, src, dst, perm);
     *launches += 1;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-
+    if (e != cudaSuccess) return e;
     return build_items(st, tile_start, total_tiles, particles_per_item, groups, ngroups, scr, item_scan, items, n_items,
                        launches);
 }

@@ -112,7 +112,7 @@ def c0_small2d(steps=50):
                           SEED_BASE + 0, tile=(8, 8, 1))
 
 
-def c1_thermal3d(n=128, ppc=32, steps=200, fraction=1.0, tile=(8, 4, 4), sort_interval=8):
+def c1_thermal3d(n=128, ppc=32, steps=200, fraction=1.0, tile=(8, 4, 4), sort_interval=6):
     """3D3V periodic n^3, electrons and ions (mass ratio 1836) ppc each, v_th,e = 0.1c,
     dt = 0.45 dx/c.  At n = 128, ppc = 32 this is 134,217,728 particles.  The
     particles are re-sorted every 8 steps: over longer intervals more of the
