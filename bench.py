@@ -804,6 +804,10 @@ def summary_line(value, ms_step, roof, gauss, fp64, batched, adjoint, laser, ord
     peak; *_rel are relative differences against the FP64 method."""
     s = {"fp32": _g(value), "fp32_ms_step": _g(ms_step), "fp32_kernel_ms": _g(roof["avg_launch_ms"]),
          "fp32_hbm_frac": _g(roof["frac"]), "sort_share": _g(roof["step_share"].get("sort"))}
+    if "issue" in roof:
+        s["fp32_issue_frac"] = _g(roof["issue"]["frac"])
+    if "shared_pipe" in roof:
+        s["fp32_shared_pipe_frac"] = _g(roof["shared_pipe"]["frac"])
     if gauss:
         s["gauss_fp32_200_steps_rel"] = _g(gauss["gauss_resid_max_rel"])
     if fp64:
@@ -966,6 +970,18 @@ def our_arm(args):
         roof["issue"] = {"achieved": issue_ach, "peak": issue_peak, "unit": "warp instructions/s",
                          "frac": issue_ach / issue_peak, "warp_instructions_per_particle": ipp,
                          "peak_source": f"4 per SM per clock x {sms} SMs x {sm_mhz:.0f} MHz (sampled)"}
+    # and the shared-memory data pipe (the gather's loads and the deposit's
+    # atomics): shared wavefronts per particle from the same profile, against one
+    # wavefront per SM per clock; `ideal` counts them without bank conflicts
+    wpp = ncu_per_particle("fp32", "shared_wavefronts_per_particle")
+    wpp_ideal = ncu_per_particle("fp32", "shared_wavefronts_ideal_per_particle")
+    if wpp:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        sh_peak = 1.0 * sms * sm_mhz * 1e6
+        sh_ach = wpp * npart / (pk_ms / pk_n * 1e-3)
+        roof["shared_pipe"] = {"achieved": sh_ach, "peak": sh_peak, "unit": "wavefronts/s", "frac": sh_ach / sh_peak,
+                               "wavefronts_per_particle": wpp, "ideal_wavefronts_per_particle": wpp_ideal,
+                               "peak_source": f"1 per SM per clock x {sms} SMs x {sm_mhz:.0f} MHz (sampled)"}
 
     # ---- end to end through the public API with host buffers ---------------------------
     # Each step uploads its whole input state from pinned host memory and reads
