@@ -389,8 +389,24 @@ int upload_groups(pic_grid *g)
     return PIC_OK;
 }
 
-int do_sort(pic_grid *g)
+// Applies a sort that pic_step left pending (the arrays in the old order and
+// the permutation in the sort scratch): used when no fused particle launch
+// follows to apply it.
+static int settle(pic_grid *g)
 {
+    if (!g->pending_perm) return PIC_OK;
+    cudaError_t e = launch_permute(g->prec, g->dims, g->stream, g->total, g->pool, g->pool_alt, g->pending_perm);
+    launch_count_add(g, 1);
+    g->pending_perm = nullptr;
+    if (e != cudaSuccess) return cuda_fail(e, "permutation");
+    std::swap(g->pool, g->pool_alt);
+    return PIC_OK;
+}
+
+int do_sort(pic_grid *g, bool defer = false)
+{
+    int rc = settle(g);
+    if (rc != PIC_OK) return rc;
     if (g->total <= 0 || g->groups.empty() || !g->tile_start) {   // nothing to sort
         g->steps_since_sort = 0;
         g->have_old = false;
@@ -398,6 +414,7 @@ int do_sort(pic_grid *g)
     }
     ProfScope ps(g, PIC_PROF_SORT);
     int nl = 0;
+    const unsigned *perm = nullptr;
     cudaError_t e = sort_and_build_items(g->prec, g->dims, g->stream, g->total, g->pool, g->pool_alt, g->d_groups,
                                          g->d_group_base, (int)g->groups.size(), g->d_runs, g->total_tiles, g->sort,
                                          g->tile_start, g->item_scan, g->items, g->n_items, g->ppi,
@@ -405,12 +422,14 @@ int do_sort(pic_grid *g)
                                          g->sort_order == PIC_SORT_BANKED ? 1 : 0, g->order2 == 5 ? 1 : 0, &nl,
                                          g->sort_order == PIC_SORT_CELL_LANES ? g->lane_cell : nullptr,
                                          g->sort_order == PIC_SORT_CELL_LANES ? g->lane_count : nullptr,
-                                         g->tiles_valid && g->sort_order != PIC_SORT_CELL_LANES ? 1 : 0);
+                                         g->tiles_valid && g->sort_order != PIC_SORT_CELL_LANES ? 1 : 0,
+                                         defer ? &perm : nullptr);
     launch_count_add(g, nl);
     g->tiles_valid = false;
     if (e != cudaSuccess) return cuda_fail(e, "tile sort");
     g->tiles_valid = true;
-    if (g->total > 0 && !g->groups.empty()) std::swap(g->pool, g->pool_alt);
+    if (perm) g->pending_perm = perm;   // the next fused particle launch moves the arrays
+    else if (g->total > 0 && !g->groups.empty()) std::swap(g->pool, g->pool_alt);
     if (!g->capturing) graph_drop(g);   // a captured graph assumes its own buffer parity
     g->steps_since_sort = 0;
     g->have_old = false;
@@ -436,11 +455,21 @@ int launch_part(pic_grid *g, int mode)
         if (e != cudaSuccess) return cuda_fail(e, "particle kernel");
         return PIC_OK;
     }
+    if (g->pending_perm && (mode != 0 || g->order2 != 3)) {
+        const int rc = settle(g);
+        if (rc != PIC_OK) return rc;
+    }
+    const unsigned *perm = g->pending_perm;
+    // after a deferred sort: read the old order through the permutation, write the new one
     cudaError_t e = launch_particles(g->dims, g->prec, mode, g->stream, g->items, g->n_items, g->max_items, g->d_runs,
-                                     g->d_groups, g->pool, g->E, g->B, g->J, g->old_cell, g->old_off, g->halo,
-                                     g->tile[0], g->tile[1], g->tile[2], g->d_err, g->pitch[0], g->pitch[1],
-                                     g->order2);
+                                     g->d_groups, perm ? g->pool_alt : g->pool, g->E, g->B, g->J, g->old_cell,
+                                     g->old_off, g->halo, g->tile[0], g->tile[1], g->tile[2], g->d_err, g->pitch[0],
+                                     g->pitch[1], g->order2, perm ? &g->pool : nullptr, perm);
     launch_count_add(g, g->max_items > 0 ? 1 : 0);
+    if (perm) {
+        g->pending_perm = nullptr;
+        std::swap(g->pool, g->pool_alt);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "particle kernel");
     return PIC_OK;
 }
@@ -1217,14 +1246,21 @@ int pic_step(pic_grid *g, int nsteps)
         }
         if (g->steps_since_sort >= limit || g->sort_due) {
             if (measure) CK(cudaEventRecord(g->ad_ev[2], g->stream), "sort policy events");
-            if ((rc = do_sort(g)) != PIC_OK) return rc;
+            // the arrays move inside this step's particle launch, unless the sort
+            // policy times the sort or another kernel (cell lanes, l_a = 2 1/2,
+            // Eq. wrong1) takes the step
+            const bool defer = !measure && g->order2 == 3 && !uses_cell_lanes(g) && g->total > 0;
+            if ((rc = do_sort(g, defer)) != PIC_OK) return rc;
             if (measure) CK(cudaEventRecord(g->ad_ev[3], g->stream), "sort policy events");
             timed_sort = measure;
         }
         const bool sorted = g->steps_since_sort == 0;
         g->sort_due = false;
         if (measure) CK(cudaMemsetAsync(g->d_err + 1, 0, sizeof(int), g->stream), "drift count");
-        if ((rc = launch_fields(g, PIC_B_HALF, 1)) != PIC_OK) return rc;
+        if ((rc = launch_fields(g, PIC_B_HALF, 1)) != PIC_OK) {
+            settle(g);
+            return rc;
+        }
         if (measure) CK(cudaEventRecord(g->ad_ev[0], g->stream), "sort policy events");
         if (g->total > 0 && (rc = launch_part(g, 0)) != PIC_OK) return rc;
         if (measure) CK(cudaEventRecord(g->ad_ev[1], g->stream), "sort policy events");

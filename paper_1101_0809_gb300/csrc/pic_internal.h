@@ -42,7 +42,11 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
                              const int *n_items, int max_items, const RunDev *runs, const GroupDev *groups,
                              const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
                              int *old_cell, void *const old_off[3], int halo, int max_tile_x,
-                             int max_tile_y, int max_tile_z, int *err, int p0, int p1, int order2 = 3);
+                             int max_tile_y, int max_tile_z, int *err, int p0, int p1, int order2 = 3,
+                             const PoolBuf *src = nullptr, const unsigned *perm = nullptr);
+// With perm (mode 0, l_a = 1 1/2): the pool was just sorted but not yet
+// permuted; particle p of the new order is read from src at perm[p] and
+// written, stepped, to P.
 // order2 = 3: l_a = 1 1/2; 5: l_a = 2 1/2 (tiles one cell wider on every side).
 size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz, int halo, int p0, int p1,
                             int order2 = 3);
@@ -89,14 +93,19 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
                                  int particles_per_item, int halo, int banked, int half, int *launches,
-                                 unsigned char *lane_cell = nullptr, int *lane_count = nullptr, int resort = 0);
+                                 unsigned char *lane_cell = nullptr, int *lane_count = nullptr, int resort = 0,
+                                 const unsigned **perm_out = nullptr);
 // With lane_cell and lane_count (total_tiles * 128 entries each) the order
 // inside a tile is the cell-lane order (PIC_SORT_CELL_LANES) instead of the
 // banked or stable one, and the two tables receive every tile's lane cells
 // and counts.  With resort (banked or stable order only), tile_start on entry
 // holds the segments of the previous sort of this same pool and group layout,
 // and only the particles whose tile changed are sorted globally; the result is
-// the same.
+// the same.  With perm_out (not for the cell-lane order) the particle arrays
+// are not moved: *perm_out receives the permutation (dst[o] = src[perm[o]], in
+// the sort scratch, valid until the next sort) for the caller to apply.
+cudaError_t launch_permute(int prec, int dims, cudaStream_t st, long long total, const PoolBuf &src,
+                           const PoolBuf &dst, const unsigned *perm);
 
 // The FP32 fused step over the cell-lane order (pic_particles_cl.cu): 3D,
 // l_a = 1 1/2, 8x4x4 tiles with halo 1; one block of 128
@@ -220,6 +229,7 @@ struct pic_grid {
     int *drift = nullptr;                 // cell-lane kernel: drift lists, pool-sized
     long long *tile_start = nullptr;
     bool tiles_valid = false;       // tile_start holds the segments of the last sort of the current pool
+    const unsigned *pending_perm = nullptr;   // sorted, not yet permuted: pool holds the old order (pic_step only)
     unsigned *item_scan = nullptr;
     pic::WorkItem *items = nullptr;
     long long *d_ant_n = nullptr;   // antenna clock per run (device)

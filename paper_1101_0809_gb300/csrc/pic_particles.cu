@@ -37,7 +37,7 @@ static cudaError_t set_limit_t(int mode, size_t bytes)
 {
     const int b = (int)bytes;
     switch (mode) {
-    case 0: return cudaFuncSetAttribute(k_particles<DIM, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 0: return set_limit_fused<DIM, R, GeoDyn>(b);
     case 1: return cudaFuncSetAttribute(k_particles<DIM, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     default: return cudaFuncSetAttribute(k_particles<DIM, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     }
@@ -60,8 +60,10 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
                              const int *n_items, int max_items, const RunDev *runs, const GroupDev *groups,
                              const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3],
                              int *old_cell, void *const old_off[3], int halo, int max_tile_x, int max_tile_y,
-                             int max_tile_z, int *err, int p0, int p1, int order2)
+                             int max_tile_z, int *err, int p0, int p1, int order2, const PoolBuf *src,
+                             const unsigned *perm)
 {
+    if (perm && (mode != 0 || order2 != 3)) return cudaErrorInvalidValue;   // read through perm: fused l_a = 1 1/2 only
     const size_t smem =
         particles_smem_bytes(dims, prec, mode, max_tile_x, max_tile_y, max_tile_z, halo, p0, p1, order2);
     if (order2 == 5) {
@@ -73,11 +75,11 @@ cudaError_t launch_particles(int dims, int prec, int mode, cudaStream_t st, cons
         return launch_particles_w1(dims, prec, mode, st, max_items, smem, items, n_items, runs, groups, P, E, B, J,
                                    old_cell, old_off, halo, err);
     if (prec == 0) {
-        auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
+        auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err, src, perm);
         return dims == 3 ? launch_mode<3, double>(mode, st, max_items, smem, a)
                          : launch_mode<2, double>(mode, st, max_items, smem, a);
     }
-    auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err);
+    auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, old_cell, old_off, halo, err, src, perm);
     if (mode == 0) {
         const int tile[3] = {max_tile_x, max_tile_y, max_tile_z};
         cudaError_t e = cudaSuccess;

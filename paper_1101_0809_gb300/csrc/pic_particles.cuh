@@ -29,6 +29,10 @@ struct PartArgs {
     const RunDev *runs;
     const GroupDev *groups;
     Pool<R> P;
+    // MODE 0 right after a sort: the particles are read from S, particle p of
+    // the new order at S[perm[p]], and written to P; otherwise S = P, perm null
+    Pool<R> S;
+    const unsigned *perm;
     Fields<R> F;
     int *old_cell;
     R *old_off[3];
@@ -161,9 +165,12 @@ __device__ __noinline__ void gather_global_w1(const Fields<R> &F, long long cb, 
 // stencil only).  ORD = 4 is the comparison scheme of Eq. wrong1: its gather
 // reaches the integer points -1..2 (field tile halo (halo + 2)); its charge and
 // current are those of l_a = 1 1/2.
-template <int DIM, typename R, int MODE, class GEO, int ORD = 3>
+template <int DIM, typename R, int MODE, class GEO, int ORD = 3, bool PERM = false>
 __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
 {
+    // MODE 0 right after a sort whose arrays have not moved: the state comes
+    // from a.S through a.perm, and the stepped particle goes to its new slot
+    constexpr bool RP = PERM && MODE == 0;
     constexpr bool FIX = sizeof(R) == 4;
     const WorkItem it = a.items[item];
     const GroupDev gr = a.groups[it.group];
@@ -360,16 +367,19 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         int s0 = 0, s1 = 0, s2 = 0;
         if (valid) {
             // ---- the particle's state at x^n (old) -------------------------------
-            const int cell0 = MODE == 2 ? a.old_cell[p] : a.P.cell[p];
-            o0 = MODE == 2 ? a.old_off[0][p] : a.P.off[0][p];
-            o1 = MODE == 2 ? a.old_off[1][p] : a.P.off[1][p];
-            o2 = DIM == 3 ? (MODE == 2 ? a.old_off[2][p] : a.P.off[2][p]) : R(0);
+            const long long sp = RP ? (long long)a.perm[p] : p;   // where the state is read
+            const Pool<R> &src = RP ? a.S : a.P;
+            const int cell0 = MODE == 2 ? a.old_cell[p] : src.cell[sp];
+            o0 = MODE == 2 ? a.old_off[0][p] : src.off[0][sp];
+            o1 = MODE == 2 ? a.old_off[1][p] : src.off[1][sp];
+            o2 = DIM == 3 ? (MODE == 2 ? a.old_off[2][p] : src.off[2][sp]) : R(0);
             R w[3] = {R(0), R(0), R(0)};
             if (MODE != 2 || DIM == 2) {
-                w[0] = a.P.w[0][p];
-                w[1] = a.P.w[1][p];
-                w[2] = a.P.w[2][p];
+                w[0] = src.w[0][sp];
+                w[1] = src.w[1][sp];
+                w[2] = src.w[2][sp];
             }
+
             const int rest = divu31(cell0, rn.div_nx);
             i = cell0 - rest * nx;
             if (DIM == 3) {
@@ -447,6 +457,14 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                 if (!finite3(w[0], w[1], w[2])) {
                     atomicOr(a.err, ERR_NONFINITE);
                     live = false;   // the particle keeps x^n and contributes no current
+                    if (RP) {   // ... in its slot of the new order, with the momentum it reached
+                        a.P.id[p] = a.S.id[sp];
+                        a.P.cell[p] = cell0;
+                        a.P.off[0][p] = o0;
+                        a.P.off[1][p] = o1;
+                        if (DIM == 3) a.P.off[2][p] = o2;
+                        for (int c = 0; c < 3; ++c) a.P.w[c][p] = w[c];
+                    }
                 } else {
                     const R ig = rsqrt_r(w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + c2);
                     s0 = renormalize(o0, w[0] * ig * cN0, n0);
@@ -461,6 +479,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                         a.old_off[1][p] = o1;
                         if (DIM == 3) a.old_off[2][p] = o2;
                     }
+                    if (RP) a.P.id[p] = a.S.id[sp];   // the id moves with the particle
                     a.P.cell[p] = cell1;
                     a.P.off[0][p] = n0;
                     a.P.off[1][p] = n1;
@@ -700,11 +719,11 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     __syncthreads();   // the shared tiles are free for the block's next item
 }
 
-template <int DIM, typename R, int MODE, class GEO = GeoDyn, int ORD = 3>
+template <int DIM, typename R, int MODE, class GEO = GeoDyn, int ORD = 3, bool PERM = false>
 __global__ void __launch_bounds__(kThreads) k_particles(const PartArgs<R> a)
 {
     if ((int)blockIdx.x >= *a.n_items) return;
-    process_item<DIM, R, MODE, GEO, ORD>(a, blockIdx.x);
+    process_item<DIM, R, MODE, GEO, ORD, PERM>(a, blockIdx.x);
 }
 
 // Run of a batch that owns concatenated cell l (run_cell_base has nruns + 1 entries).
@@ -759,8 +778,24 @@ template <int DIM, typename R, int MODE, class GEO = GeoDyn, int ORD = 3>
 static cudaError_t launch_t(cudaStream_t st, int max_items, size_t smem, const PartArgs<R> &a)
 {
     if (max_items <= 0) return cudaSuccess;
+    if constexpr (MODE == 0 && ORD == 3) {
+        if (a.perm) {   // right after a sort: the kernel that reads through the permutation
+            k_particles<DIM, R, 0, GEO, 3, true><<<max_items, kThreads, smem, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     k_particles<DIM, R, MODE, GEO, ORD><<<max_items, kThreads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// The shared-memory limit of the fused kernel of a geometry, both variants.
+template <int DIM, typename R, class GEO>
+static cudaError_t set_limit_fused(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_particles<DIM, R, 0, GEO>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_particles<DIM, R, 0, GEO, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes);
 }
 
 template <int DIM, typename R, class GEO = GeoDyn>
@@ -790,7 +825,8 @@ static cudaError_t persistent_t(cudaStream_t st, size_t smem, int nruns, const l
 template <typename R>
 inline PartArgs<R> make_args(const WorkItem *items, const int *n_items, const RunDev *runs, const GroupDev *groups,
                              const PoolBuf &P, void *const E[3], void *const B[3], void *const J[3], int *old_cell,
-                             void *const old_off[3], int halo, int *err)
+                             void *const old_off[3], int halo, int *err, const PoolBuf *S = nullptr,
+                             const unsigned *perm = nullptr)
 {
     PartArgs<R> a;
     a.items = items;
@@ -799,7 +835,13 @@ inline PartArgs<R> make_args(const WorkItem *items, const int *n_items, const Ru
     a.groups = groups;
     a.P.cell = P.cell;
     a.P.id = P.id;
+    const PoolBuf &Q = S ? *S : P;
+    a.S.cell = Q.cell;
+    a.S.id = Q.id;
+    a.perm = S ? perm : nullptr;
     for (int c = 0; c < 3; ++c) {
+        a.S.off[c] = static_cast<R *>(Q.off[c]);
+        a.S.w[c] = static_cast<R *>(Q.w[c]);
         a.P.off[c] = static_cast<R *>(P.off[c]);
         a.P.w[c] = static_cast<R *>(P.w[c]);
         a.F.E[c] = static_cast<R *>(E[c]);

@@ -58,12 +58,10 @@ bool launch_persistent_fixed(int dims, cudaStream_t st, size_t smem, int nruns, 
 cudaError_t fixed_set_smem_limit(int dims, size_t bytes)
 {
     const int b = (int)bytes;
-    if (dims == 3)
-        return cudaFuncSetAttribute(k_particles<3, float, 0, Geo3_844>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_particles<2, float, 0, Geo2_16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (dims == 3) return set_limit_fused<3, float, Geo3_844>(b);
+    cudaError_t e = set_limit_fused<2, float, Geo2_16>(b);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_particles<2, float, 0, Geo2_8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return set_limit_fused<2, float, Geo2_8>(b);
 }
 
 }  // namespace pic

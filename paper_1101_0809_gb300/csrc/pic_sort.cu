@@ -1120,8 +1120,9 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                  int ngroups, const RunDev *runs, int total_tiles, SortScratch &scr,
                                  long long *tile_start, unsigned *item_scan, WorkItem *items, int *n_items,
                                  int particles_per_item, int halo, int banked, int half, int *launches,
-                                 unsigned char *lane_cell, int *lane_count, int resort)
+                                 unsigned char *lane_cell, int *lane_count, int resort, const unsigned **perm_out)
 {
+    if (lane_cell) perm_out = nullptr;
     cudaError_t e;
     if (total <= 0 || ngroups <= 0) {
         e = cudaMemsetAsync(n_items, 0, sizeof(int), st);
@@ -1197,8 +1198,12 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
                                                                        ngroups, runs, rule, scr.vals[1 - cur]);
         *launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = launch_permute4(prec, dims, st, total, src, dst, scr.vals[1 - cur])) != cudaSuccess) return e;
-        *launches += 1;
+        if (perm_out) {
+            *perm_out = scr.vals[1 - cur];
+        } else {
+            if ((e = launch_permute4(prec, dims, st, total, src, dst, scr.vals[1 - cur])) != cudaSuccess) return e;
+            *launches += 1;
+        }
         k_resort_tile_start<<<nbt, nt, 0, st>>>(ntp, stay, tile_start);
         *launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1241,8 +1246,19 @@ cudaError_t sort_and_build_items(int prec, int dims, cudaStream_t st, long long 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         cur = 1 - cur;
     }
+    if (perm_out) {
+        *perm_out = scr.vals[cur];
+        return build_items(st, tile_start, total_tiles, particles_per_item, groups, ngroups, scr, item_scan, items,
+                           n_items, launches);
+    }
     return permute_and_build(prec, dims, st, total, src, dst, scr.vals[cur], groups, ngroups, total_tiles, scr,
                              tile_start, item_scan, items, n_items, particles_per_item, launches);
+}
+
+cudaError_t launch_permute(int prec, int dims, cudaStream_t st, long long total, const PoolBuf &src,
+                           const PoolBuf &dst, const unsigned *perm)
+{
+    return total > 0 ? launch_permute4(prec, dims, st, total, src, dst, perm) : cudaSuccess;
 }
 
 static cudaError_t permute_and_build(int prec, int dims, cudaStream_t st, long long total, const PoolBuf &src,

@@ -151,3 +151,37 @@ def test_resort_in_a_batch_of_runs(P):
         moved += check_sort(P, wl, b, before[r], True, run=r)
     assert moved > 0
     b.close()
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("order", ["banked", "stable"])
+def test_sort_inside_a_step_equals_an_explicit_sort(P, dims, prec, order):
+    """When pic_step reaches the sort interval, the sort leaves the particle
+    arrays where they are and the step's particle kernel reads them through
+    the permutation, writing the stepped particles in the new order.  From one
+    snapshot, that step equals pic_sort followed by a step, bit for bit in
+    every particle array (the push of a step does not depend on its own
+    current)."""
+    wl = plasma(dims, 0.3)
+    banked = order == "banked"
+    grid = make_grid(P, wl, P.PIC_FP32 if prec == "fp32" else P.PIC_FP64, sort_interval=4,
+                     sort_order=P.PIC_SORT_BANKED if banked else P.PIC_SORT_STABLE)
+    P.pic_step(grid.h, 4)            # the next step sorts first
+    blob = np.empty(P.pic_state_bytes(grid.h), dtype=np.uint8)
+    P.pic_state_save(grid.h, blob)
+    before = [grid.particles(s) for s in range(len(wl.species))]
+    P.pic_step(grid.h, 1)
+    inside = [grid.particles(s) for s in range(len(wl.species))]
+    P.pic_state_restore(grid.h, blob)
+    P.pic_sort(grid.h)
+    check_sort(P, wl, grid, before, banked)
+    P.pic_step(grid.h, 1)
+    for s in range(len(wl.species)):
+        got = grid.particles(s)
+        np.testing.assert_array_equal(inside[s][0], got[0])
+        np.testing.assert_array_equal(inside[s][3], got[3])
+        for a in range(3):
+            np.testing.assert_array_equal(inside[s][1][a], got[1][a])
+            np.testing.assert_array_equal(inside[s][2][a], got[2][a])
+    grid.close()
