@@ -357,9 +357,17 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     };
 
     // warps run whole rounds of 32 consecutive particles (the last one partial)
+    // RP: the permutation index of the lane's next particle is read one round ahead
+    unsigned sp_next = 0;
+    if (RP && it.begin + threadIdx.x < it.end) sp_next = a.perm[it.begin + threadIdx.x];
     for (long long pw = it.begin + (threadIdx.x & ~31); pw < it.end; pw += blockDim.x) {
         const long long p = pw + lane;
         const bool valid = p < it.end;
+        unsigned sp_cur = 0;
+        if (RP) {
+            sp_cur = sp_next;
+            if (p + blockDim.x < it.end) sp_next = a.perm[p + blockDim.x];
+        }
         bool live = false;   // the particle moves and deposits this step
         bool inr = false;
         int i = 0, j = 0, k = 0, li = 0, lj = 0, lk = 0;
@@ -367,7 +375,7 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         int s0 = 0, s1 = 0, s2 = 0;
         if (valid) {
             // ---- the particle's state at x^n (old) -------------------------------
-            const long long sp = RP ? (long long)a.perm[p] : p;   // where the state is read
+            const long long sp = RP ? (long long)sp_cur : p;   // where the state is read
             const Pool<R> &src = RP ? a.S : a.P;
             const int cell0 = MODE == 2 ? a.old_cell[p] : src.cell[sp];
             o0 = MODE == 2 ? a.old_off[0][p] : src.off[0][sp];
