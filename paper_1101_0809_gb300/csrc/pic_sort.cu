@@ -891,14 +891,8 @@ __global__ void __launch_bounds__(kSortThreads) k_resort_order(const long long *
     const unsigned share = ((nseq + W - 1) / W + 31) & ~31u;
     const unsigned k0 = min(nseq, warp * share), k1 = min(nseq, k0 + share);
     // the k-th particle of the sequence: its index v and class (kMover: not in the tile)
-    auto item = [&](unsigned k, unsigned &v) -> unsigned {
-        if (k >= k1) return kMover;
-        if (k >= nbef && k < nbef + seglen) {
-            const unsigned q = cls_off + (k - nbef);
-            v = (unsigned)sb + (k - nbef);
-            return q < cls_n ? cls_s[q] : cls[v];
-        }
-        const unsigned jm = k < nbef ? k : k - seglen;   // mover number
+    // a mover of the tile: its index v and bank
+    auto fetch_mover = [&](unsigned jm, unsigned &v) -> unsigned {
         if (jm < ncached) {
             v = mv_v[jm];
             return mv_b[jm];
@@ -906,11 +900,37 @@ __global__ void __launch_bounds__(kSortThreads) k_resort_order(const long long *
         v = mvals[mb + jm];
         return (long long)v < total ? mover_bank(v) : kMover;
     };
-    for (unsigned q0 = k0; q0 < k1; q0 += 32) {
-        unsigned v;
-        const unsigned b = item(q0 + lane, v);
+    // the warp's share of the sequence, in order, 32 positions per round; each
+    // of the three ranges has its own loop, so that a round never mixes them.
+    // body(b, v): b the particle's bank (kMover: no particle of tile t), v its index
+    auto walk = [&](auto &&body) {
+        const unsigned a1 = min(k1, nbef), a2 = min(k1, nbef + seglen);
+        for (unsigned q0 = k0; q0 < a1; q0 += 32) {   // movers from earlier segments
+            const unsigned k = q0 + lane;
+            unsigned v = 0;
+            const unsigned b = k < a1 ? fetch_mover(k, v) : kMover;
+            body(b, v);
+        }
+        for (unsigned q0 = max(k0, nbef); q0 < a2; q0 += 32) {   // segment t: its stayers
+            const unsigned k = q0 + lane;
+            unsigned v = 0, b = kMover;
+            if (k < a2) {
+                const unsigned q = cls_off + (k - nbef);
+                v = (unsigned)sb + (k - nbef);
+                b = q < cls_n ? cls_s[q] : cls[v];
+            }
+            body(b, v);
+        }
+        for (unsigned q0 = max(k0, nbef + seglen); q0 < k1; q0 += 32) {   // movers from later segments
+            const unsigned k = q0 + lane;
+            unsigned v = 0;
+            const unsigned b = k < k1 ? fetch_mover(k - seglen, v) : kMover;
+            body(b, v);
+        }
+    };
+    walk([&](unsigned b, unsigned) {
         if (b != kMover) atomicAdd(&cw[warp][b], 1u);
-    }
+    });
     __syncthreads();
     if (warp == 0) {
         unsigned run = 0;
@@ -950,9 +970,7 @@ __global__ void __launch_bounds__(kSortThreads) k_resort_order(const long long *
         }
     }
     __syncthreads();
-    for (unsigned q0 = k0; q0 < k1; q0 += 32) {
-        unsigned v = 0;
-        const unsigned b = item(q0 + lane, v);
+    walk([&](unsigned b, unsigned v) {
         const bool ok = b != kMover;
         unsigned peers = __ballot_sync(0xffffffffu, ok);   // lanes of the same bank
 #pragma unroll
@@ -964,7 +982,7 @@ __global__ void __launch_bounds__(kSortThreads) k_resort_order(const long long *
         __syncwarp();
         if (ok && (__ffs(peers) - 1) == lane) cw[warp][b] = before + __popc(peers);
         __syncwarp();
-        if (!ok) continue;
+        if (!ok) return;
         const unsigned rank = pre[warp][b] + before + __popc(peers & ltm);   // among the tile's bank b
         unsigned slot;
         if (!banked) {
@@ -981,7 +999,7 @@ __global__ void __launch_bounds__(kSortThreads) k_resort_order(const long long *
             slot = S + below;
         }
         if (slot < nT) perm[nb + slot] = v;
-    }
+    });
 }
 
 // Permute every particle array, dst[o] = src[perm[o]], four slots per thread:
