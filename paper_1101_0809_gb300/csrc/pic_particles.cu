@@ -28,7 +28,9 @@ size_t particles_smem_bytes(int dims, int prec, int mode, int tx, int ty, int tz
     const long long je = (long long)p0 * p1 * (dims == 3 ? tz + 2 * (halo + 2 + jext) : 1);
     size_t b = 0;
     if (mode != 2) b += 6 * fe * es;
-    if (mode != 1) b += (prec == 0 ? 24 : 28) * je + (size_t)(kThreads / 32) * kQueueCap * (kQueueVals * es + sizeof(int));
+    // current tile (+ per-cell counts in FP32), the warps' deposit queues and one count per warp
+    if (mode != 1)
+        b += (prec == 0 ? 24 : 28) * je + (size_t)(kThreads / 32) * (kQueueCap * (kQueueVals * es + sizeof(int)) + sizeof(int));
     return b;
 }
 

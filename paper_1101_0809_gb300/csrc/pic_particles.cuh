@@ -269,14 +269,18 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
     // the axes it crossed; it is queued and deposited later together with 31
     // other such particles, so that the wider windows are paid only by warps
     // of moved particles.  The integer current sums do not depend on the order.
-    R *qv = nullptr;
-    int *qs = nullptr;
+    // The warps' queues lie one after another (values, then codes), followed by
+    // one count per warp for the merged drain at the end of the item.
+    R *qv0 = nullptr, *qv = nullptr;
+    int *qs0 = nullptr, *qs = nullptr, *qcnt = nullptr;
     if (NEED_J) {
         unsigned char *qb = g_smem + (NEED_F ? 6 * (size_t)nf * sizeof(R) : 0) + (FIX ? 28 : 24) * (size_t)nj;
         const int warp = threadIdx.x >> 5;
-        qv = reinterpret_cast<R *>(qb) + (size_t)warp * kQueueCap * kQueueVals;
-        qs = reinterpret_cast<int *>(qb + (size_t)(kThreads / 32) * kQueueCap * kQueueVals * sizeof(R)) +
-             warp * kQueueCap;
+        qv0 = reinterpret_cast<R *>(qb);
+        qs0 = reinterpret_cast<int *>(qb + (size_t)(kThreads / 32) * kQueueCap * kQueueVals * sizeof(R));
+        qcnt = qs0 + (kThreads / 32) * kQueueCap;
+        qv = qv0 + (size_t)warp * kQueueCap * kQueueVals;
+        qs = qs0 + warp * kQueueCap;
     }
     const int lane = threadIdx.x & 31;
     int qn = 0;   // entries in this warp's queue (warp-uniform)
@@ -318,23 +322,23 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
             deposit5<DIM>(acc, X, Y, Z, kf, uz, full);
         }
     };
-    // deposits the queue entries [first, first + 32) whose lanes have `on`
-    auto drain = [&](int first, bool on) {
-        const int slot = first + lane;
+    // deposits, on each lane with `on`, entry `slot` of the queue whose values
+    // and codes start at sv and ss (a whole warp calls it)
+    auto drain = [&](const R *sv, const int *ss, int slot, bool on) {
         R d0 = R(0), d1 = R(0), d2 = R(0), e0 = R(0), e1 = R(0), e2 = R(0), u = R(0);
         int code = 1 | (1 << 2) | (1 << 4);
         if (on) {
-            d0 = qv[0 * kQueueCap + slot];
-            d1 = qv[1 * kQueueCap + slot];
-            e0 = qv[3 * kQueueCap + slot];
-            e1 = qv[4 * kQueueCap + slot];
+            d0 = sv[0 * kQueueCap + slot];
+            d1 = sv[1 * kQueueCap + slot];
+            e0 = sv[3 * kQueueCap + slot];
+            e1 = sv[4 * kQueueCap + slot];
             if (DIM == 3) {
-                d2 = qv[2 * kQueueCap + slot];
-                e2 = qv[5 * kQueueCap + slot];
+                d2 = sv[2 * kQueueCap + slot];
+                e2 = sv[5 * kQueueCap + slot];
             } else {
-                u = qv[6 * kQueueCap + slot];
+                u = sv[6 * kQueueCap + slot];
             }
-            code = qs[slot];
+            code = ss[slot];
         }
         const int q0 = (code & 3) - 1, q1 = ((code >> 2) & 3) - 1, q2 = ((code >> 4) & 3) - 1;
         const int full = (__any_sync(0xffffffffu, q0 != 0) ? 1 : 0) | (__any_sync(0xffffffffu, q1 != 0) ? 2 : 0) |
@@ -614,16 +618,35 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
         if (qn >= 32) {   // warp-uniform
             __syncwarp();
             qn -= 32;
-            drain(qn, true);
+            drain(qv, qs, qn + lane, true);
             __syncwarp();   // the drained slots are free again
         }
     }
-    if (NEED_J && qn > 0) {
-        __syncwarp();
-        drain(0, lane < qn);
-    }
-
     if (NEED_J) {
+        // The entries left in the warps' queues (fewer than 32 each) are drained
+        // together: merged entry m is slot m - (entries of the warps before) of
+        // its warp's queue, and warp w deposits the merged entries
+        // [32w, 32w + 32), [32w + 256, ...).  A block then runs about one
+        // partly filled drain per item instead of one per warp.
+        if (lane == 0) qcnt[threadIdx.x >> 5] = qn;
+        __syncthreads();
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) tot += qcnt[w];
+        for (int m0 = threadIdx.x & ~31; m0 < tot; m0 += blockDim.x) {   // uniform over the warp
+            int src = 0, slot = m0 + lane;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32 - 1; ++w) {
+                const int c = qcnt[src];
+                if (slot >= c) {
+                    slot -= c;
+                    ++src;
+                }
+            }
+            const bool on = m0 + lane < tot;
+            drain(qv0 + (size_t)(on ? src : 0) * kQueueCap * kQueueVals, qs0 + (on ? src : 0) * kQueueCap,
+                  on ? slot : 0, on);
+        }
         __syncthreads();
         const float jinv = gr.jinv;
         for (int l = threadIdx.x; l < nj; l += blockDim.x) {
