@@ -432,17 +432,30 @@ struct FixedAccT {
 };
 using FixedAcc = FixedAccT<true>;
 
-template <typename R>
+// Current accumulator on the periodic global arrays for one particle's windows:
+// the wrapped offsets of the window's NW cells along each axis (from lo) are
+// formed once, so that a contribution costs one index sum and one atomic.
+template <typename R, int NW>
 struct GlobalAcc {
     R *J[3];
-    long long cell_base;
-    int i, j, k, nx, ny, nz;
+    long long xw[NW], yw[NW], zw[NW];
+    int lox, loy, loz;
+    __device__ __forceinline__ void set(long long cb, int i, int j, int k, int nx, int ny, int nz, int lx, int ly,
+                                        int lz, bool three)
+    {
+        lox = lx;
+        loy = ly;
+        loz = three ? lz : 0;
+#pragma unroll
+        for (int m = 0; m < NW; ++m) {
+            xw[m] = cb + wrapi(i + lox + m, nx);
+            yw[m] = (long long)nx * wrapi(j + loy + m, ny);
+            zw[m] = three ? (long long)nx * ny * wrapi(k + loz + m, nz) : 0;
+        }
+    }
     __device__ __forceinline__ void add(int a, int dx, int dy, int dz, R kp, R t) const
     {
-        const R v = kp * t;
-        const long long idx = cell_base + (long long)wrapi(i + dx, nx) +
-                              (long long)nx * ((long long)wrapi(j + dy, ny) + (long long)ny * wrapi(k + dz, nz));
-        atomicAdd(&J[a][idx], v);
+        atomicAdd(&J[a][xw[dx - lox] + yw[dy - loy] + zw[dz - loz]], kp * t);
     }
 };
 

@@ -97,16 +97,18 @@ __device__ __noinline__ void gather_global(const Fields<R> &F, long long cb, int
     gather<DIM>(rd, fx, Sx, fy, Sy, fz, Sz, Ep, Bp);
 }
 
+// full: bit a set when the particle changed cell along axis a (its window
+// there has four cells and three faces; along the other axes the fourth cell
+// and the third face carry nothing and are skipped, as on the tiled path)
 template <int DIM, typename R>
 __device__ __noinline__ void deposit_global(const Fields<R> &F, long long cb, int i, int j, int k, int nx, int ny,
-                                            int nz, const AxisWin<R> *win, const R *kf, R uz)
+                                            int nz, const AxisWin<R> *win, const R *kf, R uz, int full)
 {
-    GlobalAcc<R> acc;
+    const AxisWin<R> X = win[0], Y = win[1], Z = win[2];
+    GlobalAcc<R, 4> acc;
     for (int c = 0; c < 3; ++c) acc.J[c] = F.J[c];
-    acc.cell_base = cb;
-    acc.i = i; acc.j = j; acc.k = k;
-    acc.nx = nx; acc.ny = ny; acc.nz = nz;
-    deposit<DIM>(acc, win[0], win[1], win[2], kf, uz, 7);
+    acc.set(cb, i, j, k, nx, ny, nz, X.lo, Y.lo, Z.lo, DIM == 3);
+    deposit<DIM>(acc, X, Y, Z, kf, uz, full);
 }
 
 // The same for l_a = 2 1/2; (i, j, k) is the particle's base index.
@@ -127,14 +129,13 @@ __device__ __noinline__ void gather_global5(const Fields<R> &F, long long cb, in
 
 template <int DIM, typename R>
 __device__ __noinline__ void deposit_global5(const Fields<R> &F, long long cb, int i, int j, int k, int nx, int ny,
-                                             int nz, const AxisWin5<R> *win, const R *kf, R uz)
+                                             int nz, const AxisWin5<R> *win, const R *kf, R uz, int full)
 {
-    GlobalAcc<R> acc;
+    const AxisWin5<R> X = win[0], Y = win[1], Z = win[2];
+    GlobalAcc<R, 5> acc;
     for (int c = 0; c < 3; ++c) acc.J[c] = F.J[c];
-    acc.cell_base = cb;
-    acc.i = i; acc.j = j; acc.k = k;
-    acc.nx = nx; acc.ny = ny; acc.nz = nz;
-    deposit5<DIM>(acc, win[0], win[1], win[2], kf, uz, 7);
+    acc.set(cb, i, j, k, nx, ny, nz, X.lo, Y.lo, Z.lo, DIM == 3);
+    deposit5<DIM>(acc, X, Y, Z, kf, uz, full);
 }
 
 // The comparison scheme of Eq. wrong1 on the global arrays; (i, j, k) is the cell.
@@ -589,13 +590,15 @@ __device__ __forceinline__ void process_item(const PartArgs<R> &a, int item)
                 axis_window5(a0, b0, q0, win[0]);
                 axis_window5(a1, b1, q1, win[1]);
                 if (DIM == 3) axis_window5(a2, b2, q2, win[2]); else win[2] = win[0];
-                deposit_global5<DIM, R>(a.F, cb, i + ub0, j + ub1, k + ub2, nx, ny, nz, win, kf, uz);
+                deposit_global5<DIM, R>(a.F, cb, i + ub0, j + ub1, k + ub2, nx, ny, nz, win, kf, uz,
+                                        (q0 != 0 ? 1 : 0) | (q1 != 0 ? 2 : 0) | (q2 != 0 ? 4 : 0));
             } else {
                 AxisWin<R> win[3];
                 axis_window(o0, n0, s0, win[0]);
                 axis_window(o1, n1, s1, win[1]);
                 if (DIM == 3) axis_window(o2, n2, s2, win[2]); else win[2] = win[0];
-                deposit_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, win, kf, uz);
+                deposit_global<DIM, R>(a.F, cb, i, j, k, nx, ny, nz, win, kf, uz,
+                                       (s0 != 0 ? 1 : 0) | (s1 != 0 ? 2 : 0) | (s2 != 0 ? 4 : 0));
             }
         }
         const bool enq = live && inr && moved;

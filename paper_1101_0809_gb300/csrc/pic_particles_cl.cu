@@ -630,7 +630,8 @@ __global__ void __launch_bounds__(kCells, 3) k_particles_cl(const ClArgs A)
                     axis_window(o1, n1, s1, win[1]);
                     axis_window(o2, n2, s2, win[2]);
                     const float kf[3] = {gr.kff[0], gr.kff[1], gr.kff[2]};
-                    deposit_global<3, float>(A.F, cb, i, j, kk, nx, ny, nz, win, kf, 0.f);
+                    deposit_global<3, float>(A.F, cb, i, j, kk, nx, ny, nz, win, kf, 0.f,
+                                             (s0 != 0 ? 1 : 0) | (s1 != 0 ? 2 : 0) | (s2 != 0 ? 4 : 0));
                 }
             }
         }
