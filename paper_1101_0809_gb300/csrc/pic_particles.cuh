@@ -7,8 +7,10 @@
 // halo of (halo + 1) cells in shared memory, and a current tile with a halo of
 // (halo + 2) cells.  Each thread streams particles (coalesced SoA loads),
 // gathers from shared memory, pushes, renormalizes offset and cell, writes the
-// particle back and scatters its 144 (3D) or 40 (2D) face currents into the
-// shared current tile with shared-memory atomics.  A particle that has drifted
+// particle back and scatters its face currents into the shared current tile
+// with shared-memory atomics: 54 (3D) or 21 (2D) for a particle that kept its
+// cell, at once; up to 144 or 40 for one that changed cell, through its warp's
+// queue, drained 32 particles at a time.  A particle that has drifted
 // more than `halo` cells outside the tile since the last sort takes the same
 // arithmetic on the global arrays instead (periodic indices, global atomics).
 // At the end the block adds its current tile to the global J with atomics.
