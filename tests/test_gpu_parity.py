@@ -183,11 +183,32 @@ def test_fp64_3d_with_sorts_between_steps(P):
     grid.close()
 
 
+def past_halo(wl, grid, tile, halo):
+    """Particles whose cell lies more than `halo` cells outside the tile of
+    their cell at the load (the last sort), along some axis, periodically; and
+    how many of those changed cell in the last step (x_prev: the cells before
+    it).  Such particles run on the global-memory path."""
+    past = 0
+    for s, sp in enumerate(wl.species):
+        cell, _, _, ident = grid.particles(s)
+        c = [cell % wl.n[0], (cell // wl.n[0]) % wl.n[1], cell // (wl.n[0] * wl.n[1])]
+        out = np.zeros(cell.size, dtype=bool)
+        for a in range(wl.dims):
+            c0 = np.floor(sp.x[a][ident]).astype(np.int64) % wl.n[a]
+            o = (c0 // tile[a]) * tile[a]
+            d = (c[a] - o) % wl.n[a]            # periodic offset from the tile's first cell
+            d = np.where(d >= wl.n[a] - halo - tile[a], d - wl.n[a], d)   # the nearer image below the tile
+            out |= (d < -halo) | (d >= tile[a] + halo)
+        past += int(out.sum())
+    return past
+
+
 @pytest.mark.parametrize("halo", [0, 1, 2])
 def test_fp64_particles_far_outside_their_tile_take_the_global_path(P, halo):
     wl = ragged2d(vth=0.3, steps=16)       # fast particles, no sort for 16 steps
     grid = make_grid(P, wl, P.PIC_FP64, halo=halo, sort_interval=1000, ppb=512)
     P.pic_step(grid.h, wl.steps)
+    assert past_halo(wl, grid, (8, 8, 1), halo) > 0
     g, osp, E, B, J = run_oracle(wl, wl.steps)
     _check_state(P, wl, grid, osp, E, B, J, FP64_TOL)
     grid.close()
@@ -224,6 +245,7 @@ def test_fp64_3d_particles_far_outside_their_tile_take_the_global_path(P, halo):
     wl = small3d(vth=0.3, steps=8, ions=False)     # fast electrons, no sort for 8 steps
     grid = make_grid(P, wl, P.PIC_FP64, tile=(8, 4, 4), halo=halo, sort_interval=1000, ppb=512)
     P.pic_step(grid.h, wl.steps)
+    assert past_halo(wl, grid, (8, 4, 4), halo) > 0
     g, osp, E, B, J = run_oracle(wl, wl.steps)
     tol = fp64_field_tol(wl, osp)
     _check_state(P, wl, grid, osp, E, B, J, tol)
