@@ -112,10 +112,10 @@ def c0_small2d(steps=50):
                           SEED_BASE + 0, tile=(8, 8, 1))
 
 
-def c1_thermal3d(n=128, ppc=32, steps=200, fraction=1.0, tile=(8, 4, 4), sort_interval=6):
+def c1_thermal3d(n=128, ppc=32, steps=200, fraction=1.0, tile=(8, 4, 4), sort_interval=4):
     """3D3V periodic n^3, electrons and ions (mass ratio 1836) ppc each, v_th,e = 0.1c,
     dt = 0.45 dx/c.  At n = 128, ppc = 32 this is 134,217,728 particles.  The
-    particles are re-sorted every 6 steps: electrons move 0.045 cells per step
+    particles are re-sorted every 4 steps: electrons move 0.045 cells per step
     on average (0.2 in the tail), so over longer intervals more of them collide
     on shared-memory banks or drift past the one-cell halo of their tile and
     take the slower global-memory path, while shorter ones spend more on sorts."""

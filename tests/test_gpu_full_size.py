@@ -32,7 +32,7 @@ def run():
     B.build()
     from paper_1101_0809_gb300 import pic as P
     wl = W.c1_thermal3d()
-    assert wl.n_particles == 134_217_728 and wl.tile == (8, 4, 4) and wl.sort_interval == 6
+    assert wl.n_particles == 134_217_728 and wl.tile == (8, 4, 4) and wl.sort_interval == 4
     desc = P.make_desc(3, wl.n, wl.d, wl.dt, wl.c, P.PIC_FP32, tile=wl.tile, halo=1, sort_interval=wl.sort_interval,
                        particles_per_block=8192, rho_bg=wl.rho_bg,
                        stream=torch.cuda.current_stream().cuda_stream)
