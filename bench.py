@@ -321,8 +321,8 @@ def batched_arm(P, W, torch, args, dist, hbm_peak):
     """The batched ensemble: independent 2D3V periodic runs with N ~ U{32..256}
     per axis, 4-64 electrons per cell and v_th ~ U[0.01c, 0.3c], FP32, advanced
     together by one cooperative launch per step replayed from CUDA graphs, with
-    tile, particles per block and sort interval picked by the autotuner on every
-    8th run."""
+    tile, particles per block and sort interval picked by the autotuner: all
+    24 candidates timed on every 8th run, the three fastest again on all runs."""
     from paper_1101_0809_gb300 import autotune as AT
     params = W.c3_ensemble_params(args.batch_runs)
     runs = [W.c3_run(p) for p in params]
@@ -348,8 +348,8 @@ def batched_arm(P, W, torch, args, dist, hbm_peak):
         e1.synchronize()
         return e0.elapsed_time(e1)
 
-    def time_candidate(c):
-        b = build(runs[::8], c)
+    def time_on(sub, c):
+        b = build(sub, c)
         try:
             span = 2 * c["K"]
             P.pic_step_graph(b.h, span + c["K"])
@@ -357,9 +357,15 @@ def batched_arm(P, W, torch, args, dist, hbm_peak):
         finally:
             b.close()
 
+    def time_candidate(c):
+        return time_on(runs[::8], c)
+
+    def time_full(c):
+        return time_on(runs, c)
+
     cands = [dict(tile=t, ppb=p, K=k) for t in (8, 16) for p in (2048, 4096, 8192) for k in (2, 3, 5, 8)]
     key = AT.workload_key("ensemble2d", [(r["n"], r["ppc"], round(r["vth"], 6)) for r in params[::8]])
-    best, table, cached = AT.tune(key, torch.cuda.get_device_name(), cands, time_candidate)
+    best, table, cached = AT.tune(key, torch.cuda.get_device_name(), cands, time_candidate, refine=time_full, top=3)
     b = build(runs, best)
     span = 2 * best["K"]
     P.pic_step_graph(b.h, span + best["K"])        # aligns the sort phase and captures the graph

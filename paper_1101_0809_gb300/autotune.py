@@ -2,7 +2,9 @@
 thread block and sort interval.
 
 Each candidate is timed on the caller's workload (device time per step, CUDA
-events on the grid's stream, after warm-up) and the fastest is kept.  Results
+events on the grid's stream, after warm-up) and the fastest is kept.  When the
+sweep runs on a sample of the workload, the few fastest candidates can be timed
+again on the whole of it (``refine``), and the fastest of those is kept.  Results
 are cached per (workload key, device name) in a JSON file next to this module,
 so that a later run of the same workload on the same kind of GPU skips the
 sweep.
@@ -27,13 +29,16 @@ def _load(path):
         return {}
 
 
-def tune(key, device, candidates, time_candidate, path=CACHE, refresh=False):
+def tune(key, device, candidates, time_candidate, path=CACHE, refresh=False, refine=None, top=3):
     """Return (best, table, cached).
 
     ``candidates`` is a list of dicts of launch parameters; ``time_candidate(c)``
     builds the workload with them and returns milliseconds per step (or raises
     if the candidate is not valid for this workload, e.g. a tile too large for
-    the smallest grid).  ``table`` lists (candidate, ms or None)."""
+    the smallest grid).  ``table`` lists (candidate, ms or None, reason).  With
+    ``refine``, the ``top`` fastest candidates are timed again by ``refine(c)``
+    and the fastest of those is the result; ``table`` then ends with those
+    timings, marked "refined"."""
     db = _load(path)
     entry = f"{key}|{device}"
     if not refresh and entry in db:
@@ -50,6 +55,18 @@ def tune(key, device, candidates, time_candidate, path=CACHE, refresh=False):
     if not valid:
         raise RuntimeError("no autotuning candidate ran: " + "; ".join(t[2] for t in table))
     best = min(valid, key=lambda t: t[1])[0]
+    if refine is not None:
+        final = []
+        for c, _, _ in sorted(valid, key=lambda t: t[1])[:top]:
+            try:
+                ms = float(refine(c))
+            except Exception as exc:
+                table.append((c, None, "refined: " + str(exc)[:110]))
+                continue
+            table.append((c, ms, "refined"))
+            final.append((c, ms))
+        if final:
+            best = min(final, key=lambda t: t[1])[0]
     db = _load(path)
     db[entry] = {"best": best, "table": table}
     tmp = f"{path}.tmp{os.getpid()}"

@@ -1307,17 +1307,27 @@ int pic_step(pic_grid *g, int nsteps)
 }
 
 // One step of every run in one cooperative launch (plus the sort launches
-// every sort_interval steps).
+// every sort_interval steps).  As in pic_step, a sort leaves the arrays in
+// place and the step's launch reads the particles through its permutation,
+// writing them to the other buffer in the new order.
 static int persistent_step(pic_grid *g)
 {
     int rc;
-    if (g->steps_since_sort >= g->sort_interval && (rc = do_sort(g)) != PIC_OK) return rc;
+    if (g->steps_since_sort >= g->sort_interval &&
+        (rc = do_sort(g, g->order2 == 3 && !uses_cell_lanes(g) && g->total > 0)) != PIC_OK)
+        return rc;
     ProfScope ps(g, PIC_PROF_PARTICLES);
+    const unsigned *perm = g->pending_perm;
     cudaError_t e = launch_step_persistent(g->dims, g->prec, g->stream, g->items, g->n_items, g->d_runs, g->d_groups,
-                                           g->pool, g->E, g->B, g->J, g->halo, g->tile[0], g->tile[1], g->tile[2],
-                                           g->d_err, (int)g->runs.size(), g->d_run_cell_base, &g->persist_blocks, 1,
-                                           g->pitch[0], g->pitch[1], g->d_ant_n, g->antennas);
+                                           perm ? g->pool_alt : g->pool, g->E, g->B, g->J, g->halo, g->tile[0],
+                                           g->tile[1], g->tile[2], g->d_err, (int)g->runs.size(),
+                                           g->d_run_cell_base, &g->persist_blocks, 1, g->pitch[0], g->pitch[1],
+                                           g->d_ant_n, g->antennas, perm ? &g->pool : nullptr, perm);
     launch_count_add(g, 1);
+    if (perm) {
+        g->pending_perm = nullptr;
+        std::swap(g->pool, g->pool_alt);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "persistent step");
     g->steps_since_sort += 1;
     g->have_old = false;

@@ -57,7 +57,8 @@ cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const Wo
                                    const RunDev *runs, const GroupDev *groups, const PoolBuf &P, void *const E[3],
                                    void *const B[3], void *const J[3], int halo, int tx, int ty, int tz, int *err,
                                    int nruns, const long long *run_cell_base, int *grid_blocks, int launch, int p0,
-                                   int p1, long long *ant_n, int antennas);
+                                   int p1, long long *ant_n, int antennas, const PoolBuf *src = nullptr,
+                                   const unsigned *perm = nullptr);
 cudaError_t particles_set_smem_limit(int dims, int prec, int mode, size_t bytes, int order2 = 3);
 
 cudaError_t launch_load(int prec, cudaStream_t st, long long n, const double *x0, const double *x1,

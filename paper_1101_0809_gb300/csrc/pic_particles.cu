@@ -95,16 +95,16 @@ cudaError_t launch_step_persistent(int dims, int prec, cudaStream_t st, const Wo
                                    const RunDev *runs, const GroupDev *groups, const PoolBuf &P, void *const E[3],
                                    void *const B[3], void *const J[3], int halo, int tx, int ty, int tz, int *err,
                                    int nruns, const long long *run_cell_base, int *grid_blocks, int launch, int p0,
-                                   int p1, long long *ant_n, int antennas)
+                                   int p1, long long *ant_n, int antennas, const PoolBuf *src, const unsigned *perm)
 {
     void *none[3] = {nullptr, nullptr, nullptr};
     const size_t smem = particles_smem_bytes(dims, prec, 0, tx, ty, tz, halo, p0, p1);
     if (prec == 0) {
-        auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, nullptr, none, halo, err);
+        auto a = make_args<double>(items, n_items, runs, groups, P, E, B, J, nullptr, none, halo, err, src, perm);
         return dims == 3 ? persistent_t<3, double>(st, smem, nruns, run_cell_base, a, grid_blocks, launch, ant_n, antennas)
                          : persistent_t<2, double>(st, smem, nruns, run_cell_base, a, grid_blocks, launch, ant_n, antennas);
     }
-    auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, nullptr, none, halo, err);
+    auto a = make_args<float>(items, n_items, runs, groups, P, E, B, J, nullptr, none, halo, err, src, perm);
     const int tile[3] = {tx, ty, tz};
     cudaError_t e = cudaSuccess;
     if (launch_persistent_fixed(dims, st, smem, nruns, run_cell_base, a, grid_blocks, launch, tile, halo, p0, p1,

@@ -777,7 +777,9 @@ __device__ __forceinline__ int find_run(const long long *run_cell_base, int nrun
 // step (+ J clear) over all cells, grid barrier, the fused particle work items,
 // grid barrier, B half step, grid barrier, E full step.  The grid is sized so
 // that all blocks are resident (cooperative launch), which the barriers need.
-template <int DIM, typename R, class GEO = GeoDyn>
+// PERM: the step right after a sort that left the arrays in place; the work
+// items read the particles through the permutation (as k_particles does).
+template <int DIM, typename R, class GEO = GeoDyn, bool PERM = false>
 __global__ void __launch_bounds__(kThreads) k_step_persistent(const PartArgs<R> a, int nruns,
                                                               const long long *run_cell_base, long long *ant_n,
                                                               int antennas)
@@ -792,7 +794,7 @@ __global__ void __launch_bounds__(kThreads) k_step_persistent(const PartArgs<R> 
     }
     grid.sync();
     const int ni = *a.n_items;
-    for (int it = blockIdx.x; it < ni; it += gridDim.x) process_item<DIM, R, 0, GEO>(a, it);
+    for (int it = blockIdx.x; it < ni; it += gridDim.x) process_item<DIM, R, 0, GEO, 3, PERM>(a, it);
     grid.sync();
     for (long long l = t0; l < total; l += stride) {
         const int r = find_run(run_cell_base, nruns, l);
@@ -838,17 +840,24 @@ template <int DIM, typename R, class GEO = GeoDyn>
 static cudaError_t persistent_t(cudaStream_t st, size_t smem, int nruns, const long long *run_cell_base,
                                 PartArgs<R> a, int *grid_blocks, int launch, long long *ant_n, int antennas)
 {
-    auto fn = k_step_persistent<DIM, R, GEO>;
+    auto fn0 = k_step_persistent<DIM, R, GEO, false>;
+    auto fn1 = k_step_persistent<DIM, R, GEO, true>;
+    auto fn = a.perm ? fn1 : fn0;
     cudaError_t e;
     if (*grid_blocks <= 0) {
-        // first use (outside any stream capture): shared-memory limit and grid size
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
+        // first use (outside any stream capture): shared-memory limit and grid
+        // size, the same for both variants (all blocks of either must be resident)
+        int dev = 0, sms = 0, per = 1 << 30;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem);
-        if (e != cudaSuccess) return e;
+        for (auto f : {fn0, fn1}) {
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            int pf = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, f, kThreads, smem);
+            if (e != cudaSuccess) return e;
+            per = std::min(per, pf);
+        }
         if (per <= 0) return cudaErrorInvalidConfiguration;
         *grid_blocks = sms * per;
     }
