@@ -322,7 +322,7 @@ def batched_arm(P, W, torch, args, dist, hbm_peak):
     per axis, 4-64 electrons per cell and v_th ~ U[0.01c, 0.3c], FP32, advanced
     together by one cooperative launch per step replayed from CUDA graphs, with
     tile, particles per block and sort interval picked by the autotuner: all
-    24 candidates timed on every 8th run, the three fastest again on all runs."""
+    36 candidates timed on every 8th run, the three fastest again on all runs."""
     from paper_1101_0809_gb300 import autotune as AT
     params = W.c3_ensemble_params(args.batch_runs)
     runs = [W.c3_run(p) for p in params]
@@ -363,7 +363,7 @@ def batched_arm(P, W, torch, args, dist, hbm_peak):
     def time_full(c):
         return time_on(runs, c)
 
-    cands = [dict(tile=t, ppb=p, K=k) for t in (8, 16) for p in (2048, 4096, 8192) for k in (2, 3, 5, 8)]
+    cands = [dict(tile=t, ppb=p, K=k) for t in (8, 16) for p in (2048, 4096, 8192) for k in (2, 3, 4, 5, 6, 8)]
     key = AT.workload_key("ensemble2d", [(r["n"], r["ppc"], round(r["vth"], 6)) for r in params[::8]])
     best, table, cached = AT.tune(key, torch.cuda.get_device_name(), cands, time_candidate, refine=time_full, top=3)
     b = build(runs, best)
@@ -394,6 +394,7 @@ def batched_arm(P, W, torch, args, dist, hbm_peak):
             "value": world * npart * nsteps / (ms * 1e-3), "unit": UNIT, "steps": nsteps, "ms_per_step": ms / nsteps,
             "particles": npart, "cells": ncell, "autotuned": best, "autotune_cached": cached,
             "autotune_candidates": len(table), "gpu_launches": launches,
+            "autotune_table": [[c, ms, why] for c, ms, why in table],
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                          "scope": "whole step (persistent kernel, sorts included in the time)",
                          "alg_bytes_per_step": alg},
