@@ -92,10 +92,9 @@ class DifferentiableRun:
     def forward(self, x0, w0):
         self.load(x0, w0)
         self.checkpoints = {}
-        for s in range(self.steps):
-            if s % self.ce == 0:
-                self.checkpoints[s] = self.snapshot()
-            P.pic_step(self.grid.h, 1)
+        for s in range(0, self.steps, self.ce):   # one snapshot, then one call for the segment's steps
+            self.checkpoints[s] = self.snapshot()
+            P.pic_step(self.grid.h, min(self.ce, self.steps - s))
         P.pic_sync(self.grid.h)
         L, self.lamE, self.lamB = self.loss_and_seeds()
         return L

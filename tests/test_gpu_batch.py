@@ -186,3 +186,48 @@ def test_bulk_load_equals_run_by_run_loads(env):
             close(E2[a], E1[a], FP64_TOL, f"run {r} E[{a}]")
     b1.close()
     b2.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_persistent_step_after_a_sort_equals_an_explicit_sort(env, prec):
+    """When a persistent step reaches the sort interval, the sort leaves the
+    arrays in place and the cooperative launch reads the particles through the
+    permutation, writing them in the new order.  From one snapshot that step
+    equals pic_sort followed by a persistent step: the ids slot by slot, bit for
+    bit, and positions and momenta to a few units of the last place (the two
+    launches are separate compilations of the same arithmetic)."""
+    P, torch = env
+    runs = ensemble2d(4)
+    st = torch.cuda.Stream()
+    b = make_batch(P, runs, P.PIC_FP32 if prec == "fp32" else P.PIC_FP64, stream=st.cuda_stream, sort_interval=3)
+    P.pic_step_persistent(b.h, 3)                 # the next step sorts first
+    P.pic_sync(b.h)
+    blob = np.empty(P.pic_state_bytes(b.h), dtype=np.uint8)
+    P.pic_state_save(b.h, blob)
+    P.pic_step_persistent(b.h, 1)
+    P.pic_sync(b.h)
+    inside = [b.particles_run(r, 0) for r in range(len(runs))]
+    P.pic_state_restore(b.h, blob)
+    before = [b.particles_run(r, 0)[3] for r in range(len(runs))]
+    P.pic_sort(b.h)
+    P.pic_step_persistent(b.h, 1)
+    P.pic_sync(b.h)
+    ulp = 2.0 ** -23 if prec == "fp32" else 2.0 ** -52
+    moved = 0
+    for r, wl in enumerate(runs):
+        got = b.particles_run(r, 0)
+        np.testing.assert_array_equal(inside[r][3], got[3])
+        xa = positions_from_gpu(wl, inside[r][0], inside[r][1])
+        xb = positions_from_gpu(wl, got[0], got[1])
+        for a in range(2):
+            d = xa[a] - xb[a]
+            d -= wl.n[a] * np.round(d / wl.n[a])
+            assert np.abs(d).max() <= 8 * ulp, f"run {r} axis {a}: positions differ by {np.abs(d).max()} cells"
+        for a in range(3):
+            wa = np.asarray(inside[r][2][a], np.float64)
+            wb = np.asarray(got[2][a], np.float64)
+            scale = np.sqrt(np.mean(wb * wb))
+            assert np.all(np.abs(wa - wb) <= 8 * ulp * np.maximum(np.abs(wb), scale)), f"run {r} momentum {a}"
+        moved += int(np.count_nonzero(got[3] != before[r]))
+    assert moved > 0                               # the sort did reorder particles
+    b.close()
