@@ -1,5 +1,5 @@
 """The FP32 kernels compiled for fixed tile geometries (3D 8x4x4, 2D 16x16 and
-8x8, halo 1) against the FP64 oracle.  The library picks them whenever a grid's
+8x8, halo 1; 3D 4x4x4 with halo 2) against the FP64 oracle.  The library picks them whenever a grid's
 tile, halo and shared-tile pitches equal theirs; pic_tile_layout shows the
 pitches, so each test first checks that its grid has the fixed geometry.  The
 oracle starts from exactly the FP32 state the GPU holds (positions and momenta
@@ -79,6 +79,64 @@ def test_fp32_3d_fixed_tile_keeps_gauss_law_over_100_steps(env):
     assert d["gauss_resid_max"] / scale <= 1e-6
     assert d["n_particles"] == wl.n_particles
     assert d["total_charge"] == pytest.approx(d0["total_charge"], abs=1e-9 * abs(sp.q) * sp.weight * sp.n)
+    grid.close()
+
+
+def plasma3d_444(steps, vth):
+    """3D3V electrons and ions on a grid ragged against 4x4x4 tiles."""
+    return W.thermal_plasma("3D 4x4x4 tiles", 3, (18, 14, 22), 4, vth, steps, W.SEED_BASE + 52, ions=1836.0,
+                            tile=(4, 4, 4), dt_courant=0.45)
+
+
+@pytest.mark.parametrize("steps,vth", [(1, 0.1), (10, 0.3)])
+def test_fp32_3d_444_halo2_fixed_tile_matches_oracle(env, steps, vth):
+    """The 4x4x4 tile with a two-cell halo (the laser slab's tiles at its long
+    sort interval).  Ten unsorted steps of a plasma at v_th = 0.3c carry
+    particles past one cell of halo, within two (the tiled path), and past two
+    (the global-memory path)."""
+    P, torch = env
+    wl = plasma3d_444(steps, vth)
+    grid = make_grid(P, wl, P.PIC_FP32, halo=2, sort_interval=1000)
+    assert tuple(P.pic_tile_layout(grid.h)[2]) == (12, 12), "the grid does not have the fixed 4x4x4 halo-2 geometry"
+    osp = oracle_from_gpu(wl, grid.particles)
+    g = O.Grid(wl.dims, wl.n, wl.d, wl.dt, wl.c)
+    E, B, J = g.zeros(), g.zeros(), g.zeros()
+    x_prev = [sp.x.copy() for sp in osp]
+    for _ in range(steps):
+        x_prev = [sp.x.copy() for sp in osp]
+        O.step(g, E, B, J, osp)
+    P.pic_step(grid.h, steps)
+    P.pic_sync(grid.h)
+    tol = steps * FP32_TOL
+    gE, gB, gJ = grid.get_fields()
+    for a in range(3):
+        close(gE[a], E[a], tol, f"E[{a}]")
+        close(gB[a], B[a], tol, f"B[{a}]")
+        close(gJ[a], J[a], tol, f"J[{a}]")
+    if steps == 1:
+        for s in range(len(wl.species)):
+            compare_particles(wl, s, grid, osp, FP32_TOL, x_prev=x_prev[s])
+    else:
+        for s, sp in enumerate(wl.species):
+            cell, off, w, ident = grid.particles(s)
+            order = np.argsort(ident)
+            x = positions_from_gpu(wl, cell[order], [o[order] for o in off])
+            for a in range(3):
+                d = x[a] - osp[s].x[a]
+                d -= wl.n[a] * np.round(d / wl.n[a])
+                assert np.abs(d).max() <= 1e-4, f"species {s} x[{a}]: {np.abs(d).max()} cells"
+                close(w[a][order], osp[s].w[a], tol, f"species {s} w[{a}]")
+            # some electrons ran past two cells of halo (the global path) and some past one
+            if s == 0:
+                c0 = [np.floor(sp.x[a][ident]).astype(np.int64) % wl.n[a] for a in range(3)]
+                c = [cell % wl.n[0], (cell // wl.n[0]) % wl.n[1], cell // (wl.n[0] * wl.n[1])]
+                far = np.zeros(cell.size, dtype=int)
+                for a in range(3):
+                    o = (c0[a] // 4) * 4
+                    dd = (c[a] - o) % wl.n[a]
+                    dd = np.where(dd >= wl.n[a] - 6, dd - wl.n[a], dd)
+                    far = np.maximum(far, np.maximum(-dd, dd - 3))   # cells outside the tile
+                assert (far > 2).any() and (far == 2).any()
     grid.close()
 
 
